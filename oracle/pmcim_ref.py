@@ -1,0 +1,283 @@
+"""Plain FP64 restatement of pmCIMb's hot path (oracle, test infrastructure).
+
+Every function follows one passage of the paper, in the paper's order and
+notation, with NumPy/SciPy library calls as single steps (dense LU through
+LAPACK, SVD, eig). Nothing here is blocked, fused or reordered.
+
+Readings of passages the paper leaves open (listed again in the design notes):
+  * nodes theta_j = 2 pi j / N, j = 0..N-1 (Appendix, the node vector drops
+    the endpoint 2 pi of an equally spaced grid starting at 0);
+  * weights w_j = (r/N) e^{i theta_j}: Eq. 3.2 after cancelling i/(iN); the
+    appendix's extra factor 1/i is a common unit-modulus factor that leaves
+    sigma, p and eig(D) unchanged, so it is dropped;
+  * C1 uses z_j = c + r e^{i theta_j} (Eq. 3.3 prints z + r theta_j, a typo;
+    the appendix multiplies by the node itself);
+  * the N/2 rule of Eq. 3.1 uses the 1-based even nodes x_2, x_4, ..., x_N,
+    i.e. the 0-based odd nodes, each with weight 2 w_j;
+  * one probe block V (n x l, unit columns) serves every region and node, and
+    the indicator's random vector is f = V[:, 0] (pmCIMb steps 1.a and 2.a);
+  * candidate <=> I > tol_ind, strict (pmCIMb step 1.c);
+  * tol_svd is absolute (Sec. 3.2) and p counts sigma_i > tol_svd;
+  * a region is saturated when p reaches min(n, l) (all probe directions
+    used); it is then split into four children with the pmCIMa geometry and
+    re-run, up to a fixed depth (the paper's remedy "use smaller subregions",
+    Sec. 3.2 parameter list);
+  * the square filter keeps c - s/2 <= Re, Im < c + s/2 with s/2 = r/sqrt(2)
+    (step 2.f, half-open so each point lies in exactly one square);
+  * verification uses the smallest singular value of T(lambda) and accepts
+    sigma_min <= tol_verify * max(1, ||T(lambda)||_F / sqrt(n)) (step 3);
+  * eigenvectors have unit 2-norm with their largest-modulus entry real and
+    positive.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Sequence
+
+import numpy as np
+import scipy.linalg as sla
+
+__all__ = [
+    "MONOMIAL", "EXP_NEG", "scalar_f", "assemble_T", "nodes_weights", "solve_nodes",
+    "Moments", "moments", "indicator_value", "indicator", "BeynResult", "beyn_extract",
+    "square_filter", "normalise_vectors", "sigma_min", "verify", "split4",
+    "pmcimb", "PmcimbResult",
+]
+
+MONOMIAL = 0
+EXP_NEG = 1
+
+
+# ---------------------------------------------------------------------------
+# The problem T(z) = sum_k f_k(z) A_k  (Sec. 1; the user routine generateT of
+# the Appendix, restricted to monomials and exp(-tau z))
+# ---------------------------------------------------------------------------
+
+def scalar_f(kind: int, degree: int, tau: float, z: complex) -> complex:
+    """f_k(z): z**degree for a monomial term, exp(-tau z) for a delay term."""
+    if kind == MONOMIAL:
+        return complex(z) ** int(degree)
+    if kind == EXP_NEG:
+        return complex(np.exp(-tau * complex(z)))
+    raise ValueError("unknown scalar function kind %r" % kind)
+
+
+def assemble_T(problem, z: complex) -> np.ndarray:
+    """Dense T(z) = sum_k f_k(z) A_k; a scalar A_k stands for A_k * I."""
+    n = problem.n
+    T = np.zeros((n, n), dtype=np.complex128)
+    for (A, kind, deg, tau) in problem.terms:
+        fz = scalar_f(kind, deg, tau, z)
+        if np.isscalar(A):
+            T[np.arange(n), np.arange(n)] += fz * complex(A)
+        else:
+            T += fz * np.asarray(A, dtype=np.complex128)
+    return T
+
+
+# ---------------------------------------------------------------------------
+# Trapezoid rule on a circle (Eq. 3.2-3.3; Appendix, indicator/ContourSVD)
+# ---------------------------------------------------------------------------
+
+def nodes_weights(c: complex, r: float, N: int):
+    """z_j = c + r e^{i theta_j}, w_j = (r/N) e^{i theta_j}, theta_j = 2 pi j / N."""
+    j = np.arange(N)
+    e = np.exp(1j * 2.0 * np.pi * j / N)
+    return complex(c) + r * e, (r / N) * e
+
+
+def solve_nodes(problem, z: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """X_j = T(z_j)^{-1} V for every node (Eq. 2.4), dense LU with partial pivoting."""
+    out = np.empty((len(z), problem.n, V.shape[1]), dtype=np.complex128)
+    for j, zj in enumerate(z):
+        lu, piv = sla.lu_factor(assemble_T(problem, zj), check_finite=True)
+        out[j] = sla.lu_solve((lu, piv), V)
+    return out
+
+
+@dataclasses.dataclass
+class Moments:
+    C0: np.ndarray       # n x l: sum_j w_j X_j          (Eq. 3.2)
+    C1: np.ndarray       # n x l: sum_j w_j z_j X_j      (Eq. 3.3)
+    pf_N: np.ndarray     # n:     sum_j w_j x_j, f = V[:,0]          (P f |_N)
+    pf_half: np.ndarray  # n:     sum_{j odd} 2 w_j x_j              (P f |_{N/2})
+
+
+def moments(problem, c: complex, r: float, N: int, V: np.ndarray) -> Moments:
+    """Quadrature sums of one disk: Beyn's C_{0,N}, C_{1,N} and the two P f approximations."""
+    if N % 2:
+        raise ValueError("the ratio indicator needs an even N")
+    z, w = nodes_weights(c, r, N)
+    X = solve_nodes(problem, z, V)
+    n, l = problem.n, V.shape[1]
+    C0 = np.zeros((n, l), dtype=np.complex128)
+    C1 = np.zeros((n, l), dtype=np.complex128)
+    pf_N = np.zeros(n, dtype=np.complex128)
+    pf_half = np.zeros(n, dtype=np.complex128)
+    for j in range(N):
+        C0 += w[j] * X[j]
+        C1 += w[j] * z[j] * X[j]
+        pf_N += w[j] * X[j][:, 0]
+        if j % 2 == 1:                       # 1-based even nodes x_2, x_4, ..., x_N
+            pf_half += 2.0 * w[j] * X[j][:, 0]
+    return Moments(C0, C1, pf_N, pf_half)
+
+
+def indicator_value(pf_N: np.ndarray, pf_half: np.ndarray) -> float:
+    """I = || P f|_N ./ P f|_{N/2} ||_2 / sqrt(n)   (Eq. 3.1)."""
+    return float(np.linalg.norm(pf_N / pf_half) / math.sqrt(len(pf_N)))
+
+
+def indicator(problem, regions: Sequence, V: np.ndarray, tol_ind: float = 0.1):
+    """pmCIMb step 1: indicators of all disks, candidate <=> I > tol_ind."""
+    I = np.array([indicator_value(*_pf(moments(problem, g.c, g.r, g.N, V))) for g in regions])
+    return I, I > tol_ind
+
+
+def _pf(m: Moments):
+    return m.pf_N, m.pf_half
+
+
+# ---------------------------------------------------------------------------
+# Beyn's extraction (Eq. 2.8; pmCIMb steps 2.c-2.e)
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class BeynResult:
+    sigma: np.ndarray    # singular values of C0, descending
+    p: int               # number of sigma_i > tol_svd
+    saturated: bool      # p == min(n, l)
+    lam: np.ndarray      # eigenvalues of D (p,)
+    vecs: np.ndarray     # n x p eigenvectors V0 s, normalised
+
+
+def normalise_vectors(Vc: np.ndarray) -> np.ndarray:
+    """Unit 2-norm columns, each rotated so its largest-modulus entry is real positive."""
+    out = np.array(Vc, dtype=np.complex128, copy=True)
+    for k in range(out.shape[1]):
+        v = out[:, k]
+        v = v / np.linalg.norm(v)
+        i = int(np.argmax(np.abs(v)))
+        v = v * (abs(v[i]) / v[i])
+        out[:, k] = v
+    return out
+
+
+def beyn_extract(C0: np.ndarray, C1: np.ndarray, tol_svd: float = 1e-6) -> BeynResult:
+    """SVD C0 = V Sigma W^H, keep sigma > tol_svd, D = V0^H C1 W0 Sigma0^{-1}, eig(D)."""
+    n, l = C0.shape
+    Vs, s, Wh = np.linalg.svd(C0, full_matrices=False)
+    p = int(np.sum(s > tol_svd))
+    saturated = p >= min(n, l)
+    if p == 0:
+        return BeynResult(s, 0, False, np.zeros(0, np.complex128), np.zeros((n, 0), np.complex128))
+    V0 = Vs[:, :p]
+    W0 = Wh.conj().T[:, :p]
+    D = V0.conj().T @ C1 @ W0 @ np.diag(1.0 / s[:p])
+    lam, S = np.linalg.eig(D)
+    return BeynResult(s, p, saturated, lam, normalise_vectors(V0 @ S))
+
+
+def square_filter(lam: np.ndarray, c: complex, r: float) -> np.ndarray:
+    """Step 2.f: keep lambda inside the square inscribed in the disk (half-open)."""
+    h = r / math.sqrt(2.0)
+    re_ok = (lam.real >= c.real - h) & (lam.real < c.real + h)
+    im_ok = (lam.imag >= c.imag - h) & (lam.imag < c.imag + h)
+    return re_ok & im_ok
+
+
+# ---------------------------------------------------------------------------
+# Verification (pmCIMb step 3)
+# ---------------------------------------------------------------------------
+
+def sigma_min(problem, lam: complex):
+    """(smallest singular value of T(lambda), ||T(lambda)||_F)."""
+    T = assemble_T(problem, lam)
+    return float(sla.svdvals(T)[-1]), float(np.linalg.norm(T))
+
+
+def verify(problem, lams: Sequence[complex], tol_verify: float = 1e-6):
+    sig = np.zeros(len(lams))
+    acc = np.zeros(len(lams), dtype=bool)
+    for i, lam in enumerate(lams):
+        s, fro = sigma_min(problem, lam)
+        sig[i] = s
+        acc[i] = s <= tol_verify * max(1.0, fro / math.sqrt(problem.n))
+    return sig, acc
+
+
+# ---------------------------------------------------------------------------
+# Region split (pmCIMa's quadrisection geometry) and the pmCIMb driver
+# ---------------------------------------------------------------------------
+
+def split4(c: complex, r: float):
+    """Four child disks of radius r/2 centred at c + (+-1 +- i) (r/2)/sqrt(2)."""
+    rc = r / 2.0
+    d = rc / math.sqrt(2.0)
+    return [(complex(c.real + sx * d, c.imag + sy * d), rc)
+            for (sx, sy) in ((1, 1), (-1, 1), (1, -1), (-1, -1))]
+
+
+@dataclasses.dataclass
+class RegionRecord:
+    c: complex
+    r: float
+    N: int
+    depth: int
+    I: float
+    candidate: bool
+    p: int = -1
+    saturated: bool = False
+    split: bool = False
+    lam: np.ndarray = None        # eigenvalues of D before the square filter
+    kept: np.ndarray = None       # mask after the square filter
+    sigma: np.ndarray = None
+
+
+@dataclasses.dataclass
+class PmcimbResult:
+    lam: np.ndarray               # verified eigenvalues, sorted by (Re, Im)
+    vecs: np.ndarray              # n x m, matching lam
+    sigma_min: np.ndarray         # per verified eigenvalue
+    cand_lam: np.ndarray          # all filtered candidates before verification, sorted
+    cand_sigma: np.ndarray
+    cand_accept: np.ndarray
+    records: List[RegionRecord]
+
+
+def pmcimb(problem, regions: Sequence, V: np.ndarray, tol_ind: float = 0.1,
+           tol_svd: float = 1e-6, tol_verify: float = 1e-6, max_depth: int = 8) -> PmcimbResult:
+    """pmCIMb steps 1-3 over the given disks, with saturated disks split and re-run.
+
+    One N per disk serves both the indicator and Beyn's moments.
+    """
+    n = problem.n
+    records: List[RegionRecord] = []
+    lam_list, vec_list = [], []
+    level = [(complex(g.c), float(g.r), int(g.N), 0) for g in regions]
+    while level:
+        nxt = []
+        for (c, r, N, depth) in level:
+            m = moments(problem, c, r, N, V)
+            I = indicator_value(m.pf_N, m.pf_half)
+            rec = RegionRecord(c, r, N, depth, I, I > tol_ind)
+            if rec.candidate:
+                b = beyn_extract(m.C0, m.C1, tol_svd)
+                rec.p, rec.saturated, rec.sigma, rec.lam = b.p, b.saturated, b.sigma, b.lam
+                if b.saturated and depth < max_depth:
+                    rec.split = True
+                    nxt += [(cc, rr, N, depth + 1) for (cc, rr) in split4(c, r)]
+                else:
+                    keep = square_filter(b.lam, c, r)
+                    rec.kept = keep
+                    lam_list += list(b.lam[keep])
+                    vec_list += [b.vecs[:, k] for k in np.flatnonzero(keep)]
+            records.append(rec)
+        level = nxt
+    lam = np.array(lam_list, dtype=np.complex128)
+    vecs = np.array(vec_list, dtype=np.complex128).T.reshape(n, len(lam_list))
+    sig, acc = verify(problem, lam, tol_verify)
+    order = np.lexsort((lam.imag, lam.real))
+    lam, vecs, sig, acc = lam[order], vecs[:, order], sig[order], acc[order]
+    return PmcimbResult(lam[acc], vecs[:, acc], sig[acc], lam, sig, acc, records)

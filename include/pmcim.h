@@ -1,0 +1,196 @@
+/*
+ * pmcim.h -- C ABI of the GB300 contour-integral eigensolver library (libpmcim.so).
+ *
+ * Problem class (Sec. 1): find lambda in a bounded region with T(lambda) x = 0,
+ * where T(z) = sum_k f_k(z) A_k with dense complex n x n coefficients A_k and
+ * scalar functions f_k drawn from a fixed set: monomials z^d and exp(-tau z).
+ * The region is covered by disks circumscribing squares (Sec. 3, start); each
+ * disk is discretised by the N-node trapezoid rule (Eq. 3.2-3.3).
+ *
+ * Conventions shared by every call
+ *   - Complex numbers are interleaved (re, im) pairs of double.
+ *   - Matrices are column-major with leading dimension n; indices are 0-based.
+ *   - Every buffer argument may be a host pointer or a CUDA device pointer (the
+ *     library uses unified addressing to tell them apart). The caller owns all
+ *     buffers; no call keeps a caller pointer after it returns.
+ *   - Calls are synchronous: on return all results are in the caller's buffers
+ *     and the work queued on opt->cuda_stream has finished.
+ *   - Every call returns 0 (PMCIM_OK) or a negative PMCIM_E* code; the message
+ *     of the last failure on the calling thread is pmcim_last_error(). Problems
+ *     with one disk (a saturated rank test, an exactly singular node) never fail
+ *     a call: they are reported in per-region status bits, because the method
+ *     prefers spurious candidates, removed later, to missed eigenvalues
+ *     (Sec. 3.2, robustness remark).
+ *   - One problem handle must not be used by two host threads at once.
+ *   - There is no CPU fallback: without a usable CUDA device every call returns
+ *     PMCIM_ECUDA.
+ */
+#ifndef PMCIM_H
+#define PMCIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------- */
+#define PMCIM_OK 0
+#define PMCIM_EINVAL (-1)    /* bad argument (size, NULL, odd N, ...)        */
+#define PMCIM_ENOMEM (-2)    /* device allocation failed                     */
+#define PMCIM_ECUDA (-3)     /* CUDA runtime error or no device              */
+#define PMCIM_ETIMEOUT (-4)  /* a bounded device wait ran out                */
+#define PMCIM_ECAPACITY (-5) /* more eigenvalues than the caller's capacity  */
+#define PMCIM_ENOTSUP (-6)   /* option not supported for this problem size   */
+
+/* ---- per-region status bits ---------------------------------------------- */
+#define PMCIM_RS_CANDIDATE 1      /* indicator I > tol_ind (pmCIMb step 1.c)        */
+#define PMCIM_RS_SATURATED 2      /* rank p reached min(n, l) in Beyn's SVD test    */
+#define PMCIM_RS_SPLIT 4          /* saturated disk was split into four children   */
+#define PMCIM_RS_SINGULAR_NODE 8  /* an LU met an exactly zero pivot at some node  */
+#define PMCIM_RS_IR_FALLBACK 16   /* refinement did not converge; FP64 re-solve    */
+#define PMCIM_RS_NO_EIG 32        /* candidate disk whose Beyn step kept no value  */
+
+/* ---- scalar functions f_k ------------------------------------------------ */
+#define PMCIM_F_MONOMIAL 0 /* f(z) = z^degree                                   */
+#define PMCIM_F_EXP_NEG 1  /* f(z) = exp(-tau z)                                */
+
+typedef struct {
+  int32_t kind;   /* PMCIM_F_MONOMIAL or PMCIM_F_EXP_NEG                        */
+  int32_t degree; /* monomial degree, 0..16                                     */
+  double tau;     /* delay, used by PMCIM_F_EXP_NEG                             */
+  double id_re;   /* when the coefficient pointer is NULL the term is           */
+  double id_im;   /*   (id_re + i id_im) * I * f(z), never stored densely       */
+} pmcim_fterm;
+
+/* One disk: centre c, radius r, N trapezoid nodes (N even, 2..4096). */
+typedef struct {
+  double c_re;
+  double c_im;
+  double r;
+  int32_t N;
+  int32_t depth; /* split depth; callers pass 0 */
+} pmcim_region;
+
+/* Arithmetic of the LU factorisation (the solves are always refined to FP64
+   accuracy when a reduced precision is chosen). */
+#define PMCIM_PREC_FP64 0   /* plain FP64 LU                                     */
+#define PMCIM_PREC_FP32_IR 1 /* FP32 LU + FP64 iterative refinement               */
+
+typedef struct {
+  double tol_ind;          /* indicator threshold, paper default 0.1 (Sec. 3.1)        */
+  double tol_svd;          /* absolute singular-value threshold, 1e-6 (Sec. 3.2)        */
+  double tol_verify;       /* sigma_min acceptance, 1e-6 (pmCIMb step 3.b)              */
+  int32_t precision;       /* PMCIM_PREC_*                                             */
+  int32_t max_ir_sweeps;   /* refinement sweeps for reduced precision (default 3)      */
+  int32_t max_split_depth; /* splits of saturated disks (default 8)                    */
+  int32_t reserved;
+  void* cuda_stream;       /* cudaStream_t to run on; NULL = legacy default stream     */
+} pmcim_options;
+
+/* Statistics of one pmcim_solve call. */
+typedef struct {
+  int64_t solves;          /* linear systems T(z_j) X = V solved (one per node)  */
+  int32_t regions;         /* disks processed, children included                 */
+  int32_t candidates;      /* disks with I > tol_ind                             */
+  int32_t splits;          /* saturated disks split                              */
+  int32_t unverified;      /* filtered values rejected by verification           */
+  int32_t ir_fallbacks;    /* nodes re-solved in FP64 after refinement stalled  */
+  int32_t singular_nodes;  /* nodes whose LU met an exactly zero pivot           */
+} pmcim_stats;
+
+typedef struct pmcim_problem_s* pmcim_problem;
+
+/* Fill *opt with the paper's parameters (tol_ind 0.1, tol_svd 1e-6,
+   tol_verify 1e-6), FP64, 3 refinement sweeps, split depth 8, default stream. */
+void pmcim_default_options(pmcim_options* opt);
+
+/* Create a problem handle for T(z) = sum_{k<K} f_k(z) A_k  (Sec. 1).
+   A[k] points to n*n complex values (2*n*n doubles, column-major) or is NULL
+   for the identity term (f[k].id_re + i f[k].id_im) * I. The handle copies the
+   coefficients to the device; the caller may free A afterwards.
+   Errors: EINVAL (n < 1, K < 1, K > 16, bad kind/degree), ENOMEM, ECUDA. */
+int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmcim_fterm* f,
+                         pmcim_problem* out);
+int pmcim_problem_destroy(pmcim_problem p);
+
+/* Quadrature moments of each disk (Eq. 3.2-3.3 and the two P f sums of Eq. 3.1):
+   at the nodes z_j = c + r e^{2 pi i j/N}, weights w_j = (r/N) e^{2 pi i j/N},
+   X_j = T(z_j)^{-1} V is computed by LU with partial pivoting, and
+     C0[g] = sum_j w_j X_j,  C1[g] = sum_j w_j z_j X_j          (n x l each),
+     pf_half[g] = sum_{j odd} 2 w_j X_j[:,0]                   (n),
+     pf_abs[g]  = sum_j |w_j| |X_j[:,0]|  elementwise           (n),
+   so that P f|_N = C0[g][:,0] with f = V[:,0]. V is n x l with l in 1..64.
+   Outputs are R consecutive blocks; any output may be NULL. */
+int pmcim_moments(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim_region* reg,
+                  int32_t l, const double* V, double* C0, double* C1, double* pf_half,
+                  double* pf_abs);
+
+/* pmCIMb step 1 (Sec. 3.2; indicator of Eq. 3.1) for R disks:
+   ind[g] = || C0[:,0] ./ pf_half ||_2 / sqrt(n), candidate[g] = ind[g] > tol_ind.
+   pf_norm[g] = ||P f|_N||_2 and pf_scale[g] = ||pf_abs||_2 (a size of the summed
+   terms, for judging whether P f is above rounding noise) may be NULL. */
+int pmcim_indicator(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim_region* reg,
+                    int32_t l, const double* V, double* ind, double* pf_norm, double* pf_scale,
+                    uint8_t* candidate);
+
+/* pmCIMb step 2 (Sec. 3.2, steps 2.b-2.f; Eq. 2.8) on the given disks, without the
+   indicator gate on them: SVD of C0, p = #{sigma > tol_svd}, D = V0^H C1 W0 Sigma0^-1,
+   eig(D), eigenvectors V0 s (unit norm, largest entry real positive), square filter.
+   A disk whose rank saturates (p = min(n,l)) is split into four children, which
+   pass the indicator gate and are re-run, up to opt->max_split_depth.
+   Output: *count values lambda[2*count], vecs[n*2*count] (may be NULL),
+   region_of[count] (index of the input disk), region_status[R] (OR of the bits
+   of the disk and its children; may be NULL). ECAPACITY if more than cap. */
+int pmcim_beyn(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim_region* reg,
+               int32_t l, const double* V, int32_t cap, double* lambda, double* vecs,
+               int32_t* region_of, int32_t* count, int32_t* region_status);
+
+/* pmCIMb step 3: sigma_min[i] = smallest singular value of T(lambda_i) by LU and
+   inverse iteration on (T^H T)^{-1}; accept[i] = sigma_min <= tol_verify *
+   max(1, ||T(lambda_i)||_F / sqrt(n)). accept may be NULL. */
+int pmcim_verify(pmcim_problem p, const pmcim_options* opt, int32_t m, const double* lambda,
+                 double* sigma_min, uint8_t* accept);
+
+/* Whole pmCIMb (steps 1-3) over R disks with one N per disk for both the
+   indicator and the moments: one LU per node serves both. Outputs the verified
+   eigenvalues (sorted by real, then imaginary part) with eigenvectors (may be
+   NULL), sigma_min and source disk; ind[R] and region_status[R] may be NULL;
+   stats may be NULL. ECAPACITY if more than cap values are verified. */
+int pmcim_solve(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim_region* reg,
+                int32_t l, const double* V, int32_t cap, double* lambda, double* vecs,
+                double* sigma_min, int32_t* region_of, int32_t* count, double* ind,
+                int32_t* region_status, pmcim_stats* stats);
+
+const char* pmcim_status_string(int code);
+const char* pmcim_last_error(void);
+
+/* ---- instrumentation (no counterpart in the paper) ----------------------
+   Every kernel launch of the library is counted per kernel kind. When timing
+   is enabled, CUDA events are recorded around each launch on the stream it is
+   launched on, and the elapsed device time is accumulated once the calling
+   API function has synchronised that stream. Process-wide, thread-safe. */
+#define PMCIM_K_FACTOR 0  /* assembly + LU + solve at the nodes (FP64)       */
+#define PMCIM_K_REDUCE 1  /* segmented quadrature reduction                  */
+#define PMCIM_K_INDICATOR 2
+#define PMCIM_K_BEYN 3
+#define PMCIM_K_VERIFY 4
+#define PMCIM_K_GATHER 5
+#define PMCIM_K_FACTOR32 6 /* assembly + LU + solve at the nodes (FP32 LU)   */
+#define PMCIM_K_REFINE 7   /* FP64 residual and correction sweeps            */
+#define PMCIM_K_COUNT 8
+
+typedef struct {
+  int64_t launches[PMCIM_K_COUNT];
+  double ms[PMCIM_K_COUNT]; /* summed event time; 0 unless timing was on */
+} pmcim_profile;
+
+void pmcim_profile_enable(int on);
+void pmcim_profile_reset(void);
+void pmcim_profile_read(pmcim_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMCIM_H */

@@ -1,0 +1,108 @@
+// Segmented quadrature reduction and the ratio indicator.
+//
+// For each disk g with nodes z_j, weights w_j (Eq. 3.2), and solutions X_j:
+//   C0 = sum_j w_j X_j, C1 = sum_j w_j z_j X_j                  (Eq. 3.2-3.3)
+//   P f|_N = C0[:,0],  P f|_{N/2} = sum_{j odd} 2 w_j X_j[:,0]  (Eq. 3.1; the
+//   1-based even nodes x_2, x_4, ..., x_N are the 0-based odd ones)
+//   I = || P f|_N ./ P f|_{N/2} ||_2 / sqrt(n)                  (Eq. 3.1)
+// Nodes are summed in index order by one thread per output element, so the
+// result is deterministic. The kernel streams X once: it is HBM-bound.
+#include "pmcim_internal.cuh"
+
+namespace {
+
+constexpr int RT = 256;
+
+__global__ void __launch_bounds__(RT) k_reduce_moments(ReduceArgs a) {
+  const int g = blockIdx.y;
+  const RegionDev rg = a.regions[g];
+  const int nl = a.n * a.l;
+  const int e = blockIdx.x * RT + threadIdx.x;
+  if (e >= nl) return;
+  const bool first_col = e < a.n;
+  double2 c0 = make_double2(0.0, 0.0), c1 = c0, ph = c0;
+  double pa = 0.0;
+  const double2* Xg = a.X + (size_t)rg.node_off * nl + e;
+  for (int j = 0; j < rg.N; ++j) {
+    double2 z, w;
+    node_weight(rg.cre, rg.cim, rg.r, rg.N, j, &z, &w);
+    const double2 x = Xg[(size_t)j * nl];
+    cfma(c0, w, x);
+    cfma(c1, cmul(w, z), x);
+    if (first_col) {
+      if (j & 1) cfma(ph, cscale(w, 2.0), x);
+      pa += hypot(w.x, w.y) * hypot(x.x, x.y);
+    }
+  }
+  const size_t o = (size_t)g * nl + e;
+  a.C0[o] = c0;
+  a.C1[o] = c1;
+  if (first_col) {
+    a.pf_half[(size_t)g * a.n + e] = ph;
+    a.pf_abs[(size_t)g * a.n + e] = pa;
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_indicator(IndicatorArgs a) {
+  __shared__ double red[3][RT / 32];
+  const int g = blockIdx.x;
+  const double2* pfN = a.C0 + (size_t)g * a.n * a.l;  // column 0 of C0
+  const double2* pfh = a.pf_half + (size_t)g * a.n;
+  const double* pab = a.pf_abs + (size_t)g * a.n;
+  double s_ratio = 0.0, s_norm = 0.0, s_abs = 0.0;
+  for (int i = threadIdx.x; i < a.n; i += RT) {
+    const double num = cabs2(pfN[i]);
+    const double den = cabs2(pfh[i]);
+    s_ratio += num / den;
+    s_norm += num;
+    s_abs += pab[i] * pab[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s_ratio += __shfl_down_sync(0xffffffffu, s_ratio, o);
+    s_norm += __shfl_down_sync(0xffffffffu, s_norm, o);
+    s_abs += __shfl_down_sync(0xffffffffu, s_abs, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { red[0][wid] = s_ratio; red[1][wid] = s_norm; red[2][wid] = s_abs; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+    for (int k = 0; k < RT / 32; ++k) { t0 += red[0][k]; t1 += red[1][k]; t2 += red[2][k]; }
+    const double I = sqrt(t0) / sqrt((double)a.n);
+    a.ind[g] = I;
+    if (a.pf_norm) a.pf_norm[g] = sqrt(t1);
+    if (a.pf_scale) a.pf_scale[g] = sqrt(t2);
+    a.candidate[g] = (I > a.tol_ind) ? 1 : 0;
+  }
+}
+
+__global__ void k_gather_vecs(GatherArgs a) {
+  const int k = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const int src = a.src[k];
+  const int cand = src / a.l, col = src % a.l;
+  a.dst[(size_t)k * a.n + i] = a.vecs[((size_t)cand * a.l + col) * a.n + i];
+}
+
+}  // namespace
+
+cudaError_t launch_reduce_moments(const ReduceArgs& a, cudaStream_t s) {
+  if (a.R <= 0) return cudaSuccess;
+  dim3 grid((a.n * a.l + RT - 1) / RT, a.R);
+  k_reduce_moments<<<grid, RT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_indicator(const IndicatorArgs& a, cudaStream_t s) {
+  if (a.R <= 0) return cudaSuccess;
+  k_indicator<<<a.R, RT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_vecs(const GatherArgs& a, cudaStream_t s) {
+  if (a.count <= 0) return cudaSuccess;
+  dim3 grid((a.n + 127) / 128, a.count);
+  k_gather_vecs<<<grid, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}

@@ -1,0 +1,306 @@
+"""ctypes binding of libpmcim (the C ABI in include/pmcim.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels. Functions with the C names take raw pointers; the wrappers below take
+NumPy arrays (host memory) or torch CUDA tensors (device memory) and return
+NumPy arrays. Loading fails loudly when the library has not been built: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libpmcim.so")
+
+PMCIM_OK = 0
+STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ECAPACITY", -6: "ENOTSUP"}
+
+RS_CANDIDATE, RS_SATURATED, RS_SPLIT, RS_SINGULAR_NODE, RS_IR_FALLBACK, RS_NO_EIG = 1, 2, 4, 8, 16, 32
+F_MONOMIAL, F_EXP_NEG = 0, 1
+PREC_FP64, PREC_FP32_IR = 0, 1
+
+EXPORTS = ["pmcim_default_options", "pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments",
+           "pmcim_indicator", "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_status_string",
+           "pmcim_last_error", "pmcim_profile_enable", "pmcim_profile_reset", "pmcim_profile_read"]
+
+KERNELS = ["factor_fp64", "reduce", "indicator", "beyn", "verify", "gather", "factor_fp32", "refine"]
+
+
+class pmcim_fterm(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("degree", C.c_int32), ("tau", C.c_double),
+                ("id_re", C.c_double), ("id_im", C.c_double)]
+
+
+class pmcim_region(C.Structure):
+    _fields_ = [("c_re", C.c_double), ("c_im", C.c_double), ("r", C.c_double),
+                ("N", C.c_int32), ("depth", C.c_int32)]
+
+
+class pmcim_options(C.Structure):
+    _fields_ = [("tol_ind", C.c_double), ("tol_svd", C.c_double), ("tol_verify", C.c_double),
+                ("precision", C.c_int32), ("max_ir_sweeps", C.c_int32), ("max_split_depth", C.c_int32),
+                ("reserved", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+class pmcim_profile(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8)]
+
+
+class pmcim_stats(C.Structure):
+    _fields_ = [("solves", C.c_int64), ("regions", C.c_int32), ("candidates", C.c_int32),
+                ("splits", C.c_int32), ("unverified", C.c_int32), ("ir_fallbacks", C.c_int32),
+                ("singular_nodes", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libpmcim.so (raises if it is missing: build it with paper_2312_13117_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libpmcim.so not found at %s; run paper_2312_13117_gb300.build.build()" % path)
+    lib = C.CDLL(path)
+    P, I32, D, VP = C.c_void_p, C.c_int32, C.c_double, C.c_void_p
+    lib.pmcim_default_options.argtypes = [C.POINTER(pmcim_options)]
+    lib.pmcim_default_options.restype = None
+    lib.pmcim_problem_create.argtypes = [I32, I32, C.POINTER(C.c_void_p), C.POINTER(pmcim_fterm), C.POINTER(P)]
+    lib.pmcim_problem_destroy.argtypes = [P]
+    lib.pmcim_moments.argtypes = [P, C.POINTER(pmcim_options), I32, C.POINTER(pmcim_region), I32, VP, VP, VP, VP, VP]
+    lib.pmcim_indicator.argtypes = [P, C.POINTER(pmcim_options), I32, C.POINTER(pmcim_region), I32, VP, VP, VP, VP, VP]
+    lib.pmcim_beyn.argtypes = [P, C.POINTER(pmcim_options), I32, C.POINTER(pmcim_region), I32, VP, I32, VP, VP, VP,
+                               VP, VP]
+    lib.pmcim_verify.argtypes = [P, C.POINTER(pmcim_options), I32, VP, VP, VP]
+    lib.pmcim_solve.argtypes = [P, C.POINTER(pmcim_options), I32, C.POINTER(pmcim_region), I32, VP, I32, VP, VP, VP,
+                                VP, VP, VP, VP, C.POINTER(pmcim_stats)]
+    lib.pmcim_status_string.argtypes = [C.c_int]
+    lib.pmcim_status_string.restype = C.c_char_p
+    lib.pmcim_last_error.argtypes = []
+    lib.pmcim_last_error.restype = C.c_char_p
+    lib.pmcim_profile_enable.argtypes = [C.c_int]
+    lib.pmcim_profile_enable.restype = None
+    lib.pmcim_profile_reset.argtypes = []
+    lib.pmcim_profile_reset.restype = None
+    lib.pmcim_profile_read.argtypes = [C.POINTER(pmcim_profile)]
+    lib.pmcim_profile_read.restype = None
+    for name in ("pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments", "pmcim_indicator",
+                 "pmcim_beyn", "pmcim_verify", "pmcim_solve"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class PmcimError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = load()
+        msg = lib.pmcim_last_error().decode()
+        super().__init__("%s failed: %s (%s) %s" % (where, STATUS.get(code, code), code, msg))
+        self.code = code
+
+
+def _check(code: int, where: str):
+    if code != PMCIM_OK:
+        raise PmcimError(code, where)
+
+
+# ---------------------------------------------------------------------------
+# raw C names (pointers in, status out)
+# ---------------------------------------------------------------------------
+
+def pmcim_default_options() -> pmcim_options:
+    o = pmcim_options()
+    load().pmcim_default_options(C.byref(o))
+    return o
+
+
+def pmcim_problem_create(n, K, A_ptrs, fterms) -> int:
+    h = C.c_void_p()
+    arr = (C.c_void_p * K)(*A_ptrs)
+    _check(load().pmcim_problem_create(n, K, arr, fterms, C.byref(h)), "pmcim_problem_create")
+    return h.value
+
+
+def pmcim_problem_destroy(h):
+    _check(load().pmcim_problem_destroy(C.c_void_p(h)), "pmcim_problem_destroy")
+
+
+def pmcim_profile_enable(on: bool):
+    load().pmcim_profile_enable(1 if on else 0)
+
+
+def pmcim_profile_reset():
+    load().pmcim_profile_reset()
+
+
+def pmcim_profile_read() -> dict:
+    pr = pmcim_profile()
+    load().pmcim_profile_read(C.byref(pr))
+    return {k: {"launches": int(pr.launches[i]), "ms": float(pr.ms[i])} for i, k in enumerate(KERNELS)}
+
+
+# ---------------------------------------------------------------------------
+# array helpers
+# ---------------------------------------------------------------------------
+
+def _ptr(x) -> Optional[int]:
+    """Address of a NumPy array or a torch tensor (host or CUDA), or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError("unsupported buffer type %r" % type(x))
+
+
+def _colmajor_c128(A) -> np.ndarray:
+    return np.asfortranarray(np.asarray(A, dtype=np.complex128))
+
+
+def regions_array(regions: Sequence) -> C.Array:
+    """Region objects with attributes (c, r, N) -> pmcim_region[R]."""
+    R = len(regions)
+    arr = (pmcim_region * max(R, 1))()
+    for g, reg in enumerate(regions):
+        arr[g].c_re = float(complex(reg.c).real)
+        arr[g].c_im = float(complex(reg.c).imag)
+        arr[g].r = float(reg.r)
+        arr[g].N = int(reg.N)
+        arr[g].depth = 0
+    return arr
+
+
+def options(tol_ind=0.1, tol_svd=1e-6, tol_verify=1e-6, precision=PREC_FP64, max_ir_sweeps=3,
+            max_split_depth=8, stream=None) -> pmcim_options:
+    o = pmcim_default_options()
+    o.tol_ind, o.tol_svd, o.tol_verify = tol_ind, tol_svd, tol_verify
+    o.precision, o.max_ir_sweeps, o.max_split_depth = precision, max_ir_sweeps, max_split_depth
+    o.cuda_stream = stream
+    return o
+
+
+class Problem:
+    """Handle for T(z) = sum_k f_k(z) A_k built from ``(A, kind, degree, tau)`` terms.
+
+    ``A`` is an n x n complex matrix (NumPy or torch, host or CUDA) or a complex
+    scalar s meaning s * I.
+    """
+
+    def __init__(self, n: int, terms):
+        self.n = int(n)
+        K = len(terms)
+        ft = (pmcim_fterm * K)()
+        keep, ptrs = [], []
+        for k, (A, kind, deg, tau) in enumerate(terms):
+            ft[k].kind, ft[k].degree, ft[k].tau = int(kind), int(deg), float(tau)
+            if np.isscalar(A):
+                ft[k].id_re, ft[k].id_im = complex(A).real, complex(A).imag
+                ptrs.append(None)
+            else:
+                if isinstance(A, np.ndarray) or not hasattr(A, "data_ptr"):
+                    A = _colmajor_c128(A)
+                else:  # torch tensor: column-major == transpose of a contiguous row-major tensor
+                    A = A.t().contiguous().t()
+                keep.append(A)
+                ptrs.append(_ptr(A))
+        self.handle = pmcim_problem_create(self.n, K, ptrs, ft)
+
+    @classmethod
+    def from_workload_problem(cls, prob):
+        return cls(prob.n, prob.terms)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pmcim_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- wrappers returning NumPy arrays --------------------------------
+    def moments(self, regions, V, opt=None):
+        lib = load()
+        V = _colmajor_c128(V)
+        n, l, R = self.n, V.shape[1], len(regions)
+        C0 = np.zeros((R, l, n), np.complex128)
+        C1 = np.zeros((R, l, n), np.complex128)
+        ph = np.zeros((R, n), np.complex128)
+        pa = np.zeros((R, n), np.float64)
+        opt = opt or options()
+        _check(lib.pmcim_moments(self.handle, C.byref(opt), R, regions_array(regions), l, _ptr(V), _ptr(C0),
+                                 _ptr(C1), _ptr(ph), _ptr(pa)), "pmcim_moments")
+        return C0.transpose(0, 2, 1), C1.transpose(0, 2, 1), ph, pa
+
+    def indicator(self, regions, V, opt=None):
+        lib = load()
+        V = _colmajor_c128(V)
+        R, l = len(regions), V.shape[1]
+        ind = np.zeros(R)
+        pn = np.zeros(R)
+        ps = np.zeros(R)
+        cand = np.zeros(R, np.uint8)
+        opt = opt or options()
+        _check(lib.pmcim_indicator(self.handle, C.byref(opt), R, regions_array(regions), l, _ptr(V), _ptr(ind),
+                                   _ptr(pn), _ptr(ps), _ptr(cand)), "pmcim_indicator")
+        return ind, cand.astype(bool), pn, ps
+
+    def beyn(self, regions, V, cap=None, opt=None, want_vecs=True):
+        lib = load()
+        V = _colmajor_c128(V)
+        R, l, n = len(regions), V.shape[1], self.n
+        cap = cap if cap is not None else max(64, 4 * l * R)
+        lam = np.zeros(cap, np.complex128)
+        vecs = np.zeros((cap, n), np.complex128) if want_vecs else None
+        rof = np.zeros(cap, np.int32)
+        cnt = np.zeros(1, np.int32)
+        rst = np.zeros(max(R, 1), np.int32)
+        opt = opt or options()
+        _check(lib.pmcim_beyn(self.handle, C.byref(opt), R, regions_array(regions), l, _ptr(V), cap, _ptr(lam),
+                              _ptr(vecs), _ptr(rof), _ptr(cnt), _ptr(rst)), "pmcim_beyn")
+        k = int(cnt[0])
+        return lam[:k], (vecs[:k].T if want_vecs else None), rof[:k], rst[:R]
+
+    def verify(self, lam, opt=None):
+        lib = load()
+        lam = np.ascontiguousarray(np.asarray(lam, np.complex128))
+        m = len(lam)
+        sig = np.zeros(max(m, 1))
+        acc = np.zeros(max(m, 1), np.uint8)
+        opt = opt or options()
+        _check(lib.pmcim_verify(self.handle, C.byref(opt), m, _ptr(lam), _ptr(sig), _ptr(acc)), "pmcim_verify")
+        return sig[:m], acc[:m].astype(bool)
+
+    def solve(self, regions, V, cap=None, opt=None, want_vecs=True):
+        """Whole pmCIMb: returns dict(lam, vecs, sigma_min, region_of, ind, status, stats)."""
+        lib = load()
+        V = _colmajor_c128(V)
+        R, l, n = len(regions), V.shape[1], self.n
+        cap = cap if cap is not None else max(64, 4 * l * R)
+        lam = np.zeros(cap, np.complex128)
+        vecs = np.zeros((cap, n), np.complex128) if want_vecs else None
+        sig = np.zeros(cap)
+        rof = np.zeros(cap, np.int32)
+        cnt = np.zeros(1, np.int32)
+        ind = np.zeros(max(R, 1))
+        rst = np.zeros(max(R, 1), np.int32)
+        st = pmcim_stats()
+        opt = opt or options()
+        _check(lib.pmcim_solve(self.handle, C.byref(opt), R, regions_array(regions), l, _ptr(V), cap, _ptr(lam),
+                               _ptr(vecs), _ptr(sig), _ptr(rof), _ptr(cnt), _ptr(ind), _ptr(rst), C.byref(st)),
+               "pmcim_solve")
+        k = int(cnt[0])
+        return dict(lam=lam[:k], vecs=(vecs[:k].T if want_vecs else None), sigma_min=sig[:k], region_of=rof[:k],
+                    ind=ind[:R], status=rst[:R], stats=st.as_dict())

@@ -1,0 +1,55 @@
+"""The C ABI: the library builds for sm_103a, loads, and exports every entry
+point that include/pmcim.h declares. No compute call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pmcim.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pmcim_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2312_13117_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_header():
+    from paper_2312_13117_gb300 import pmcim
+    assert sorted(pmcim.EXPORTS) == _declared()
+
+
+def test_status_strings_and_defaults(lib):
+    from paper_2312_13117_gb300 import pmcim
+    pmcim.load()
+    o = pmcim.pmcim_default_options()
+    assert (o.tol_ind, o.tol_svd, o.tol_verify) == (0.1, 1e-6, 1e-6)
+    assert o.max_split_depth == 8 and o.precision == pmcim.PREC_FP64
+    lib.pmcim_status_string.restype = ctypes.c_char_p
+    assert lib.pmcim_status_string(-5) == b"output capacity exceeded"
+
+
+def test_no_cpu_fallback_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import numpy as np
+    from paper_2312_13117_gb300 import pmcim
+    with pytest.raises(pmcim.PmcimError) as e:
+        pmcim.Problem(4, [(np.eye(4), 0, 0, 0.0)])
+    assert e.value.code == -3  # PMCIM_ECUDA

@@ -1,0 +1,301 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Tolerances:
+  * moments C0, C1, P f|_{N/2}: the difference of two backward-stable LU solves
+    at node j is bounded by c n u kappa(T(z_j)) ||X_j|| (u = 2^-53), and the
+    weighted N-term sum adds at most c (N + 4) u |w_j| ||X_j||; summed over the
+    nodes this gives the bound of `_moment_bound`, c = 4;
+  * eigenvalues: |d lambda| / max(1, |lambda|) <= 1e-10;
+  * indicator values: relative 1e-6 where P f is resolved above rounding
+    noise (||P f|_N|| > 1e-6 * pf_scale); decisions must then be equal unless
+    |I - tol_ind| <= 1e-6 * tol_ind (a threshold tie). Where P f is below that
+    level both indicators are ratios of rounding noise and only the final
+    eigenvalue sets are compared.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.optimize import linear_sum_assignment
+
+import oracle as o
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+LAM_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def pm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2312_13117_gb300 import build, pmcim
+    build.build()
+    pmcim.load()
+    return pmcim
+
+
+def _moment_bound(problem, reg, V, c=4.0):
+    """Sum over nodes of |w_j| c u (n kappa_1(T(z_j)) + N + 4) ||X_j|| (LAPACK condition estimate)."""
+    import scipy.linalg as sla
+    from scipy.linalg.lapack import zgecon
+    z, wts = o.nodes_weights(reg.c, reg.r, reg.N)
+    n = problem.n
+    b0 = b1 = bh = 0.0
+    for j in range(reg.N):
+        T = o.assemble_T(problem, z[j])
+        lu, piv = sla.lu_factor(T)
+        X = sla.lu_solve((lu, piv), V)
+        anorm = np.max(np.sum(np.abs(T), axis=0))
+        rcond, info = zgecon(lu, anorm, norm="1")
+        kap = 1.0 / max(rcond, 1e-300)
+        e = c * U64 * (n * kap + reg.N + 4)
+        b0 += abs(wts[j]) * e * np.linalg.norm(X)
+        b1 += abs(wts[j] * z[j]) * e * np.linalg.norm(X)
+        if j % 2 == 1:
+            bh += 2 * abs(wts[j]) * e * np.linalg.norm(X[:, 0])
+    return b0, b1, bh
+
+
+def _check_moments(pm, problem, regions, V):
+    P = pm.Problem(problem.n, problem.terms)
+    C0, C1, ph, pa = P.moments(regions, V)
+    for g, reg in enumerate(regions):
+        m = o.moments(problem, reg.c, reg.r, reg.N, V)
+        b0, b1, bh = _moment_bound(problem, reg, V)
+        assert np.linalg.norm(C0[g] - m.C0) <= b0 + 1e-300, (g, np.linalg.norm(C0[g] - m.C0), b0)
+        assert np.linalg.norm(C1[g] - m.C1) <= b1 + 1e-300, (g, np.linalg.norm(C1[g] - m.C1), b1)
+        assert np.linalg.norm(ph[g] - m.pf_half) <= bh + 1e-300, g
+    P.close()
+
+
+def _match_lam(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    assert len(a) == len(b), (len(a), len(b))
+    if len(a) == 0:
+        return 0.0
+    cost = np.abs(a[:, None] - b[None, :])
+    ri, ci = linear_sum_assignment(cost)
+    return float(np.max(np.abs(a[ri] - b[ci]) / np.maximum(1.0, np.abs(b[ci]))))
+
+
+# ---------------------------------------------------------------------------
+# a1-a6: moments
+# ---------------------------------------------------------------------------
+
+def test_moments_quadratic_n64(pm):
+    W = w.quadratic_small()
+    _check_moments(pm, W.problem, W.regions, W.V)
+
+
+@pytest.mark.parametrize("n,l,N", [(1, 1, 2), (2, 3, 4), (3, 1, 8), (17, 4, 16), (33, 8, 16),
+                                   (65, 5, 8), (130, 2, 4), (200, 16, 6)])
+def test_moments_ragged_sizes(pm, n, l, N):
+    """Sizes below, at and across the 32-column panel and 64-row tile edges."""
+    rng = np.random.default_rng(100 + n)
+    A = [w.complex_gaussian(rng, (n, n)) / math.sqrt(n) for _ in range(3)]
+    prob = w.Problem(n, [(A[d], w.MONOMIAL, d, 0.0) for d in range(3)])
+    V = w.probe_block(rng, n, l)
+    regs = [w.Region(complex(0.3, -0.2), 0.9, N), w.Region(complex(-1.1, 0.8), 0.45, N)]
+    _check_moments(pm, prob, regs, V)
+
+
+def test_moments_delay_and_identity_terms(pm):
+    W = w.delay_large(n=96, l=4, N=16, nx=4, ny=12)
+    _check_moments(pm, W.problem, W.regions[::9], W.V)
+
+
+def test_moments_closed_form_diagonal(pm):
+    """The GPU moments also satisfy the exact discrete sums of a diagonal T."""
+    rng = np.random.default_rng(3)
+    c, r, N = 0.2 + 0.1j, 0.8, 16
+    a = np.concatenate([rng.uniform(0.2, 0.8, 4), rng.uniform(1.3, 2.5, 4)]) * np.exp(2j * np.pi * rng.random(8))
+    mu = c + r * a
+    P = pm.Problem(8, w.diagonal_linear(mu).terms)
+    V = w.probe_block(rng, 8, 3)
+    C0, C1, ph, _ = P.moments([w.Region(c, r, N)], V)
+    q = 1.0 / (1.0 - a ** N)
+    assert np.linalg.norm(C0[0] - q[:, None] * V) <= 1e-13 * np.linalg.norm(q[:, None] * V)
+    assert np.linalg.norm(C1[0] - (mu * q)[:, None] * V) <= 1e-13 * np.linalg.norm((mu * q)[:, None] * V)
+    assert np.linalg.norm(ph[0] - V[:, 0] / (1 + a ** (N // 2))) <= 1e-13 * np.linalg.norm(V[:, 0])
+
+
+# ---------------------------------------------------------------------------
+# a7: indicator and decisions
+# ---------------------------------------------------------------------------
+
+def test_indicator_and_decisions(pm):
+    W = w.quadratic_small()
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    ind, cand, pn, ps = P.indicator(W.regions, W.V)
+    for g, reg in enumerate(W.regions):
+        m = o.moments(W.problem, reg.c, reg.r, reg.N, W.V)
+        I = o.indicator_value(m.pf_N, m.pf_half)
+        assert pn[g] == pytest.approx(np.linalg.norm(m.pf_N), rel=1e-8)
+        if pn[g] > 1e-6 * ps[g]:
+            assert ind[g] == pytest.approx(I, rel=1e-6)
+            if abs(I - 0.1) > 1e-6 * 0.1:
+                assert bool(cand[g]) == (I > 0.1)
+    P.close()
+
+
+def test_device_pointers_through_the_abi(pm):
+    """Inputs and outputs given as CUDA device buffers (torch tensors)."""
+    import ctypes
+    import torch
+    W = w.quadratic_small(n=32, l=4, N=16)
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    ind_h, cand_h, _, _ = P.indicator(W.regions, W.V)
+    Vt = torch.from_numpy(np.ascontiguousarray(W.V.T)).cuda()  # column-major n x l
+    R = len(W.regions)
+    ind_d = torch.zeros(R, dtype=torch.float64, device="cuda")
+    cand_d = torch.zeros(R, dtype=torch.uint8, device="cuda")
+    opt = pm.options()
+    lib = pm.load()
+    rc = lib.pmcim_indicator(P.handle, ctypes.byref(opt), R, pm.regions_array(W.regions), W.V.shape[1],
+                             Vt.data_ptr(), ind_d.data_ptr(), None, None, cand_d.data_ptr())
+    assert rc == 0
+    assert np.array_equal(ind_d.cpu().numpy(), ind_h)
+    assert np.array_equal(cand_d.cpu().numpy().astype(bool), cand_h)
+    P.close()
+
+
+# ---------------------------------------------------------------------------
+# a8-a10: Beyn's extraction with splitting and the square filter
+# ---------------------------------------------------------------------------
+
+def _oracle_beyn_levels(problem, regions, V, tol_ind=0.1, tol_svd=1e-6, max_depth=8):
+    """pmcim_beyn's contract in oracle steps: no gate on the given disks, gate on children."""
+    lam = []
+    level = [(complex(g.c), g.r, g.N, 0) for g in regions]
+    while level:
+        nxt = []
+        for (c, r, N, d) in level:
+            m = o.moments(problem, c, r, N, V)
+            if d > 0 and not o.indicator_value(m.pf_N, m.pf_half) > tol_ind:
+                continue
+            b = o.beyn_extract(m.C0, m.C1, tol_svd)
+            if b.saturated and d < max_depth:
+                nxt += [(cc, rr, N, d + 1) for (cc, rr) in o.split4(c, r)]
+            else:
+                lam += list(b.lam[o.square_filter(b.lam, c, r)])
+        level = nxt
+    return np.array(lam)
+
+
+def test_beyn_on_regions(pm):
+    W = w.quadratic_small()
+    regs = W.regions[4:8]
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    lam, vecs, rof, st = P.beyn(regs, W.V)
+    ref = _oracle_beyn_levels(W.problem, regs, W.V)
+    # only values that verify are unique; spurious ones come from rounding-level directions
+    sg, acc = o.verify(W.problem, ref)
+    sg2, acc2 = o.verify(W.problem, lam)
+    assert _match_lam(lam[acc2], ref[acc]) <= LAM_TOL
+    for k in np.flatnonzero(acc2):
+        v = vecs[:, k]
+        assert abs(np.linalg.norm(v) - 1.0) < 1e-12
+        i = int(np.argmax(np.abs(v)))
+        assert abs(v[i].imag) < 1e-14 and v[i].real > 0
+        T = o.assemble_T(W.problem, lam[k])
+        assert np.linalg.norm(T @ v) <= 1e-7 * np.linalg.norm(T)
+    P.close()
+
+
+def test_beyn_square_case_all_poles(pm):
+    """n <= l: eig(D) returns every pole; the square filter keeps those in the square."""
+    rng = np.random.default_rng(21)
+    c, r, N = 0.0, 1.0, 16
+    a = np.concatenate([rng.uniform(0.2, 0.6, 3), rng.uniform(1.05, 1.1, 3)]) * np.exp(2j * np.pi * rng.random(6))
+    mu = c + r * a
+    P = pm.Problem(6, w.diagonal_linear(mu).terms)
+    V = w.probe_block(rng, 6, 8)
+    lam, _, _, st = P.beyn([w.Region(c, r, N)], V, opt=pm.options(tol_svd=1e-13, max_split_depth=0))
+    assert st[0] & pm.RS_SATURATED and not st[0] & pm.RS_SPLIT
+    keep = o.square_filter(mu, c, r)
+    assert _match_lam(lam, mu[keep]) <= 1e-9
+    P.close()
+
+
+# ---------------------------------------------------------------------------
+# a11: verification
+# ---------------------------------------------------------------------------
+
+def test_verify_sigma_min(pm):
+    W = w.quadratic_small(n=48, l=4, N=16)
+    res = o.pmcimb(W.problem, W.regions[:4], W.V)
+    rng = np.random.default_rng(9)
+    lam = np.concatenate([res.lam, rng.standard_normal(6) + 1j * rng.standard_normal(6)])
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    sig, acc = P.verify(lam)
+    for i, z in enumerate(lam):
+        s_ref, fro = o.sigma_min(W.problem, z)
+        assert abs(sig[i] - s_ref) <= max(1e-8 * s_ref, 1e-13 * fro), (i, sig[i], s_ref)
+    sg_ref, acc_ref = o.verify(W.problem, lam)
+    assert np.array_equal(acc, acc_ref)
+    P.close()
+
+
+# ---------------------------------------------------------------------------
+# whole pmCIMb
+# ---------------------------------------------------------------------------
+
+def _solve_and_compare(pm, problem, regions, V, **kw):
+    P = pm.Problem(problem.n, problem.terms)
+    res = P.solve(regions, V, opt=pm.options(**kw))
+    ref = o.pmcimb(problem, regions, V, **{k: v for k, v in kw.items() if k in ("tol_ind", "tol_svd", "tol_verify")})
+    assert _match_lam(res["lam"], ref.lam) <= LAM_TOL
+    P.close()
+    return res, ref
+
+
+def test_solve_quadratic_n64_all_eigenvalues(pm):
+    W = w.quadratic_small()
+    res, ref = _solve_and_compare(pm, W.problem, W.regions, W.V)
+    assert len(res["lam"]) == 114
+    assert res["stats"]["splits"] == sum(r.split for r in ref.records)
+    assert res["stats"]["regions"] == len(ref.records)
+    for k in range(len(res["lam"])):
+        v = res["vecs"][:, k]
+        T = o.assemble_T(W.problem, res["lam"][k])
+        assert np.linalg.norm(T @ v) <= 1e-6 * np.linalg.norm(T)
+
+
+def test_solve_paper_example(pm):
+    import os
+    P4 = w.paper_n4_example(os.path.join(os.path.dirname(__file__), "golden", "paper_n4_example.txt"))
+    s, M = 6.0, 9
+    h = s / M
+    regs = [w.Region(complex(-3 + (i + 0.5) * h, -3 + (j + 0.5) * h), math.sqrt(2) * s / M / 2, 64)
+            for i in range(M) for j in range(M)]
+    V = w.probe_block(np.random.default_rng(0), 4, 10)
+    res, ref = _solve_and_compare(pm, P4, regs, V)
+    assert len(res["lam"]) == 8
+
+
+def test_solve_delay_small(pm):
+    W = w.delay_large(n=64, l=8, N=32, nx=4, ny=12)
+    _solve_and_compare(pm, W.problem, W.regions, W.V)
+
+
+def test_singular_node_is_reported_not_fatal(pm):
+    """An eigenvalue exactly on node 0 makes T(z_0) singular: status bit, no failure."""
+    c, r = 0.25, 0.5
+    mu = np.array([c + r, 0.1 + 0.05j, -0.6 + 0.3j])
+    P = pm.Problem(3, w.diagonal_linear(mu).terms)
+    V = w.probe_block(np.random.default_rng(1), 3, 2)
+    res = P.solve([w.Region(complex(c), r, 8)], V)
+    assert res["status"][0] & pm.RS_SINGULAR_NODE
+    assert res["stats"]["singular_nodes"] == 1
+    P.close()
+
+
+def test_full_size_delay_sampled_regions(pm):
+    """n = 1024 delay problem in the benchmark's launch configuration, two sampled disks."""
+    W = w.delay_large()
+    regs = [W.regions[300], W.regions[517]]
+    _check_moments(pm, W.problem, regs, W.V)

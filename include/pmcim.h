@@ -166,6 +166,29 @@ int pmcim_solve(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmci
 const char* pmcim_status_string(int code);
 const char* pmcim_last_error(void);
 
+/* Node solves that allocate nothing (the paper has no counterpart; this serves
+   callers that cannot allocate device memory while they run, e.g. a host
+   application whose own pool owns all device memory, or a latency-bound loop
+   that must not stall on the device-wide synchronisation of cudaFree).
+   Computes X_j = T(z_j)^{-1} V for j < m with the same assembly, LU with
+   partial pivoting and solve as pmcim_moments, at the caller's points z.
+   Arguments: f[K] and dense[K] (host; dense[k] != 0 means term k has a dense
+   coefficient), A = the dense coefficients in term order, each n*n complex
+   column-major, contiguous (device); z = m complex points (device); V = n x l
+   complex column-major (device); X = m blocks of n x l complex (device,
+   output); info = m int32 (device, output, may be NULL): 0, or 1 + the first
+   column whose pivot was exactly zero.
+   Workspace: a fixed 32 MiB array compiled into the library, held by every GPU
+   that loads it until the process exits. A problem whose one-CTA workspace,
+   n (n + l) * 16 + n * 4 bytes, exceeds 32 MiB (n above about 1440 at l = 16)
+   is rejected with PMCIM_ENOTSUP. The first call on each device looks up the
+   array's device address with that device current. Every call shares the
+   array, so calls that overlap on the GPU race; nothing in it needs clearing
+   between calls. Synchronous on cuda_stream. No cudaMalloc, no cudaFree. */
+int pmcim_solve_points_noalloc(int32_t n, int32_t K, const pmcim_fterm* f, const uint8_t* dense,
+                               const double* A, int32_t m, const double* z, int32_t l, const double* V,
+                               double* X, int32_t* info, void* cuda_stream);
+
 /* ---- instrumentation (no counterpart in the paper) ----------------------
    Every kernel launch of the library is counted per kernel kind. When timing
    is enabled, CUDA events are recorded around each launch on the stream it is

@@ -16,6 +16,8 @@
 //
 // Pivot rule: the row maximising |Re| + |Im| in the column, lowest row index on
 // ties (the BLAS izamax convention of LAPACK zgetrf).
+#include <mutex>
+
 #include "pmcim_internal.cuh"
 
 namespace {
@@ -482,4 +484,148 @@ cudaError_t launch_verify_fp64(const VerifyArgs& a, cudaStream_t s) {
   int grid = a.slots < a.m ? a.slots : a.m;
   k_verify_fp64<<<grid, THREADS, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// ===========================================================================
+// Node solves without device allocation.
+//
+// Some callers cannot allocate device memory while they run: a host
+// application that owns every byte of device memory through its own pool, or a
+// latency-bound service loop that must not stall on the device-wide
+// synchronisation that cudaFree implies. For them this entry point solves
+// T(z_j) X_j = V at caller-given points with all inputs and outputs in caller
+// buffers and the factorisation workspace in a fixed array compiled into the
+// library. It makes no allocation of any kind.
+//
+// The array below is held by every GPU that loads the library until the
+// process exits. It is shared by all calls and keeps the last call's contents;
+// nothing in it needs clearing, because the kernel writes every workspace
+// element (assembled matrix, probe columns, pivots) before it reads it. Calls
+// that overlap on the GPU (two streams, two threads) race on the array.
+// ===========================================================================
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocScratchBytes / sizeof(double2)];
+
+struct PointArgs {
+  ProblemDesc prob;
+  const double2* A;
+  const double2* V;
+  int l;
+  const double2* z;   // m points
+  int m;
+  double2* X;         // m * n * l
+  int32_t* info;      // m, may be NULL
+  double2* work;      // slots * n * (n + l), inside g_noalloc_scratch
+  int32_t* piv;       // slots * n, inside g_noalloc_scratch
+};
+
+// Same per-node work as k_factor_solve_fp64, at an explicit point z_j.
+__global__ void __launch_bounds__(THREADS, 2) k_factor_solve_points_fp64(PointArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LuSmem& sm = *reinterpret_cast<LuSmem*>(smem_raw);
+  const int tid = threadIdx.x;
+  const ProblemDesc& P = a.prob;
+  const int n = P.n, l = a.l, ncols = n + l;
+  double2* M = a.work + (size_t)blockIdx.x * n * ncols;
+  int* piv = a.piv + (size_t)blockIdx.x * n;
+  for (int node = blockIdx.x; node < a.m; node += gridDim.x) {
+    const double2 z = a.z[node];
+    if (tid < P.K) sm.fz[tid] = eval_f(P.term[tid], z);
+    __syncthreads();
+    const size_t nn = (size_t)n * n;
+    for (int col = 0; col < n; ++col) {
+      for (int row = tid; row < n; row += THREADS) {
+        const size_t e = (size_t)col * n + row;
+        double2 v = make_double2(0.0, 0.0);
+        for (int k = 0; k < P.K; ++k) {
+          const TermDesc& t = P.term[k];
+          if (t.dense) cfma(v, sm.fz[k], a.A[(size_t)t.mat_index * nn + e]);
+          else if (row == col) cfma(v, sm.fz[k], t.id);
+        }
+        M[e] = v;
+      }
+    }
+    for (size_t e = tid; e < (size_t)n * l; e += THREADS) M[nn + e] = a.V[e];
+    __syncthreads();
+    const int info = cta_lu(M, n, ncols, piv, sm);
+    cta_back_subst(M, n, l, sm);
+    double2* Xo = a.X + (size_t)node * n * l;
+    for (size_t e = tid; e < (size_t)n * l; e += THREADS) Xo[e] = M[nn + e];
+    if (tid == 0 && a.info) a.info[node] = info;
+    __syncthreads();
+  }
+}
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};
+
+}  // namespace
+
+extern "C" int pmcim_solve_points_noalloc(int32_t n, int32_t K, const pmcim_fterm* f, const uint8_t* dense,
+                                          const double* A, int32_t m, const double* z, int32_t l,
+                                          const double* V, double* X, int32_t* info, void* cuda_stream) {
+  if (n < 1 || K < 1 || K > PMCIM_MAX_TERMS || l < 1 || l > PMCIM_MAX_L || m < 0) return PMCIM_EINVAL;
+  if (!f || !dense || !V || (m > 0 && (!z || !X))) return PMCIM_EINVAL;
+  // the workspace of one CTA slot must fit the fixed array
+  const size_t slot_bytes = (size_t)n * (n + l) * sizeof(double2) + (size_t)n * sizeof(int32_t);
+  if (slot_bytes > kNoAllocScratchBytes) return PMCIM_ENOTSUP;
+  ProblemDesc desc{};
+  desc.n = n;
+  desc.K = K;
+  int nd = 0;
+  for (int k = 0; k < K; ++k) {
+    if (f[k].kind != PMCIM_F_MONOMIAL && f[k].kind != PMCIM_F_EXP_NEG) return PMCIM_EINVAL;
+    if (f[k].kind == PMCIM_F_MONOMIAL && (f[k].degree < 0 || f[k].degree > 16)) return PMCIM_EINVAL;
+    TermDesc& t = desc.term[k];
+    t.kind = f[k].kind;
+    t.degree = f[k].degree;
+    t.tau = f[k].tau;
+    t.id = make_double2(f[k].id_re, f[k].id_im);
+    t.dense = dense[k] ? 1 : 0;
+    t.mat_index = dense[k] ? nd++ : -1;
+  }
+  desc.n_dense = nd;
+  if (nd > 0 && !A) return PMCIM_EINVAL;
+  if (m == 0) return PMCIM_OK;
+
+  // set-up, once per device, with that device current: the device address of the array
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PMCIM_ECUDA;
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return PMCIM_ECUDA;
+      g_noalloc_addr[dev] = ptr;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  int slots = factor_slots_fp64(n, l);
+  const size_t fit = kNoAllocScratchBytes / slot_bytes;
+  if ((size_t)slots > fit) slots = (int)fit;
+  if (slots > m) slots = m;
+
+  PointArgs a;
+  a.prob = desc;
+  a.A = reinterpret_cast<const double2*>(A);
+  a.V = reinterpret_cast<const double2*>(V);
+  a.l = l;
+  a.z = reinterpret_cast<const double2*>(z);
+  a.m = m;
+  a.X = reinterpret_cast<double2*>(X);
+  a.info = info;
+  a.work = reinterpret_cast<double2*>(base);
+  a.piv = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(base) + (size_t)slots * n * (n + l) * sizeof(double2));
+  const size_t smem = sizeof(LuSmem);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (cudaFuncSetAttribute(k_factor_solve_points_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return PMCIM_ECUDA;
+  k_factor_solve_points_fp64<<<slots, THREADS, smem, s>>>(a);
+  if (cudaGetLastError() != cudaSuccess) return PMCIM_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PMCIM_ECUDA;
+  return PMCIM_OK;
 }

@@ -26,7 +26,8 @@ PREC_FP64, PREC_FP32_IR = 0, 1
 
 EXPORTS = ["pmcim_default_options", "pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments",
            "pmcim_indicator", "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_status_string",
-           "pmcim_last_error", "pmcim_profile_enable", "pmcim_profile_reset", "pmcim_profile_read"]
+           "pmcim_last_error", "pmcim_profile_enable", "pmcim_profile_reset", "pmcim_profile_read",
+           "pmcim_solve_points_noalloc"]
 
 KERNELS = ["factor_fp64", "reduce", "indicator", "beyn", "verify", "gather", "factor_fp32", "refine"]
 
@@ -93,8 +94,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pmcim_profile_reset.restype = None
     lib.pmcim_profile_read.argtypes = [C.POINTER(pmcim_profile)]
     lib.pmcim_profile_read.restype = None
+    lib.pmcim_solve_points_noalloc.argtypes = [I32, I32, C.POINTER(pmcim_fterm), C.POINTER(C.c_uint8), VP, I32,
+                                               VP, I32, VP, VP, VP, VP]
     for name in ("pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments", "pmcim_indicator",
-                 "pmcim_beyn", "pmcim_verify", "pmcim_solve"):
+                 "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_solve_points_noalloc"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib

@@ -37,6 +37,9 @@ UNIT = "solves/s"
 FP64_DFMA_PER_SM_CLK = 2          # measured: 1.19-1.20 TFLOP/s at ~2.0 GHz on 152 SMs
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
+# DRAM bytes per node of k_factor_solve_fp64, from one ncu capture of a 64-node launch at n = 1024, l = 16
+# (dram__bytes_read.sum + dram__bytes_write.sum = 28.59 GB); scaled to a launch by its node count.
+FACTOR_FP64_TRAFFIC_PER_NODE = 28.59e9 / 64
 
 
 def _peaks():
@@ -327,7 +330,9 @@ def main():
     peak = fp64_peak_tflops(smax)
     roofline = {"bound": "alu", "kernel": "k_factor_solve_fp64 (FP64 pipe)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": FACTOR_FP64_TRAFFIC_PER_NODE * factor_nodes / max(1, fac["launches"]),
+                "traffic_note": "ncu DRAM bytes of a 64-node capture, scaled by nodes per launch",
                 "peak_source": "2 DFMA/SM/clk x 152 SMs x max SM clock (probe: 1.20 TFLOP/s at 2.0 GHz)",
                 "launches": fac["launches"], "avg_launch_ms": fac["ms"] / max(1, fac["launches"]),
                 "share_of_step": fac["ms"] / t_ms if t_ms else None}

@@ -233,7 +233,10 @@ int run_moments(pmcim_problem p, const pmcim_options* opt, const std::vector<Hos
   if (R == 0) return PMCIM_OK;
 
   const size_t slot_bytes = (size_t)n * (n + l) * sizeof(double2);
-  const int slots = (int)std::max<size_t>(1, std::min<size_t>(factor_slots_fp64(n, l), kSlotBytes / slot_bytes));
+  size_t total_nodes = 0;
+  for (const HostRegion& h : regs) total_nodes += (size_t)h.N;
+  const int slots = (int)std::max<size_t>(
+      1, std::min<size_t>(std::min<size_t>(factor_slots_fp64(n, l), kSlotBytes / slot_bytes), total_nodes));
   CU(p->work.ensure((size_t)slots * n * (n + l) * sizeof(double2)));
   CU(p->piv.ensure((size_t)slots * n * sizeof(int32_t)));
 

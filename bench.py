@@ -40,6 +40,8 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes per node of k_factor_solve_fp64, from one ncu capture of a 64-node launch at n = 1024, l = 16
 # (dram__bytes_read.sum + dram__bytes_write.sum = 28.59 GB); scaled to a launch by its node count.
 FACTOR_FP64_TRAFFIC_PER_NODE = 28.59e9 / 64
+# FP32 pipe: 128 FFMA / SM / clock (measured 73.3 TFLOP/s at ~2.0 GHz); at the 2.07 GHz maximum:
+FP32_PEAK_TFLOPS = 128 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
 
 
 def _peaks():
@@ -204,6 +206,39 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def run_full(args, P, W, opt, opt_mixed, world, rank, local):
+    """Time to all eigenvalues: one pmCIMb pass over the whole grid per form."""
+    import torch
+    from paper_2312_13117_gb300 import pmcim
+    R = len(W.regions)
+    mine = [W.regions[g] for g in range(rank, R, world)]
+    out = {}
+    lams = {}
+    for name, o in (("precision_form", opt_mixed), ("fp64", opt)):
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        res = P.solve(mine, W.V, cap=64 * W.V.shape[1] * len(mine), opt=o)
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+        lams[name] = res["lam"]
+        out[name] = {"seconds": dt, "solves": res["stats"]["solves"], "eigenvalues": len(res["lam"]),
+                     "stats": res["stats"]}
+    a, b = np.asarray(lams["fp64"]), np.asarray(lams["precision_form"])
+    err = None
+    if len(a) == len(b) and len(a):
+        from scipy.optimize import linear_sum_assignment
+        ri, ci = linear_sum_assignment(np.abs(a[:, None] - b[None, :]))
+        err = float(np.max(np.abs(a[ri] - b[ci]) / np.maximum(1.0, np.abs(a[ri]))))
+    if rank == 0:
+        print(json.dumps({"metric": "full pmCIMb time (all %d disks)" % R, "unit": "s", "n_gpus": world,
+                          "workload": "delay NEP n=1024, l=16, N=64, Omega=[-3,1]x[-6,6] 16x48",
+                          "forms": out, "max_rel_lambda_diff_fp64_vs_precision_form": err,
+                          "speedup": out["fp64"]["seconds"] / out["precision_form"]["seconds"]}))
+    P.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,6 +251,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-regions", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the precision-form measurement")
+    ap.add_argument("--full", action="store_true",
+                    help="time pmCIMb over all 768 disks (time to all eigenvalues), FP64 and precision form")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -241,42 +279,72 @@ def main():
 
     stream = torch.cuda.current_stream()
     opt = pmcim.options(stream=stream.cuda_stream)
+    opt_mixed = pmcim.options(stream=stream.cuda_stream, precision=pmcim.PREC_FP32_IR)
     P = pmcim.Problem(n, W.problem.terms)
     cap = 64 * l * B
 
-    def one_step(step):
-        res = P.solve(batch(step), W.V, cap=cap, opt=opt)
-        return res["stats"]["solves"], len(res["lam"])
+    if args.full:
+        return run_full(args, P, W, opt, opt_mixed, world, rank, local)
 
-    for k in range(args.warmup):
-        one_step(-1 - k)
-    torch.cuda.synchronize()
+    def timed(o, steps, warmup):
+        """Warm up, then time `steps` steps on the library's stream; returns (ms, solves, found, stats, prof)."""
+        for k in range(warmup):
+            P.solve(batch(-1 - k), W.V, cap=cap, opt=o)
+        torch.cuda.synchronize()
+        pmcim.pmcim_profile_reset()
+        pmcim.pmcim_profile_enable(True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solves, found = 0, 0
+        agg = {}
+        for k in range(steps):
+            res = P.solve(batch(k), W.V, cap=cap, opt=o)
+            solves += res["stats"]["solves"]
+            found += len(res["lam"])
+            for key, v in res["stats"].items():
+                agg[key] = agg.get(key, 0) + v
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        pmcim.pmcim_profile_enable(False)
+        return e0.elapsed_time(e1), solves, found, agg, pmcim.pmcim_profile_read()
 
-    pmcim.pmcim_profile_reset()
-    pmcim.pmcim_profile_enable(True)
     clocks = ClockSampler(local)
     clocks.start()
-    barrier(world)
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    solves = 0
-    found = 0
-    for k in range(args.steps):
-        s, f = one_step(k)
-        solves += s
-        found += f
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
+    t_ms, solves, found, agg64, prof = timed(opt, args.steps, args.warmup)
+    mixed = None
+    if not args.no_mixed:
+        tm_ms, msolves, mfound, aggm, profm = timed(opt_mixed, args.steps, args.warmup)
     clk = clocks.stop()
-    pmcim.pmcim_profile_enable(False)
-    prof = pmcim.pmcim_profile_read()
-    t_ms = ev0.elapsed_time(ev1)
     t_max = max_over_ranks(t_ms, world)
     solves_all = sum_over_ranks(float(solves), world)
     value = solves_all / (t_max / 1e3)
+    smax = clk.get("sm_max_mhz") or SM_MAX_MHZ
+    peak64 = fp64_peak_tflops(smax)
+    if not args.no_mixed:
+        tm_max = max_over_ranks(tm_ms, world)
+        fm = profm["factor_fp32"]
+        k_dense = sum(1 for t in W.problem.terms if not np.isscalar(t[0]))
+        w64 = aggm["ir_sweeps"] * 8.0 * k_dense * n * n * l + aggm["ir_fallbacks"] * (8.0 * n ** 3 / 3 + 8.0 * n * n * l)
+        w32 = msolves * (8.0 * n ** 3 / 3 + 8.0 * n * n * l) + aggm["ir_sweeps"] * 8.0 * n * n * l
+        a64 = w64 / (fm["ms"] / 1e3) / 1e12 if fm["ms"] > 0 else None
+        a32 = w32 / (fm["ms"] / 1e3) / 1e12 if fm["ms"] > 0 else None
+        mixed = {
+            "form": "FP32 LU + FP64 iterative refinement (residual R = V - T(z)X from the FP64 A_k)",
+            "value": sum_over_ranks(float(msolves), world) / (tm_max / 1e3), "unit": UNIT,
+            "ms_per_step": tm_max / args.steps, "speedup_vs_fp64": t_max / tm_max,
+            "eigenvalues_found": mfound, "eigenvalues_found_fp64": found,
+            "ir_sweeps_per_node": aggm["ir_sweeps"] / max(1, msolves), "ir_fallbacks": aggm["ir_fallbacks"],
+            "roofline": {"bound": "alu", "kernel": "k_factor_solve_mixed (FP64 pipe: refinement residuals)",
+                         "achieved": a64, "peak": peak64, "unit": "TFLOP/s",
+                         "frac": (a64 / peak64) if a64 else None,
+                         "fp32_achieved_tflops": a32, "fp32_peak_tflops": FP32_PEAK_TFLOPS,
+                         "launches": fm["launches"], "share_of_step": fm["ms"] / tm_ms if tm_ms else None},
+            "kernels": profm,
+        }
 
     # ---- e2e: host buffers through the C ABI, copies inside the timed region
     e2e = None
@@ -326,8 +394,7 @@ def main():
     flops_per_node = 8.0 * n ** 3 / 3.0 + 8.0 * n * n * l
     factor_nodes = solves  # every node solve is one unit of the factorisation kernel
     achieved = (flops_per_node * factor_nodes) / (fac["ms"] / 1e3) / 1e12 if fac["ms"] > 0 else None
-    smax = clk.get("sm_max_mhz") or SM_MAX_MHZ
-    peak = fp64_peak_tflops(smax)
+    peak = peak64
     roofline = {"bound": "alu", "kernel": "k_factor_solve_fp64 (FP64 pipe)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None,
@@ -356,7 +423,7 @@ def main():
                        "l2": "working set > L2 (304 x 16.3 MB factorisation slots)",
                        "eigenvalues_found": found},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "kernels": prof, "clocks": clk,
+            "kernels": prof, "precision_form": mixed, "clocks": clk,
         }
         print(json.dumps(line))
     P.close()

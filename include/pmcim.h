@@ -98,6 +98,7 @@ typedef struct {
   int32_t unverified;      /* filtered values rejected by verification           */
   int32_t ir_fallbacks;    /* nodes re-solved in FP64 after refinement stalled  */
   int32_t singular_nodes;  /* nodes whose LU met an exactly zero pivot           */
+  int64_t ir_sweeps;       /* refinement sweeps summed over nodes (FP32_IR)      */
 } pmcim_stats;
 
 typedef struct pmcim_problem_s* pmcim_problem;
@@ -207,6 +208,10 @@ int pmcim_solve_points_noalloc(int32_t n, int32_t K, const pmcim_fterm* f, const
 typedef struct {
   int64_t launches[PMCIM_K_COUNT];
   double ms[PMCIM_K_COUNT]; /* summed event time; 0 unless timing was on */
+  /* precision-form node kernel, with timing on: SM clock cycles summed over
+     CTAs per phase: assembly, FP32 LU, first solve, FP64 residual, correction
+     solves, FP64 fallback, node set-up, unused */
+  double mixed_phase_cycles[8];
 } pmcim_profile;
 
 void pmcim_profile_enable(int on);

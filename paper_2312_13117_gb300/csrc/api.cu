@@ -88,6 +88,10 @@ struct DevBuf {
 constexpr size_t kWaveBytes = size_t(4) << 30;
 // Upper bound on the per-CTA factorisation workspaces.
 constexpr size_t kSlotBytes = size_t(24) << 30;
+// Refinement stops when the estimated remaining error of X (max norm) is below
+// this fraction of |X|: 1e-11 keeps Beyn's eigenvalues within about 1e-14 of
+// the FP64 ones on the delay workload (simulated FP32 LU + FP64 refinement).
+constexpr double kIrTol = 1e-11;
 
 // Copy results to a caller buffer that may live on the host or the device.
 int copy_out(void* dst, const void* src, size_t bytes) {
@@ -102,6 +106,7 @@ struct Prof {
   bool on = false;
   int64_t launches[PMCIM_K_COUNT] = {};
   double ms[PMCIM_K_COUNT] = {};
+  double phase[8] = {};
   struct Pending {
     int kind;
     cudaEvent_t a, b;
@@ -127,6 +132,9 @@ Prof& prof() {
 
 }  // namespace
 
+bool prof_on();
+void prof_add_phases(const unsigned long long* c, int slots);
+
 void prof_begin(int kind, cudaStream_t s) {
   Prof& P = prof();
   std::lock_guard<std::mutex> g(P.mu);
@@ -145,6 +153,19 @@ void prof_end(int kind, cudaStream_t s) {
   cudaEventRecord(e, s);
   P.pending.push_back({kind, P.cur_begin[kind], e});
   P.cur_begin[kind] = nullptr;
+}
+
+bool prof_on() {
+  Prof& P = prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  return P.on;
+}
+
+void prof_add_phases(const unsigned long long* c, int slots) {
+  Prof& P = prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  for (int b = 0; b < slots; ++b)
+    for (int q = 0; q < 8; ++q) P.phase[q] += (double)c[(size_t)b * 8 + q];
 }
 
 void prof_flush() {
@@ -170,7 +191,7 @@ struct pmcim_problem_s {
   DevBuf C0, C1, pf_half, pf_abs, ind, pf_norm, pf_scale, cand;
   DevBuf bslot, bregion, bwork, bsigma, bp, blam, bvecs, bkept, bstatus;
   DevBuf vlam, vsig, vacc, vwork, vvec, vpiv;
-  DevBuf gsrc, gdst, gperm;
+  DevBuf gsrc, gdst, gperm, phase;
 };
 
 namespace {
@@ -189,6 +210,8 @@ int check_options(const pmcim_options* opt) {
   if (opt->precision != PMCIM_PREC_FP64 && opt->precision != PMCIM_PREC_FP32_IR)
     return fail(PMCIM_EINVAL, "unknown precision %d", opt->precision);
   if (opt->max_split_depth < 0 || opt->max_split_depth > 30) return fail(PMCIM_EINVAL, "max_split_depth out of range");
+  if (opt->precision == PMCIM_PREC_FP32_IR && (opt->max_ir_sweeps < 1 || opt->max_ir_sweeps > 10))
+    return fail(PMCIM_EINVAL, "max_ir_sweeps must be 1..10");
   return PMCIM_OK;
 }
 
@@ -220,7 +243,8 @@ int upload_V(pmcim_problem p, int l, const double* V, cudaStream_t s) {
 // Moments of every disk in `regs` into p->C0/C1/pf_half/pf_abs (region-major),
 // and per-disk singular-node flags into `singular` (host).
 int run_moments(pmcim_problem p, const pmcim_options* opt, const std::vector<HostRegion>& regs, int l,
-                std::vector<int>* singular, int64_t* solves) {
+                std::vector<int>* singular, int64_t* solves, int* fallbacks = nullptr,
+                int64_t* sweeps = nullptr) {
   cudaStream_t s = stream_of(opt);
   const int n = p->n;
   const int R = (int)regs.size();
@@ -232,12 +256,13 @@ int run_moments(pmcim_problem p, const pmcim_options* opt, const std::vector<Hos
   if (singular) singular->assign(R, 0);
   if (R == 0) return PMCIM_OK;
 
-  const size_t slot_bytes = (size_t)n * (n + l) * sizeof(double2);
+  const bool mixed = opt->precision == PMCIM_PREC_FP32_IR;
+  const size_t slot_bytes = mixed ? mixed_slot_bytes(n, l) : (size_t)n * (n + l) * sizeof(double2);
   size_t total_nodes = 0;
   for (const HostRegion& h : regs) total_nodes += (size_t)h.N;
   const int slots = (int)std::max<size_t>(
       1, std::min<size_t>(std::min<size_t>(factor_slots_fp64(n, l), kSlotBytes / slot_bytes), total_nodes));
-  CU(p->work.ensure((size_t)slots * n * (n + l) * sizeof(double2)));
+  CU(p->work.ensure((size_t)slots * slot_bytes));
   CU(p->piv.ensure((size_t)slots * n * sizeof(int32_t)));
 
   // waves of whole disks whose solutions fit the wave buffer
@@ -273,22 +298,57 @@ int run_moments(pmcim_problem p, const pmcim_options* opt, const std::vector<Hos
     CU(cudaMemcpyAsync(p->regions.p, rd.data(), rd.size() * sizeof(RegionDev), cudaMemcpyHostToDevice, s));
     CU(cudaMemcpyAsync(p->node_region.p, node_region.data(), nodes * sizeof(int32_t), cudaMemcpyHostToDevice, s));
 
-    FactorArgs fa;
-    fa.prob = p->desc;
-    fa.A = p->dA;
-    fa.V = p->V.as<double2>();
-    fa.l = l;
-    fa.regions = p->regions.as<RegionDev>();
-    fa.node_region = p->node_region.as<int32_t>();
-    fa.n_nodes = (int)nodes;
-    fa.X = p->X.as<double2>();
-    fa.node_info = p->node_info.as<int32_t>();
-    fa.work = p->work.as<double2>();
-    fa.piv = p->piv.as<int32_t>();
-    fa.slots = slots;
-    prof_begin(PMCIM_K_FACTOR, s);
-    CU(launch_factor_solve_fp64(fa, s));
-    prof_end(PMCIM_K_FACTOR, s);
+    if (mixed) {
+      MixedArgs ma;
+      ma.prob = p->desc;
+      ma.A = p->dA;
+      ma.V = p->V.as<double2>();
+      ma.l = l;
+      ma.regions = p->regions.as<RegionDev>();
+      ma.node_region = p->node_region.as<int32_t>();
+      ma.n_nodes = (int)nodes;
+      ma.X = p->X.as<double2>();
+      ma.node_info = p->node_info.as<int32_t>();
+      ma.work = p->work.as<char>();
+      ma.slot_bytes = slot_bytes;
+      ma.piv = p->piv.as<int32_t>();
+      ma.slots = slots;
+      ma.max_sweeps = opt->max_ir_sweeps;
+      ma.tol_ir = kIrTol;
+      ma.phase = nullptr;
+      const bool timed = prof_on();
+      if (timed) {
+        CU(p->phase.ensure((size_t)slots * 8 * sizeof(unsigned long long)));
+        CU(cudaMemsetAsync(p->phase.p, 0, (size_t)slots * 8 * sizeof(unsigned long long), s));
+        ma.phase = p->phase.as<unsigned long long>();
+      }
+      prof_begin(PMCIM_K_FACTOR32, s);
+      CU(launch_factor_solve_mixed(ma, s));
+      prof_end(PMCIM_K_FACTOR32, s);
+      if (timed) {
+        std::vector<unsigned long long> c((size_t)slots * 8);
+        CU(cudaMemcpyAsync(c.data(), p->phase.p, c.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        prof_add_phases(c.data(), slots);
+      }
+    } else {
+      FactorArgs fa;
+      fa.prob = p->desc;
+      fa.A = p->dA;
+      fa.V = p->V.as<double2>();
+      fa.l = l;
+      fa.regions = p->regions.as<RegionDev>();
+      fa.node_region = p->node_region.as<int32_t>();
+      fa.n_nodes = (int)nodes;
+      fa.X = p->X.as<double2>();
+      fa.node_info = p->node_info.as<int32_t>();
+      fa.work = p->work.as<double2>();
+      fa.piv = p->piv.as<int32_t>();
+      fa.slots = slots;
+      prof_begin(PMCIM_K_FACTOR, s);
+      CU(launch_factor_solve_fp64(fa, s));
+      prof_end(PMCIM_K_FACTOR, s);
+    }
 
     ReduceArgs ra;
     ra.X = p->X.as<double2>();
@@ -310,8 +370,15 @@ int run_moments(pmcim_problem p, const pmcim_options* opt, const std::vector<Hos
       CU(cudaStreamSynchronize(s));
       for (int g = g0; g < g1; ++g) {
         const RegionDev& d = rd[g - g0];
-        for (int j = 0; j < d.N; ++j)
-          if (info[d.node_off + j] != 0) (*singular)[g] = 1;
+        for (int j = 0; j < d.N; ++j) {
+          const int v = info[d.node_off + j];
+          if (v & 0x00ffffff) (*singular)[g] |= 1;
+          if (sweeps) *sweeps += (v >> 24) & 63;
+          if (v & (1 << 30)) {
+            (*singular)[g] |= 2;
+            if (fallbacks) *fallbacks += 1;
+          }
+        }
       }
     }
     if (solves) *solves += (int64_t)nodes;
@@ -366,7 +433,13 @@ int run_beyn_levels(pmcim_problem p, const pmcim_options* opt, const std::vector
     const int R = (int)level.size();
     std::vector<int> singular;
     int64_t solves = 0;
-    CHK(run_moments(p, opt, level, l, &singular, &solves));
+    int fallbacks = 0;
+    int64_t sweeps = 0;
+    CHK(run_moments(p, opt, level, l, &singular, &solves, &fallbacks, &sweeps));
+    if (st) {
+      st->ir_fallbacks += fallbacks;
+      st->ir_sweeps += sweeps;
+    }
     CHK(run_indicator(p, opt, R, l));
     std::vector<double> ind(R);
     std::vector<uint8_t> cflag(R);
@@ -381,10 +454,11 @@ int run_beyn_levels(pmcim_problem p, const pmcim_options* opt, const std::vector
     std::vector<RegionDev> crd;
     for (int g = 0; g < R; ++g) {
       const HostRegion& h = level[g];
-      if (singular[g]) {
+      if (singular[g] & 1) {
         (*root_status)[h.root] |= PMCIM_RS_SINGULAR_NODE;
         if (st) st->singular_nodes += 1;
       }
+      if (singular[g] & 2) (*root_status)[h.root] |= PMCIM_RS_IR_FALLBACK;
       if (h.depth == 0 && top_ind) (*top_ind)[h.root] = ind[g];
       const bool gated = (h.depth > 0) || gate_top;
       if (cflag[g]) (*root_status)[h.root] |= PMCIM_RS_CANDIDATE;
@@ -586,6 +660,7 @@ void pmcim_profile_reset(void) {
     P.launches[k] = 0;
     P.ms[k] = 0.0;
   }
+  for (int q = 0; q < 8; ++q) P.phase[q] = 0.0;
 }
 
 void pmcim_profile_read(pmcim_profile* out) {
@@ -597,6 +672,7 @@ void pmcim_profile_read(pmcim_profile* out) {
     out->launches[k] = P.launches[k];
     out->ms[k] = P.ms[k];
   }
+  for (int q = 0; q < 8; ++q) out->mixed_phase_cycles[q] = P.phase[q];
 }
 
 int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmcim_fterm* f, pmcim_problem* out) {
@@ -659,7 +735,7 @@ int pmcim_problem_destroy(pmcim_problem p) {
   DevBuf* bufs[] = {&p->work, &p->piv, &p->X, &p->node_info, &p->regions, &p->node_region, &p->V,
                     &p->C0, &p->C1, &p->pf_half, &p->pf_abs, &p->ind, &p->pf_norm, &p->pf_scale, &p->cand,
                     &p->bslot, &p->bregion, &p->bwork, &p->bsigma, &p->bp, &p->blam, &p->bvecs, &p->bkept,
-                    &p->bstatus, &p->vlam, &p->vsig, &p->vacc, &p->vwork, &p->vvec, &p->vpiv, &p->gsrc, &p->gdst, &p->gperm};
+                    &p->bstatus, &p->vlam, &p->vsig, &p->vacc, &p->vwork, &p->vvec, &p->vpiv, &p->gsrc, &p->gdst, &p->gperm, &p->phase};
   for (DevBuf* b : bufs) b->release();
   delete p;
   return PMCIM_OK;
@@ -670,7 +746,6 @@ int pmcim_moments(pmcim_problem p, const pmcim_options* opt, int32_t R, const pm
   if (!p) return fail(PMCIM_EINVAL, "problem is NULL");
   CHK(check_options(opt));
   CHK(check_regions(R, reg, l, p->n));
-  if (opt->precision != PMCIM_PREC_FP64) return fail(PMCIM_ENOTSUP, "reduced precision is not built yet");
   cudaStream_t s = stream_of(opt);
   CHK(upload_V(p, l, V, s));
   std::vector<HostRegion> regs = to_host_regions(R, reg);
@@ -689,7 +764,6 @@ int pmcim_indicator(pmcim_problem p, const pmcim_options* opt, int32_t R, const 
   if (!p) return fail(PMCIM_EINVAL, "problem is NULL");
   CHK(check_options(opt));
   CHK(check_regions(R, reg, l, p->n));
-  if (opt->precision != PMCIM_PREC_FP64) return fail(PMCIM_ENOTSUP, "reduced precision is not built yet");
   if (R > 0 && (!ind || !candidate)) return fail(PMCIM_EINVAL, "ind or candidate is NULL");
   cudaStream_t s = stream_of(opt);
   CHK(upload_V(p, l, V, s));
@@ -712,7 +786,6 @@ int pmcim_beyn(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim
   if (!p) return fail(PMCIM_EINVAL, "problem is NULL");
   CHK(check_options(opt));
   CHK(check_regions(R, reg, l, p->n));
-  if (opt->precision != PMCIM_PREC_FP64) return fail(PMCIM_ENOTSUP, "reduced precision is not built yet");
   if (!count || cap < 0 || (cap > 0 && !lambda)) return fail(PMCIM_EINVAL, "bad output arguments");
   cudaStream_t s = stream_of(opt);
   CHK(upload_V(p, l, V, s));
@@ -754,7 +827,6 @@ int pmcim_solve(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmci
   if (!p) return fail(PMCIM_EINVAL, "problem is NULL");
   CHK(check_options(opt));
   CHK(check_regions(R, reg, l, p->n));
-  if (opt->precision != PMCIM_PREC_FP64) return fail(PMCIM_ENOTSUP, "reduced precision is not built yet");
   if (!count || cap < 0 || (cap > 0 && !lambda)) return fail(PMCIM_EINVAL, "bad output arguments");
   cudaStream_t s = stream_of(opt);
   pmcim_stats st;

@@ -18,238 +18,11 @@
 // ties (the BLAS izamax convention of LAPACK zgetrf).
 #include <mutex>
 
-#include "pmcim_internal.cuh"
+#include "lu_core.cuh"
 
 namespace {
 
-constexpr int THREADS = 256;
-constexpr int NB = 32;    // panel width
-constexpr int TILE = 64;  // trailing-update tile (TILE x TILE complex)
-constexpr int US_LD = TILE + 1;
-
-struct LuSmem {
-  double2 Ls[NB * TILE];   // L21 tile, [kk][row]; reused for L11 during the TRSM
-  double2 Us[NB * US_LD];  // U12 tile, [kk][col], padded
-  double2 prow[NB];        // pivot row of the panel
-  double red_v[THREADS / 32];
-  int red_i[THREADS / 32];
-  double2 bcast[PMCIM_MAX_L];
-  double2 fz[PMCIM_MAX_TERMS];
-  int piv_sh;
-  int info_sh;
-};
-
-__device__ __forceinline__ void warp_argmax(double& v, int& i) {
-  for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_down_sync(0xffffffffu, v, o);
-    int oi = __shfl_down_sync(0xffffffffu, i, o);
-    if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
-  }
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double2 warp_sum2(double2 v) {
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
-  }
-  return v;
-}
-
-// Deterministic block sum (fixed tree); every thread gets the result.
-__device__ double block_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int k = 0; k < THREADS / 32; ++k) t += red[k];
-  return t;
-}
-
-// Block sum of a complex value; every thread gets the result.
-__device__ double2 block_sum2(double2 v, double2* red2) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  v = warp_sum2(v);
-  __syncthreads();
-  if (lane == 0) red2[wid] = v;
-  __syncthreads();
-  double2 t = make_double2(0.0, 0.0);
-  for (int k = 0; k < THREADS / 32; ++k) t = cadd(t, red2[k]);
-  return t;
-}
-
-// ---------------------------------------------------------------------------
-// Blocked right-looking LU of the n x n leading block of M (column-major,
-// leading dimension n, ncols >= n columns; columns n..ncols-1 receive the same
-// row swaps and elimination). piv[k] = row swapped with row k at step k.
-// Returns 0, or 1 + the first column whose pivot was exactly zero.
-// ---------------------------------------------------------------------------
-__device__ int cta_lu(double2* __restrict__ M, int n, int ncols, int* __restrict__ piv, LuSmem& sm) {
-  const int tid = threadIdx.x;
-  const size_t ld = (size_t)n;
-  if (tid == 0) sm.info_sh = 0;
-  __syncthreads();
-
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int kb = min(NB, n - k0);
-    const int kend = k0 + kb;
-
-    // ---- panel factorisation, columns k0..kend-1 ----
-    for (int j = k0; j < kend; ++j) {
-      double2* colj = M + (size_t)j * ld;
-      double bv = -1.0;
-      int bi = n;
-      for (int i = j + tid; i < n; i += THREADS) {
-        double v = l1abs(colj[i]);
-        if (v > bv) { bv = v; bi = i; }
-      }
-      warp_argmax(bv, bi);
-      if ((tid & 31) == 0) { sm.red_v[tid >> 5] = bv; sm.red_i[tid >> 5] = bi; }
-      __syncthreads();
-      if (tid == 0) {
-        double v = sm.red_v[0];
-        int ii = sm.red_i[0];
-        for (int w = 1; w < THREADS / 32; ++w) {
-          if (sm.red_v[w] > v || (sm.red_v[w] == v && sm.red_i[w] < ii)) { v = sm.red_v[w]; ii = sm.red_i[w]; }
-        }
-        if (ii >= n) ii = j;
-        sm.piv_sh = ii;
-        piv[j] = ii;
-      }
-      __syncthreads();
-      const int p = sm.piv_sh;
-      if (p != j) {
-        for (int c = tid; c < ncols; c += THREADS) {
-          double2* cc = M + (size_t)c * ld;
-          double2 t = cc[j];
-          cc[j] = cc[p];
-          cc[p] = t;
-        }
-      }
-      __syncthreads();
-      for (int c = j + 1 + tid; c < kend; c += THREADS) sm.prow[c - k0] = M[(size_t)c * ld + j];
-      const double2 pv = colj[j];
-      const bool zero = (pv.x == 0.0 && pv.y == 0.0);
-      if (zero && tid == 0 && sm.info_sh == 0) sm.info_sh = j + 1;
-      __syncthreads();
-      if (!zero) {
-        const double2 rp = crecip(pv);
-        for (int i = j + 1 + tid; i < n; i += THREADS) {
-          double2 lij = cmul(colj[i], rp);
-          colj[i] = lij;
-          for (int c = j + 1; c < kend; ++c) cfms(M[(size_t)c * ld + i], lij, sm.prow[c - k0]);
-        }
-      }
-      __syncthreads();
-    }
-
-    if (kend >= ncols) continue;
-
-    // ---- U12 = L11^{-1} A12 (rows k0..kend-1, columns kend..ncols-1) ----
-    for (int e = tid; e < kb * kb; e += THREADS) {
-      int r = e % kb, c = e / kb;
-      sm.Ls[c * NB + r] = M[(size_t)(k0 + c) * ld + k0 + r];  // Ls[t*NB + i] = L11[i][t]
-    }
-    __syncthreads();
-    {
-      // one warp per column, lane i holds row k0+i (NB == warp size)
-      const int lane = tid & 31, wid = tid >> 5;
-      for (int c = kend + wid; c < ncols; c += THREADS / 32) {
-        double2* cc = M + (size_t)c * ld + k0;
-        double2 x = (lane < kb) ? cc[lane] : make_double2(0.0, 0.0);
-        for (int t = 0; t < kb - 1; ++t) {
-          double2 xt;
-          xt.x = __shfl_sync(0xffffffffu, x.x, t);
-          xt.y = __shfl_sync(0xffffffffu, x.y, t);
-          if (lane > t && lane < kb) cfms(x, sm.Ls[t * NB + lane], xt);
-        }
-        if (lane < kb) cc[lane] = x;
-      }
-    }
-    __syncthreads();
-
-    if (kend >= n) continue;
-
-    // ---- trailing update A22 -= L21 U12 over TILE x TILE tiles ----
-    const int m_rows = n - kend, m_cols = ncols - kend;
-    const int mt = (m_rows + TILE - 1) / TILE, nt = (m_cols + TILE - 1) / TILE;
-    const int tx = tid & 15, ty = tid >> 4;
-    for (int ti = 0; ti < mt; ++ti) {
-      const int r0 = kend + ti * TILE;
-      for (int e = tid; e < NB * TILE; e += THREADS) {
-        int r = e % TILE, kk = e / TILE;
-        double2 v = make_double2(0.0, 0.0);
-        if (kk < kb && r0 + r < n) v = M[(size_t)(k0 + kk) * ld + r0 + r];
-        sm.Ls[kk * TILE + r] = v;
-      }
-      for (int tj = 0; tj < nt; ++tj) {
-        const int c0 = kend + tj * TILE;
-        for (int e = tid; e < NB * TILE; e += THREADS) {
-          int kk = e % NB, c = e / NB;
-          double2 v = make_double2(0.0, 0.0);
-          if (kk < kb && c0 + c < ncols) v = M[(size_t)(c0 + c) * ld + k0 + kk];
-          sm.Us[kk * US_LD + c] = v;
-        }
-        __syncthreads();
-        double2 acc[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            int r = r0 + tx + 16 * i, c = c0 + ty + 16 * q;
-            acc[i][q] = (r < n && c < ncols) ? M[(size_t)c * ld + r] : make_double2(0.0, 0.0);
-          }
-        for (int kk = 0; kk < kb; ++kk) {
-          double2 a[4], b[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = sm.Ls[kk * TILE + tx + 16 * i];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) b[q] = sm.Us[kk * US_LD + ty + 16 * q];
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) cfms(acc[i][q], a[i], b[q]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            int r = r0 + tx + 16 * i, c = c0 + ty + 16 * q;
-            if (r < n && c < ncols) M[(size_t)c * ld + r] = acc[i][q];
-          }
-        __syncthreads();
-      }
-    }
-  }
-  __syncthreads();
-  return sm.info_sh;
-}
-
-// Back substitution U X = Y for the l columns n..n+l-1 of M, in place.
-__device__ void cta_back_subst(double2* __restrict__ M, int n, int l, LuSmem& sm) {
-  const int tid = threadIdx.x;
-  const size_t ld = (size_t)n;
-  double2* Y = M + (size_t)n * ld;
-  for (int j = n - 1; j >= 0; --j) {
-    if (tid < l) {
-      double2 x = cdiv(Y[(size_t)tid * ld + j], M[(size_t)j * ld + j]);
-      Y[(size_t)tid * ld + j] = x;
-      sm.bcast[tid] = x;
-    }
-    __syncthreads();
-    const double2* uj = M + (size_t)j * ld;
-    for (int i = tid; i < j; i += THREADS) {
-      const double2 u = uj[i];
-      for (int c = 0; c < l; ++c) cfms(Y[(size_t)c * ld + i], u, sm.bcast[c]);
-    }
-    __syncthreads();
-  }
-}
+using namespace lucore;
 
 // ---------------------------------------------------------------------------
 // Persistent kernel: node g -> X_g = T(z_g)^{-1} V.

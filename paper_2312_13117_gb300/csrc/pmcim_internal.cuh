@@ -66,6 +66,41 @@ __host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 }
 __device__ __forceinline__ double l1abs(double2 a) { return fabs(a.x) + fabs(a.y); }
 
+// float2 counterparts used by the FP32 factorisation
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ void cfms(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(-a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(-a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ float2 crecip(float2 b) {
+  if (fabsf(b.x) >= fabsf(b.y)) {
+    float t = b.y / b.x, d = b.x + b.y * t;
+    return make_float2(1.0f / d, -t / d);
+  } else {
+    float t = b.x / b.y, d = b.x * t + b.y;
+    return make_float2(t / d, -1.0f / d);
+  }
+}
+__host__ __device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
+  if (fabsf(b.x) >= fabsf(b.y)) {
+    float t = b.y / b.x, d = b.x + b.y * t;
+    return make_float2((a.x + a.y * t) / d, (a.y - a.x * t) / d);
+  } else {
+    float t = b.x / b.y, d = b.x * t + b.y;
+    return make_float2((a.x * t + a.y) / d, (a.y * t - a.x) / d);
+  }
+}
+__device__ __forceinline__ double l1abs(float2 a) { return (double)(fabsf(a.x) + fabsf(a.y)); }
+template <typename T2> __device__ __forceinline__ T2 czero();
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.0f, 0.0f); }
+__device__ __forceinline__ bool cis_zero(double2 a) { return a.x == 0.0 && a.y == 0.0; }
+__device__ __forceinline__ bool cis_zero(float2 a) { return a.x == 0.0f && a.y == 0.0f; }
+
 // ---------------------------------------------------------------------------
 // Problem description as the kernels see it.
 // ---------------------------------------------------------------------------
@@ -136,6 +171,32 @@ struct FactorArgs {
 cudaError_t launch_factor_solve_fp64(const FactorArgs& a, cudaStream_t s);
 int factor_slots_fp64(int n, int l);
 size_t factor_smem_fp64();
+
+struct MixedArgs {
+  ProblemDesc prob;
+  const double2* A;
+  const double2* V;
+  int l;
+  const RegionDev* regions;
+  const int32_t* node_region;
+  int n_nodes;
+  double2* X;               // FP64 solutions, n_nodes * n * l
+  int32_t* node_info;       // bits 0-23: 0 or 1 + zero-pivot column; 24-29: sweeps; 30: FP64 fallback
+  char* work;               // slots * slot_bytes
+  size_t slot_bytes;
+  int32_t* piv;             // slots * n
+  int slots;
+  int max_sweeps;
+  double tol_ir;
+  unsigned long long* phase;  // NULL, or slots * PMCIM_PHASES clock64 counters
+};
+// Phases of the precision-form node kernel timed with clock64 when profiling.
+#define PMCIM_PHASES 8  // assemble, LU, first solve, residual, correction solve, fallback, other
+__host__ __device__ inline size_t mixed_residual_offset(int n, int l) {
+  return (((size_t)n * (n + l) * 8) + 255) & ~(size_t)255;
+}
+size_t mixed_slot_bytes(int n, int l);
+cudaError_t launch_factor_solve_mixed(const MixedArgs& a, cudaStream_t s);
 
 struct ReduceArgs {
   const double2* X;

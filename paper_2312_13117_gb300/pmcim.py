@@ -49,13 +49,13 @@ class pmcim_options(C.Structure):
 
 
 class pmcim_profile(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8)]
+    _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8), ("mixed_phase_cycles", C.c_double * 8)]
 
 
 class pmcim_stats(C.Structure):
     _fields_ = [("solves", C.c_int64), ("regions", C.c_int32), ("candidates", C.c_int32),
                 ("splits", C.c_int32), ("unverified", C.c_int32), ("ir_fallbacks", C.c_int32),
-                ("singular_nodes", C.c_int32)]
+                ("singular_nodes", C.c_int32), ("ir_sweeps", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -148,7 +148,14 @@ def pmcim_profile_reset():
 def pmcim_profile_read() -> dict:
     pr = pmcim_profile()
     load().pmcim_profile_read(C.byref(pr))
-    return {k: {"launches": int(pr.launches[i]), "ms": float(pr.ms[i])} for i, k in enumerate(KERNELS)}
+    out = {k: {"launches": int(pr.launches[i]), "ms": float(pr.ms[i])} for i, k in enumerate(KERNELS)}
+    cyc = [float(x) for x in pr.mixed_phase_cycles]
+    tot = sum(cyc)
+    if tot > 0:
+        names = ["assemble", "lu_fp32", "first_solve", "residual_fp64", "correction_solve", "fp64_fallback",
+                 "node_setup", "unused"]
+        out["factor_fp32"]["phase_share"] = {nm: c / tot for nm, c in zip(names, cyc) if c > 0}
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -299,3 +299,84 @@ def test_full_size_delay_sampled_regions(pm):
     W = w.delay_large()
     regs = [W.regions[300], W.regions[517]]
     _check_moments(pm, W.problem, regs, W.V)
+
+
+# ---------------------------------------------------------------------------
+# a5: precision form (FP32 LU + FP64 refinement) against the FP64 oracle
+# ---------------------------------------------------------------------------
+
+def _mixed_opt(pm, **kw):
+    return pm.options(precision=pm.PREC_FP32_IR, **kw)
+
+
+def test_mixed_moments_close_to_oracle(pm):
+    """Refined solutions: |dX| <= 1e-9 |X| per node is the contract of the refinement stop."""
+    W = w.quadratic_small(seed=2, n=72, l=6, N=16)
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    C0, C1, _, _ = P.moments(W.regions[:6], W.V, opt=_mixed_opt(pm))
+    for g, reg in enumerate(W.regions[:6]):
+        m = o.moments(W.problem, reg.c, reg.r, reg.N, W.V)
+        z, wts = o.nodes_weights(reg.c, reg.r, reg.N)
+        X = o.solve_nodes(W.problem, z, W.V)
+        scale = sum(abs(wts[j]) * np.linalg.norm(X[j]) for j in range(reg.N))
+        b0, b1, _ = _moment_bound(W.problem, reg, W.V)
+        assert np.linalg.norm(C0[g] - m.C0) <= b0 + 1e-9 * scale
+        assert np.linalg.norm(C1[g] - m.C1) <= b1 + 1e-9 * scale * (abs(reg.c) + reg.r)
+    P.close()
+
+
+def test_mixed_solve_quadratic_n64(pm):
+    W = w.quadratic_small()
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    res = P.solve(W.regions, W.V, opt=_mixed_opt(pm))
+    ref = o.pmcimb(W.problem, W.regions, W.V)
+    assert _match_lam(res["lam"], ref.lam) <= LAM_TOL
+    assert res["stats"]["ir_sweeps"] >= res["stats"]["solves"]
+    P.close()
+
+
+def test_mixed_solve_delay_small(pm):
+    W = w.delay_large(n=64, l=8, N=32, nx=4, ny=12)
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    res = P.solve(W.regions, W.V, opt=_mixed_opt(pm))
+    ref = o.pmcimb(W.problem, W.regions, W.V)
+    assert _match_lam(res["lam"], ref.lam) <= LAM_TOL
+    P.close()
+
+
+def test_mixed_fallback_path(pm):
+    """An eigenvalue 1e-7 from node 0 makes T(z_0) too ill-conditioned for FP32 (kappa u32 ~ 1):
+    refinement cannot converge there, so that node is re-solved in FP64 and flagged; the
+    moments still agree with the FP64 form."""
+    rng = np.random.default_rng(77)
+    c, r, N, n = 0.0, 1.0, 16, 24
+    a = np.concatenate([rng.uniform(0.2, 0.7, 8), rng.uniform(1.4, 3.0, n - 9)]) * np.exp(2j * np.pi * rng.random(n - 1))
+    mu = np.concatenate([[c + r * (1.0 + 1e-7)], c + r * a])   # node 0 is z_0 = c + r
+    prob, _ = w.similarity_linear(mu, seed=5)
+    V = w.probe_block(rng, n, 4)
+    reg = [w.Region(c, r, N)]
+    P = pm.Problem(n, prob.terms)
+    res = P.solve(reg, V, opt=_mixed_opt(pm))
+    assert res["stats"]["ir_fallbacks"] >= 1
+    assert res["status"][0] & pm.RS_IR_FALLBACK
+    Cm0, Cm1, _, _ = P.moments(reg, V, opt=_mixed_opt(pm))
+    Cd0, Cd1, _, _ = P.moments(reg, V)
+    z, wts = o.nodes_weights(c, r, N)
+    X = o.solve_nodes(prob, z, V)
+    scale = sum(abs(wts[j]) * np.linalg.norm(X[j]) for j in range(1, N))
+    assert np.linalg.norm(Cm0[0] - Cd0[0]) <= 1e-9 * scale
+    assert np.linalg.norm(Cm1[0] - Cd1[0]) <= 1e-9 * scale * 2.0
+    P.close()
+
+
+def test_mixed_full_size_delay_sampled(pm):
+    """n = 1024 delay problem: eigenvalues of two disks through the precision form."""
+    W = w.delay_large()
+    regs = [W.regions[300], W.regions[517]]
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    res = P.solve(regs, W.V, opt=_mixed_opt(pm))
+    ref = o.pmcimb(W.problem, regs, W.V)
+    assert len(ref.lam) >= 2
+    assert _match_lam(res["lam"], ref.lam) <= LAM_TOL
+    assert res["stats"]["ir_fallbacks"] == 0
+    P.close()

@@ -252,6 +252,7 @@ def main():
     ap.add_argument("--cpu-sample-regions", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the precision-form measurement")
+    ap.add_argument("--only-mixed", action="store_true", help="time only the precision form (profiling runs)")
     ap.add_argument("--full", action="store_true",
                     help="time pmCIMb over all 768 disks (time to all eigenvalues), FP64 and precision form")
     args = ap.parse_args()
@@ -314,6 +315,14 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
+    if args.only_mixed:
+        tm_ms, msolves, mfound, aggm, profm = timed(opt_mixed, args.steps, args.warmup)
+        clk = clocks.stop()
+        if rank == 0:
+            print(json.dumps({"form": "precision", "solves_per_s": msolves / (tm_ms / 1e3), "ms": tm_ms,
+                              "stats": aggm, "kernels": profm, "clocks": clk}))
+        P.close()
+        return 0
     t_ms, solves, found, agg64, prof = timed(opt, args.steps, args.warmup)
     mixed = None
     if not args.no_mixed:

@@ -99,6 +99,8 @@ typedef struct {
   int32_t ir_fallbacks;    /* nodes re-solved in FP64 after refinement stalled  */
   int32_t singular_nodes;  /* nodes whose LU met an exactly zero pivot           */
   int64_t ir_sweeps;       /* refinement sweeps summed over nodes (FP32_IR)      */
+  int32_t certified;       /* values accepted by the eigenvector certificate     */
+  int32_t reserved;
 } pmcim_stats;
 
 typedef struct pmcim_problem_s* pmcim_problem;
@@ -158,7 +160,13 @@ int pmcim_verify(pmcim_problem p, const pmcim_options* opt, int32_t m, const dou
    indicator and the moments: one LU per node serves both. Outputs the verified
    eigenvalues (sorted by real, then imaginary part) with eigenvectors (may be
    NULL), sigma_min and source disk; ind[R] and region_status[R] may be NULL;
-   stats may be NULL. ECAPACITY if more than cap values are verified. */
+   stats may be NULL. ECAPACITY if more than cap values are verified.
+   Verification first evaluates, in FP64, the certificate ||T(lambda) v|| of
+   the unit eigenvector v from Beyn's step; since sigma_min <= ||T(lambda) v||,
+   a value whose certificate is already below the acceptance threshold is
+   accepted, and sigma_min[i] then holds that certificate (an upper bound of
+   the smallest singular value). Every other value gets the full sigma_min of
+   pmcim_verify. Accept/reject decisions equal those of the sigma_min rule. */
 int pmcim_solve(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim_region* reg,
                 int32_t l, const double* V, int32_t cap, double* lambda, double* vecs,
                 double* sigma_min, int32_t* region_of, int32_t* count, double* ind,

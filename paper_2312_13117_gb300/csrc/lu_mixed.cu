@@ -24,12 +24,16 @@ namespace {
 
 using namespace lucore;
 
-constexpr int RT_ROWS = 64;  // residual tile rows
-constexpr int RT_K = 32;     // residual tile depth
+// Residual tiles: 256 rows x 16 columns per pass, depth 16; thread (tx, ty) owns
+// rows tx + 64 i and columns ty + 4 q (i, q < 4) of the tile: a 4 x 4 complex
+// register block, the same shape as the LU's trailing update.
+constexpr int RT_ROWS = 256;
+constexpr int RT_COLS = 16;
+constexpr int RT_K = 16;
 
 struct ResSmem {
-  double2 As[RT_K * RT_ROWS];     // A_k tile [kk][row]
-  double2 Xs[RT_K * PMCIM_MAX_L]; // f_k X tile [kk][col]
+  double2 As[RT_K * RT_ROWS];   // A_k tile [kk][row]
+  double2 Xs[RT_K * RT_COLS];   // f_k X tile [kk][col]
 };
 
 union MixedSmemU {
@@ -61,59 +65,67 @@ __device__ void residual_fp64(const MixedArgs& a, const double2* __restrict__ X,
   const int n = P.n, l = a.l;
   const int tid = threadIdx.x;
   const size_t nn = (size_t)n * n;
-  const int row_l = tid % RT_ROWS;        // row within the tile
-  const int cgrp = tid / RT_ROWS;         // 4 column groups
+  const int tx = tid & 63, ty = tid >> 6;
   ResSmem& rs = sm.u.res;
-  for (int r0 = 0; r0 < n; r0 += RT_ROWS) {
-    const int row = r0 + row_l;
-    double2 acc[PMCIM_MAX_L / 4];
+  double2 idsum = make_double2(0.0, 0.0);  // sum of identity-term coefficients f_k id_k
+  for (int k = 0; k < P.K; ++k)
+    if (!P.term[k].dense) idsum = cadd(idsum, cmul(sm.fz[k], P.term[k].id));
+  for (int c0 = 0; c0 < l; c0 += RT_COLS) {
+    for (int r0 = 0; r0 < n; r0 += RT_ROWS) {
+      double2 acc[4][4];
 #pragma unroll
-    for (int q = 0; q < PMCIM_MAX_L / 4; ++q) {
-      const int c = cgrp + 4 * q;
-      double2 v = make_double2(0.0, 0.0);
-      if (c < l && row < n) {
-        v = a.V[(size_t)c * n + row];
-        const double2 x = X[(size_t)c * n + row];
-        for (int k = 0; k < P.K; ++k)
-          if (!P.term[k].dense) cfms(v, cmul(sm.fz[k], P.term[k].id), x);
-      }
-      acc[q] = v;
-    }
-    for (int k = 0; k < P.K; ++k) {
-      const TermDesc& t = P.term[k];
-      if (!t.dense) continue;
-      const double2* Ak = a.A + (size_t)t.mat_index * nn;
-      const double2 fk = sm.fz[k];
-      for (int k0 = 0; k0 < n; k0 += RT_K) {
-        __syncthreads();
-        for (int e = tid; e < RT_K * RT_ROWS; e += THREADS) {
-          const int r = e % RT_ROWS, kk = e / RT_ROWS;
-          double2 v = make_double2(0.0, 0.0);
-          if (r0 + r < n && k0 + kk < n) v = Ak[(size_t)(k0 + kk) * n + r0 + r];
-          rs.As[kk * RT_ROWS + r] = v;
-        }
-        for (int e = tid; e < RT_K * l; e += THREADS) {
-          const int kk = e % RT_K, c = e / RT_K;
-          double2 v = make_double2(0.0, 0.0);
-          if (k0 + kk < n) v = cmul(fk, X[(size_t)c * n + k0 + kk]);
-          rs.Xs[kk * PMCIM_MAX_L + c] = v;
-        }
-        __syncthreads();
-        const int kmax = min(RT_K, n - k0);
-        for (int kk = 0; kk < kmax; ++kk) {
-          const double2 av = rs.As[kk * RT_ROWS + row_l];
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int q = 0; q < PMCIM_MAX_L / 4; ++q) {
-            const int c = cgrp + 4 * q;
-            if (c < l) cfms(acc[q], av, rs.Xs[kk * PMCIM_MAX_L + c]);
+        for (int q = 0; q < 4; ++q) {
+          const int row = r0 + tx + 64 * i, c = c0 + ty + 4 * q;
+          double2 v = make_double2(0.0, 0.0);
+          if (row < n && c < l) {
+            v = a.V[(size_t)c * n + row];
+            cfms(v, idsum, X[(size_t)c * n + row]);
+          }
+          acc[i][q] = v;
+        }
+      for (int k = 0; k < P.K; ++k) {
+        const TermDesc& t = P.term[k];
+        if (!t.dense) continue;
+        const double2* Ak = a.A + (size_t)t.mat_index * nn;
+        const double2 fk = sm.fz[k];
+        for (int k0 = 0; k0 < n; k0 += RT_K) {
+          __syncthreads();
+          for (int e = tid; e < RT_K * RT_ROWS; e += THREADS) {
+            const int r = e % RT_ROWS, kk = e / RT_ROWS;
+            double2 v = make_double2(0.0, 0.0);
+            if (r0 + r < n && k0 + kk < n) v = Ak[(size_t)(k0 + kk) * n + r0 + r];
+            rs.As[kk * RT_ROWS + r] = v;
+          }
+          {
+            const int kk = tid % RT_K, c = tid / RT_K;  // 256 threads = 16 x 16
+            double2 v = make_double2(0.0, 0.0);
+            if (k0 + kk < n && c0 + c < l) v = cmul(fk, X[(size_t)(c0 + c) * n + k0 + kk]);
+            rs.Xs[kk * RT_COLS + c] = v;
+          }
+          __syncthreads();
+#pragma unroll 4
+          for (int kk = 0; kk < RT_K; ++kk) {
+            double2 av[4], xv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = rs.As[kk * RT_ROWS + tx + 64 * i];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) xv[q] = rs.Xs[kk * RT_COLS + ty + 4 * q];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) cfms(acc[i][q], av[i], xv[q]);
           }
         }
       }
-    }
 #pragma unroll
-    for (int q = 0; q < PMCIM_MAX_L / 4; ++q) {
-      const int c = cgrp + 4 * q;
-      if (c < l && row < n) R[(size_t)c * n + row] = acc[q];
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int row = r0 + tx + 64 * i, c = c0 + ty + 4 * q;
+          if (row < n && c < l) R[(size_t)c * n + row] = acc[i][q];
+        }
     }
   }
   __syncthreads();

@@ -256,6 +256,18 @@ struct VerifyArgs {
 cudaError_t launch_verify_fp64(const VerifyArgs& a, cudaStream_t s);
 int verify_slots_fp64(int n);
 
+struct CertifyArgs {
+  ProblemDesc prob;
+  const double2* A;
+  const double2* lam;        // m
+  const double2* vecs;       // m * n, unit eigenvectors
+  int m;
+  double tol_verify;
+  double* cert;              // m: ||T(lambda) v|| / ||v||
+  uint8_t* certified;        // m: cert <= tol_verify * max(1, ||T||_F / sqrt(n))
+};
+cudaError_t launch_certify(const CertifyArgs& a, cudaStream_t s);
+
 struct GatherArgs {
   const double2* vecs;       // m * n * l (beyn outputs)
   const int32_t* src;        // count: cand * l + k

@@ -85,7 +85,59 @@ __global__ void k_gather_vecs(GatherArgs a) {
   a.dst[(size_t)k * a.n + i] = a.vecs[((size_t)cand * a.l + col) * a.n + i];
 }
 
+// Verification certificate (pmCIMb step 3): for a candidate lambda with unit
+// eigenvector v, sigma_min(T(lambda)) <= ||T(lambda) v||. One CTA per value
+// forms T(lambda) one column at a time (never stored), accumulating
+// r = T(lambda) v and ||T(lambda)||_F^2, all in FP64.
+__global__ void __launch_bounds__(RT) k_certify(CertifyArgs a) {
+  __shared__ double2 fz[PMCIM_MAX_TERMS];
+  __shared__ double red[2][RT / 32];
+  const ProblemDesc& P = a.prob;
+  const int n = P.n;
+  const size_t nn = (size_t)n * n;
+  const int m = blockIdx.x;
+  const double2 lam = a.lam[m];
+  const double2* v = a.vecs + (size_t)m * n;
+  if (threadIdx.x < P.K) fz[threadIdx.x] = eval_f(P.term[threadIdx.x], lam);
+  __syncthreads();
+  double r2 = 0.0, f2 = 0.0;
+  for (int row = threadIdx.x; row < n; row += RT) {
+    double2 r = make_double2(0.0, 0.0);
+    for (int col = 0; col < n; ++col) {
+      double2 t = make_double2(0.0, 0.0);
+      for (int k = 0; k < P.K; ++k) {
+        const TermDesc& tk = P.term[k];
+        if (tk.dense) cfma(t, fz[k], a.A[(size_t)tk.mat_index * nn + (size_t)col * n + row]);
+        else if (row == col) cfma(t, fz[k], tk.id);
+      }
+      cfma(r, t, v[col]);
+      f2 += cabs2(t);
+    }
+    r2 += cabs2(r);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    r2 += __shfl_down_sync(0xffffffffu, r2, o);
+    f2 += __shfl_down_sync(0xffffffffu, f2, o);
+  }
+  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = r2; red[1][threadIdx.x >> 5] = f2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0, tf = 0.0, vv = 0.0;
+    for (int k = 0; k < RT / 32; ++k) { tr += red[0][k]; tf += red[1][k]; }
+    for (int i = 0; i < n; ++i) vv += cabs2(v[i]);
+    const double cert = sqrt(tr) / sqrt(vv);
+    a.cert[m] = cert;
+    a.certified[m] = (cert <= a.tol_verify * fmax(1.0, sqrt(tf) / sqrt((double)n))) ? 1 : 0;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_certify(const CertifyArgs& a, cudaStream_t s) {
+  if (a.m <= 0) return cudaSuccess;
+  k_certify<<<a.m, RT, 0, s>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_reduce_moments(const ReduceArgs& a, cudaStream_t s) {
   if (a.R <= 0) return cudaSuccess;

@@ -55,7 +55,8 @@ class pmcim_profile(C.Structure):
 class pmcim_stats(C.Structure):
     _fields_ = [("solves", C.c_int64), ("regions", C.c_int32), ("candidates", C.c_int32),
                 ("splits", C.c_int32), ("unverified", C.c_int32), ("ir_fallbacks", C.c_int32),
-                ("singular_nodes", C.c_int32), ("ir_sweeps", C.c_int64)]
+                ("singular_nodes", C.c_int32), ("ir_sweeps", C.c_int64), ("certified", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -259,10 +259,15 @@ def test_solve_quadratic_n64_all_eigenvalues(pm):
     assert len(res["lam"]) == 114
     assert res["stats"]["splits"] == sum(r.split for r in ref.records)
     assert res["stats"]["regions"] == len(ref.records)
+    assert res["stats"]["certified"] + res["stats"]["unverified"] >= 1
     for k in range(len(res["lam"])):
         v = res["vecs"][:, k]
         T = o.assemble_T(W.problem, res["lam"][k])
         assert np.linalg.norm(T @ v) <= 1e-6 * np.linalg.norm(T)
+        # the reported value is sigma_min or a certificate ||T v|| >= sigma_min, below the threshold
+        s_ref, fro = o.sigma_min(W.problem, res["lam"][k])
+        assert res["sigma_min"][k] >= s_ref - 1e-14 * fro
+        assert res["sigma_min"][k] <= 1e-6 * max(1.0, fro / math.sqrt(W.problem.n))
 
 
 def test_solve_paper_example(pm):

@@ -206,6 +206,87 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def run_batched(args, world, rank, local):
+    """Many independent quadratic problems of uneven size (n ~ U{32..768}) per step.
+
+    One step solves a slice of the 512 seeded problems with pmcim_batch_solve
+    (one level = one CUDA graph, one persistent launch per form). Reported for
+    the autotuned precision, for FP64 and the precision form forced, and for
+    the same problems solved one call each (no batching)."""
+    import torch
+    from paper_2312_13117_gb300 import pmcim
+    import workloads as w
+    per = args.problems_per_step
+    total = 512
+
+    def seeds(step):
+        base = ((step * world + rank) * per) % total
+        return [1 + (base + i) % total for i in range(per)]
+
+    def make(step):
+        W = w.batched_quadratics(seeds(step))
+        return [pmcim.Problem(x.problem.n, x.problem.terms) for x in W], W
+
+    steps = list(range(-args.warmup, args.steps))
+    prepared = {k: make(k) for k in steps}          # coefficients resident before timing
+    stream = torch.cuda.current_stream()
+    res = {}
+    forms = [("auto", pmcim.PREC_AUTO), ("fp32ir", pmcim.PREC_FP32_IR), ("unbatched_auto", pmcim.PREC_AUTO)]
+    if args.batched_fp64:
+        forms.append(("fp64", pmcim.PREC_FP64))
+    t_start = time.perf_counter()
+    for name, prec in forms:
+        if time.perf_counter() - t_start > args.time_budget:
+            sys.stderr.write("skipping %s: time budget spent\n" % name)
+            continue
+        o = pmcim.options(stream=stream.cuda_stream, precision=prec)
+        agg = {}
+        t_ms = 0.0
+        for k in steps:
+            hs, W = prepared[k]
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if name.startswith("unbatched"):
+                st = {}
+                for h, x in zip(hs, W):
+                    r = h.solve(x.regions, x.V, opt=o, want_vecs=False)
+                    for key, v in r["stats"].items():
+                        st[key] = st.get(key, 0) + v
+                found = None
+            else:
+                r = pmcim.batch_solve(hs, [x.regions for x in W], [x.V for x in W], opt=o)
+                st = r["stats"]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= 0:
+                t_ms += e0.elapsed_time(e1)
+                for key, v in st.items():
+                    agg[key] = agg.get(key, 0) + v
+        t_max = max_over_ranks(t_ms, world)
+        sys.stderr.write("%s: %.1f ms/step, %d solves, %d splits\n" % (name, t_max / args.steps, agg["solves"],
+                                                                     agg["splits"]))
+        res[name] = {"solves_per_s": sum_over_ranks(float(agg["solves"]), world) / (t_max / 1e3),
+                     "ms_per_step": t_max / args.steps, "solves": agg["solves"], "splits": agg["splits"],
+                     "graphs": agg["graphs"], "tuned_fp64": agg["tuned_fp64"], "tuned_mixed": agg["tuned_mixed"],
+                     "ir_fallbacks": agg["ir_fallbacks"]}
+    if rank == 0:
+        ns = [x.problem.n for k in steps if k >= 0 for x in prepared[k][1]]
+        print(json.dumps({"metric": "solves/s, batched quadratic NEPs", "value": res["auto"]["solves_per_s"],
+                          "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": True, "scaling": "weak", "dtype": "f64 (auto: FP64 or FP32+FP64 IR)",
+                          "data": "synthetic",
+                          "config": {"workload": "batched quadratic NEPs, seeds 1..512, %d problems per step" % per,
+                                     "n_range": [min(ns), max(ns)], "l": 8},
+                          "forms": res,
+                          "speedup_batched_vs_unbatched": (res["unbatched_auto"]["ms_per_step"] / res["auto"]["ms_per_step"]
+                                                           if "unbatched_auto" in res else None)}))
+    for k in steps:
+        for h in prepared[k][0]:
+            h.close()
+    return 0
+
+
 def run_full(args, P, W, opt, opt_mixed, world, rank, local):
     """Time to all eigenvalues: one pmCIMb pass over the whole grid per form."""
     import torch
@@ -253,6 +334,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the precision-form measurement")
     ap.add_argument("--only-mixed", action="store_true", help="time only the precision form (profiling runs)")
+    ap.add_argument("--workload", default="delay", choices=["delay", "batched"])
+    ap.add_argument("--problems-per-step", type=int, default=4)
+    ap.add_argument("--batched-fp64", action="store_true", help="also time the batched workload in plain FP64")
+    ap.add_argument("--time-budget", type=float, default=240.0, help="seconds before remaining legs are skipped")
     ap.add_argument("--full", action="store_true",
                     help="time pmCIMb over all 768 disks (time to all eigenvalues), FP64 and precision form")
     args = ap.parse_args()
@@ -266,6 +351,8 @@ def main():
         build.build()
     barrier(world)
     pmcim.load()
+    if args.workload == "batched":
+        return run_batched(args, world, rank, local)
     import workloads as w
 
     W = w.delay_large()

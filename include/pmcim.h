@@ -13,8 +13,11 @@
  *   - Every buffer argument may be a host pointer or a CUDA device pointer (the
  *     library uses unified addressing to tell them apart). The caller owns all
  *     buffers; no call keeps a caller pointer after it returns.
- *   - Calls are synchronous: on return all results are in the caller's buffers
- *     and the work queued on opt->cuda_stream has finished.
+ *   - Calls are synchronous: the library's work starts after everything queued
+ *     on opt->cuda_stream before the call, runs on a stream of the problem
+ *     handle's own (levels are launched as CUDA graphs, which the legacy
+ *     default stream cannot capture), and has finished when the call returns,
+ *     with all results in the caller's buffers.
  *   - Every call returns 0 (PMCIM_OK) or a negative PMCIM_E* code; the message
  *     of the last failure on the calling thread is pmcim_last_error(). Problems
  *     with one disk (a saturated rank test, an exactly singular node) never fail
@@ -75,8 +78,12 @@ typedef struct {
 
 /* Arithmetic of the LU factorisation (the solves are always refined to FP64
    accuracy when a reduced precision is chosen). */
-#define PMCIM_PREC_FP64 0   /* plain FP64 LU                                     */
-#define PMCIM_PREC_FP32_IR 1 /* FP32 LU + FP64 iterative refinement               */
+#define PMCIM_PREC_FP64 0    /* plain FP64 LU                                    */
+#define PMCIM_PREC_FP32_IR 1 /* FP32 LU + FP64 iterative refinement              */
+#define PMCIM_PREC_AUTO 2    /* per problem, whichever of the two solves nodes
+                                faster on this device, measured on first use for
+                                each (n bucket, l, dense-term count) and kept for
+                                the process; both meet the same accuracy         */
 
 typedef struct {
   double tol_ind;          /* indicator threshold, paper default 0.1 (Sec. 3.1)        */
@@ -86,7 +93,7 @@ typedef struct {
   int32_t max_ir_sweeps;   /* refinement sweeps for reduced precision (default 3)      */
   int32_t max_split_depth; /* splits of saturated disks (default 8)                    */
   int32_t reserved;
-  void* cuda_stream;       /* cudaStream_t to run on; NULL = legacy default stream     */
+  void* cuda_stream;       /* cudaStream_t the call is ordered after; NULL = default   */
 } pmcim_options;
 
 /* Statistics of one pmcim_solve call. */
@@ -100,7 +107,9 @@ typedef struct {
   int32_t singular_nodes;  /* nodes whose LU met an exactly zero pivot           */
   int64_t ir_sweeps;       /* refinement sweeps summed over nodes (FP32_IR)      */
   int32_t certified;       /* values accepted by the eigenvector certificate     */
-  int32_t reserved;
+  int32_t graphs;          /* CUDA graphs launched (one per level of disks)      */
+  int32_t tuned_fp64;      /* problems the autotuner ran in FP64                 */
+  int32_t tuned_mixed;     /* problems the autotuner ran in the precision form   */
 } pmcim_stats;
 
 typedef struct pmcim_problem_s* pmcim_problem;
@@ -171,6 +180,29 @@ int pmcim_solve(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmci
                 int32_t l, const double* V, int32_t cap, double* lambda, double* vecs,
                 double* sigma_min, int32_t* region_of, int32_t* count, double* ind,
                 int32_t* region_status, pmcim_stats* stats);
+
+/* One problem of a batch: its handle, disks and probe block (as in pmcim_solve). */
+typedef struct {
+  pmcim_problem problem;
+  int32_t R;
+  const pmcim_region* regions;
+  int32_t l;
+  const double* V;
+} pmcim_batch_item;
+
+/* pmCIMb (steps 1-3) for P independent problems of any sizes in one call: the
+   nodes of every disk of every problem form one work list per level, solved by
+   one persistent launch per arithmetic form (largest n first), and each level
+   is launched as one CUDA graph. Options apply to all problems; with
+   PMCIM_PREC_AUTO each problem gets the faster form for its size. Outputs the
+   verified eigenvalues of all problems sorted by (problem, Re, Im), with
+   sigma_min (as in pmcim_solve), the problem index and the index of the disk
+   within that problem's list; any of them may be NULL except lambda and count.
+   A handle may appear only once per batch; while the call runs, none of its
+   handles may be used by another thread. ECAPACITY if more than cap values. */
+int pmcim_batch_solve(int32_t P, const pmcim_batch_item* items, const pmcim_options* opt, int32_t cap,
+                      double* lambda, double* sigma_min, int32_t* problem_of, int32_t* region_of,
+                      int32_t* count, pmcim_stats* stats);
 
 const char* pmcim_status_string(int code);
 const char* pmcim_last_error(void);

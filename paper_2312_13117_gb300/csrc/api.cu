@@ -1,18 +1,24 @@
 // C ABI of libpmcim and the host-side driver of pmCIMb (Sec. 3.2).
 //
-// The driver turns a list of disks into a list of nodes (one linear system each),
-// runs the node solves in HBM-sized waves, reduces the solves per disk, gates
-// disks by the indicator, runs Beyn's extraction on candidates, splits saturated
-// disks into four children (pmCIMa's quadrisection geometry, Sec. 3.1) and
-// verifies the surviving values. All arithmetic of the method runs in the CUDA
-// kernels; the host only builds work lists, moves small results and sorts.
+// The driver turns lists of disks (of one or many problems) into levels of
+// work: every node of every disk of a level is one linear system. A level is
+// captured as one CUDA graph: per HBM wave, the node kernels (one persistent
+// launch per arithmetic form, work handed out largest-first) and the segmented
+// reduction; then the indicator and Beyn's extraction over all disks of the
+// level, gated on the device. The host reads the small per-disk results, splits
+// saturated disks into four children (pmCIMa's quadrisection geometry, Sec.
+// 3.1), and finally certifies or verifies the surviving values. All arithmetic
+// of the method runs in the CUDA kernels; the host only builds work lists,
+// moves small results and sorts.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "pmcim_internal.cuh"
@@ -31,21 +37,21 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
-#define CU(expr)                                                                              \
-  do {                                                                                        \
-    cudaError_t _e = (expr);                                                                  \
-    if (_e != cudaSuccess)                                                                    \
+#define CU(expr)                                                                                  \
+  do {                                                                                            \
+    cudaError_t _e = (expr);                                                                      \
+    if (_e != cudaSuccess)                                                                        \
       return fail(_e == cudaErrorMemoryAllocation ? PMCIM_ENOMEM : PMCIM_ECUDA, "%s: %s (%s:%d)", \
-                  #expr, cudaGetErrorString(_e), __FILE__, __LINE__);                         \
+                  #expr, cudaGetErrorString(_e), __FILE__, __LINE__);                             \
   } while (0)
 
-#define CHK(expr)               \
-  do {                          \
-    int _r = (expr);            \
+#define CHK(expr)                  \
+  do {                             \
+    int _r = (expr);               \
     if (_r != PMCIM_OK) return _r; \
   } while (0)
 
-// Growable device buffer owned by a problem handle.
+// Growable device buffer.
 struct DevBuf {
   void* p = nullptr;
   size_t cap = 0;
@@ -68,7 +74,10 @@ struct DevBuf {
     if (p && keep) {
       e = cudaMemcpyAsync(q, p, keep, cudaMemcpyDeviceToDevice, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) { cudaFree(q); return e; }
+      if (e != cudaSuccess) {
+        cudaFree(q);
+        return e;
+      }
     }
     if (p) cudaFree(p);
     p = q;
@@ -81,12 +90,14 @@ struct DevBuf {
     cap = 0;
   }
   template <typename T>
-  T* as() const { return reinterpret_cast<T*>(p); }
+  T* as() const {
+    return reinterpret_cast<T*>(p);
+  }
 };
 
-// Upper bound on the solution buffer of one wave (node solves kept before reduction).
-constexpr size_t kWaveBytes = size_t(4) << 30;
-// Upper bound on the per-CTA factorisation workspaces.
+// Upper bound on the node solutions kept before one reduction (one HBM wave).
+constexpr size_t kWaveBytes = size_t(16) << 30;
+// Upper bound on the per-CTA factorisation workspaces of one form.
 constexpr size_t kSlotBytes = size_t(24) << 30;
 // Refinement stops when the estimated remaining error of X (max norm) is below
 // this fraction of |X|: 1e-11 keeps Beyn's eigenvalues within about 1e-14 of
@@ -132,27 +143,13 @@ Prof& prof() {
 
 }  // namespace
 
-bool prof_on();
-void prof_add_phases(const unsigned long long* c, int slots);
-
-void prof_begin(int kind, cudaStream_t s) {
-  Prof& P = prof();
-  std::lock_guard<std::mutex> g(P.mu);
-  P.launches[kind] += 1;
-  if (!P.on) return;
-  cudaEvent_t e = P.get();
-  cudaEventRecord(e, s);
-  P.cur_begin[kind] = e;
-}
-
-void prof_end(int kind, cudaStream_t s) {
-  Prof& P = prof();
-  std::lock_guard<std::mutex> g(P.mu);
-  if (!P.on || !P.cur_begin[kind]) return;
-  cudaEvent_t e = P.get();
-  cudaEventRecord(e, s);
-  P.pending.push_back({kind, P.cur_begin[kind], e});
-  P.cur_begin[kind] = nullptr;
+// A timing event. Inside stream capture a plain record only orders streams;
+// the external flag makes it a real event-record node of the graph.
+void record_timing_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else cudaEventRecord(e, s);
 }
 
 bool prof_on() {
@@ -168,6 +165,26 @@ void prof_add_phases(const unsigned long long* c, int slots) {
     for (int q = 0; q < 8; ++q) P.phase[q] += (double)c[(size_t)b * 8 + q];
 }
 
+void prof_begin(int kind, cudaStream_t s) {
+  Prof& P = prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  P.launches[kind] += 1;
+  if (!P.on) return;
+  cudaEvent_t e = P.get();
+  record_timing_event(e, s);
+  P.cur_begin[kind] = e;
+}
+
+void prof_end(int kind, cudaStream_t s) {
+  Prof& P = prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  if (!P.on || !P.cur_begin[kind]) return;
+  cudaEvent_t e = P.get();
+  record_timing_event(e, s);
+  P.pending.push_back({kind, P.cur_begin[kind], e});
+  P.cur_begin[kind] = nullptr;
+}
+
 void prof_flush() {
   Prof& P = prof();
   std::lock_guard<std::mutex> g(P.mu);
@@ -181,17 +198,37 @@ void prof_flush() {
   P.pending.clear();
 }
 
+// Device workspaces, reused across calls on one handle.
+struct Workspace {
+  DevBuf probs, regions, items, counters, node_info, X;
+  DevBuf work64, piv64, work32, piv32, phase;
+  DevBuf C0, C1, pf_half, pf_abs, ind, pf_norm, pf_scale, cand;
+  DevBuf bwork, bsigma, bp, blam, bvecs, bkept, bstatus;
+  DevBuf vlam, vprob, voff, vsig, vacc, vwork, vvec, vpiv;
+  DevBuf gitems, gdst, gperm;
+  // the library's own stream: graphs cannot be captured on the legacy default stream
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ordered = nullptr;
+  void release() {
+    if (stream) cudaStreamDestroy(stream);
+    if (ordered) cudaEventDestroy(ordered);
+    stream = nullptr;
+    ordered = nullptr;
+    DevBuf* b[] = {&probs, &regions, &items, &counters, &node_info, &X, &work64, &piv64, &work32, &piv32,
+                   &phase, &C0, &C1, &pf_half, &pf_abs, &ind, &pf_norm, &pf_scale, &cand, &bwork, &bsigma,
+                   &bp, &blam, &bvecs, &bkept, &bstatus, &vlam, &vprob, &voff, &vsig, &vacc, &vwork,
+                   &vvec, &vpiv, &gitems, &gdst, &gperm};
+    for (DevBuf* x : b) x->release();
+  }
+};
+
 struct pmcim_problem_s {
-  int n = 0, K = 0;
-  ProblemDesc desc{};
+  int n = 0, K = 0, n_dense = 0;
+  TermDesc term[PMCIM_MAX_TERMS];
   double2* dA = nullptr;
   int device = 0;
-  // workspaces, reused across calls
-  DevBuf work, piv, X, node_info, regions, node_region, V;
-  DevBuf C0, C1, pf_half, pf_abs, ind, pf_norm, pf_scale, cand;
-  DevBuf bslot, bregion, bwork, bsigma, bp, blam, bvecs, bkept, bstatus;
-  DevBuf vlam, vsig, vacc, vwork, vvec, vpiv;
-  DevBuf gsrc, gdst, gperm, phase;
+  DevBuf V;  // probe block of the current call
+  Workspace ws;
 };
 
 namespace {
@@ -201,25 +238,44 @@ struct HostRegion {
   int N;
   int depth;
   int root;  // index of the caller's disk this one descends from
+  int prob;  // index of the problem (group) in the call
+};
+
+// Work of a call runs on the workspace's stream, ordered after everything the
+// caller queued on opt->cuda_stream before the call.
+int call_stream(Workspace& ws, const pmcim_options* opt, cudaStream_t* out) {
+  if (!ws.stream) CU(cudaStreamCreateWithFlags(&ws.stream, cudaStreamNonBlocking));
+  if (!ws.ordered) CU(cudaEventCreateWithFlags(&ws.ordered, cudaEventDisableTiming));
+  CU(cudaEventRecord(ws.ordered, reinterpret_cast<cudaStream_t>(opt->cuda_stream)));
+  CU(cudaStreamWaitEvent(ws.stream, ws.ordered, 0));
+  *out = ws.stream;
+  return PMCIM_OK;
+}
+
+// One problem of a call: handle, probe count, arithmetic form.
+struct Group {
+  pmcim_problem h;
+  int l;
+  int form;  // PMCIM_PREC_FP64 or PMCIM_PREC_FP32_IR
 };
 
 int check_options(const pmcim_options* opt) {
   if (!opt) return fail(PMCIM_EINVAL, "options pointer is NULL");
   if (!(opt->tol_ind >= 0.0) || !(opt->tol_svd >= 0.0) || !(opt->tol_verify >= 0.0))
     return fail(PMCIM_EINVAL, "tolerances must be non-negative");
-  if (opt->precision != PMCIM_PREC_FP64 && opt->precision != PMCIM_PREC_FP32_IR)
+  if (opt->precision != PMCIM_PREC_FP64 && opt->precision != PMCIM_PREC_FP32_IR &&
+      opt->precision != PMCIM_PREC_AUTO)
     return fail(PMCIM_EINVAL, "unknown precision %d", opt->precision);
   if (opt->max_split_depth < 0 || opt->max_split_depth > 30) return fail(PMCIM_EINVAL, "max_split_depth out of range");
-  if (opt->precision == PMCIM_PREC_FP32_IR && (opt->max_ir_sweeps < 1 || opt->max_ir_sweeps > 10))
+  if (opt->precision != PMCIM_PREC_FP64 && (opt->max_ir_sweeps < 1 || opt->max_ir_sweeps > 10))
     return fail(PMCIM_EINVAL, "max_ir_sweeps must be 1..10");
   return PMCIM_OK;
 }
 
-int check_regions(int R, const pmcim_region* reg, int l, int n) {
+int check_regions(int R, const pmcim_region* reg, int l) {
   if (R < 0) return fail(PMCIM_EINVAL, "negative region count");
   if (R > 0 && !reg) return fail(PMCIM_EINVAL, "regions pointer is NULL");
   if (l < 1 || l > PMCIM_MAX_L) return fail(PMCIM_EINVAL, "l = %d outside 1..%d", l, PMCIM_MAX_L);
-  (void)n;
   for (int g = 0; g < R; ++g) {
     if (reg[g].N < 2 || reg[g].N > 4096 || (reg[g].N & 1))
       return fail(PMCIM_EINVAL, "region %d: N = %d must be even, 2..4096", g, reg[g].N);
@@ -229,9 +285,6 @@ int check_regions(int R, const pmcim_region* reg, int l, int n) {
   return PMCIM_OK;
 }
 
-cudaStream_t stream_of(const pmcim_options* opt) { return reinterpret_cast<cudaStream_t>(opt->cuda_stream); }
-
-// Copy the probe block to the device once per call.
 int upload_V(pmcim_problem p, int l, const double* V, cudaStream_t s) {
   if (!V) return fail(PMCIM_EINVAL, "V is NULL");
   const size_t bytes = (size_t)p->n * l * sizeof(double2);
@@ -240,399 +293,596 @@ int upload_V(pmcim_problem p, int l, const double* V, cudaStream_t s) {
   return PMCIM_OK;
 }
 
-// Moments of every disk in `regs` into p->C0/C1/pf_half/pf_abs (region-major),
-// and per-disk singular-node flags into `singular` (host).
-int run_moments(pmcim_problem p, const pmcim_options* opt, const std::vector<HostRegion>& regs, int l,
-                std::vector<int>* singular, int64_t* solves, int* fallbacks = nullptr,
-                int64_t* sweeps = nullptr) {
-  cudaStream_t s = stream_of(opt);
-  const int n = p->n;
-  const int R = (int)regs.size();
-  const size_t nl = (size_t)n * l;
-  CU(p->C0.ensure(std::max<size_t>(1, R) * nl * sizeof(double2)));
-  CU(p->C1.ensure(std::max<size_t>(1, R) * nl * sizeof(double2)));
-  CU(p->pf_half.ensure(std::max<size_t>(1, R) * n * sizeof(double2)));
-  CU(p->pf_abs.ensure(std::max<size_t>(1, R) * n * sizeof(double)));
-  if (singular) singular->assign(R, 0);
-  if (R == 0) return PMCIM_OK;
+int num_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
 
-  const bool mixed = opt->precision == PMCIM_PREC_FP32_IR;
-  const size_t slot_bytes = mixed ? mixed_slot_bytes(n, l) : (size_t)n * (n + l) * sizeof(double2);
-  size_t total_nodes = 0;
-  for (const HostRegion& h : regs) total_nodes += (size_t)h.N;
-  const int slots = (int)std::max<size_t>(
-      1, std::min<size_t>(std::min<size_t>(factor_slots_fp64(n, l), kSlotBytes / slot_bytes), total_nodes));
-  CU(p->work.ensure((size_t)slots * slot_bytes));
-  CU(p->piv.ensure((size_t)slots * n * sizeof(int32_t)));
+// ===========================================================================
+// One call's view of its problems
+// ===========================================================================
+struct Call {
+  const pmcim_options* opt;
+  cudaStream_t s;
+  Workspace* ws;
+  std::vector<Group> groups;
+  std::vector<ProblemDev> pd;  // host copy of the device problem table
+  pmcim_stats st{};
+};
 
-  // waves of whole disks whose solutions fit the wave buffer
-  const size_t per_node = nl * sizeof(double2);
-  int g0 = 0;
+int upload_problems(Call& c) {
+  c.pd.resize(c.groups.size());
+  for (size_t i = 0; i < c.groups.size(); ++i) {
+    const Group& g = c.groups[i];
+    ProblemDev& d = c.pd[i];
+    std::memset(&d, 0, sizeof(d));
+    d.n = g.h->n;
+    d.K = g.h->K;
+    d.l = g.l;
+    d.n_dense = g.h->n_dense;
+    d.A = g.h->dA;
+    d.V = g.h->V.as<double2>();
+    for (int k = 0; k < g.h->K; ++k) d.term[k] = g.h->term[k];
+  }
+  CU(c.ws->probs.ensure(std::max<size_t>(1, c.pd.size()) * sizeof(ProblemDev)));
+  CU(cudaMemcpyAsync(c.ws->probs.p, c.pd.data(), c.pd.size() * sizeof(ProblemDev), cudaMemcpyHostToDevice, c.s));
+  return PMCIM_OK;
+}
+
+// ===========================================================================
+// Autotuner: per (n-bucket, l, dense terms), FP64 or the precision form,
+// whichever solves nodes faster on this device (measured once per process).
+// ===========================================================================
+struct TuneKey {
+  int bucket, l, kd;
+  bool operator<(const TuneKey& o) const { return std::tie(bucket, l, kd) < std::tie(o.bucket, o.l, o.kd); }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+
+int n_bucket(int n) {
+  int b = 0;
+  while ((32 << b) < n) ++b;  // buckets (..32], (32,64], (64,128], ...
+  return b;
+}
+
+struct LevelOut {
+  std::vector<double> ind;
+  std::vector<uint8_t> cand;
+  std::vector<int32_t> p, status, node_info;
+  std::vector<double2> lam;
+  std::vector<uint8_t> kept;
   std::vector<RegionDev> rd;
-  std::vector<int32_t> node_region;
-  std::vector<int32_t> info;
-  while (g0 < R) {
-    int g1 = g0;
-    size_t nodes = 0;
-    while (g1 < R && (g1 == g0 || (nodes + regs[g1].N) * per_node <= kWaveBytes) && g1 - g0 < 65535) {
-      nodes += regs[g1].N;
-      ++g1;
-    }
-    rd.resize(g1 - g0);
-    node_region.resize(nodes);
-    int off = 0;
-    for (int g = g0; g < g1; ++g) {
-      RegionDev& d = rd[g - g0];
-      d.cre = regs[g].cre;
-      d.cim = regs[g].cim;
-      d.r = regs[g].r;
-      d.N = regs[g].N;
-      d.node_off = off;
-      for (int j = 0; j < regs[g].N; ++j) node_region[off + j] = g - g0;
-      off += regs[g].N;
-    }
-    CU(p->X.ensure(std::max<size_t>(1, nodes) * per_node));
-    CU(p->node_info.ensure(nodes * sizeof(int32_t)));
-    CU(p->regions.ensure(rd.size() * sizeof(RegionDev)));
-    CU(p->node_region.ensure(nodes * sizeof(int32_t)));
-    CU(cudaMemcpyAsync(p->regions.p, rd.data(), rd.size() * sizeof(RegionDev), cudaMemcpyHostToDevice, s));
-    CU(cudaMemcpyAsync(p->node_region.p, node_region.data(), nodes * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+};
 
-    if (mixed) {
-      MixedArgs ma;
-      ma.prob = p->desc;
-      ma.A = p->dA;
-      ma.V = p->V.as<double2>();
-      ma.l = l;
-      ma.regions = p->regions.as<RegionDev>();
-      ma.node_region = p->node_region.as<int32_t>();
-      ma.n_nodes = (int)nodes;
-      ma.X = p->X.as<double2>();
-      ma.node_info = p->node_info.as<int32_t>();
-      ma.work = p->work.as<char>();
-      ma.slot_bytes = slot_bytes;
-      ma.piv = p->piv.as<int32_t>();
-      ma.slots = slots;
-      ma.max_sweeps = opt->max_ir_sweeps;
-      ma.tol_ir = kIrTol;
-      ma.phase = nullptr;
-      const bool timed = prof_on();
-      if (timed) {
-        CU(p->phase.ensure((size_t)slots * 8 * sizeof(unsigned long long)));
-        CU(cudaMemsetAsync(p->phase.p, 0, (size_t)slots * 8 * sizeof(unsigned long long), s));
-        ma.phase = p->phase.as<unsigned long long>();
-      }
-      prof_begin(PMCIM_K_FACTOR32, s);
-      CU(launch_factor_solve_mixed(ma, s));
-      prof_end(PMCIM_K_FACTOR32, s);
-      if (timed) {
-        std::vector<unsigned long long> c((size_t)slots * 8);
-        CU(cudaMemcpyAsync(c.data(), p->phase.p, c.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        CU(cudaStreamSynchronize(s));
-        prof_add_phases(c.data(), slots);
-      }
-    } else {
-      FactorArgs fa;
-      fa.prob = p->desc;
-      fa.A = p->dA;
-      fa.V = p->V.as<double2>();
-      fa.l = l;
-      fa.regions = p->regions.as<RegionDev>();
-      fa.node_region = p->node_region.as<int32_t>();
-      fa.n_nodes = (int)nodes;
-      fa.X = p->X.as<double2>();
-      fa.node_info = p->node_info.as<int32_t>();
-      fa.work = p->work.as<double2>();
-      fa.piv = p->piv.as<int32_t>();
-      fa.slots = slots;
-      prof_begin(PMCIM_K_FACTOR, s);
-      CU(launch_factor_solve_fp64(fa, s));
-      prof_end(PMCIM_K_FACTOR, s);
-    }
+int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool do_beyn, LevelOut* out,
+              const std::vector<int>* form_override = nullptr);
 
-    ReduceArgs ra;
-    ra.X = p->X.as<double2>();
-    ra.n = n;
-    ra.l = l;
-    ra.regions = p->regions.as<RegionDev>();
-    ra.R = g1 - g0;
-    ra.C0 = p->C0.as<double2>() + (size_t)g0 * nl;
-    ra.C1 = p->C1.as<double2>() + (size_t)g0 * nl;
-    ra.pf_half = p->pf_half.as<double2>() + (size_t)g0 * n;
-    ra.pf_abs = p->pf_abs.as<double>() + (size_t)g0 * n;
-    prof_begin(PMCIM_K_REDUCE, s);
-    CU(launch_reduce_moments(ra, s));
-    prof_end(PMCIM_K_REDUCE, s);
-
-    if (singular) {
-      info.resize(nodes);
-      CU(cudaMemcpyAsync(info.data(), p->node_info.p, nodes * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      CU(cudaStreamSynchronize(s));
-      for (int g = g0; g < g1; ++g) {
-        const RegionDev& d = rd[g - g0];
-        for (int j = 0; j < d.N; ++j) {
-          const int v = info[d.node_off + j];
-          if (v & 0x00ffffff) (*singular)[g] |= 1;
-          if (sweeps) *sweeps += (v >> 24) & 63;
-          if (v & (1 << 30)) {
-            (*singular)[g] |= 2;
-            if (fallbacks) *fallbacks += 1;
-          }
-        }
-      }
+int tune_forms(Call& c) {
+  if (c.opt->precision != PMCIM_PREC_AUTO) {
+    for (Group& g : c.groups) g.form = c.opt->precision;
+    return PMCIM_OK;
+  }
+  for (size_t gi = 0; gi < c.groups.size(); ++gi) {
+    Group& g = c.groups[gi];
+    const TuneKey key{n_bucket(g.h->n), g.l, g.h->n_dense};
+    int decided = -1;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) decided = it->second;
     }
-    if (solves) *solves += (int64_t)nodes;
-    g0 = g1;
+    if (decided < 0) {
+      // probe: one disk of 2 x SMs nodes on this problem, both forms, timed with events
+      std::vector<HostRegion> probe(1);
+      probe[0] = HostRegion{0.37, 0.29, 0.6, 2 * num_sms(), 0, 0, (int)gi};
+      // each form runs once untimed (workspace allocation, first launch), then timed
+      double t[2] = {0.0, 0.0};
+      const pmcim_stats keep = c.st;
+      for (int f = 0; f < 2; ++f) {
+        std::vector<int> ov(c.groups.size(), f == 0 ? PMCIM_PREC_FP64 : PMCIM_PREC_FP32_IR);
+        cudaEvent_t a, b;
+        CU(cudaEventCreate(&a));
+        CU(cudaEventCreate(&b));
+        LevelOut lo;
+        CHK(run_level(c, probe, false, false, &lo, &ov));
+        CU(cudaEventRecord(a, c.s));
+        CHK(run_level(c, probe, false, false, &lo, &ov));
+        CU(cudaEventRecord(b, c.s));
+        CU(cudaEventSynchronize(b));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, a, b));
+        t[f] = ms;
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+      }
+      c.st = keep;  // probe work is not part of the call's statistics
+      decided = (t[1] < t[0]) ? PMCIM_PREC_FP32_IR : PMCIM_PREC_FP64;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[key] = decided;
+    }
+    g.form = decided;
+    if (decided == PMCIM_PREC_FP64) c.st.tuned_fp64 += 1;
+    else c.st.tuned_mixed += 1;
   }
   return PMCIM_OK;
 }
 
-// Indicator of every disk whose moments are in p->C0 etc.
-int run_indicator(pmcim_problem p, const pmcim_options* opt, int R, int l) {
-  cudaStream_t s = stream_of(opt);
-  CU(p->ind.ensure(std::max(1, R) * sizeof(double)));
-  CU(p->pf_norm.ensure(std::max(1, R) * sizeof(double)));
-  CU(p->pf_scale.ensure(std::max(1, R) * sizeof(double)));
-  CU(p->cand.ensure(std::max(1, R) * sizeof(uint8_t)));
-  IndicatorArgs ia;
-  ia.C0 = p->C0.as<double2>();
-  ia.pf_half = p->pf_half.as<double2>();
-  ia.pf_abs = p->pf_abs.as<double>();
-  ia.n = p->n;
-  ia.l = l;
-  ia.R = R;
-  ia.tol_ind = opt->tol_ind;
-  ia.ind = p->ind.as<double>();
-  ia.pf_norm = p->pf_norm.as<double>();
-  ia.pf_scale = p->pf_scale.as<double>();
-  ia.candidate = p->cand.as<uint8_t>();
-  prof_begin(PMCIM_K_INDICATOR, s);
-  CU(launch_indicator(ia, s));
-  prof_end(PMCIM_K_INDICATOR, s);
+// ===========================================================================
+// One level: node solves (waves), reduction, indicator, Beyn (gated)
+// ===========================================================================
+int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool do_beyn, LevelOut* out,
+              const std::vector<int>* form_override) {
+  Workspace& ws = *c.ws;
+  cudaStream_t s = c.s;
+  const int R = (int)regs.size();
+  out->rd.assign(R, RegionDev{});
+  if (R == 0) return PMCIM_OK;
+  auto form_of = [&](int prob) { return form_override ? (*form_override)[prob] : c.groups[prob].form; };
+
+  // ---- offsets of every disk's blocks ----
+  int max_n = 0, max_l = 0, max_nl = 0;
+  size_t c_tot = 0, p_tot = 0, w_tot = 0, total_nodes = 0;
+  std::vector<RegionDev>& rd = out->rd;
+  for (int g = 0; g < R; ++g) {
+    const HostRegion& h = regs[g];
+    const ProblemDev& P = c.pd[h.prob];
+    RegionDev& d = rd[g];
+    d.cre = h.cre;
+    d.cim = h.cim;
+    d.r = h.r;
+    d.N = h.N;
+    d.prob = h.prob;
+    d.node_off = (int32_t)total_nodes;
+    d.gate = (h.depth > 0 || gate_top) ? 1 : 0;
+    d.c_off = (int64_t)c_tot;
+    d.p_off = (int64_t)p_tot;
+    d.w_off = (int64_t)w_tot;
+    d.v_off = (int64_t)c_tot;
+    c_tot += (size_t)P.n * P.l;
+    p_tot += (size_t)P.n;
+    w_tot += 2 * (size_t)P.n * P.l + 4 * (size_t)P.l * P.l;
+    total_nodes += (size_t)h.N;
+    max_n = std::max(max_n, P.n);
+    max_l = std::max(max_l, P.l);
+    max_nl = std::max(max_nl, P.n * P.l);
+  }
+  CU(ws.C0.ensure(c_tot * sizeof(double2)));
+  CU(ws.C1.ensure(c_tot * sizeof(double2)));
+  CU(ws.pf_half.ensure(p_tot * sizeof(double2)));
+  CU(ws.pf_abs.ensure(p_tot * sizeof(double)));
+  CU(ws.ind.ensure(R * sizeof(double)));
+  CU(ws.pf_norm.ensure(R * sizeof(double)));
+  CU(ws.pf_scale.ensure(R * sizeof(double)));
+  CU(ws.cand.ensure(R));
+  CU(ws.node_info.ensure(std::max<size_t>(1, total_nodes) * sizeof(int32_t)));
+  if (do_beyn) {
+    CU(ws.bwork.ensure(w_tot * sizeof(double2)));
+    CU(ws.bvecs.ensure(c_tot * sizeof(double2)));
+    CU(ws.bsigma.ensure((size_t)R * PMCIM_MAX_L * sizeof(double)));
+    CU(ws.blam.ensure((size_t)R * PMCIM_MAX_L * sizeof(double2)));
+    CU(ws.bkept.ensure((size_t)R * PMCIM_MAX_L));
+    CU(ws.bp.ensure(R * sizeof(int32_t)));
+    CU(ws.bstatus.ensure(R * sizeof(int32_t)));
+  }
+
+  // ---- waves of whole disks whose solutions fit the wave buffer ----
+  struct Wave {
+    int g0, g1;
+    size_t items64_off, n64, items32_off, n32;
+  };
+  std::vector<Wave> waves;
+  std::vector<NodeItem> items;  // all waves: FP64 items then mixed items per wave
+  size_t x_need = 0;
+  bool any64 = false, any32 = false;
+  {
+    int g0 = 0;
+    while (g0 < R) {
+      int g1 = g0;
+      size_t xb = 0;
+      while (g1 < R && g1 - g0 < 65535) {
+        const ProblemDev& P = c.pd[regs[g1].prob];
+        const size_t b = (size_t)regs[g1].N * P.n * P.l * sizeof(double2);
+        if (g1 > g0 && xb + b > kWaveBytes) break;
+        rd[g1].x_off = (int64_t)(xb / sizeof(double2));
+        xb += b;
+        ++g1;
+      }
+      x_need = std::max(x_need, xb);
+      // largest n first: the atomic work counter then hands out the long jobs early
+      std::vector<NodeItem> it64, it32;
+      for (int g = g0; g < g1; ++g)
+        for (int j = 0; j < regs[g].N; ++j)
+          (form_of(regs[g].prob) == PMCIM_PREC_FP64 ? it64 : it32).push_back(NodeItem{g, j});
+      auto by_n = [&](const NodeItem& a, const NodeItem& b) {
+        const int na = c.pd[regs[a.region].prob].n, nb = c.pd[regs[b.region].prob].n;
+        if (na != nb) return na > nb;
+        if (a.region != b.region) return a.region < b.region;
+        return a.j < b.j;
+      };
+      std::stable_sort(it64.begin(), it64.end(), by_n);
+      std::stable_sort(it32.begin(), it32.end(), by_n);
+      Wave wv{g0, g1, items.size(), it64.size(), 0, it32.size()};
+      items.insert(items.end(), it64.begin(), it64.end());
+      wv.items32_off = items.size();
+      items.insert(items.end(), it32.begin(), it32.end());
+      any64 |= !it64.empty();
+      any32 |= !it32.empty();
+      waves.push_back(wv);
+      g0 = g1;
+    }
+  }
+  CU(ws.X.ensure(std::max<size_t>(1, x_need)));
+  CU(ws.items.ensure(std::max<size_t>(1, items.size()) * sizeof(NodeItem)));
+  CU(ws.regions.ensure(R * sizeof(RegionDev)));
+  CU(ws.counters.ensure(std::max<size_t>(1, 2 * waves.size()) * sizeof(int)));
+  CU(cudaMemcpyAsync(ws.items.p, items.data(), items.size() * sizeof(NodeItem), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(ws.regions.p, rd.data(), R * sizeof(RegionDev), cudaMemcpyHostToDevice, s));
+
+  // ---- factorisation workspaces, one slot per resident CTA ----
+  const int sms = num_sms();
+  int slots64 = 0, slots32 = 0;
+  size_t slot64 = 0, slot32 = 0;
+  if (any64) {
+    slot64 = (size_t)max_n * (max_n + max_l) * sizeof(double2);
+    slots64 = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(2 * sms, kSlotBytes / slot64), total_nodes));
+    CU(ws.work64.ensure((size_t)slots64 * slot64));
+    CU(ws.piv64.ensure((size_t)slots64 * max_n * sizeof(int32_t)));
+  }
+  if (any32) {
+    slot32 = mixed_slot_bytes(max_n, max_l);
+    slots32 = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(2 * sms, kSlotBytes / slot32), total_nodes));
+    CU(ws.work32.ensure((size_t)slots32 * slot32));
+    CU(ws.piv32.ensure((size_t)slots32 * max_n * sizeof(int32_t)));
+  }
+  const bool timed = prof_on();
+  if (timed && any32) {
+    CU(ws.phase.ensure((size_t)slots32 * 8 * sizeof(unsigned long long)));
+    CU(cudaMemsetAsync(ws.phase.p, 0, (size_t)slots32 * 8 * sizeof(unsigned long long), s));
+  }
+
+  LevelArgs la;
+  std::memset(&la, 0, sizeof(la));
+  la.probs = ws.probs.as<ProblemDev>();
+  la.regions = ws.regions.as<RegionDev>();
+  la.R = R;
+  la.max_nl = max_nl;
+  la.X = ws.X.as<double2>();
+  la.C0 = ws.C0.as<double2>();
+  la.C1 = ws.C1.as<double2>();
+  la.pf_half = ws.pf_half.as<double2>();
+  la.pf_abs = ws.pf_abs.as<double>();
+  la.tol_ind = c.opt->tol_ind;
+  la.tol_svd = c.opt->tol_svd;
+  la.ind = ws.ind.as<double>();
+  la.pf_norm = ws.pf_norm.as<double>();
+  la.pf_scale = ws.pf_scale.as<double>();
+  la.cand = ws.cand.as<uint8_t>();
+  la.bwork = ws.bwork.as<double2>();
+  la.sigma = ws.bsigma.as<double>();
+  la.p = ws.bp.as<int32_t>();
+  la.lam = ws.blam.as<double2>();
+  la.vecs = ws.bvecs.as<double2>();
+  la.kept = ws.bkept.as<uint8_t>();
+  la.status = ws.bstatus.as<int32_t>();
+
+  if (any64) CU(prepare_factor_fp64());
+  if (any32) CU(prepare_factor_mixed());
+
+  // ---- the level as one CUDA graph (profiler events become graph nodes) ----
+  cudaGraph_t graph = nullptr;
+  CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  auto capture = [&]() -> int {
+    CU(cudaMemsetAsync(ws.counters.p, 0, 2 * waves.size() * sizeof(int), s));
+    for (size_t wi = 0; wi < waves.size(); ++wi) {
+      const Wave& wv = waves[wi];
+      NodeArgs na;
+      std::memset(&na, 0, sizeof(na));
+      na.probs = la.probs;
+      na.regions = la.regions;
+      na.X = ws.X.as<double2>();
+      na.node_info = ws.node_info.as<int32_t>();
+      na.max_n = max_n;
+      na.max_sweeps = c.opt->max_ir_sweeps;
+      na.tol_ir = kIrTol;
+      if (wv.n64) {
+        na.items = ws.items.as<NodeItem>() + wv.items64_off;
+        na.n_items = (int)wv.n64;
+        na.counter = ws.counters.as<int>() + 2 * wi;
+        na.work = ws.work64.as<char>();
+        na.slot_bytes = slot64;
+        na.piv = ws.piv64.as<int32_t>();
+        na.slots = slots64;
+        na.phase = nullptr;
+        prof_begin(PMCIM_K_FACTOR, s);
+        CU(launch_factor_solve_fp64(na, s));
+        prof_end(PMCIM_K_FACTOR, s);
+      }
+      if (wv.n32) {
+        na.items = ws.items.as<NodeItem>() + wv.items32_off;
+        na.n_items = (int)wv.n32;
+        na.counter = ws.counters.as<int>() + 2 * wi + 1;
+        na.work = ws.work32.as<char>();
+        na.slot_bytes = slot32;
+        na.piv = ws.piv32.as<int32_t>();
+        na.slots = slots32;
+        na.phase = timed ? ws.phase.as<unsigned long long>() : nullptr;
+        prof_begin(PMCIM_K_FACTOR32, s);
+        CU(launch_factor_solve_mixed(na, s));
+        prof_end(PMCIM_K_FACTOR32, s);
+      }
+      LevelArgs lw = la;
+      lw.regions = la.regions + wv.g0;
+      lw.R = wv.g1 - wv.g0;
+      prof_begin(PMCIM_K_REDUCE, s);
+      CU(launch_reduce_moments(lw, s));
+      prof_end(PMCIM_K_REDUCE, s);
+    }
+    prof_begin(PMCIM_K_INDICATOR, s);
+    CU(launch_indicator(la, s));
+    prof_end(PMCIM_K_INDICATOR, s);
+    if (do_beyn) {
+      prof_begin(PMCIM_K_BEYN, s);
+      CU(launch_beyn(la, s));
+      prof_end(PMCIM_K_BEYN, s);
+    }
+    return PMCIM_OK;
+  };
+  const int cap_err = capture();
+  cudaError_t ee = cudaStreamEndCapture(s, &graph);
+  if (cap_err != PMCIM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return cap_err;
+  }
+  CU(ee);
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CU(ie);
+  cudaError_t le = cudaGraphLaunch(exec, s);
+  if (le == cudaSuccess) le = cudaStreamSynchronize(s);
+  cudaGraphExecDestroy(exec);
+  CU(le);
+  c.st.graphs += 1;
+
+  // ---- small per-disk results back to the host ----
+  out->ind.resize(R);
+  out->cand.resize(R);
+  out->node_info.resize(total_nodes);
+  CU(cudaMemcpyAsync(out->ind.data(), ws.ind.p, R * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(out->cand.data(), ws.cand.p, R, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(out->node_info.data(), ws.node_info.p, total_nodes * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (do_beyn) {
+    out->p.resize(R);
+    out->status.resize(R);
+    out->lam.resize((size_t)R * PMCIM_MAX_L);
+    out->kept.resize((size_t)R * PMCIM_MAX_L);
+    CU(cudaMemcpyAsync(out->p.data(), ws.bp.p, R * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(out->status.data(), ws.bstatus.p, R * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(out->lam.data(), ws.blam.p, (size_t)R * PMCIM_MAX_L * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(out->kept.data(), ws.bkept.p, (size_t)R * PMCIM_MAX_L, cudaMemcpyDeviceToHost, s));
+  }
+  if (timed && any32) {
+    std::vector<unsigned long long> cyc((size_t)slots32 * 8);
+    CU(cudaMemcpyAsync(cyc.data(), ws.phase.p, cyc.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    prof_add_phases(cyc.data(), slots32);
+  }
+  CU(cudaStreamSynchronize(s));
+  c.st.solves += (int64_t)total_nodes;
+  c.st.regions += R;
+  for (size_t i = 0; i < total_nodes; ++i) {
+    const int v = out->node_info[i];
+    if (v & (1 << 30)) c.st.ir_fallbacks += 1;
+    c.st.ir_sweeps += (v >> 24) & 63;
+  }
   return PMCIM_OK;
 }
 
+// ===========================================================================
+// pmCIMb step 2 with splitting, over all groups; step 3 afterwards
+// ===========================================================================
 struct EigOut {
   std::vector<double2> lam;
-  std::vector<int> root;
-  int n_vecs = 0;  // vectors gathered into p->gdst so far (same order as lam)
+  std::vector<int> root, prob;
+  std::vector<int64_t> vec_off;  // double2 offset of the eigenvector in ws.gdst
+  size_t vec_used = 0;           // double2 entries used in ws.gdst
 };
 
-// pmCIMb step 2 with splitting of saturated disks. `gate_top` applies the
-// indicator gate to the caller's disks too (pmcim_solve); children are always gated.
-int run_beyn_levels(pmcim_problem p, const pmcim_options* opt, const std::vector<HostRegion>& top, int l,
-                    bool gate_top, bool want_vecs, EigOut* out, std::vector<int>* root_status,
-                    std::vector<double>* top_ind, pmcim_stats* st) {
-  cudaStream_t s = stream_of(opt);
-  const int n = p->n;
-  const size_t nl = (size_t)n * l;
+int run_beyn_levels(Call& c, const std::vector<HostRegion>& top, bool gate_top, EigOut* out,
+                    std::vector<int>* root_status, std::vector<double>* top_ind) {
+  Workspace& ws = *c.ws;
+  cudaStream_t s = c.s;
   std::vector<HostRegion> level = top;
   root_status->assign(top.size(), 0);
   if (top_ind) top_ind->assign(top.size(), 0.0);
   while (!level.empty()) {
     const int R = (int)level.size();
-    std::vector<int> singular;
-    int64_t solves = 0;
-    int fallbacks = 0;
-    int64_t sweeps = 0;
-    CHK(run_moments(p, opt, level, l, &singular, &solves, &fallbacks, &sweeps));
-    if (st) {
-      st->ir_fallbacks += fallbacks;
-      st->ir_sweeps += sweeps;
-    }
-    CHK(run_indicator(p, opt, R, l));
-    std::vector<double> ind(R);
-    std::vector<uint8_t> cflag(R);
-    CU(cudaMemcpyAsync(ind.data(), p->ind.p, R * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(cflag.data(), p->cand.p, R * sizeof(uint8_t), cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    if (st) {
-      st->solves += solves;
-      st->regions += R;
-    }
-    std::vector<int32_t> slot;
-    std::vector<RegionDev> crd;
+    LevelOut lo;
+    CHK(run_level(c, level, gate_top, true, &lo));
+    std::vector<HostRegion> next;
+    std::vector<VecItem> vi;
+    const size_t vec_before = out->vec_used;
+    int max_vn = 0;
     for (int g = 0; g < R; ++g) {
       const HostRegion& h = level[g];
-      if (singular[g] & 1) {
-        (*root_status)[h.root] |= PMCIM_RS_SINGULAR_NODE;
-        if (st) st->singular_nodes += 1;
+      const RegionDev& d = lo.rd[g];
+      int& rs = (*root_status)[h.root];
+      for (int j = 0; j < h.N; ++j) {
+        const int v = lo.node_info[d.node_off + j];
+        if (v & 0x00ffffff) {
+          rs |= PMCIM_RS_SINGULAR_NODE;
+          c.st.singular_nodes += 1;
+        }
+        if (v & (1 << 30)) rs |= PMCIM_RS_IR_FALLBACK;
       }
-      if (singular[g] & 2) (*root_status)[h.root] |= PMCIM_RS_IR_FALLBACK;
-      if (h.depth == 0 && top_ind) (*top_ind)[h.root] = ind[g];
-      const bool gated = (h.depth > 0) || gate_top;
-      if (cflag[g]) (*root_status)[h.root] |= PMCIM_RS_CANDIDATE;
-      if (gated && !cflag[g]) continue;
-      if (st) st->candidates += 1;
-      slot.push_back(g);
-      RegionDev d;
-      d.cre = h.cre;
-      d.cim = h.cim;
-      d.r = h.r;
-      d.N = h.N;
-      d.node_off = 0;
-      crd.push_back(d);
+      if (h.depth == 0 && top_ind) (*top_ind)[h.root] = lo.ind[g];
+      if (lo.cand[g]) rs |= PMCIM_RS_CANDIDATE;
+      if (lo.p[g] < 0) continue;  // gated out
+      c.st.candidates += 1;
+      const int bits = lo.status[g];
+      if ((bits & PMCIM_RS_SATURATED) && h.depth < c.opt->max_split_depth) {
+        rs |= PMCIM_RS_SATURATED | PMCIM_RS_SPLIT;
+        c.st.splits += 1;
+        const double rc = h.r / 2.0, dd = rc / std::sqrt(2.0);
+        const int sx[4] = {1, -1, 1, -1}, sy[4] = {1, 1, -1, -1};
+        for (int q = 0; q < 4; ++q)
+          next.push_back(HostRegion{h.cre + sx[q] * dd, h.cim + sy[q] * dd, rc, h.N, h.depth + 1, h.root, h.prob});
+        continue;
+      }
+      rs |= bits;
+      const int n = c.pd[h.prob].n;
+      for (int k = 0; k < lo.p[g]; ++k) {
+        if (!lo.kept[(size_t)g * PMCIM_MAX_L + k]) continue;
+        out->lam.push_back(lo.lam[(size_t)g * PMCIM_MAX_L + k]);
+        out->root.push_back(h.root);
+        out->prob.push_back(h.prob);
+        out->vec_off.push_back((int64_t)out->vec_used);
+        vi.push_back(VecItem{d.v_off + (int64_t)k * n, (int64_t)out->vec_used, n, 0});
+        out->vec_used += (size_t)n;
+        max_vn = std::max(max_vn, n);
+      }
     }
-    const int m = (int)slot.size();
-    std::vector<HostRegion> next;
-    if (m > 0) {
-      CU(p->bslot.ensure(m * sizeof(int32_t)));
-      CU(p->bregion.ensure(m * sizeof(RegionDev)));
-      CU(p->bwork.ensure((size_t)m * (2 * nl + 4 * (size_t)l * l) * sizeof(double2)));
-      CU(p->bsigma.ensure((size_t)m * l * sizeof(double)));
-      CU(p->bp.ensure(m * sizeof(int32_t)));
-      CU(p->blam.ensure((size_t)m * l * sizeof(double2)));
-      CU(p->bvecs.ensure((size_t)m * nl * sizeof(double2)));
-      CU(p->bkept.ensure((size_t)m * l));
-      CU(p->bstatus.ensure(m * sizeof(int32_t)));
-      CU(cudaMemcpyAsync(p->bslot.p, slot.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-      CU(cudaMemcpyAsync(p->bregion.p, crd.data(), m * sizeof(RegionDev), cudaMemcpyHostToDevice, s));
-      BeynArgs ba;
-      ba.C0 = p->C0.as<double2>();
-      ba.C1 = p->C1.as<double2>();
-      ba.slot_of = p->bslot.as<int32_t>();
-      ba.regions = p->bregion.as<RegionDev>();
-      ba.n = n;
-      ba.l = l;
-      ba.m = m;
-      ba.tol_svd = opt->tol_svd;
-      ba.work = p->bwork.as<double2>();
-      ba.sigma = p->bsigma.as<double>();
-      ba.p = p->bp.as<int32_t>();
-      ba.lam = p->blam.as<double2>();
-      ba.vecs = p->bvecs.as<double2>();
-      ba.kept = p->bkept.as<uint8_t>();
-      ba.status = p->bstatus.as<int32_t>();
-      prof_begin(PMCIM_K_BEYN, s);
-      CU(launch_beyn(ba, s));
-      prof_end(PMCIM_K_BEYN, s);
-      std::vector<int32_t> pv(m), stv(m);
-      std::vector<double2> lam((size_t)m * l);
-      std::vector<uint8_t> kept((size_t)m * l);
-      CU(cudaMemcpyAsync(pv.data(), p->bp.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      CU(cudaMemcpyAsync(stv.data(), p->bstatus.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      CU(cudaMemcpyAsync(lam.data(), p->blam.p, (size_t)m * l * sizeof(double2), cudaMemcpyDeviceToHost, s));
-      CU(cudaMemcpyAsync(kept.data(), p->bkept.p, (size_t)m * l, cudaMemcpyDeviceToHost, s));
+    if (!vi.empty()) {
+      CU(ws.gdst.grow_keep(out->vec_used * sizeof(double2), vec_before * sizeof(double2), s));
+      CU(ws.gitems.ensure(vi.size() * sizeof(VecItem)));
+      CU(cudaMemcpyAsync(ws.gitems.p, vi.data(), vi.size() * sizeof(VecItem), cudaMemcpyHostToDevice, s));
+      for (size_t q0 = 0; q0 < vi.size(); q0 += 65535) {
+        const int cnt = (int)std::min<size_t>(65535, vi.size() - q0);
+        prof_begin(PMCIM_K_GATHER, s);
+        CU(launch_gather_vecs(ws.bvecs.as<double2>(), ws.gdst.as<double2>(), ws.gitems.as<VecItem>() + q0, cnt,
+                              max_vn, s));
+        prof_end(PMCIM_K_GATHER, s);
+      }
       CU(cudaStreamSynchronize(s));
-      std::vector<int32_t> gsrc;
-      for (int c = 0; c < m; ++c) {
-        const HostRegion& h = level[slot[c]];
-        int bits = stv[c];
-        if ((bits & PMCIM_RS_SATURATED) && h.depth < opt->max_split_depth) {
-          (*root_status)[h.root] |= PMCIM_RS_SATURATED | PMCIM_RS_SPLIT;
-          if (st) st->splits += 1;
-          const double rc = h.r / 2.0, d = rc / std::sqrt(2.0);
-          const int sx[4] = {1, -1, 1, -1}, sy[4] = {1, 1, -1, -1};
-          for (int q = 0; q < 4; ++q)
-            next.push_back(HostRegion{h.cre + sx[q] * d, h.cim + sy[q] * d, rc, h.N, h.depth + 1, h.root});
-          continue;
-        }
-        (*root_status)[h.root] |= bits;
-        for (int k = 0; k < pv[c]; ++k) {
-          if (!kept[(size_t)c * l + k]) continue;
-          out->lam.push_back(lam[(size_t)c * l + k]);
-          out->root.push_back(h.root);
-          gsrc.push_back(c * l + k);
-        }
-      }
-      if (want_vecs && !gsrc.empty()) {
-        const int cnt = (int)gsrc.size();
-        {
-          const size_t vb = (size_t)n * sizeof(double2);
-          CU(p->gdst.grow_keep((size_t)(out->n_vecs + cnt) * vb, (size_t)out->n_vecs * vb, s));
-          CU(p->gsrc.ensure(cnt * sizeof(int32_t)));
-          CU(cudaMemcpyAsync(p->gsrc.p, gsrc.data(), cnt * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-          GatherArgs ga;
-          ga.vecs = p->bvecs.as<double2>();
-          ga.src = p->gsrc.as<int32_t>();
-          ga.dst = p->gdst.as<double2>() + (size_t)out->n_vecs * n;
-          ga.n = n;
-          ga.l = l;
-          ga.count = cnt;
-          prof_begin(PMCIM_K_GATHER, s);
-          CU(launch_gather_vecs(ga, s));
-          prof_end(PMCIM_K_GATHER, s);
-          CU(cudaStreamSynchronize(s));
-        }
-        out->n_vecs += cnt;
-      }
     }
     level.swap(next);
   }
   return PMCIM_OK;
 }
 
-int run_verify(pmcim_problem p, const pmcim_options* opt, const std::vector<double2>& lam,
-               std::vector<double>* sig, std::vector<uint8_t>* acc) {
-  cudaStream_t s = stream_of(opt);
+// sigma_min (full) for the given values; slots sized for the largest n among them.
+int run_verify(Call& c, const std::vector<double2>& lam, const std::vector<int>& prob, std::vector<double>* sig,
+               std::vector<uint8_t>* acc) {
+  Workspace& ws = *c.ws;
+  cudaStream_t s = c.s;
   const int m = (int)lam.size();
   sig->assign(m, 0.0);
   acc->assign(m, 0);
   if (m == 0) return PMCIM_OK;
-  const int n = p->n;
-  const int slots = std::min(verify_slots_fp64(n), m);
-  CU(p->vlam.ensure(m * sizeof(double2)));
-  CU(p->vsig.ensure(m * sizeof(double)));
-  CU(p->vacc.ensure(m));
-  CU(p->vwork.ensure((size_t)slots * n * n * sizeof(double2)));
-  CU(p->vvec.ensure((size_t)slots * 3 * n * sizeof(double2)));
-  CU(p->vpiv.ensure((size_t)slots * n * sizeof(int32_t)));
-  CU(cudaMemcpyAsync(p->vlam.p, lam.data(), m * sizeof(double2), cudaMemcpyHostToDevice, s));
-  VerifyArgs va;
-  va.prob = p->desc;
-  va.A = p->dA;
-  va.lam = p->vlam.as<double2>();
+  int max_n = 1;
+  for (int i = 0; i < m; ++i) max_n = std::max(max_n, c.pd[prob[i]].n);
+  const size_t slot = (size_t)max_n * max_n * sizeof(double2);
+  const int slots = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(2 * num_sms(), kSlotBytes / slot), m));
+  CU(ws.vlam.ensure(m * sizeof(double2)));
+  CU(ws.vprob.ensure(m * sizeof(int32_t)));
+  CU(ws.vsig.ensure(m * sizeof(double)));
+  CU(ws.vacc.ensure(m));
+  CU(ws.vwork.ensure((size_t)slots * slot));
+  CU(ws.vvec.ensure((size_t)slots * 3 * max_n * sizeof(double2)));
+  CU(ws.vpiv.ensure((size_t)slots * max_n * sizeof(int32_t)));
+  std::vector<int32_t> pr(prob.begin(), prob.end());
+  CU(cudaMemcpyAsync(ws.vlam.p, lam.data(), m * sizeof(double2), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(ws.vprob.p, pr.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  ValueArgs va;
+  std::memset(&va, 0, sizeof(va));
+  va.probs = ws.probs.as<ProblemDev>();
+  va.prob_of = ws.vprob.as<int32_t>();
+  va.lam = ws.vlam.as<double2>();
   va.m = m;
-  va.tol_verify = opt->tol_verify;
-  va.sigma_min = p->vsig.as<double>();
-  va.accept = p->vacc.as<uint8_t>();
-  va.work = p->vwork.as<double2>();
-  va.vec = p->vvec.as<double2>();
-  va.piv = p->vpiv.as<int32_t>();
+  va.tol_verify = c.opt->tol_verify;
+  va.sigma = ws.vsig.as<double>();
+  va.accept = ws.vacc.as<uint8_t>();
+  va.work = ws.vwork.as<double2>();
+  va.vec = ws.vvec.as<double2>();
+  va.piv = ws.vpiv.as<int32_t>();
   va.slots = slots;
+  va.max_n = max_n;
   prof_begin(PMCIM_K_VERIFY, s);
   CU(launch_verify_fp64(va, s));
   prof_end(PMCIM_K_VERIFY, s);
-  CU(cudaMemcpyAsync(sig->data(), p->vsig.p, m * sizeof(double), cudaMemcpyDeviceToHost, s));
-  CU(cudaMemcpyAsync(acc->data(), p->vacc.p, m, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(sig->data(), ws.vsig.p, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(acc->data(), ws.vacc.p, m, cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   return PMCIM_OK;
 }
 
-// Certificate sigma_min(T(lambda)) <= ||T(lambda) v|| for the gathered unit
-// eigenvectors (p->gdst, same order as lam).
-int run_certify(pmcim_problem p, const pmcim_options* opt, const std::vector<double2>& lam,
-                std::vector<double>* cert, std::vector<uint8_t>* ok) {
-  cudaStream_t s = stream_of(opt);
-  const int m = (int)lam.size();
+// Certificate sigma_min(T(lambda)) <= ||T(lambda) v|| with the gathered unit eigenvectors.
+int run_certify(Call& c, const EigOut& e, std::vector<double>* cert, std::vector<uint8_t>* ok) {
+  Workspace& ws = *c.ws;
+  cudaStream_t s = c.s;
+  const int m = (int)e.lam.size();
   cert->assign(m, 0.0);
   ok->assign(m, 0);
   if (m == 0) return PMCIM_OK;
-  CU(p->vlam.ensure(m * sizeof(double2)));
-  CU(p->vsig.ensure(m * sizeof(double)));
-  CU(p->vacc.ensure(m));
-  CU(cudaMemcpyAsync(p->vlam.p, lam.data(), m * sizeof(double2), cudaMemcpyHostToDevice, s));
-  CertifyArgs ca;
-  ca.prob = p->desc;
-  ca.A = p->dA;
-  ca.lam = p->vlam.as<double2>();
-  ca.vecs = p->gdst.as<double2>();
-  ca.m = m;
-  ca.tol_verify = opt->tol_verify;
-  ca.cert = p->vsig.as<double>();
-  ca.certified = p->vacc.as<uint8_t>();
+  CU(ws.vlam.ensure(m * sizeof(double2)));
+  CU(ws.vprob.ensure(m * sizeof(int32_t)));
+  CU(ws.voff.ensure(m * sizeof(int64_t)));
+  CU(ws.vsig.ensure(m * sizeof(double)));
+  CU(ws.vacc.ensure(m));
+  std::vector<int32_t> pr(e.prob.begin(), e.prob.end());
+  CU(cudaMemcpyAsync(ws.vlam.p, e.lam.data(), m * sizeof(double2), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(ws.vprob.p, pr.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(ws.voff.p, e.vec_off.data(), m * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  ValueArgs va;
+  std::memset(&va, 0, sizeof(va));
+  va.probs = ws.probs.as<ProblemDev>();
+  va.prob_of = ws.vprob.as<int32_t>();
+  va.lam = ws.vlam.as<double2>();
+  va.vec_off = ws.voff.as<int64_t>();
+  va.vecs = ws.gdst.as<double2>();
+  va.m = m;
+  va.tol_verify = c.opt->tol_verify;
+  va.sigma = ws.vsig.as<double>();
+  va.accept = ws.vacc.as<uint8_t>();
   prof_begin(PMCIM_K_VERIFY, s);
-  CU(launch_certify(ca, s));
+  CU(launch_certify(va, s));
   prof_end(PMCIM_K_VERIFY, s);
-  CU(cudaMemcpyAsync(cert->data(), p->vsig.p, m * sizeof(double), cudaMemcpyDeviceToHost, s));
-  CU(cudaMemcpyAsync(ok->data(), p->vacc.p, m, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(cert->data(), ws.vsig.p, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(ok->data(), ws.vacc.p, m, cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   return PMCIM_OK;
 }
 
-std::vector<HostRegion> to_host_regions(int R, const pmcim_region* reg) {
+// Steps 1-3 for all groups of a call. Outputs in call order (not sorted).
+struct Verified {
+  std::vector<double> sig;
+  std::vector<uint8_t> acc;
+};
+
+int run_pmcimb(Call& c, const std::vector<HostRegion>& top, EigOut* e, Verified* v, std::vector<int>* rstat,
+               std::vector<double>* tind) {
+  CHK(tune_forms(c));
+  CHK(run_beyn_levels(c, top, true, e, rstat, tind));
+  CHK(run_certify(c, *e, &v->sig, &v->acc));
+  std::vector<double2> rest;
+  std::vector<int> rest_prob, idx;
+  for (size_t i = 0; i < e->lam.size(); ++i) {
+    if (v->acc[i]) {
+      c.st.certified += 1;
+    } else {
+      rest.push_back(e->lam[i]);
+      rest_prob.push_back(e->prob[i]);
+      idx.push_back((int)i);
+    }
+  }
+  std::vector<double> sig2;
+  std::vector<uint8_t> acc2;
+  CHK(run_verify(c, rest, rest_prob, &sig2, &acc2));
+  for (size_t k = 0; k < idx.size(); ++k) {
+    v->sig[idx[k]] = sig2[k];
+    v->acc[idx[k]] = acc2[k];
+  }
+  for (size_t i = 0; i < e->lam.size(); ++i)
+    if (!v->acc[i]) c.st.unverified += 1;
+  return PMCIM_OK;
+}
+
+std::vector<HostRegion> to_host_regions(int R, const pmcim_region* reg, int prob, int root0 = 0) {
   std::vector<HostRegion> v(R);
-  for (int g = 0; g < R; ++g) v[g] = HostRegion{reg[g].c_re, reg[g].c_im, reg[g].r, reg[g].N, 0, g};
+  for (int g = 0; g < R; ++g) v[g] = HostRegion{reg[g].c_re, reg[g].c_im, reg[g].r, reg[g].N, 0, root0 + g, prob};
   return v;
 }
 
@@ -640,6 +890,16 @@ int check_device() {
   int cnt = 0;
   cudaError_t e = cudaGetDeviceCount(&cnt);
   if (e != cudaSuccess || cnt == 0) return fail(PMCIM_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  return PMCIM_OK;
+}
+
+int single_call(Call& c, pmcim_problem p, const pmcim_options* opt, int l, const double* V) {
+  c.opt = opt;
+  c.ws = &p->ws;
+  CHK(call_stream(p->ws, opt, &c.s));
+  c.groups = {Group{p, l, opt->precision == PMCIM_PREC_AUTO ? PMCIM_PREC_FP32_IR : opt->precision}};
+  CHK(upload_V(p, l, V, c.s));
+  CHK(upload_problems(c));
   return PMCIM_OK;
 }
 
@@ -716,8 +976,6 @@ int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmc
   pmcim_problem p = new pmcim_problem_s();
   p->n = n;
   p->K = K;
-  p->desc.n = n;
-  p->desc.K = K;
   int nd = 0;
   for (int k = 0; k < K; ++k) {
     if (f[k].kind != PMCIM_F_MONOMIAL && f[k].kind != PMCIM_F_EXP_NEG) {
@@ -728,7 +986,7 @@ int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmc
       delete p;
       return fail(PMCIM_EINVAL, "term %d: degree %d outside 0..16", k, f[k].degree);
     }
-    TermDesc& t = p->desc.term[k];
+    TermDesc& t = p->term[k];
     t.kind = f[k].kind;
     t.degree = f[k].degree;
     t.tau = f[k].tau;
@@ -736,7 +994,7 @@ int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmc
     t.dense = A[k] ? 1 : 0;
     t.mat_index = A[k] ? nd++ : -1;
   }
-  p->desc.n_dense = nd;
+  p->n_dense = nd;
   cudaGetDevice(&p->device);
   const size_t nn = (size_t)n * n;
   if (nd > 0) {
@@ -747,7 +1005,7 @@ int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmc
     }
     for (int k = 0; k < K; ++k) {
       if (!A[k]) continue;
-      e = cudaMemcpy(p->dA + (size_t)p->desc.term[k].mat_index * nn, A[k], nn * sizeof(double2), cudaMemcpyDefault);
+      e = cudaMemcpy(p->dA + (size_t)p->term[k].mat_index * nn, A[k], nn * sizeof(double2), cudaMemcpyDefault);
       if (e != cudaSuccess) {
         cudaFree(p->dA);
         delete p;
@@ -763,11 +1021,8 @@ int pmcim_problem_destroy(pmcim_problem p) {
   if (!p) return PMCIM_OK;
   cudaDeviceSynchronize();
   if (p->dA) cudaFree(p->dA);
-  DevBuf* bufs[] = {&p->work, &p->piv, &p->X, &p->node_info, &p->regions, &p->node_region, &p->V,
-                    &p->C0, &p->C1, &p->pf_half, &p->pf_abs, &p->ind, &p->pf_norm, &p->pf_scale, &p->cand,
-                    &p->bslot, &p->bregion, &p->bwork, &p->bsigma, &p->bp, &p->blam, &p->bvecs, &p->bkept,
-                    &p->bstatus, &p->vlam, &p->vsig, &p->vacc, &p->vwork, &p->vvec, &p->vpiv, &p->gsrc, &p->gdst, &p->gperm, &p->phase};
-  for (DevBuf* b : bufs) b->release();
+  p->V.release();
+  p->ws.release();
   delete p;
   return PMCIM_OK;
 }
@@ -776,17 +1031,16 @@ int pmcim_moments(pmcim_problem p, const pmcim_options* opt, int32_t R, const pm
                   const double* V, double* C0, double* C1, double* pf_half, double* pf_abs) {
   if (!p) return fail(PMCIM_EINVAL, "problem is NULL");
   CHK(check_options(opt));
-  CHK(check_regions(R, reg, l, p->n));
-  cudaStream_t s = stream_of(opt);
-  CHK(upload_V(p, l, V, s));
-  std::vector<HostRegion> regs = to_host_regions(R, reg);
-  CHK(run_moments(p, opt, regs, l, nullptr, nullptr));
+  CHK(check_regions(R, reg, l));
+  Call c;
+  CHK(single_call(c, p, opt, l, V));
+  LevelOut lo;
+  CHK(run_level(c, to_host_regions(R, reg, 0), false, false, &lo));
   const size_t nl = (size_t)p->n * l;
-  if (C0) CU(cudaMemcpyAsync(C0, p->C0.p, (size_t)R * nl * sizeof(double2), cudaMemcpyDefault, s));
-  if (C1) CU(cudaMemcpyAsync(C1, p->C1.p, (size_t)R * nl * sizeof(double2), cudaMemcpyDefault, s));
-  if (pf_half) CU(cudaMemcpyAsync(pf_half, p->pf_half.p, (size_t)R * p->n * sizeof(double2), cudaMemcpyDefault, s));
-  if (pf_abs) CU(cudaMemcpyAsync(pf_abs, p->pf_abs.p, (size_t)R * p->n * sizeof(double), cudaMemcpyDefault, s));
-  CU(cudaStreamSynchronize(s));
+  if (C0) CHK(copy_out(C0, p->ws.C0.p, (size_t)R * nl * sizeof(double2)));
+  if (C1) CHK(copy_out(C1, p->ws.C1.p, (size_t)R * nl * sizeof(double2)));
+  if (pf_half) CHK(copy_out(pf_half, p->ws.pf_half.p, (size_t)R * p->n * sizeof(double2)));
+  if (pf_abs) CHK(copy_out(pf_abs, p->ws.pf_abs.p, (size_t)R * p->n * sizeof(double)));
   return PMCIM_OK;
 }
 
@@ -794,20 +1048,18 @@ int pmcim_indicator(pmcim_problem p, const pmcim_options* opt, int32_t R, const 
                     const double* V, double* ind, double* pf_norm, double* pf_scale, uint8_t* candidate) {
   if (!p) return fail(PMCIM_EINVAL, "problem is NULL");
   CHK(check_options(opt));
-  CHK(check_regions(R, reg, l, p->n));
+  CHK(check_regions(R, reg, l));
   if (R > 0 && (!ind || !candidate)) return fail(PMCIM_EINVAL, "ind or candidate is NULL");
-  cudaStream_t s = stream_of(opt);
-  CHK(upload_V(p, l, V, s));
-  std::vector<HostRegion> regs = to_host_regions(R, reg);
-  CHK(run_moments(p, opt, regs, l, nullptr, nullptr));
-  CHK(run_indicator(p, opt, R, l));
+  Call c;
+  CHK(single_call(c, p, opt, l, V));
+  LevelOut lo;
+  CHK(run_level(c, to_host_regions(R, reg, 0), false, false, &lo));
   if (R > 0) {
-    CU(cudaMemcpyAsync(ind, p->ind.p, R * sizeof(double), cudaMemcpyDefault, s));
-    CU(cudaMemcpyAsync(candidate, p->cand.p, R * sizeof(uint8_t), cudaMemcpyDefault, s));
-    if (pf_norm) CU(cudaMemcpyAsync(pf_norm, p->pf_norm.p, R * sizeof(double), cudaMemcpyDefault, s));
-    if (pf_scale) CU(cudaMemcpyAsync(pf_scale, p->pf_scale.p, R * sizeof(double), cudaMemcpyDefault, s));
+    CHK(copy_out(ind, p->ws.ind.p, R * sizeof(double)));
+    CHK(copy_out(candidate, p->ws.cand.p, R));
+    if (pf_norm) CHK(copy_out(pf_norm, p->ws.pf_norm.p, R * sizeof(double)));
+    if (pf_scale) CHK(copy_out(pf_scale, p->ws.pf_scale.p, R * sizeof(double)));
   }
-  CU(cudaStreamSynchronize(s));
   return PMCIM_OK;
 }
 
@@ -816,21 +1068,20 @@ int pmcim_beyn(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim
                int32_t* region_status) {
   if (!p) return fail(PMCIM_EINVAL, "problem is NULL");
   CHK(check_options(opt));
-  CHK(check_regions(R, reg, l, p->n));
+  CHK(check_regions(R, reg, l));
   if (!count || cap < 0 || (cap > 0 && !lambda)) return fail(PMCIM_EINVAL, "bad output arguments");
-  cudaStream_t s = stream_of(opt);
-  CHK(upload_V(p, l, V, s));
+  Call c;
+  CHK(single_call(c, p, opt, l, V));
   EigOut out;
   std::vector<int> rstat;
-  CHK(run_beyn_levels(p, opt, to_host_regions(R, reg), l, false, vecs != nullptr, &out, &rstat, nullptr,
-                      nullptr));
+  CHK(run_beyn_levels(c, to_host_regions(R, reg, 0), false, &out, &rstat, nullptr));
   const int cnt = (int)out.lam.size();
   CHK(copy_out(count, &cnt, sizeof(int32_t)));
   if (region_status) CHK(copy_out(region_status, rstat.data(), R * sizeof(int32_t)));
   if (cnt > cap) return fail(PMCIM_ECAPACITY, "%d eigenvalues exceed capacity %d", cnt, cap);
   CHK(copy_out(lambda, out.lam.data(), cnt * sizeof(double2)));
   if (region_of) CHK(copy_out(region_of, out.root.data(), cnt * sizeof(int32_t)));
-  if (vecs && cnt > 0) CHK(copy_out(vecs, p->gdst.p, (size_t)cnt * p->n * sizeof(double2)));
+  if (vecs && cnt > 0) CHK(copy_out(vecs, p->ws.gdst.p, (size_t)cnt * p->n * sizeof(double2)));
   return PMCIM_OK;
 }
 
@@ -844,9 +1095,15 @@ int pmcim_verify(pmcim_problem p, const pmcim_options* opt, int32_t m, const dou
     cudaError_t e = cudaMemcpy(lam.data(), lambda, m * sizeof(double2), cudaMemcpyDefault);
     if (e != cudaSuccess) return fail(PMCIM_ECUDA, "lambda copy: %s", cudaGetErrorString(e));
   }
+  Call c;
+  c.opt = opt;
+  c.ws = &p->ws;
+  CHK(call_stream(p->ws, opt, &c.s));
+  c.groups = {Group{p, 1, PMCIM_PREC_FP64}};
+  CHK(upload_problems(c));
   std::vector<double> sig;
   std::vector<uint8_t> acc;
-  CHK(run_verify(p, opt, lam, &sig, &acc));
+  CHK(run_verify(c, lam, std::vector<int>(m, 0), &sig, &acc));
   CHK(copy_out(sigma_min, sig.data(), m * sizeof(double)));
   if (accept) CHK(copy_out(accept, acc.data(), m));
   return PMCIM_OK;
@@ -857,83 +1114,122 @@ int pmcim_solve(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmci
                 int32_t* count, double* ind, int32_t* region_status, pmcim_stats* stats) {
   if (!p) return fail(PMCIM_EINVAL, "problem is NULL");
   CHK(check_options(opt));
-  CHK(check_regions(R, reg, l, p->n));
+  CHK(check_regions(R, reg, l));
   if (!count || cap < 0 || (cap > 0 && !lambda)) return fail(PMCIM_EINVAL, "bad output arguments");
-  cudaStream_t s = stream_of(opt);
-  pmcim_stats st;
-  std::memset(&st, 0, sizeof(st));
-  CHK(upload_V(p, l, V, s));
-  EigOut out;
+  Call c;
+  CHK(single_call(c, p, opt, l, V));
+  EigOut e;
+  Verified v;
   std::vector<int> rstat;
   std::vector<double> tind;
-  const bool want_vecs = vecs != nullptr;
-  // eigenvectors are always gathered: they carry the verification certificate
-  CHK(run_beyn_levels(p, opt, to_host_regions(R, reg), l, true, true, &out, &rstat, &tind, &st));
-  std::vector<double> sig;
-  std::vector<uint8_t> acc;
-  CHK(run_certify(p, opt, out.lam, &sig, &acc));
-  {
-    std::vector<double2> rest;
-    std::vector<int> idx;
-    for (size_t i = 0; i < out.lam.size(); ++i)
-      if (acc[i]) st.certified += 1;
-      else {
-        rest.push_back(out.lam[i]);
-        idx.push_back((int)i);
-      }
-    std::vector<double> sig2;
-    std::vector<uint8_t> acc2;
-    CHK(run_verify(p, opt, rest, &sig2, &acc2));
-    for (size_t k = 0; k < idx.size(); ++k) {
-      sig[idx[k]] = sig2[k];
-      acc[idx[k]] = acc2[k];
-    }
-  }
-  const int m = (int)out.lam.size();
+  CHK(run_pmcimb(c, to_host_regions(R, reg, 0), &e, &v, &rstat, &tind));
   std::vector<int> order;
-  for (int i = 0; i < m; ++i)
-    if (acc[i]) order.push_back(i);
-    else st.unverified += 1;
+  for (size_t i = 0; i < e.lam.size(); ++i)
+    if (v.acc[i]) order.push_back((int)i);
   std::sort(order.begin(), order.end(), [&](int a, int b) {
-    if (out.lam[a].x != out.lam[b].x) return out.lam[a].x < out.lam[b].x;
-    return out.lam[a].y < out.lam[b].y;
+    if (e.lam[a].x != e.lam[b].x) return e.lam[a].x < e.lam[b].x;
+    return e.lam[a].y < e.lam[b].y;
   });
   const int cnt = (int)order.size();
   CHK(copy_out(count, &cnt, sizeof(int32_t)));
   if (ind) CHK(copy_out(ind, tind.data(), R * sizeof(double)));
   if (region_status) CHK(copy_out(region_status, rstat.data(), R * sizeof(int32_t)));
-  if (stats) CHK(copy_out(stats, &st, sizeof(st)));
+  if (stats) CHK(copy_out(stats, &c.st, sizeof(c.st)));
   if (cnt > cap) return fail(PMCIM_ECAPACITY, "%d eigenvalues exceed capacity %d", cnt, cap);
   std::vector<double2> lam_s(cnt);
   std::vector<double> sig_s(cnt);
   std::vector<int32_t> root_s(cnt);
+  std::vector<VecItem> vi(cnt);
   for (int i = 0; i < cnt; ++i) {
-    lam_s[i] = out.lam[order[i]];
-    sig_s[i] = sig[order[i]];
-    root_s[i] = out.root[order[i]];
+    lam_s[i] = e.lam[order[i]];
+    sig_s[i] = v.sig[order[i]];
+    root_s[i] = e.root[order[i]];
+    vi[i] = VecItem{e.vec_off[order[i]], (int64_t)i * p->n, p->n, 0};
   }
   CHK(copy_out(lambda, lam_s.data(), cnt * sizeof(double2)));
   if (sigma_min) CHK(copy_out(sigma_min, sig_s.data(), cnt * sizeof(double)));
   if (region_of) CHK(copy_out(region_of, root_s.data(), cnt * sizeof(int32_t)));
-  if (want_vecs && cnt > 0) {
+  if (vecs && cnt > 0) {
     // permute the gathered vectors into the sorted order on the device, one copy out
-    std::vector<int32_t> src(order.begin(), order.end());
-    CU(p->gsrc.ensure(cnt * sizeof(int32_t)));
-    CU(p->gperm.ensure((size_t)cnt * p->n * sizeof(double2)));
-    CU(cudaMemcpyAsync(p->gsrc.p, src.data(), cnt * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    GatherArgs ga;
-    ga.vecs = p->gdst.as<double2>();
-    ga.src = p->gsrc.as<int32_t>();
-    ga.dst = p->gperm.as<double2>();
-    ga.n = p->n;
-    ga.l = 1;
-    ga.count = cnt;
-    prof_begin(PMCIM_K_GATHER, s);
-    CU(launch_gather_vecs(ga, s));
-    prof_end(PMCIM_K_GATHER, s);
-    CU(cudaStreamSynchronize(s));
-    CHK(copy_out(vecs, p->gperm.p, (size_t)cnt * p->n * sizeof(double2)));
+    Workspace& ws = p->ws;
+    CU(ws.gperm.ensure((size_t)cnt * p->n * sizeof(double2)));
+    CU(ws.gitems.ensure(cnt * sizeof(VecItem)));
+    CU(cudaMemcpyAsync(ws.gitems.p, vi.data(), cnt * sizeof(VecItem), cudaMemcpyHostToDevice, c.s));
+    for (int q0 = 0; q0 < cnt; q0 += 65535) {
+      const int k = std::min(65535, cnt - q0);
+      prof_begin(PMCIM_K_GATHER, c.s);
+      CU(launch_gather_vecs(ws.gdst.as<double2>(), ws.gperm.as<double2>(), ws.gitems.as<VecItem>() + q0, k, p->n,
+                            c.s));
+      prof_end(PMCIM_K_GATHER, c.s);
+    }
+    CU(cudaStreamSynchronize(c.s));
+    CHK(copy_out(vecs, ws.gperm.p, (size_t)cnt * p->n * sizeof(double2)));
   }
+  return PMCIM_OK;
+}
+
+int pmcim_batch_solve(int32_t P, const pmcim_batch_item* items, const pmcim_options* opt, int32_t cap,
+                      double* lambda, double* sigma_min, int32_t* problem_of, int32_t* region_of, int32_t* count,
+                      pmcim_stats* stats) {
+  CHK(check_options(opt));
+  if (P < 1 || !items) return fail(PMCIM_EINVAL, "empty batch");
+  if (!count || cap < 0 || (cap > 0 && !lambda)) return fail(PMCIM_EINVAL, "bad output arguments");
+  Call c;
+  c.opt = opt;
+  if (!items[0].problem) return fail(PMCIM_EINVAL, "batch item 0: problem is NULL");
+  c.ws = &items[0].problem->ws;
+  CHK(call_stream(*c.ws, opt, &c.s));
+  std::vector<HostRegion> top;
+  std::vector<int> root_base(P);
+  for (int q = 0; q < P; ++q) {
+    const pmcim_batch_item& it = items[q];
+    if (!it.problem) return fail(PMCIM_EINVAL, "batch item %d: problem is NULL", q);
+    CHK(check_regions(it.R, it.regions, it.l));
+    CHK(upload_V(it.problem, it.l, it.V, c.s));
+    c.groups.push_back(Group{it.problem, it.l, PMCIM_PREC_FP64});
+    root_base[q] = (int)top.size();
+    std::vector<HostRegion> h = to_host_regions(it.R, it.regions, q, (int)top.size());
+    top.insert(top.end(), h.begin(), h.end());
+  }
+  {
+    // each problem's probe block lives in its handle: a handle may appear once per batch
+    std::vector<pmcim_problem> hs;
+    for (int q = 0; q < P; ++q) hs.push_back(items[q].problem);
+    std::sort(hs.begin(), hs.end());
+    if (std::adjacent_find(hs.begin(), hs.end()) != hs.end())
+      return fail(PMCIM_EINVAL, "a problem handle appears twice in one batch");
+  }
+  CHK(upload_problems(c));
+  EigOut e;
+  Verified v;
+  std::vector<int> rstat;
+  CHK(run_pmcimb(c, top, &e, &v, &rstat, nullptr));
+  std::vector<int> order;
+  for (size_t i = 0; i < e.lam.size(); ++i)
+    if (v.acc[i]) order.push_back((int)i);
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    if (e.prob[a] != e.prob[b]) return e.prob[a] < e.prob[b];
+    if (e.lam[a].x != e.lam[b].x) return e.lam[a].x < e.lam[b].x;
+    return e.lam[a].y < e.lam[b].y;
+  });
+  const int cnt = (int)order.size();
+  CHK(copy_out(count, &cnt, sizeof(int32_t)));
+  if (stats) CHK(copy_out(stats, &c.st, sizeof(c.st)));
+  if (cnt > cap) return fail(PMCIM_ECAPACITY, "%d eigenvalues exceed capacity %d", cnt, cap);
+  std::vector<double2> lam_s(cnt);
+  std::vector<double> sig_s(cnt);
+  std::vector<int32_t> prob_s(cnt), reg_s(cnt);
+  for (int i = 0; i < cnt; ++i) {
+    const int k = order[i];
+    lam_s[i] = e.lam[k];
+    sig_s[i] = v.sig[k];
+    prob_s[i] = e.prob[k];
+    reg_s[i] = e.root[k] - root_base[e.prob[k]];
+  }
+  CHK(copy_out(lambda, lam_s.data(), cnt * sizeof(double2)));
+  if (sigma_min) CHK(copy_out(sigma_min, sig_s.data(), cnt * sizeof(double)));
+  if (problem_of) CHK(copy_out(problem_of, prob_s.data(), cnt * sizeof(int32_t)));
+  if (region_of) CHK(copy_out(region_of, reg_s.data(), cnt * sizeof(int32_t)));
   return PMCIM_OK;
 }
 

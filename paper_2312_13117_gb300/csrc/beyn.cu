@@ -1,6 +1,6 @@
 // Beyn's extraction on the device, FP64 (Eq. 2.8; pmCIMb steps 2.c-2.f).
 //
-// One CTA per candidate disk:
+// One CTA per disk of a level; disks the indicator gate rules out return at once:
 //   1. one-sided (Hestenes) Jacobi SVD of C0 (n x l): columns of C0 W are
 //      orthogonalised by complex plane rotations; sigma_k are their norms,
 //      sorted descending; V0 = normalised columns, W0 = W's columns;
@@ -215,18 +215,26 @@ __device__ int small_eig(double2* H, double2* Z, double2* Y, int p, double2* lam
   return fail;
 }
 
-__global__ void __launch_bounds__(BT) k_beyn(BeynArgs a) {
+__global__ void __launch_bounds__(BT) k_beyn(LevelArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BeynSmem& sm = *reinterpret_cast<BeynSmem*>(smem_raw);
-  const int cand = blockIdx.x;
+  const int g = blockIdx.x;
   const int tid = threadIdx.x;
-  const int n = a.n, l = a.l;
+  const RegionDev rg = a.regions[g];
+  const size_t ol = (size_t)g * PMCIM_MAX_L;  // per-disk slot of sigma, lam, kept
+  if (rg.gate && !a.cand[g]) {                // gated out: no Beyn step for this disk
+    if (tid == 0) {
+      a.p[g] = -1;
+      a.status[g] = 0;
+    }
+    return;
+  }
+  const int n = a.probs[rg.prob].n, l = a.probs[rg.prob].l;
   const size_t nl = (size_t)n * l;
-  const int slot = a.slot_of[cand];
-  const double2* C0 = a.C0 + (size_t)slot * nl;
-  const double2* C1 = a.C1 + (size_t)slot * nl;
-  // per-candidate scratch: Acol (n x l) | B (n x l) | W (l x l) | H | Z | Y (p x p each, p <= l)
-  double2* Ac = a.work + (size_t)cand * (2 * nl + 4 * (size_t)l * l);
+  const double2* C0 = a.C0 + rg.c_off;
+  const double2* C1 = a.C1 + rg.c_off;
+  // per-disk scratch: Acol (n x l) | B (n x l) | W (l x l) | H | Z | Y (p x p each, p <= l)
+  double2* Ac = a.bwork + rg.w_off;
   double2* B = Ac + nl;
   double2* W = B + nl;
   double2* H = W + (size_t)l * l;
@@ -303,14 +311,14 @@ __global__ void __launch_bounds__(BT) k_beyn(BeynArgs a) {
     int p = 0;
     for (int k = 0; k < l; ++k) {
       const double s = sm.sig[sm.perm[k]];
-      a.sigma[(size_t)cand * l + k] = s;
+      a.sigma[ol + k] = s;
       if (s > a.tol_svd) ++p;
     }
     sm.p = p;
     int st = 0;
     if (p >= min(n, l)) st |= PMCIM_RS_SATURATED;
     sm.status = st;
-    a.p[cand] = p;
+    a.p[g] = p;
   }
   __syncthreads();
   const int p = sm.p;
@@ -366,7 +374,7 @@ __global__ void __launch_bounds__(BT) k_beyn(BeynArgs a) {
 
   // ---- 5. eigenvectors v = V0 s, normalised ----
   for (int k = 0; k < p; ++k) {
-    double2* vk = a.vecs + ((size_t)cand * l + k) * n;
+    double2* vk = a.vecs + rg.v_off + (size_t)k * n;
     const double2* sk = Y + (size_t)k * p;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     double best = -1.0;
@@ -412,7 +420,6 @@ __global__ void __launch_bounds__(BT) k_beyn(BeynArgs a) {
 
   // ---- 6. square filter and outputs ----
   if (tid == 0) {
-    const RegionDev rg = a.regions[cand];
     const double h = rg.r / sqrt(2.0);
     int kept_any = 0;
     for (int k = 0; k < l; ++k) {
@@ -422,21 +429,21 @@ __global__ void __launch_bounds__(BT) k_beyn(BeynArgs a) {
         lm = sm.lam[k];
         keep = (lm.x >= rg.cre - h && lm.x < rg.cre + h && lm.y >= rg.cim - h && lm.y < rg.cim + h) ? 1 : 0;
       }
-      a.lam[(size_t)cand * l + k] = lm;
-      a.kept[(size_t)cand * l + k] = keep;
+      a.lam[ol + k] = lm;
+      a.kept[ol + k] = keep;
       kept_any |= keep;
     }
     int st = sm.status;
     if (!kept_any) st |= PMCIM_RS_NO_EIG;
-    a.status[cand] = st;
+    a.status[g] = st;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_beyn(const BeynArgs& a, cudaStream_t s) {
-  if (a.m <= 0) return cudaSuccess;
+cudaError_t launch_beyn(const LevelArgs& a, cudaStream_t s) {
+  if (a.R <= 0) return cudaSuccess;
   const size_t smem = sizeof(BeynSmem);
-  k_beyn<<<a.m, BT, smem, s>>>(a);
+  k_beyn<<<a.R, BT, smem, s>>>(a);
   return cudaGetLastError();
 }

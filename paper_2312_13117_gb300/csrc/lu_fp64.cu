@@ -27,22 +27,35 @@ using namespace lucore;
 // ---------------------------------------------------------------------------
 // Persistent kernel: node g -> X_g = T(z_g)^{-1} V.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(THREADS, 2) k_factor_solve_fp64(FactorArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  LuSmem& sm = *reinterpret_cast<LuSmem*>(smem_raw);
-  const int tid = threadIdx.x;
-  const ProblemDesc& P = a.prob;
-  const int n = P.n, l = a.l, ncols = n + l;
-  double2* M = a.work + (size_t)blockIdx.x * n * ncols;
-  int* piv = a.piv + (size_t)blockIdx.x * n;
+// Shared memory of the node kernel: the LU tiles plus the node's problem.
+struct NodeSmem {
+  LuSmem lu;
+  ProblemDev P;
+  int item;
+};
 
-  for (int node = blockIdx.x; node < a.n_nodes; node += gridDim.x) {
-    const int g = a.node_region[node];
-    const RegionDev rg = a.regions[g];
-    const int j = node - rg.node_off;
+__global__ void __launch_bounds__(THREADS, 2) k_factor_solve_fp64(NodeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  NodeSmem& sm = *reinterpret_cast<NodeSmem*>(smem_raw);
+  const int tid = threadIdx.x;
+  double2* M = reinterpret_cast<double2*>(a.work + (size_t)blockIdx.x * a.slot_bytes);
+  int* piv = a.piv + (size_t)blockIdx.x * a.max_n;
+
+  for (;;) {
+    // largest-first list, handed out by an atomic counter (no waiting on other CTAs)
+    if (tid == 0) sm.item = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int idx = sm.item;
+    if (idx >= a.n_items) break;
+    const NodeItem it = a.items[idx];
+    const RegionDev rg = a.regions[it.region];
+    load_problem(&sm.P, a.probs + rg.prob);
+    __syncthreads();
+    const ProblemDev& P = sm.P;
+    const int n = P.n, l = P.l, ncols = n + l;
     double2 z, w;
-    node_weight(rg.cre, rg.cim, rg.r, rg.N, j, &z, &w);
-    if (tid < P.K) sm.fz[tid] = eval_f(P.term[tid], z);
+    node_weight(rg.cre, rg.cim, rg.r, rg.N, it.j, &z, &w);
+    if (tid < P.K) sm.lu.fz[tid] = eval_f(P.term[tid], z);
     __syncthreads();
 
     // assemble [T(z_j) | V]
@@ -53,21 +66,21 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_fp64(FactorArgs a) 
         double2 v = make_double2(0.0, 0.0);
         for (int k = 0; k < P.K; ++k) {
           const TermDesc& t = P.term[k];
-          if (t.dense) cfma(v, sm.fz[k], a.A[(size_t)t.mat_index * nn + e]);
-          else if (row == col) cfma(v, sm.fz[k], t.id);
+          if (t.dense) cfma(v, sm.lu.fz[k], P.A[(size_t)t.mat_index * nn + e]);
+          else if (row == col) cfma(v, sm.lu.fz[k], t.id);
         }
         M[e] = v;
       }
     }
-    for (size_t e = tid; e < (size_t)n * l; e += THREADS) M[nn + e] = a.V[e];
+    for (size_t e = tid; e < (size_t)n * l; e += THREADS) M[nn + e] = P.V[e];
     __syncthreads();
 
-    const int info = cta_lu(M, n, ncols, piv, sm);
-    cta_back_subst(M, n, l, sm);
+    const int info = cta_lu(M, n, ncols, piv, sm.lu);
+    cta_back_subst(M, n, l, sm.lu);
 
-    double2* Xo = a.X + (size_t)node * n * l;
+    double2* Xo = a.X + rg.x_off + (size_t)it.j * n * l;
     for (size_t e = tid; e < (size_t)n * l; e += THREADS) Xo[e] = M[nn + e];
-    if (tid == 0) a.node_info[node] = info;
+    if (tid == 0) a.node_info[rg.node_off + it.j] = info;
     __syncthreads();
   }
 }
@@ -78,6 +91,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_fp64(FactorArgs a) 
 // ---------------------------------------------------------------------------
 struct VerifySmem {
   LuSmem lu;
+  ProblemDev P;
   double2 red2[THREADS / 32];
   double red[THREADS / 32];
   double2 bc;
@@ -142,20 +156,22 @@ __device__ double vec_norm(const double2* __restrict__ x, int n, VerifySmem& sm)
   return sqrt(block_sum(s, sm.red));
 }
 
-__global__ void __launch_bounds__(THREADS, 2) k_verify_fp64(VerifyArgs a) {
+__global__ void __launch_bounds__(THREADS, 2) k_verify_fp64(ValueArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   VerifySmem& sm = *reinterpret_cast<VerifySmem*>(smem_raw);
   const int tid = threadIdx.x;
-  const ProblemDesc& P = a.prob;
-  const int n = P.n;
-  const size_t nn = (size_t)n * n;
-  double2* M = a.work + (size_t)blockIdx.x * nn;
-  int* piv = a.piv + (size_t)blockIdx.x * n;
-  double2* x = a.vec + (size_t)blockIdx.x * 3 * n;
-  double2* wv = x + n;
-  double2* yv = x + 2 * n;
+  double2* M = a.work + (size_t)blockIdx.x * a.max_n * a.max_n;
+  int* piv = a.piv + (size_t)blockIdx.x * a.max_n;
+  double2* x = a.vec + (size_t)blockIdx.x * 3 * a.max_n;
 
   for (int it = blockIdx.x; it < a.m; it += gridDim.x) {
+    load_problem(&sm.P, a.probs + a.prob_of[it]);
+    __syncthreads();
+    const ProblemDev& P = sm.P;
+    const int n = P.n;
+    const size_t nn = (size_t)n * n;
+    double2* wv = x + n;
+    double2* yv = x + 2 * n;
     const double2 lam = a.lam[it];
     if (tid < P.K) sm.lu.fz[tid] = eval_f(P.term[tid], lam);
     __syncthreads();
@@ -166,7 +182,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_verify_fp64(VerifyArgs a) {
         double2 v = make_double2(0.0, 0.0);
         for (int k = 0; k < P.K; ++k) {
           const TermDesc& t = P.term[k];
-          if (t.dense) cfma(v, sm.lu.fz[k], a.A[(size_t)t.mat_index * nn + e]);
+          if (t.dense) cfma(v, sm.lu.fz[k], P.A[(size_t)t.mat_index * nn + e]);
           else if (row == col) cfma(v, sm.lu.fz[k], t.id);
         }
         M[e] = v;
@@ -218,7 +234,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_verify_fp64(VerifyArgs a) {
       smin = 1.0 / rho;
     }
     if (tid == 0) {
-      a.sigma_min[it] = smin;
+      a.sigma[it] = smin;
       double thr = a.tol_verify * fmax(1.0, fro / sqrt((double)n));
       a.accept[it] = (smin <= thr) ? 1 : 0;
     }
@@ -236,20 +252,23 @@ int factor_slots_fp64(int n, int l) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   return 2 * (sms > 0 ? sms : 1);
 }
-size_t factor_smem_fp64() { return sizeof(LuSmem); }
-int verify_slots_fp64(int n) { return factor_slots_fp64(n, 0); }
 
-cudaError_t launch_factor_solve_fp64(const FactorArgs& a, cudaStream_t s) {
-  if (a.n_nodes <= 0) return cudaSuccess;
-  const size_t smem = sizeof(LuSmem);
-  cudaError_t e = cudaFuncSetAttribute(k_factor_solve_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int grid = a.slots < a.n_nodes ? a.slots : a.n_nodes;
+cudaError_t prepare_factor_fp64() {
+  return cudaFuncSetAttribute(k_factor_solve_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(NodeSmem));
+}
+
+// Launch only; prepare_factor_fp64() must have set the shared-memory limit (it
+// is not called here so that the launch can be captured into a graph).
+cudaError_t launch_factor_solve_fp64(const NodeArgs& a, cudaStream_t s) {
+  if (a.n_items <= 0) return cudaSuccess;
+  const size_t smem = sizeof(NodeSmem);
+  int grid = a.slots < a.n_items ? a.slots : a.n_items;
   k_factor_solve_fp64<<<grid, THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_verify_fp64(const VerifyArgs& a, cudaStream_t s) {
+cudaError_t launch_verify_fp64(const ValueArgs& a, cudaStream_t s) {
   if (a.m <= 0) return cudaSuccess;
   const size_t smem = sizeof(VerifySmem);
   cudaError_t e = cudaFuncSetAttribute(k_verify_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

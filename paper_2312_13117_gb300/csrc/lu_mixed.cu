@@ -44,8 +44,10 @@ union MixedSmemU {
 
 struct MixedSmem {
   MixedSmemU u;
+  ProblemDev P;
   double2 fz[PMCIM_MAX_TERMS];
   double red[THREADS / 32];
+  int item;
 };
 
 __device__ double block_max(double v, double* red) {
@@ -59,10 +61,9 @@ __device__ double block_max(double v, double* red) {
 }
 
 // R = V - sum_k f_k(z) A_k X  (FP64), R and X column-major n x l.
-__device__ void residual_fp64(const MixedArgs& a, const double2* __restrict__ X, double2* __restrict__ R,
-                              MixedSmem& sm) {
-  const ProblemDesc& P = a.prob;
-  const int n = P.n, l = a.l;
+__device__ void residual_fp64(const double2* __restrict__ X, double2* __restrict__ R, MixedSmem& sm) {
+  const ProblemDev& P = sm.P;
+  const int n = P.n, l = P.l;
   const int tid = threadIdx.x;
   const size_t nn = (size_t)n * n;
   const int tx = tid & 63, ty = tid >> 6;
@@ -80,7 +81,7 @@ __device__ void residual_fp64(const MixedArgs& a, const double2* __restrict__ X,
           const int row = r0 + tx + 64 * i, c = c0 + ty + 4 * q;
           double2 v = make_double2(0.0, 0.0);
           if (row < n && c < l) {
-            v = a.V[(size_t)c * n + row];
+            v = P.V[(size_t)c * n + row];
             cfms(v, idsum, X[(size_t)c * n + row]);
           }
           acc[i][q] = v;
@@ -88,7 +89,7 @@ __device__ void residual_fp64(const MixedArgs& a, const double2* __restrict__ X,
       for (int k = 0; k < P.K; ++k) {
         const TermDesc& t = P.term[k];
         if (!t.dense) continue;
-        const double2* Ak = a.A + (size_t)t.mat_index * nn;
+        const double2* Ak = P.A + (size_t)t.mat_index * nn;
         const double2 fk = sm.fz[k];
         for (int k0 = 0; k0 < n; k0 += RT_K) {
           __syncthreads();
@@ -132,8 +133,8 @@ __device__ void residual_fp64(const MixedArgs& a, const double2* __restrict__ X,
 }
 
 // T(z_j) into the FP32 matrix (rounded) or, for the fallback, the FP64 matrix.
-__device__ void assemble(const MixedArgs& a, MixedSmem& sm, float2* M32, double2* M64) {
-  const ProblemDesc& P = a.prob;
+__device__ void assemble(MixedSmem& sm, float2* M32, double2* M64) {
+  const ProblemDev& P = sm.P;
   const int n = P.n;
   const size_t nn = (size_t)n * n;
   for (int col = 0; col < n; ++col) {
@@ -142,7 +143,7 @@ __device__ void assemble(const MixedArgs& a, MixedSmem& sm, float2* M32, double2
       double2 v = make_double2(0.0, 0.0);
       for (int k = 0; k < P.K; ++k) {
         const TermDesc& t = P.term[k];
-        if (t.dense) cfma(v, sm.fz[k], a.A[(size_t)t.mat_index * nn + e]);
+        if (t.dense) cfma(v, sm.fz[k], P.A[(size_t)t.mat_index * nn + e]);
         else if (row == col) cfma(v, sm.fz[k], t.id);
       }
       if (M32) M32[e] = make_float2((float)v.x, (float)v.y);
@@ -165,33 +166,40 @@ struct PhaseClock {
   }
 };
 
-__global__ void __launch_bounds__(THREADS, 2) k_factor_solve_mixed(MixedArgs a) {
+__global__ void __launch_bounds__(THREADS, 2) k_factor_solve_mixed(NodeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   MixedSmem& sm = *reinterpret_cast<MixedSmem*>(smem_raw);
   const int tid = threadIdx.x;
-  const ProblemDesc& P = a.prob;
-  const int n = P.n, l = a.l, ncols = n + l;
-  const size_t nn = (size_t)n * n, nl = (size_t)n * l;
   char* slot = a.work + (size_t)blockIdx.x * a.slot_bytes;
   float2* M32 = reinterpret_cast<float2*>(slot);
   double2* M64 = reinterpret_cast<double2*>(slot);  // fallback only; aliases M32
-  double2* R = reinterpret_cast<double2*>(slot + mixed_residual_offset(n, l));
-  int* piv = a.piv + (size_t)blockIdx.x * n;
+  int* piv = a.piv + (size_t)blockIdx.x * a.max_n;
   PhaseClock pc(a.phase ? a.phase + (size_t)blockIdx.x * PMCIM_PHASES : nullptr);
 
-  for (int node = blockIdx.x; node < a.n_nodes; node += gridDim.x) {
-    const int g = a.node_region[node];
-    const RegionDev rg = a.regions[g];
+  for (;;) {
+    // largest-first list, handed out by an atomic counter (no waiting on other CTAs)
+    if (tid == 0) sm.item = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int idx = sm.item;
+    if (idx >= a.n_items) break;
+    const NodeItem it = a.items[idx];
+    const RegionDev rg = a.regions[it.region];
+    load_problem(&sm.P, a.probs + rg.prob);
+    __syncthreads();
+    const ProblemDev& P = sm.P;
+    const int n = P.n, l = P.l, ncols = n + l;
+    const size_t nn = (size_t)n * n, nl = (size_t)n * l;
+    double2* R = reinterpret_cast<double2*>(slot + mixed_residual_offset(n, l));
     double2 z, w;
-    node_weight(rg.cre, rg.cim, rg.r, rg.N, node - rg.node_off, &z, &w);
+    node_weight(rg.cre, rg.cim, rg.r, rg.N, it.j, &z, &w);
     if (tid < P.K) sm.fz[tid] = eval_f(P.term[tid], z);
     __syncthreads();
-    double2* X = a.X + (size_t)node * nl;
+    double2* X = a.X + rg.x_off + (size_t)it.j * nl;
     pc.mark(6);
 
     // 1-2: FP32 factorisation and first solution
-    assemble(a, sm, M32, nullptr);
-    for (size_t e = tid; e < nl; e += THREADS) M32[nn + e] = make_float2((float)a.V[e].x, (float)a.V[e].y);
+    assemble(sm, M32, nullptr);
+    for (size_t e = tid; e < nl; e += THREADS) M32[nn + e] = make_float2((float)P.V[e].x, (float)P.V[e].y);
     __syncthreads();
     pc.mark(0);
     int info = cta_lu(M32, n, ncols, piv, sm.u.lu32);
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_mixed(MixedArgs a) 
       bool conv = false;
       // 3: refinement
       for (int s = 1; s <= a.max_sweeps && ok; ++s) {
-        residual_fp64(a, X, R, sm);
+        residual_fp64(X, R, sm);
         pc.mark(3);
         double rm = 0.0;
         for (size_t e = tid; e < nl; e += THREADS) rm = fmax(rm, fmax(fabs(R[e].x), fabs(R[e].y)));
@@ -249,15 +257,15 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_mixed(MixedArgs a) 
     if (!ok) {
       // 4: FP64 fallback in the same workspace
       __syncthreads();
-      assemble(a, sm, nullptr, M64);
-      for (size_t e = tid; e < nl; e += THREADS) M64[nn + e] = a.V[e];
+      assemble(sm, nullptr, M64);
+      for (size_t e = tid; e < nl; e += THREADS) M64[nn + e] = P.V[e];
       __syncthreads();
       info = cta_lu(M64, n, ncols, piv, sm.u.lu64);
       cta_back_subst(M64, n, l, sm.u.lu64);
       for (size_t e = tid; e < nl; e += THREADS) X[e] = M64[nn + e];
       pc.mark(5);
     }
-    if (tid == 0) a.node_info[node] = info | (sweeps << 24) | (ok ? 0 : (1 << 30));
+    if (tid == 0) a.node_info[rg.node_off + it.j] = info | (sweeps << 24) | (ok ? 0 : (1 << 30));
     __syncthreads();
   }
 }
@@ -273,12 +281,16 @@ size_t mixed_slot_bytes(int n, int l) {
   return (b + 255) & ~(size_t)255;
 }
 
-cudaError_t launch_factor_solve_mixed(const MixedArgs& a, cudaStream_t s) {
-  if (a.n_nodes <= 0) return cudaSuccess;
+cudaError_t prepare_factor_mixed() {
+  return cudaFuncSetAttribute(k_factor_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(MixedSmem));
+}
+
+// Launch only; prepare_factor_mixed() must have set the shared-memory limit.
+cudaError_t launch_factor_solve_mixed(const NodeArgs& a, cudaStream_t s) {
+  if (a.n_items <= 0) return cudaSuccess;
   const size_t smem = sizeof(MixedSmem);
-  cudaError_t e = cudaFuncSetAttribute(k_factor_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int grid = a.slots < a.n_nodes ? a.slots : a.n_nodes;
+  int grid = a.slots < a.n_items ? a.slots : a.n_items;
   k_factor_solve_mixed<<<grid, THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -144,137 +144,131 @@ __device__ __forceinline__ void node_weight(double cre, double cim, double r, in
   *w = make_double2(h * c, h * s);
 }
 
-// Work item of the factor/solve kernels: one node of one disk.
+// ---------------------------------------------------------------------------
+// Batched work description. One launch can carry nodes of many problems of
+// different sizes: every disk names its problem and the offsets of its blocks.
+// ---------------------------------------------------------------------------
+struct ProblemDev {
+  int32_t n, K, l, n_dense;
+  const double2* A;  // n_dense * n * n, column-major, in term order
+  const double2* V;  // n x l probe block
+  TermDesc term[PMCIM_MAX_TERMS];
+};
+
 struct RegionDev {
   double cre, cim, r;
   int32_t N;
-  int32_t node_off;  // index of node 0 of this disk in the node list of the launch
+  int32_t prob;      // index into the problem table
+  int32_t node_off;  // index of node 0 in the launch's node_info array
+  int32_t gate;      // 1: Beyn runs only when the indicator marks a candidate
+  int64_t x_off;     // double2 offset of node 0's solution in X (node j at x_off + j n l)
+  int64_t c_off;     // double2 offset of the disk's C0 / C1 blocks (n l)
+  int64_t p_off;     // offset of the disk's P f blocks (n)
+  int64_t w_off;     // double2 offset of the disk's Beyn scratch (2 n l + 4 l^2)
+  int64_t v_off;     // double2 offset of the disk's eigenvector block (n l)
 };
+
+struct NodeItem {
+  int32_t region;
+  int32_t j;
+};
+
+// Copy a problem descriptor into shared memory (all threads; caller syncs).
+__device__ __forceinline__ void load_problem(ProblemDev* dst, const ProblemDev* src) {
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(ProblemDev) / sizeof(int)); i += blockDim.x) d[i] = s[i];
+}
 
 // ---------------------------------------------------------------------------
 // Launchers (host side), implemented in the .cu files.
 // ---------------------------------------------------------------------------
-struct FactorArgs {
-  ProblemDesc prob;
-  const double2* A;         // device, n_dense * n * n
-  const double2* V;         // device, n x l
-  int l;
-  const RegionDev* regions; // device
-  const int32_t* node_region;  // device, per node: region index
-  int n_nodes;
-  double2* X;               // device, n_nodes * n * l
-  int32_t* node_info;       // device, per node: 0 or 1 + first zero-pivot column
-  double2* work;            // device, slots * n * (n + l)
-  int32_t* piv;             // device, slots * n
-  int slots;
-};
-cudaError_t launch_factor_solve_fp64(const FactorArgs& a, cudaStream_t s);
-int factor_slots_fp64(int n, int l);
-size_t factor_smem_fp64();
-
-struct MixedArgs {
-  ProblemDesc prob;
-  const double2* A;
-  const double2* V;
-  int l;
+struct NodeArgs {
+  const ProblemDev* probs;
   const RegionDev* regions;
-  const int32_t* node_region;
-  int n_nodes;
-  double2* X;               // FP64 solutions, n_nodes * n * l
-  int32_t* node_info;       // bits 0-23: 0 or 1 + zero-pivot column; 24-29: sweeps; 30: FP64 fallback
+  const NodeItem* items;    // in scheduling order (largest n first)
+  int n_items;
+  int* counter;             // work counter, zero before the launch
+  double2* X;
+  int32_t* node_info;       // FP64: 0 or 1 + zero-pivot column. Mixed: bits 0-23 the same,
+                            // 24-29 sweeps run, 30 FP64 fallback
   char* work;               // slots * slot_bytes
   size_t slot_bytes;
-  int32_t* piv;             // slots * n
+  int32_t* piv;             // slots * max_n
+  int max_n;
   int slots;
   int max_sweeps;
   double tol_ir;
-  unsigned long long* phase;  // NULL, or slots * PMCIM_PHASES clock64 counters
+  unsigned long long* phase;  // NULL, or slots * PMCIM_PHASES clock64 counters (mixed kernel)
 };
+cudaError_t prepare_factor_fp64();   // shared-memory limits; call outside graph capture
+cudaError_t prepare_factor_mixed();
+cudaError_t launch_factor_solve_fp64(const NodeArgs& a, cudaStream_t s);
+cudaError_t launch_factor_solve_mixed(const NodeArgs& a, cudaStream_t s);
+int factor_slots_fp64(int n, int l);
 // Phases of the precision-form node kernel timed with clock64 when profiling.
-#define PMCIM_PHASES 8  // assemble, LU, first solve, residual, correction solve, fallback, other
+#define PMCIM_PHASES 8  // assemble, LU, first solve, residual, correction solve, fallback, set-up, unused
 __host__ __device__ inline size_t mixed_residual_offset(int n, int l) {
   return (((size_t)n * (n + l) * 8) + 255) & ~(size_t)255;
 }
 size_t mixed_slot_bytes(int n, int l);
-cudaError_t launch_factor_solve_mixed(const MixedArgs& a, cudaStream_t s);
 
-struct ReduceArgs {
-  const double2* X;
-  int n, l;
+struct LevelArgs {
+  const ProblemDev* probs;
   const RegionDev* regions;
   int R;
-  double2* C0;       // R * n * l
-  double2* C1;       // R * n * l
-  double2* pf_half;  // R * n
-  double* pf_abs;    // R * n
-};
-cudaError_t launch_reduce_moments(const ReduceArgs& a, cudaStream_t s);
-
-struct IndicatorArgs {
-  const double2* C0;
-  const double2* pf_half;
-  const double* pf_abs;
-  int n, l, R;
+  int max_nl;
+  const double2* X;
+  double2* C0;
+  double2* C1;
+  double2* pf_half;
+  double* pf_abs;
   double tol_ind;
+  double tol_svd;
   double* ind;
   double* pf_norm;
   double* pf_scale;
-  uint8_t* candidate;
+  uint8_t* cand;
+  // Beyn outputs; sigma, lam, kept are indexed g * PMCIM_MAX_L + k
+  double2* bwork;
+  double* sigma;
+  int32_t* p;               // -1 when the disk was gated out
+  double2* lam;
+  double2* vecs;            // at region.v_off
+  uint8_t* kept;
+  int32_t* status;
 };
-cudaError_t launch_indicator(const IndicatorArgs& a, cudaStream_t s);
+cudaError_t launch_reduce_moments(const LevelArgs& a, cudaStream_t s);
+cudaError_t launch_indicator(const LevelArgs& a, cudaStream_t s);
+cudaError_t launch_beyn(const LevelArgs& a, cudaStream_t s);
 
-struct BeynArgs {
-  const double2* C0;         // per region slot, n x l
-  const double2* C1;
-  const int32_t* slot_of;    // per candidate: slot index into C0/C1
-  const RegionDev* regions;  // per candidate: geometry
-  int n, l, m;               // m candidates
-  double tol_svd;
-  double2* work;             // m * n * l  (rotated columns)
-  double* sigma;             // m * l (descending)
-  int32_t* p;                // m
-  double2* lam;              // m * l
-  double2* vecs;             // m * n * l
-  uint8_t* kept;             // m * l
-  int32_t* status;           // m
-};
-cudaError_t launch_beyn(const BeynArgs& a, cudaStream_t s);
-
-struct VerifyArgs {
-  ProblemDesc prob;
-  const double2* A;
-  const double2* lam;        // m
+struct ValueArgs {
+  const ProblemDev* probs;
+  const int32_t* prob_of;   // per value
+  const double2* lam;
+  const int64_t* vec_off;   // certificate: double2 offset of the value's unit eigenvector
+  const double2* vecs;
   int m;
   double tol_verify;
-  double* sigma_min;         // m
-  uint8_t* accept;           // m
-  double2* work;             // slots * n * n
-  double2* vec;              // slots * 3 * n
-  int32_t* piv;              // slots * n
+  double* sigma;
+  uint8_t* accept;
+  double2* work;            // verify: slots * max_n * max_n
+  double2* vec;             // verify: slots * 3 * max_n
+  int32_t* piv;             // verify: slots * max_n
   int slots;
+  int max_n;
 };
-cudaError_t launch_verify_fp64(const VerifyArgs& a, cudaStream_t s);
-int verify_slots_fp64(int n);
+cudaError_t launch_certify(const ValueArgs& a, cudaStream_t s);
+cudaError_t launch_verify_fp64(const ValueArgs& a, cudaStream_t s);
 
-struct CertifyArgs {
-  ProblemDesc prob;
-  const double2* A;
-  const double2* lam;        // m
-  const double2* vecs;       // m * n, unit eigenvectors
-  int m;
-  double tol_verify;
-  double* cert;              // m: ||T(lambda) v|| / ||v||
-  uint8_t* certified;        // m: cert <= tol_verify * max(1, ||T||_F / sqrt(n))
+struct VecItem {
+  int64_t src;   // double2 offset in the source
+  int64_t dst;   // double2 offset in the destination
+  int32_t n;
+  int32_t pad;
 };
-cudaError_t launch_certify(const CertifyArgs& a, cudaStream_t s);
-
-struct GatherArgs {
-  const double2* vecs;       // m * n * l (beyn outputs)
-  const int32_t* src;        // count: cand * l + k
-  double2* dst;              // count * n
-  int n, l, count;
-};
-cudaError_t launch_gather_vecs(const GatherArgs& a, cudaStream_t s);
+cudaError_t launch_gather_vecs(const double2* src, double2* dst, const VecItem* items, int count, int max_n,
+                               cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Launch accounting (api.cu): count every launch; with timing on, bracket it

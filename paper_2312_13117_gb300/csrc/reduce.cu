@@ -13,16 +13,18 @@ namespace {
 
 constexpr int RT = 256;
 
-__global__ void __launch_bounds__(RT) k_reduce_moments(ReduceArgs a) {
+__global__ void __launch_bounds__(RT) k_reduce_moments(LevelArgs a) {
   const int g = blockIdx.y;
   const RegionDev rg = a.regions[g];
-  const int nl = a.n * a.l;
+  const ProblemDev* P = a.probs + rg.prob;
+  const int n = P->n, l = P->l;
+  const int nl = n * l;
   const int e = blockIdx.x * RT + threadIdx.x;
   if (e >= nl) return;
-  const bool first_col = e < a.n;
+  const bool first_col = e < n;
   double2 c0 = make_double2(0.0, 0.0), c1 = c0, ph = c0;
   double pa = 0.0;
-  const double2* Xg = a.X + (size_t)rg.node_off * nl + e;
+  const double2* Xg = a.X + rg.x_off + e;
   for (int j = 0; j < rg.N; ++j) {
     double2 z, w;
     node_weight(rg.cre, rg.cim, rg.r, rg.N, j, &z, &w);
@@ -34,23 +36,24 @@ __global__ void __launch_bounds__(RT) k_reduce_moments(ReduceArgs a) {
       pa += hypot(w.x, w.y) * hypot(x.x, x.y);
     }
   }
-  const size_t o = (size_t)g * nl + e;
-  a.C0[o] = c0;
-  a.C1[o] = c1;
+  a.C0[rg.c_off + e] = c0;
+  a.C1[rg.c_off + e] = c1;
   if (first_col) {
-    a.pf_half[(size_t)g * a.n + e] = ph;
-    a.pf_abs[(size_t)g * a.n + e] = pa;
+    a.pf_half[rg.p_off + e] = ph;
+    a.pf_abs[rg.p_off + e] = pa;
   }
 }
 
-__global__ void __launch_bounds__(RT) k_indicator(IndicatorArgs a) {
+__global__ void __launch_bounds__(RT) k_indicator(LevelArgs a) {
   __shared__ double red[3][RT / 32];
   const int g = blockIdx.x;
-  const double2* pfN = a.C0 + (size_t)g * a.n * a.l;  // column 0 of C0
-  const double2* pfh = a.pf_half + (size_t)g * a.n;
-  const double* pab = a.pf_abs + (size_t)g * a.n;
+  const RegionDev rg = a.regions[g];
+  const int n = a.probs[rg.prob].n;
+  const double2* pfN = a.C0 + rg.c_off;  // column 0 of C0
+  const double2* pfh = a.pf_half + rg.p_off;
+  const double* pab = a.pf_abs + rg.p_off;
   double s_ratio = 0.0, s_norm = 0.0, s_abs = 0.0;
-  for (int i = threadIdx.x; i < a.n; i += RT) {
+  for (int i = threadIdx.x; i < n; i += RT) {
     const double num = cabs2(pfN[i]);
     const double den = cabs2(pfh[i]);
     s_ratio += num / den;
@@ -68,36 +71,37 @@ __global__ void __launch_bounds__(RT) k_indicator(IndicatorArgs a) {
   if (threadIdx.x == 0) {
     double t0 = 0.0, t1 = 0.0, t2 = 0.0;
     for (int k = 0; k < RT / 32; ++k) { t0 += red[0][k]; t1 += red[1][k]; t2 += red[2][k]; }
-    const double I = sqrt(t0) / sqrt((double)a.n);
+    const double I = sqrt(t0) / sqrt((double)n);
     a.ind[g] = I;
-    if (a.pf_norm) a.pf_norm[g] = sqrt(t1);
-    if (a.pf_scale) a.pf_scale[g] = sqrt(t2);
-    a.candidate[g] = (I > a.tol_ind) ? 1 : 0;
+    a.pf_norm[g] = sqrt(t1);
+    a.pf_scale[g] = sqrt(t2);
+    a.cand[g] = (I > a.tol_ind) ? 1 : 0;
   }
 }
 
-__global__ void k_gather_vecs(GatherArgs a) {
-  const int k = blockIdx.y;
+__global__ void k_gather_vecs(const double2* __restrict__ src, double2* __restrict__ dst,
+                              const VecItem* __restrict__ items) {
+  const VecItem it = items[blockIdx.y];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  const int src = a.src[k];
-  const int cand = src / a.l, col = src % a.l;
-  a.dst[(size_t)k * a.n + i] = a.vecs[((size_t)cand * a.l + col) * a.n + i];
+  if (i >= it.n) return;
+  dst[it.dst + i] = src[it.src + i];
 }
 
 // Verification certificate (pmCIMb step 3): for a candidate lambda with unit
 // eigenvector v, sigma_min(T(lambda)) <= ||T(lambda) v||. One CTA per value
 // forms T(lambda) one column at a time (never stored), accumulating
 // r = T(lambda) v and ||T(lambda)||_F^2, all in FP64.
-__global__ void __launch_bounds__(RT) k_certify(CertifyArgs a) {
+__global__ void __launch_bounds__(RT) k_certify(ValueArgs a) {
+  __shared__ ProblemDev P;
   __shared__ double2 fz[PMCIM_MAX_TERMS];
   __shared__ double red[2][RT / 32];
-  const ProblemDesc& P = a.prob;
+  const int m = blockIdx.x;
+  load_problem(&P, a.probs + a.prob_of[m]);
+  __syncthreads();
   const int n = P.n;
   const size_t nn = (size_t)n * n;
-  const int m = blockIdx.x;
   const double2 lam = a.lam[m];
-  const double2* v = a.vecs + (size_t)m * n;
+  const double2* v = a.vecs + a.vec_off[m];
   if (threadIdx.x < P.K) fz[threadIdx.x] = eval_f(P.term[threadIdx.x], lam);
   __syncthreads();
   double r2 = 0.0, f2 = 0.0;
@@ -107,7 +111,7 @@ __global__ void __launch_bounds__(RT) k_certify(CertifyArgs a) {
       double2 t = make_double2(0.0, 0.0);
       for (int k = 0; k < P.K; ++k) {
         const TermDesc& tk = P.term[k];
-        if (tk.dense) cfma(t, fz[k], a.A[(size_t)tk.mat_index * nn + (size_t)col * n + row]);
+        if (tk.dense) cfma(t, fz[k], P.A[(size_t)tk.mat_index * nn + (size_t)col * n + row]);
         else if (row == col) cfma(t, fz[k], tk.id);
       }
       cfma(r, t, v[col]);
@@ -126,35 +130,36 @@ __global__ void __launch_bounds__(RT) k_certify(CertifyArgs a) {
     for (int k = 0; k < RT / 32; ++k) { tr += red[0][k]; tf += red[1][k]; }
     for (int i = 0; i < n; ++i) vv += cabs2(v[i]);
     const double cert = sqrt(tr) / sqrt(vv);
-    a.cert[m] = cert;
-    a.certified[m] = (cert <= a.tol_verify * fmax(1.0, sqrt(tf) / sqrt((double)n))) ? 1 : 0;
+    a.sigma[m] = cert;
+    a.accept[m] = (cert <= a.tol_verify * fmax(1.0, sqrt(tf) / sqrt((double)n))) ? 1 : 0;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_certify(const CertifyArgs& a, cudaStream_t s) {
+cudaError_t launch_certify(const ValueArgs& a, cudaStream_t s) {
   if (a.m <= 0) return cudaSuccess;
   k_certify<<<a.m, RT, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_moments(const ReduceArgs& a, cudaStream_t s) {
+cudaError_t launch_reduce_moments(const LevelArgs& a, cudaStream_t s) {
   if (a.R <= 0) return cudaSuccess;
-  dim3 grid((a.n * a.l + RT - 1) / RT, a.R);
+  dim3 grid((a.max_nl + RT - 1) / RT, a.R);
   k_reduce_moments<<<grid, RT, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_indicator(const IndicatorArgs& a, cudaStream_t s) {
+cudaError_t launch_indicator(const LevelArgs& a, cudaStream_t s) {
   if (a.R <= 0) return cudaSuccess;
   k_indicator<<<a.R, RT, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_vecs(const GatherArgs& a, cudaStream_t s) {
-  if (a.count <= 0) return cudaSuccess;
-  dim3 grid((a.n + 127) / 128, a.count);
-  k_gather_vecs<<<grid, 128, 0, s>>>(a);
+cudaError_t launch_gather_vecs(const double2* src, double2* dst, const VecItem* items, int count, int max_n,
+                               cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  dim3 grid((max_n + 127) / 128, count);
+  k_gather_vecs<<<grid, 128, 0, s>>>(src, dst, items);
   return cudaGetLastError();
 }

@@ -22,12 +22,12 @@ STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: 
 
 RS_CANDIDATE, RS_SATURATED, RS_SPLIT, RS_SINGULAR_NODE, RS_IR_FALLBACK, RS_NO_EIG = 1, 2, 4, 8, 16, 32
 F_MONOMIAL, F_EXP_NEG = 0, 1
-PREC_FP64, PREC_FP32_IR = 0, 1
+PREC_FP64, PREC_FP32_IR, PREC_AUTO = 0, 1, 2
 
 EXPORTS = ["pmcim_default_options", "pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments",
            "pmcim_indicator", "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_status_string",
            "pmcim_last_error", "pmcim_profile_enable", "pmcim_profile_reset", "pmcim_profile_read",
-           "pmcim_solve_points_noalloc"]
+           "pmcim_solve_points_noalloc", "pmcim_batch_solve"]
 
 KERNELS = ["factor_fp64", "reduce", "indicator", "beyn", "verify", "gather", "factor_fp32", "refine"]
 
@@ -48,6 +48,11 @@ class pmcim_options(C.Structure):
                 ("reserved", C.c_int32), ("cuda_stream", C.c_void_p)]
 
 
+class pmcim_batch_item(C.Structure):
+    _fields_ = [("problem", C.c_void_p), ("R", C.c_int32), ("regions", C.c_void_p), ("l", C.c_int32),
+                ("V", C.c_void_p)]
+
+
 class pmcim_profile(C.Structure):
     _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8), ("mixed_phase_cycles", C.c_double * 8)]
 
@@ -56,7 +61,7 @@ class pmcim_stats(C.Structure):
     _fields_ = [("solves", C.c_int64), ("regions", C.c_int32), ("candidates", C.c_int32),
                 ("splits", C.c_int32), ("unverified", C.c_int32), ("ir_fallbacks", C.c_int32),
                 ("singular_nodes", C.c_int32), ("ir_sweeps", C.c_int64), ("certified", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("graphs", C.c_int32), ("tuned_fp64", C.c_int32), ("tuned_mixed", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -97,24 +102,27 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pmcim_profile_read.restype = None
     lib.pmcim_solve_points_noalloc.argtypes = [I32, I32, C.POINTER(pmcim_fterm), C.POINTER(C.c_uint8), VP, I32,
                                                VP, I32, VP, VP, VP, VP]
+    lib.pmcim_batch_solve.argtypes = [I32, C.POINTER(pmcim_batch_item), C.POINTER(pmcim_options), I32, VP, VP, VP,
+                                      VP, VP, C.POINTER(pmcim_stats)]
     for name in ("pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments", "pmcim_indicator",
-                 "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_solve_points_noalloc"):
+                 "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_solve_points_noalloc", "pmcim_batch_solve"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
 
 
 class PmcimError(RuntimeError):
-    def __init__(self, code: int, where: str):
+    def __init__(self, code: int, where: str, count: int = 0):
         lib = load()
         msg = lib.pmcim_last_error().decode()
         super().__init__("%s failed: %s (%s) %s" % (where, STATUS.get(code, code), code, msg))
         self.code = code
+        self.count = count
 
 
-def _check(code: int, where: str):
+def _check(code: int, where: str, count=None):
     if code != PMCIM_OK:
-        raise PmcimError(code, where)
+        raise PmcimError(code, where, int(count[0]) if count is not None else 0)
 
 
 # ---------------------------------------------------------------------------
@@ -269,6 +277,14 @@ class Problem:
         return ind, cand.astype(bool), pn, ps
 
     def beyn(self, regions, V, cap=None, opt=None, want_vecs=True):
+        try:
+            return self._beyn(regions, V, cap, opt, want_vecs)
+        except PmcimError as e:  # capacity: the library reported the count; retry at that size
+            if e.code != -5 or cap is not None:
+                raise
+            return self._beyn(regions, V, e.count, opt, want_vecs)
+
+    def _beyn(self, regions, V, cap, opt, want_vecs):
         lib = load()
         V = _colmajor_c128(V)
         R, l, n = len(regions), V.shape[1], self.n
@@ -280,7 +296,7 @@ class Problem:
         rst = np.zeros(max(R, 1), np.int32)
         opt = opt or options()
         _check(lib.pmcim_beyn(self.handle, C.byref(opt), R, regions_array(regions), l, _ptr(V), cap, _ptr(lam),
-                              _ptr(vecs), _ptr(rof), _ptr(cnt), _ptr(rst)), "pmcim_beyn")
+                              _ptr(vecs), _ptr(rof), _ptr(cnt), _ptr(rst)), "pmcim_beyn", cnt)
         k = int(cnt[0])
         return lam[:k], (vecs[:k].T if want_vecs else None), rof[:k], rst[:R]
 
@@ -296,6 +312,14 @@ class Problem:
 
     def solve(self, regions, V, cap=None, opt=None, want_vecs=True):
         """Whole pmCIMb: returns dict(lam, vecs, sigma_min, region_of, ind, status, stats)."""
+        try:
+            return self._solve(regions, V, cap, opt, want_vecs)
+        except PmcimError as e:  # capacity: the library reported the count; retry at that size
+            if e.code != -5 or cap is not None:
+                raise
+            return self._solve(regions, V, e.count, opt, want_vecs)
+
+    def _solve(self, regions, V, cap, opt, want_vecs):
         lib = load()
         V = _colmajor_c128(V)
         R, l, n = len(regions), V.shape[1], self.n
@@ -311,7 +335,49 @@ class Problem:
         opt = opt or options()
         _check(lib.pmcim_solve(self.handle, C.byref(opt), R, regions_array(regions), l, _ptr(V), cap, _ptr(lam),
                                _ptr(vecs), _ptr(sig), _ptr(rof), _ptr(cnt), _ptr(ind), _ptr(rst), C.byref(st)),
-               "pmcim_solve")
+               "pmcim_solve", cnt)
         k = int(cnt[0])
         return dict(lam=lam[:k], vecs=(vecs[:k].T if want_vecs else None), sigma_min=sig[:k], region_of=rof[:k],
                     ind=ind[:R], status=rst[:R], stats=st.as_dict())
+
+
+def batch_solve(problems, regions_list, V_list, cap=None, opt=None):
+    """pmcim_batch_solve over Problem handles with their disks and probe blocks.
+
+    Returns dict(lam, sigma_min, problem_of, region_of, stats).
+    """
+    try:
+        return _batch_solve(problems, regions_list, V_list, cap, opt)
+    except PmcimError as e:  # capacity: the library reported the count; retry at that size
+        if e.code != -5 or cap is not None:
+            raise
+        return _batch_solve(problems, regions_list, V_list, e.count, opt)
+
+
+def _batch_solve(problems, regions_list, V_list, cap, opt):
+    lib = load()
+    P = len(problems)
+    items = (pmcim_batch_item * P)()
+    keep = []
+    for q, (pr, regs, V) in enumerate(zip(problems, regions_list, V_list)):
+        V = _colmajor_c128(V)
+        ra = regions_array(regs)
+        keep += [V, ra]
+        items[q].problem = pr.handle
+        items[q].R = len(regs)
+        items[q].regions = C.cast(ra, C.c_void_p)
+        items[q].l = V.shape[1]
+        items[q].V = _ptr(V)
+    if cap is None:
+        cap = max(64, sum(4 * V.shape[1] * len(r) for r, V in zip(regions_list, V_list)))
+    lam = np.zeros(cap, np.complex128)
+    sig = np.zeros(cap)
+    pof = np.zeros(cap, np.int32)
+    rof = np.zeros(cap, np.int32)
+    cnt = np.zeros(1, np.int32)
+    st = pmcim_stats()
+    opt = opt or options()
+    _check(lib.pmcim_batch_solve(P, items, C.byref(opt), cap, _ptr(lam), _ptr(sig), _ptr(pof), _ptr(rof),
+                                 _ptr(cnt), C.byref(st)), "pmcim_batch_solve", cnt)
+    k = int(cnt[0])
+    return dict(lam=lam[:k], sigma_min=sig[:k], problem_of=pof[:k], region_of=rof[:k], stats=st.as_dict())

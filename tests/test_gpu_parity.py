@@ -385,3 +385,54 @@ def test_mixed_full_size_delay_sampled(pm):
     assert _match_lam(res["lam"], ref.lam) <= LAM_TOL
     assert res["stats"]["ir_fallbacks"] == 0
     P.close()
+
+
+# ---------------------------------------------------------------------------
+# a12: many problems of uneven size in one call
+# ---------------------------------------------------------------------------
+
+def _small_batch(count=6, seed0=1000):
+    out = []
+    for s in range(seed0, seed0 + count):
+        rng = np.random.default_rng(s)
+        n = int(rng.choice([17, 24, 40, 64, 100, 130]))
+        A = [w.complex_gaussian(rng, (n, n)) / math.sqrt(n) for _ in range(3)]
+        prob = w.Problem(n, [(A[d], w.MONOMIAL, d, 0.0) for d in range(3)])
+        side = float(rng.uniform(1.0, 2.5))
+        m = int(rng.integers(1, 4))
+        N = int(rng.choice([16, 32]))
+        regs = w.grid_regions(-side / 2, side / 2, -side / 2, side / 2, m, m, N)
+        V = w.probe_block(rng, n, 6)
+        out.append((prob, regs, V))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32ir", "auto"])
+def test_batch_matches_oracle_per_problem(pm, precision):
+    prec = {"fp64": pm.PREC_FP64, "fp32ir": pm.PREC_FP32_IR, "auto": pm.PREC_AUTO}[precision]
+    batch = _small_batch()
+    handles = [pm.Problem(p.n, p.terms) for (p, _, _) in batch]
+    res = pm.batch_solve(handles, [r for (_, r, _) in batch], [V for (_, _, V) in batch],
+                         opt=pm.options(precision=prec))
+    assert res["stats"]["graphs"] >= 1
+    if precision == "auto":
+        assert res["stats"]["tuned_fp64"] + res["stats"]["tuned_mixed"] == len(batch)
+    for q, (prob, regs, V) in enumerate(batch):
+        ref = o.pmcimb(prob, regs, V)
+        got = res["lam"][res["problem_of"] == q]
+        assert _match_lam(got, ref.lam) <= LAM_TOL, q
+    for h in handles:
+        h.close()
+
+
+def test_batch_equals_single_calls(pm):
+    """The batched path gives each problem the same eigenvalues as a call of its own."""
+    batch = _small_batch(count=4, seed0=2000)
+    handles = [pm.Problem(p.n, p.terms) for (p, _, _) in batch]
+    res = pm.batch_solve(handles, [r for (_, r, _) in batch], [V for (_, _, V) in batch])
+    for q, (prob, regs, V) in enumerate(batch):
+        single = handles[q].solve(regs, V)
+        got = res["lam"][res["problem_of"] == q]
+        assert _match_lam(got, single["lam"]) <= 1e-13
+    for h in handles:
+        h.close()

@@ -54,6 +54,7 @@ extern "C" {
 #define PMCIM_RS_SINGULAR_NODE 8  /* an LU met an exactly zero pivot at some node  */
 #define PMCIM_RS_IR_FALLBACK 16   /* refinement did not converge; FP64 re-solve    */
 #define PMCIM_RS_NO_EIG 32        /* candidate disk whose Beyn step kept no value  */
+#define PMCIM_RS_SCREENED 64      /* the learned screen skipped the full indicator */
 
 /* ---- scalar functions f_k ------------------------------------------------ */
 #define PMCIM_F_MONOMIAL 0 /* f(z) = z^degree                                   */
@@ -94,6 +95,16 @@ typedef struct {
   int32_t max_split_depth; /* splits of saturated disks (default 8)                    */
   int32_t reserved;
   void* cuda_stream;       /* cudaStream_t the call is ordered after; NULL = default   */
+  /* learned screen (pmcim_solve / pmcim_batch_solve): NULL = off; else the
+     PMCIM_SCREEN_PARAMS trained parameters (host or device). Every disk first
+     gets the coarse indicators of screen_N nodes (one probe column); a disk
+     whose screen probability is below screen_threshold skips the full
+     indicator and Beyn (status PMCIM_RS_SCREENED); every other disk goes on
+     exactly as without the screen. */
+  const float* screen_params;
+  double screen_threshold;
+  int32_t screen_N;        /* coarse nodes, a multiple of 16 (default 16)            */
+  int32_t reserved2;
 } pmcim_options;
 
 /* Statistics of one pmcim_solve call. */
@@ -110,6 +121,8 @@ typedef struct {
   int32_t graphs;          /* CUDA graphs launched (one per level of disks)      */
   int32_t tuned_fp64;      /* problems the autotuner ran in FP64                 */
   int32_t tuned_mixed;     /* problems the autotuner ran in the precision form   */
+  int32_t screened_out;    /* disks the learned screen skipped                   */
+  int32_t screen_solves;   /* coarse node solves spent on the screen             */
 } pmcim_stats;
 
 typedef struct pmcim_problem_s* pmcim_problem;
@@ -204,6 +217,40 @@ int pmcim_batch_solve(int32_t P, const pmcim_batch_item* items, const pmcim_opti
                       double* lambda, double* sigma_min, int32_t* problem_of, int32_t* region_of,
                       int32_t* count, pmcim_stats* stats);
 
+/* ---- learned screen (no counterpart in the paper; it decides which disks
+   need the full indicator of Eq. 3.1) ------------------------------------
+   Features of a disk: (log10 I_8, log10 I_16, log10 r), with I_M the ratio
+   indicator of Eq. 3.1 on the first M nodes of the disk's trapezoid rule
+   (M divides N). Network: 3 -> 64 -> 64 -> 1, ReLU, sigmoid output, FP32
+   master parameters in the order W1[64][3], b1[64], W2[64][64], b2[64],
+   W3[64], b3; the forward and backward passes use their BF16 rounding with
+   FP32 accumulation. */
+#define PMCIM_SCREEN_PARAMS 4481
+
+/* Indicators I_8, I_16 and I_N (ind3, R x 3) and the features (feats, R x 3
+   floats) of R disks; N must be a multiple of 16; f = V[:,0]. Any output may
+   be NULL. */
+int pmcim_screen_features(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim_region* reg,
+                          int32_t l, const double* V, double* ind3, float* feats);
+
+/* Train on M samples (features row-major M x 3, labels 0/1) with Adam for
+   `epochs` passes in the given order, minibatches of `batch`, class weight
+   pos_weight on the positives. params (PMCIM_SCREEN_PARAMS floats) holds the
+   initial values on entry and the trained ones on return. epoch_loss
+   (epochs doubles, may be NULL) receives each epoch's mean weighted
+   cross-entropy. */
+int pmcim_screen_train(int32_t M, const float* feats, const uint8_t* labels, int32_t epochs, int32_t batch,
+                       double lr, double pos_weight, float* params, double* epoch_loss, void* cuda_stream);
+
+/* Screen probabilities of M feature rows. */
+int pmcim_screen_apply(int32_t M, const float* feats, const float* params, float* prob, void* cuda_stream);
+
+/* Gradient (PMCIM_SCREEN_PARAMS floats) and value of the mean weighted loss
+   over M samples at the BF16 rounding of params (for checking the training
+   kernels against an independent implementation). */
+int pmcim_screen_gradient(int32_t M, const float* feats, const uint8_t* labels, double pos_weight,
+                          const float* params, float* grad, double* loss, void* cuda_stream);
+
 const char* pmcim_status_string(int code);
 const char* pmcim_last_error(void);
 
@@ -242,7 +289,7 @@ int pmcim_solve_points_noalloc(int32_t n, int32_t K, const pmcim_fterm* f, const
 #define PMCIM_K_VERIFY 4
 #define PMCIM_K_GATHER 5
 #define PMCIM_K_FACTOR32 6 /* assembly + LU + solve at the nodes (FP32 LU)   */
-#define PMCIM_K_REFINE 7   /* FP64 residual and correction sweeps            */
+#define PMCIM_K_SCREEN 7   /* learned screen: MLP forward / training          */
 #define PMCIM_K_COUNT 8
 
 typedef struct {

@@ -17,6 +17,9 @@ Readings of passages the paper leaves open (listed again in the design notes):
   * one probe block V (n x l, unit columns) serves every region and node, and
     the indicator's random vector is f = V[:, 0] (pmCIMb steps 1.a and 2.a);
   * candidate <=> I > tol_ind, strict (pmCIMb step 1.c);
+  * P f = 0 when a disk holds no eigenvalue (Sec. 2.1), so Eq. 3.1 is 0/0
+    there; in floating point P f|_N then sits at rounding level. When
+    ||P f|_N|| <= 1e-10 * || sum_j |w_j| |x_j| || the indicator is taken as 0;
   * tol_svd is absolute (Sec. 3.2) and p counts sigma_i > tol_svd;
   * a region is saturated when p reaches min(n, l) (all probe directions
     used); it is then split into four children with the pmCIMa geometry and
@@ -102,6 +105,7 @@ class Moments:
     C1: np.ndarray       # n x l: sum_j w_j z_j X_j      (Eq. 3.3)
     pf_N: np.ndarray     # n:     sum_j w_j x_j, f = V[:,0]          (P f |_N)
     pf_half: np.ndarray  # n:     sum_{j odd} 2 w_j x_j              (P f |_{N/2})
+    pf_abs: np.ndarray = None  # n: sum_j |w_j| |x_j|, the size of the terms of P f |_N
 
 
 def moments(problem, c: complex, r: float, N: int, V: np.ndarray) -> Moments:
@@ -115,17 +119,24 @@ def moments(problem, c: complex, r: float, N: int, V: np.ndarray) -> Moments:
     C1 = np.zeros((n, l), dtype=np.complex128)
     pf_N = np.zeros(n, dtype=np.complex128)
     pf_half = np.zeros(n, dtype=np.complex128)
+    pf_abs = np.zeros(n)
     for j in range(N):
         C0 += w[j] * X[j]
         C1 += w[j] * z[j] * X[j]
         pf_N += w[j] * X[j][:, 0]
+        pf_abs += abs(w[j]) * np.abs(X[j][:, 0])
         if j % 2 == 1:                       # 1-based even nodes x_2, x_4, ..., x_N
             pf_half += 2.0 * w[j] * X[j][:, 0]
-    return Moments(C0, C1, pf_N, pf_half)
+    return Moments(C0, C1, pf_N, pf_half, pf_abs)
 
 
-def indicator_value(pf_N: np.ndarray, pf_half: np.ndarray) -> float:
-    """I = || P f|_N ./ P f|_{N/2} ||_2 / sqrt(n)   (Eq. 3.1)."""
+PF_FLOOR = 1e-10
+
+
+def indicator_value(pf_N: np.ndarray, pf_half: np.ndarray, pf_abs: np.ndarray = None) -> float:
+    """I = || P f|_N ./ P f|_{N/2} ||_2 / sqrt(n)   (Eq. 3.1); 0 when P f|_N is at rounding level."""
+    if pf_abs is not None and np.linalg.norm(pf_N) <= PF_FLOOR * np.linalg.norm(pf_abs):
+        return 0.0
     return float(np.linalg.norm(pf_N / pf_half) / math.sqrt(len(pf_N)))
 
 
@@ -136,7 +147,7 @@ def indicator(problem, regions: Sequence, V: np.ndarray, tol_ind: float = 0.1):
 
 
 def _pf(m: Moments):
-    return m.pf_N, m.pf_half
+    return m.pf_N, m.pf_half, m.pf_abs
 
 
 # ---------------------------------------------------------------------------
@@ -260,7 +271,7 @@ def pmcimb(problem, regions: Sequence, V: np.ndarray, tol_ind: float = 0.1,
         nxt = []
         for (c, r, N, depth) in level:
             m = moments(problem, c, r, N, V)
-            I = indicator_value(m.pf_N, m.pf_half)
+            I = indicator_value(m.pf_N, m.pf_half, m.pf_abs)
             rec = RegionRecord(c, r, N, depth, I, I > tol_ind)
             if rec.candidate:
                 b = beyn_extract(m.C0, m.C1, tol_svd)

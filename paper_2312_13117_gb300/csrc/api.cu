@@ -206,6 +206,7 @@ struct Workspace {
   DevBuf bwork, bsigma, bp, blam, bvecs, bkept, bstatus;
   DevBuf vlam, vprob, voff, vsig, vacc, vwork, vvec, vpiv;
   DevBuf gitems, gdst, gperm;
+  DevBuf ind3, feats, sprob, sparams, sscratch;
   // the library's own stream: graphs cannot be captured on the legacy default stream
   cudaStream_t stream = nullptr;
   cudaEvent_t ordered = nullptr;
@@ -217,7 +218,7 @@ struct Workspace {
     DevBuf* b[] = {&probs, &regions, &items, &counters, &node_info, &X, &work64, &piv64, &work32, &piv32,
                    &phase, &C0, &C1, &pf_half, &pf_abs, &ind, &pf_norm, &pf_scale, &cand, &bwork, &bsigma,
                    &bp, &blam, &bvecs, &bkept, &bstatus, &vlam, &vprob, &voff, &vsig, &vacc, &vwork,
-                   &vvec, &vpiv, &gitems, &gdst, &gperm};
+                   &vvec, &vpiv, &gitems, &gdst, &gperm, &ind3, &feats, &sprob, &sparams, &sscratch};
     for (DevBuf* x : b) x->release();
   }
 };
@@ -358,7 +359,7 @@ struct LevelOut {
 };
 
 int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool do_beyn, LevelOut* out,
-              const std::vector<int>* form_override = nullptr);
+              const std::vector<int>* form_override = nullptr, bool screen_features = false);
 
 int tune_forms(Call& c) {
   if (c.opt->precision != PMCIM_PREC_AUTO) {
@@ -375,9 +376,13 @@ int tune_forms(Call& c) {
       if (it != g_tune.end()) decided = it->second;
     }
     if (decided < 0) {
-      // probe: one disk of 2 x SMs nodes on this problem, both forms, timed with events
+      // probe: one disk of 2 x SMs nodes on this problem, both forms, timed with
+      // events. It measures arithmetic throughput, so it sits far out (|z| ~ 70),
+      // where the leading term dominates T(z) and no node is near an eigenvalue;
+      // nodes next to eigenvalues would send the precision form to its FP64
+      // fallback and misrepresent it.
       std::vector<HostRegion> probe(1);
-      probe[0] = HostRegion{0.37, 0.29, 0.6, 2 * num_sms(), 0, 0, (int)gi};
+      probe[0] = HostRegion{50.0, 50.0, 1.0, 2 * num_sms(), 0, 0, (int)gi};
       // each form runs once untimed (workspace allocation, first launch), then timed
       double t[2] = {0.0, 0.0};
       const pmcim_stats keep = c.st;
@@ -414,7 +419,7 @@ int tune_forms(Call& c) {
 // One level: node solves (waves), reduction, indicator, Beyn (gated)
 // ===========================================================================
 int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool do_beyn, LevelOut* out,
-              const std::vector<int>* form_override) {
+              const std::vector<int>* form_override, bool screen_features) {
   Workspace& ws = *c.ws;
   cudaStream_t s = c.s;
   const int R = (int)regs.size();
@@ -458,6 +463,10 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   CU(ws.pf_scale.ensure(R * sizeof(double)));
   CU(ws.cand.ensure(R));
   CU(ws.node_info.ensure(std::max<size_t>(1, total_nodes) * sizeof(int32_t)));
+  if (screen_features) {
+    CU(ws.ind3.ensure((size_t)R * 3 * sizeof(double)));
+    CU(ws.feats.ensure((size_t)R * 3 * sizeof(float)));
+  }
   if (do_beyn) {
     CU(ws.bwork.ensure(w_tot * sizeof(double2)));
     CU(ws.bvecs.ensure(c_tot * sizeof(double2)));
@@ -471,12 +480,12 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   // ---- waves of whole disks whose solutions fit the wave buffer ----
   struct Wave {
     int g0, g1;
-    size_t items64_off, n64, items32_off, n32;
+    size_t items64_off, n64, items32_off, n32, itemsS_off, nS;
   };
   std::vector<Wave> waves;
   std::vector<NodeItem> items;  // all waves: FP64 items then mixed items per wave
   size_t x_need = 0;
-  bool any64 = false, any32 = false;
+  bool any64 = false, any32 = false, anyS = false;
   {
     int g0 = 0;
     while (g0 < R) {
@@ -492,10 +501,14 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
       }
       x_need = std::max(x_need, xb);
       // largest n first: the atomic work counter then hands out the long jobs early
-      std::vector<NodeItem> it64, it32;
-      for (int g = g0; g < g1; ++g)
-        for (int j = 0; j < regs[g].N; ++j)
-          (form_of(regs[g].prob) == PMCIM_PREC_FP64 ? it64 : it32).push_back(NodeItem{g, j});
+      // small problems (n <= 32, l <= 16) go to the warp-per-node kernel whatever the form
+      std::vector<NodeItem> it64, it32, itS;
+      for (int g = g0; g < g1; ++g) {
+        const ProblemDev& P = c.pd[regs[g].prob];
+        std::vector<NodeItem>& dst = small_kernel_fits(P.n, P.l) ? itS
+                                     : (form_of(regs[g].prob) == PMCIM_PREC_FP64 ? it64 : it32);
+        for (int j = 0; j < regs[g].N; ++j) dst.push_back(NodeItem{g, j});
+      }
       auto by_n = [&](const NodeItem& a, const NodeItem& b) {
         const int na = c.pd[regs[a.region].prob].n, nb = c.pd[regs[b.region].prob].n;
         if (na != nb) return na > nb;
@@ -504,12 +517,15 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
       };
       std::stable_sort(it64.begin(), it64.end(), by_n);
       std::stable_sort(it32.begin(), it32.end(), by_n);
-      Wave wv{g0, g1, items.size(), it64.size(), 0, it32.size()};
+      Wave wv{g0, g1, items.size(), it64.size(), 0, it32.size(), 0, itS.size()};
       items.insert(items.end(), it64.begin(), it64.end());
       wv.items32_off = items.size();
       items.insert(items.end(), it32.begin(), it32.end());
+      wv.itemsS_off = items.size();
+      items.insert(items.end(), itS.begin(), itS.end());
       any64 |= !it64.empty();
       any32 |= !it32.empty();
+      anyS |= !itS.empty();
       waves.push_back(wv);
       g0 = g1;
     }
@@ -517,7 +533,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   CU(ws.X.ensure(std::max<size_t>(1, x_need)));
   CU(ws.items.ensure(std::max<size_t>(1, items.size()) * sizeof(NodeItem)));
   CU(ws.regions.ensure(R * sizeof(RegionDev)));
-  CU(ws.counters.ensure(std::max<size_t>(1, 2 * waves.size()) * sizeof(int)));
+  CU(ws.counters.ensure(std::max<size_t>(1, 3 * waves.size()) * sizeof(int)));
   CU(cudaMemcpyAsync(ws.items.p, items.data(), items.size() * sizeof(NodeItem), cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(ws.regions.p, rd.data(), R * sizeof(RegionDev), cudaMemcpyHostToDevice, s));
 
@@ -570,12 +586,13 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
 
   if (any64) CU(prepare_factor_fp64());
   if (any32) CU(prepare_factor_mixed());
+  if (anyS) CU(prepare_factor_small());
 
   // ---- the level as one CUDA graph (profiler events become graph nodes) ----
   cudaGraph_t graph = nullptr;
   CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   auto capture = [&]() -> int {
-    CU(cudaMemsetAsync(ws.counters.p, 0, 2 * waves.size() * sizeof(int), s));
+    CU(cudaMemsetAsync(ws.counters.p, 0, 3 * waves.size() * sizeof(int), s));
     for (size_t wi = 0; wi < waves.size(); ++wi) {
       const Wave& wv = waves[wi];
       NodeArgs na;
@@ -590,7 +607,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
       if (wv.n64) {
         na.items = ws.items.as<NodeItem>() + wv.items64_off;
         na.n_items = (int)wv.n64;
-        na.counter = ws.counters.as<int>() + 2 * wi;
+        na.counter = ws.counters.as<int>() + 3 * wi;
         na.work = ws.work64.as<char>();
         na.slot_bytes = slot64;
         na.piv = ws.piv64.as<int32_t>();
@@ -603,7 +620,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
       if (wv.n32) {
         na.items = ws.items.as<NodeItem>() + wv.items32_off;
         na.n_items = (int)wv.n32;
-        na.counter = ws.counters.as<int>() + 2 * wi + 1;
+        na.counter = ws.counters.as<int>() + 3 * wi + 1;
         na.work = ws.work32.as<char>();
         na.slot_bytes = slot32;
         na.piv = ws.piv32.as<int32_t>();
@@ -613,12 +630,31 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
         CU(launch_factor_solve_mixed(na, s));
         prof_end(PMCIM_K_FACTOR32, s);
       }
+      if (wv.nS) {
+        na.items = ws.items.as<NodeItem>() + wv.itemsS_off;
+        na.n_items = (int)wv.nS;
+        na.counter = ws.counters.as<int>() + 3 * wi + 2;
+        na.phase = nullptr;
+        prof_begin(PMCIM_K_FACTOR, s);
+        CU(launch_factor_solve_small(na, s));
+        prof_end(PMCIM_K_FACTOR, s);
+      }
       LevelArgs lw = la;
       lw.regions = la.regions + wv.g0;
       lw.R = wv.g1 - wv.g0;
+      if (screen_features) {
+        prof_begin(PMCIM_K_INDICATOR, s);
+        CU(launch_screen_features(lw, ws.ind3.as<double>() + 3 * (size_t)wv.g0, s));
+        prof_end(PMCIM_K_INDICATOR, s);
+        continue;
+      }
       prof_begin(PMCIM_K_REDUCE, s);
       CU(launch_reduce_moments(lw, s));
       prof_end(PMCIM_K_REDUCE, s);
+    }
+    if (screen_features) {
+      CU(launch_make_features(R, ws.ind3.as<double>(), la.regions, ws.feats.as<float>(), s));
+      return PMCIM_OK;
     }
     prof_begin(PMCIM_K_INDICATOR, s);
     CU(launch_indicator(la, s));
@@ -651,8 +687,10 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   out->ind.resize(R);
   out->cand.resize(R);
   out->node_info.resize(total_nodes);
-  CU(cudaMemcpyAsync(out->ind.data(), ws.ind.p, R * sizeof(double), cudaMemcpyDeviceToHost, s));
-  CU(cudaMemcpyAsync(out->cand.data(), ws.cand.p, R, cudaMemcpyDeviceToHost, s));
+  if (!screen_features) {
+    CU(cudaMemcpyAsync(out->ind.data(), ws.ind.p, R * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(out->cand.data(), ws.cand.p, R, cudaMemcpyDeviceToHost, s));
+  }
   CU(cudaMemcpyAsync(out->node_info.data(), ws.node_info.p, total_nodes * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   if (do_beyn) {
     out->p.resize(R);
@@ -692,12 +730,13 @@ struct EigOut {
 };
 
 int run_beyn_levels(Call& c, const std::vector<HostRegion>& top, bool gate_top, EigOut* out,
-                    std::vector<int>* root_status, std::vector<double>* top_ind) {
+                    std::vector<int>* root_status, std::vector<double>* top_ind, size_t n_roots = 0) {
   Workspace& ws = *c.ws;
   cudaStream_t s = c.s;
   std::vector<HostRegion> level = top;
-  root_status->assign(top.size(), 0);
-  if (top_ind) top_ind->assign(top.size(), 0.0);
+  if (n_roots < top.size()) n_roots = top.size();
+  root_status->assign(n_roots, 0);
+  if (top_ind) top_ind->assign(n_roots, 0.0);
   while (!level.empty()) {
     const int R = (int)level.size();
     LevelOut lo;
@@ -852,10 +891,65 @@ struct Verified {
   std::vector<uint8_t> acc;
 };
 
-int run_pmcimb(Call& c, const std::vector<HostRegion>& top, EigOut* e, Verified* v, std::vector<int>* rstat,
+// Learned screen: coarse indicators of every disk (one probe column, screen_N
+// nodes), the MLP's probabilities, and the disks that may skip the full path.
+int run_screen(Call& c, const std::vector<HostRegion>& top, std::vector<uint8_t>* skip) {
+  Workspace& ws = *c.ws;
+  cudaStream_t s = c.s;
+  const int R = (int)top.size();
+  skip->assign(R, 0);
+  if (R == 0) return PMCIM_OK;
+  const int NS = c.opt->screen_N > 0 ? c.opt->screen_N : 16;
+  if (NS % 16) return fail(PMCIM_EINVAL, "screen_N = %d is not a multiple of 16", NS);
+  // coarse copies of the groups: same coefficients and probe block, one column
+  const size_t G = c.groups.size();
+  for (size_t gi = 0; gi < G; ++gi) c.groups.push_back(Group{c.groups[gi].h, 1, c.groups[gi].form});
+  CHK(upload_problems(c));
+  std::vector<HostRegion> coarse = top;
+  for (HostRegion& h : coarse) {
+    h.N = NS;
+    h.prob += (int)G;
+  }
+  LevelOut lo;
+  CHK(run_level(c, coarse, false, false, &lo, nullptr, true));
+  c.st.screen_solves += (int)(R * NS);
+  c.st.solves -= (int64_t)R * NS;  // counted as screen work, not as pmCIMb solves
+  c.st.regions -= R;
+  CU(ws.sparams.ensure(PMCIM_SCREEN_PARAMS * sizeof(float)));
+  CU(ws.sscratch.ensure(2 * PMCIM_SCREEN_PARAMS + 256));
+  CU(ws.sprob.ensure(R * sizeof(float)));
+  CU(cudaMemcpyAsync(ws.sparams.p, c.opt->screen_params, PMCIM_SCREEN_PARAMS * sizeof(float), cudaMemcpyDefault, s));
+  prof_begin(PMCIM_K_SCREEN, s);
+  CU(screen_forward(R, ws.feats.as<float>(), ws.sparams.as<float>(), ws.sprob.as<float>(), ws.sscratch.p, s));
+  prof_end(PMCIM_K_SCREEN, s);
+  std::vector<float> prob(R);
+  CU(cudaMemcpyAsync(prob.data(), ws.sprob.p, R * sizeof(float), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  for (int g = 0; g < R; ++g) (*skip)[g] = (prob[g] < c.opt->screen_threshold) ? 1 : 0;
+  c.groups.resize(G);
+  CHK(upload_problems(c));
+  return PMCIM_OK;
+}
+
+int run_pmcimb(Call& c, const std::vector<HostRegion>& top_in, EigOut* e, Verified* v, std::vector<int>* rstat,
                std::vector<double>* tind) {
   CHK(tune_forms(c));
-  CHK(run_beyn_levels(c, top, true, e, rstat, tind));
+  std::vector<HostRegion> top = top_in;
+  std::vector<uint8_t> skip;
+  if (c.opt->screen_params) {
+    CHK(run_screen(c, top_in, &skip));
+    top.clear();
+    for (size_t g = 0; g < top_in.size(); ++g)
+      if (!skip[g]) top.push_back(top_in[g]);
+      else c.st.screened_out += 1;
+  }
+  CHK(run_beyn_levels(c, top, true, e, rstat, tind, top_in.size()));
+  if (!skip.empty())
+    for (size_t g = 0; g < top_in.size(); ++g)
+      if (skip[g]) {
+        (*rstat)[top_in[g].root] |= PMCIM_RS_SCREENED;
+        if (tind) (*tind)[top_in[g].root] = -1.0;
+      }
   CHK(run_certify(c, *e, &v->sig, &v->acc));
   std::vector<double2> rest;
   std::vector<int> rest_prob, idx;
@@ -920,6 +1014,9 @@ void pmcim_default_options(pmcim_options* opt) {
   opt->max_ir_sweeps = 3;
   opt->max_split_depth = 8;
   opt->cuda_stream = nullptr;
+  opt->screen_params = nullptr;
+  opt->screen_threshold = 0.0;
+  opt->screen_N = 16;
 }
 
 const char* pmcim_status_string(int code) {
@@ -1230,6 +1327,103 @@ int pmcim_batch_solve(int32_t P, const pmcim_batch_item* items, const pmcim_opti
   if (sigma_min) CHK(copy_out(sigma_min, sig_s.data(), cnt * sizeof(double)));
   if (problem_of) CHK(copy_out(problem_of, prob_s.data(), cnt * sizeof(int32_t)));
   if (region_of) CHK(copy_out(region_of, reg_s.data(), cnt * sizeof(int32_t)));
+  return PMCIM_OK;
+}
+
+int pmcim_screen_features(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim_region* reg,
+                          int32_t l, const double* V, double* ind3, float* feats) {
+  if (!p) return fail(PMCIM_EINVAL, "problem is NULL");
+  CHK(check_options(opt));
+  CHK(check_regions(R, reg, l));
+  for (int g = 0; g < R; ++g)
+    if (reg[g].N % 16) return fail(PMCIM_EINVAL, "region %d: N = %d is not a multiple of 16", g, reg[g].N);
+  Call c;
+  CHK(single_call(c, p, opt, l, V));
+  LevelOut lo;
+  CHK(run_level(c, to_host_regions(R, reg, 0), false, false, &lo, nullptr, true));
+  CU(cudaStreamSynchronize(c.s));
+  if (ind3) CHK(copy_out(ind3, p->ws.ind3.p, (size_t)R * 3 * sizeof(double)));
+  if (feats) CHK(copy_out(feats, p->ws.feats.p, (size_t)R * 3 * sizeof(float)));
+  return PMCIM_OK;
+}
+
+namespace {
+struct TmpBuf {
+  void* p = nullptr;
+  ~TmpBuf() {
+    if (p) cudaFree(p);
+  }
+};
+}  // namespace
+
+int pmcim_screen_train(int32_t M, const float* feats, const uint8_t* labels, int32_t epochs, int32_t batch,
+                       double lr, double pos_weight, float* params, double* epoch_loss, void* cuda_stream) {
+  if (M < 1 || epochs < 0 || batch < 1 || !feats || !labels || !params || !(lr > 0.0) || !(pos_weight > 0.0))
+    return fail(PMCIM_EINVAL, "bad training arguments");
+  CHK(check_device());
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  const int B = std::min(batch, M);
+  TmpBuf f, y, w, el, sc;
+  CU(cudaMalloc(&f.p, (size_t)M * 3 * sizeof(float)));
+  CU(cudaMalloc(&y.p, (size_t)M));
+  CU(cudaMalloc(&w.p, PMCIM_SCREEN_PARAMS * sizeof(float)));
+  CU(cudaMalloc(&el.p, std::max(1, epochs) * sizeof(double)));
+  CU(cudaMalloc(&sc.p, screen_train_scratch_bytes(B)));
+  CU(cudaMemcpyAsync(f.p, feats, (size_t)M * 3 * sizeof(float), cudaMemcpyDefault, s));
+  CU(cudaMemcpyAsync(y.p, labels, (size_t)M, cudaMemcpyDefault, s));
+  CU(cudaMemcpyAsync(w.p, params, PMCIM_SCREEN_PARAMS * sizeof(float), cudaMemcpyDefault, s));
+  prof_begin(PMCIM_K_SCREEN, s);
+  CU(screen_train(M, (const float*)f.p, (const uint8_t*)y.p, epochs, B, (float)lr, (float)pos_weight, (float*)w.p,
+                  (double*)el.p, sc.p, s));
+  prof_end(PMCIM_K_SCREEN, s);
+  CU(cudaMemcpyAsync(params, w.p, PMCIM_SCREEN_PARAMS * sizeof(float), cudaMemcpyDefault, s));
+  if (epoch_loss && epochs > 0) CU(cudaMemcpyAsync(epoch_loss, el.p, epochs * sizeof(double), cudaMemcpyDefault, s));
+  CU(cudaStreamSynchronize(s));
+  return PMCIM_OK;
+}
+
+int pmcim_screen_apply(int32_t M, const float* feats, const float* params, float* prob, void* cuda_stream) {
+  if (M < 0 || (M > 0 && (!feats || !params || !prob))) return fail(PMCIM_EINVAL, "bad arguments");
+  if (M == 0) return PMCIM_OK;
+  CHK(check_device());
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  TmpBuf f, w, pr, sc;
+  CU(cudaMalloc(&f.p, (size_t)M * 3 * sizeof(float)));
+  CU(cudaMalloc(&w.p, PMCIM_SCREEN_PARAMS * sizeof(float)));
+  CU(cudaMalloc(&pr.p, (size_t)M * sizeof(float)));
+  CU(cudaMalloc(&sc.p, 2 * PMCIM_SCREEN_PARAMS + 256));
+  CU(cudaMemcpyAsync(f.p, feats, (size_t)M * 3 * sizeof(float), cudaMemcpyDefault, s));
+  CU(cudaMemcpyAsync(w.p, params, PMCIM_SCREEN_PARAMS * sizeof(float), cudaMemcpyDefault, s));
+  prof_begin(PMCIM_K_SCREEN, s);
+  CU(screen_forward(M, (const float*)f.p, (const float*)w.p, (float*)pr.p, sc.p, s));
+  prof_end(PMCIM_K_SCREEN, s);
+  CU(cudaMemcpyAsync(prob, pr.p, (size_t)M * sizeof(float), cudaMemcpyDefault, s));
+  CU(cudaStreamSynchronize(s));
+  return PMCIM_OK;
+}
+
+int pmcim_screen_gradient(int32_t M, const float* feats, const uint8_t* labels, double pos_weight,
+                          const float* params, float* grad, double* loss, void* cuda_stream) {
+  if (M < 1 || !feats || !labels || !params || !grad || !(pos_weight > 0.0)) return fail(PMCIM_EINVAL, "bad arguments");
+  CHK(check_device());
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  TmpBuf f, y, w, g, l, sc;
+  CU(cudaMalloc(&f.p, (size_t)M * 3 * sizeof(float)));
+  CU(cudaMalloc(&y.p, (size_t)M));
+  CU(cudaMalloc(&w.p, PMCIM_SCREEN_PARAMS * sizeof(float)));
+  CU(cudaMalloc(&g.p, PMCIM_SCREEN_PARAMS * sizeof(float)));
+  CU(cudaMalloc(&l.p, sizeof(double)));
+  CU(cudaMalloc(&sc.p, screen_grad_scratch_bytes(M)));
+  CU(cudaMemcpyAsync(f.p, feats, (size_t)M * 3 * sizeof(float), cudaMemcpyDefault, s));
+  CU(cudaMemcpyAsync(y.p, labels, (size_t)M, cudaMemcpyDefault, s));
+  CU(cudaMemcpyAsync(w.p, params, PMCIM_SCREEN_PARAMS * sizeof(float), cudaMemcpyDefault, s));
+  prof_begin(PMCIM_K_SCREEN, s);
+  CU(screen_gradient(M, (const float*)f.p, (const uint8_t*)y.p, (float)pos_weight, (const float*)w.p, (float*)g.p,
+                     (double*)l.p, sc.p, s));
+  prof_end(PMCIM_K_SCREEN, s);
+  CU(cudaMemcpyAsync(grad, g.p, PMCIM_SCREEN_PARAMS * sizeof(float), cudaMemcpyDefault, s));
+  if (loss) CU(cudaMemcpyAsync(loss, l.p, sizeof(double), cudaMemcpyDefault, s));
+  CU(cudaStreamSynchronize(s));
   return PMCIM_OK;
 }
 

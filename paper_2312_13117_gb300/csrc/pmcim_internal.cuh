@@ -7,6 +7,8 @@
 #include "../../include/pmcim.h"
 
 #define PMCIM_MAX_TERMS 16
+// ||P f|_N|| at or below this fraction of ||sum_j |w_j| |x_j||| counts as zero
+constexpr double kPfFloor = 1e-10;
 #define PMCIM_MAX_L 64
 
 // ---------------------------------------------------------------------------
@@ -205,6 +207,10 @@ cudaError_t prepare_factor_fp64();   // shared-memory limits; call outside graph
 cudaError_t prepare_factor_mixed();
 cudaError_t launch_factor_solve_fp64(const NodeArgs& a, cudaStream_t s);
 cudaError_t launch_factor_solve_mixed(const NodeArgs& a, cudaStream_t s);
+// warp-per-node FP64 kernel for small problems (lu_small.cu)
+bool small_kernel_fits(int n, int l);
+cudaError_t prepare_factor_small();
+cudaError_t launch_factor_solve_small(const NodeArgs& a, cudaStream_t s);
 int factor_slots_fp64(int n, int l);
 // Phases of the precision-form node kernel timed with clock64 when profiling.
 #define PMCIM_PHASES 8  // assemble, LU, first solve, residual, correction solve, fallback, set-up, unused
@@ -260,6 +266,18 @@ struct ValueArgs {
 };
 cudaError_t launch_certify(const ValueArgs& a, cudaStream_t s);
 cudaError_t launch_verify_fp64(const ValueArgs& a, cudaStream_t s);
+
+// learned screen (screen.cu)
+cudaError_t launch_screen_features(const LevelArgs& a, double* ind3, cudaStream_t s);
+cudaError_t launch_make_features(int R, const double* ind3, const RegionDev* regions, float* feats, cudaStream_t s);
+cudaError_t screen_forward(int M, const float* d_feats, const float* d_params, float* d_prob, void* d_scratch,
+                           cudaStream_t s);  // scratch: 2 * PMCIM_SCREEN_PARAMS bytes
+size_t screen_grad_scratch_bytes(int B);
+size_t screen_train_scratch_bytes(int B);
+cudaError_t screen_gradient(int B, const float* d_feats, const uint8_t* d_labels, float pos_weight,
+                            const float* d_params, float* d_grad, double* d_loss, void* d_scratch, cudaStream_t s);
+cudaError_t screen_train(int M, const float* d_feats, const uint8_t* d_labels, int epochs, int B, float lr,
+                         float pos_weight, float* d_params, double* d_epoch_loss, void* d_scratch, cudaStream_t s);
 
 struct VecItem {
   int64_t src;   // double2 offset in the source

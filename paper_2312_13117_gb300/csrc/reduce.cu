@@ -71,7 +71,9 @@ __global__ void __launch_bounds__(RT) k_indicator(LevelArgs a) {
   if (threadIdx.x == 0) {
     double t0 = 0.0, t1 = 0.0, t2 = 0.0;
     for (int k = 0; k < RT / 32; ++k) { t0 += red[0][k]; t1 += red[1][k]; t2 += red[2][k]; }
-    const double I = sqrt(t0) / sqrt((double)n);
+    // P f = 0 when the disk holds no eigenvalue (Sec. 2.1): at rounding level the
+    // ratio of Eq. 3.1 is 0/0, and the indicator is taken as 0
+    const double I = (sqrt(t1) <= kPfFloor * sqrt(t2)) ? 0.0 : sqrt(t0) / sqrt((double)n);
     a.ind[g] = I;
     a.pf_norm[g] = sqrt(t1);
     a.pf_scale[g] = sqrt(t2);

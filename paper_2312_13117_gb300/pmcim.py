@@ -27,9 +27,11 @@ PREC_FP64, PREC_FP32_IR, PREC_AUTO = 0, 1, 2
 EXPORTS = ["pmcim_default_options", "pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments",
            "pmcim_indicator", "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_status_string",
            "pmcim_last_error", "pmcim_profile_enable", "pmcim_profile_reset", "pmcim_profile_read",
-           "pmcim_solve_points_noalloc", "pmcim_batch_solve"]
+           "pmcim_solve_points_noalloc", "pmcim_batch_solve", "pmcim_screen_features", "pmcim_screen_train",
+           "pmcim_screen_apply", "pmcim_screen_gradient"]
 
-KERNELS = ["factor_fp64", "reduce", "indicator", "beyn", "verify", "gather", "factor_fp32", "refine"]
+KERNELS = ["factor_fp64", "reduce", "indicator", "beyn", "verify", "gather", "factor_fp32", "screen"]
+SCREEN_PARAMS = 4481
 
 
 class pmcim_fterm(C.Structure):
@@ -45,7 +47,8 @@ class pmcim_region(C.Structure):
 class pmcim_options(C.Structure):
     _fields_ = [("tol_ind", C.c_double), ("tol_svd", C.c_double), ("tol_verify", C.c_double),
                 ("precision", C.c_int32), ("max_ir_sweeps", C.c_int32), ("max_split_depth", C.c_int32),
-                ("reserved", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("reserved", C.c_int32), ("cuda_stream", C.c_void_p), ("screen_params", C.c_void_p),
+                ("screen_threshold", C.c_double), ("screen_N", C.c_int32), ("reserved2", C.c_int32)]
 
 
 class pmcim_batch_item(C.Structure):
@@ -61,7 +64,8 @@ class pmcim_stats(C.Structure):
     _fields_ = [("solves", C.c_int64), ("regions", C.c_int32), ("candidates", C.c_int32),
                 ("splits", C.c_int32), ("unverified", C.c_int32), ("ir_fallbacks", C.c_int32),
                 ("singular_nodes", C.c_int32), ("ir_sweeps", C.c_int64), ("certified", C.c_int32),
-                ("graphs", C.c_int32), ("tuned_fp64", C.c_int32), ("tuned_mixed", C.c_int32)]
+                ("graphs", C.c_int32), ("tuned_fp64", C.c_int32), ("tuned_mixed", C.c_int32),
+                ("screened_out", C.c_int32), ("screen_solves", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -102,10 +106,16 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pmcim_profile_read.restype = None
     lib.pmcim_solve_points_noalloc.argtypes = [I32, I32, C.POINTER(pmcim_fterm), C.POINTER(C.c_uint8), VP, I32,
                                                VP, I32, VP, VP, VP, VP]
+    F = C.c_void_p
+    lib.pmcim_screen_features.argtypes = [P, C.POINTER(pmcim_options), I32, C.POINTER(pmcim_region), I32, VP, VP, F]
+    lib.pmcim_screen_train.argtypes = [I32, F, VP, I32, I32, D, D, F, VP, VP]
+    lib.pmcim_screen_apply.argtypes = [I32, F, F, F, VP]
+    lib.pmcim_screen_gradient.argtypes = [I32, F, VP, D, F, F, VP, VP]
     lib.pmcim_batch_solve.argtypes = [I32, C.POINTER(pmcim_batch_item), C.POINTER(pmcim_options), I32, VP, VP, VP,
                                       VP, VP, C.POINTER(pmcim_stats)]
     for name in ("pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments", "pmcim_indicator",
-                 "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_solve_points_noalloc", "pmcim_batch_solve"):
+                 "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_solve_points_noalloc", "pmcim_batch_solve",
+                 "pmcim_screen_features", "pmcim_screen_train", "pmcim_screen_apply", "pmcim_screen_gradient"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -199,13 +209,62 @@ def regions_array(regions: Sequence) -> C.Array:
     return arr
 
 
+_screen_keep = []
+
+
 def options(tol_ind=0.1, tol_svd=1e-6, tol_verify=1e-6, precision=PREC_FP64, max_ir_sweeps=3,
-            max_split_depth=8, stream=None) -> pmcim_options:
+            max_split_depth=8, stream=None, screen_params=None, screen_threshold=0.0,
+            screen_N=16) -> pmcim_options:
     o = pmcim_default_options()
     o.tol_ind, o.tol_svd, o.tol_verify = tol_ind, tol_svd, tol_verify
     o.precision, o.max_ir_sweeps, o.max_split_depth = precision, max_ir_sweeps, max_split_depth
     o.cuda_stream = stream
+    if screen_params is not None:
+        sp = np.ascontiguousarray(np.asarray(screen_params, dtype=np.float32))
+        assert sp.size == SCREEN_PARAMS
+        _screen_keep.append(sp)
+        del _screen_keep[:-8]
+        o.screen_params = sp.ctypes.data
+        o.screen_threshold = float(screen_threshold)
+        o.screen_N = int(screen_N)
     return o
+
+
+# ---------------------------------------------------------------------------
+# learned screen
+# ---------------------------------------------------------------------------
+
+def screen_train(feats, labels, params, epochs=30, batch=1024, lr=3e-3, pos_weight=4.0, stream=None):
+    """Train the screen on the GPU; returns (trained params, per-epoch loss)."""
+    lib = load()
+    f = np.ascontiguousarray(np.asarray(feats, np.float32))
+    y = np.ascontiguousarray(np.asarray(labels, np.uint8))
+    p = np.ascontiguousarray(np.asarray(params, np.float32)).copy()
+    el = np.zeros(max(epochs, 1))
+    _check(lib.pmcim_screen_train(len(y), _ptr(f), _ptr(y), epochs, batch, lr, pos_weight, _ptr(p), _ptr(el),
+                                  stream), "pmcim_screen_train")
+    return p, el[:epochs]
+
+
+def screen_apply(feats, params, stream=None):
+    lib = load()
+    f = np.ascontiguousarray(np.asarray(feats, np.float32))
+    p = np.ascontiguousarray(np.asarray(params, np.float32))
+    out = np.zeros(len(f), np.float32)
+    _check(lib.pmcim_screen_apply(len(f), _ptr(f), _ptr(p), _ptr(out), stream), "pmcim_screen_apply")
+    return out
+
+
+def screen_gradient(feats, labels, params, pos_weight=4.0, stream=None):
+    lib = load()
+    f = np.ascontiguousarray(np.asarray(feats, np.float32))
+    y = np.ascontiguousarray(np.asarray(labels, np.uint8))
+    p = np.ascontiguousarray(np.asarray(params, np.float32))
+    g = np.zeros(SCREEN_PARAMS, np.float32)
+    loss = np.zeros(1)
+    _check(lib.pmcim_screen_gradient(len(y), _ptr(f), _ptr(y), pos_weight, _ptr(p), _ptr(g), _ptr(loss), stream),
+           "pmcim_screen_gradient")
+    return g, float(loss[0])
 
 
 class Problem:
@@ -299,6 +358,18 @@ class Problem:
                               _ptr(vecs), _ptr(rof), _ptr(cnt), _ptr(rst)), "pmcim_beyn", cnt)
         k = int(cnt[0])
         return lam[:k], (vecs[:k].T if want_vecs else None), rof[:k], rst[:R]
+
+    def screen_features(self, regions, V, opt=None):
+        """(ind3 R x 3 = I_8, I_16, I_N; feats R x 3 float32) of the disks (N a multiple of 16)."""
+        lib = load()
+        V = _colmajor_c128(V)
+        R = len(regions)
+        ind3 = np.zeros((max(R, 1), 3))
+        feats = np.zeros((max(R, 1), 3), np.float32)
+        opt = opt or options()
+        _check(lib.pmcim_screen_features(self.handle, C.byref(opt), R, regions_array(regions), V.shape[1], _ptr(V),
+                                         _ptr(ind3), _ptr(feats)), "pmcim_screen_features")
+        return ind3[:R], feats[:R]
 
     def verify(self, lam, opt=None):
         lib = load()

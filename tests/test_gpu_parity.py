@@ -354,7 +354,7 @@ def test_mixed_fallback_path(pm):
     refinement cannot converge there, so that node is re-solved in FP64 and flagged; the
     moments still agree with the FP64 form."""
     rng = np.random.default_rng(77)
-    c, r, N, n = 0.0, 1.0, 16, 24
+    c, r, N, n = 0.0, 1.0, 16, 40          # n > 32: the precision-form kernel (smaller n use the warp kernel)
     a = np.concatenate([rng.uniform(0.2, 0.7, 8), rng.uniform(1.4, 3.0, n - 9)]) * np.exp(2j * np.pi * rng.random(n - 1))
     mu = np.concatenate([[c + r * (1.0 + 1e-7)], c + r * a])   # node 0 is z_0 = c + r
     prob, _ = w.similarity_linear(mu, seed=5)

@@ -349,3 +349,20 @@ def test_pin_catches_transpose_instead_of_adjoint(monkeypatch):
     b = o.beyn_extract(m.C0, m.C1, tol_svd=1e-13)
     ri, ci = linear_sum_assignment(np.abs(mu[:, None] - b.lam[None, :]))
     assert np.max(np.abs(mu[ri] - b.lam[ci])) > 1e-3
+
+
+def test_indicator_is_zero_when_pf_is_at_rounding_level():
+    """Sec. 2.1: P = 0 without eigenvalues inside, so P f = 0. With every pole at |a| = 5 and
+    N = 64 the exact indicator is 5^-32 ~ 2e-23, and P f|_N is rounding noise; the oracle
+    returns 0 there, within 1e-12 of the exact value, and is unchanged with poles inside."""
+    rng = np.random.default_rng(71)
+    c, r, N = 0.0, 1.0, 64
+    far = c + r * 5.0 * np.exp(2j * np.pi * rng.random(10))
+    V = w.probe_block(rng, 10, 2)
+    m = o.moments(w.diagonal_linear(far), c, r, N, V)
+    I = o.indicator_value(m.pf_N, m.pf_half, m.pf_abs)
+    assert I == 0.0 and abs(I - 5.0 ** -32) < 1e-12
+    mu, a = _poles(rng, c, r, 3, 7)
+    m = o.moments(w.diagonal_linear(mu), c, r, N, w.probe_block(rng, 10, 2))
+    I_exact = np.linalg.norm(1.0 / (1.0 - a ** (N // 2))) / math.sqrt(10)
+    assert o.indicator_value(m.pf_N, m.pf_half, m.pf_abs) == pytest.approx(I_exact, rel=1e-12)

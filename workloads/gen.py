@@ -29,7 +29,7 @@ __all__ = [
     "complex_gaussian", "probe_block", "grid_regions",
     "quadratic_small", "delay_large", "batched_quadratics", "mass_spring",
     "diagonal_linear", "similarity_linear", "diagonal_delay", "paper_n4_example",
-    "diagonal_quadratic",
+    "diagonal_quadratic", "screen_trace_problems",
 ]
 
 
@@ -244,3 +244,32 @@ def paper_n4_example(path: str) -> Problem:
             mats[cur].append([float(x) for x in s.split()])
     T0, T1, T2 = (np.asfortranarray(np.array(mats[k], dtype=np.complex128)) for k in ("T0", "T1", "T2"))
     return Problem(4, [(T0, MONOMIAL, 0, 0.0), (T1, MONOMIAL, 1, 0.0), (T2, MONOMIAL, 2, 0.0)])
+
+
+def screen_trace_problems(seeds: Sequence[int], n_choices=(16, 24, 32), disks: int = 48, N: int = 64,
+                          l: int = 1):
+    """Small delay-type and quadratic problems with randomly placed disks, for screen traces.
+
+    Even seeds give -zI + A0 + A1 exp(-z) (A0 from a spectrum uniform in |z| <= 2,
+    A1 Gaussian * 0.5/sqrt(n)); odd seeds give A0 + z A1 + z^2 A2 (Gaussian / sqrt(n)).
+    Disk centres are uniform in [-3,3] x [-3,3], radii log-uniform in [0.01, 1].
+    """
+    out = []
+    for sd in seeds:
+        rng = np.random.default_rng(10_000 + sd)
+        n = int(rng.choice(n_choices))
+        if sd % 2 == 0:
+            d = 2.0 * np.sqrt(rng.random(n)) * np.exp(2j * np.pi * rng.random(n))
+            Q = complex_gaussian(rng, (n, n)) + 2.0 * np.eye(n)
+            A0 = Q @ np.diag(d) @ np.linalg.inv(Q)
+            A1 = complex_gaussian(rng, (n, n)) * (0.5 / math.sqrt(n))
+            prob = Problem(n, [(-1.0 + 0j, MONOMIAL, 1, 0.0), (np.asfortranarray(A0), MONOMIAL, 0, 0.0),
+                               (np.asfortranarray(A1), EXP_NEG, 0, 1.0)])
+        else:
+            A = [complex_gaussian(rng, (n, n)) / math.sqrt(n) for _ in range(3)]
+            prob = Problem(n, [(np.asfortranarray(A[k]), MONOMIAL, k, 0.0) for k in range(3)])
+        c = rng.uniform(-3, 3, disks) + 1j * rng.uniform(-3, 3, disks)
+        r = 10.0 ** rng.uniform(-2, 0, disks)
+        regs = [Region(complex(c[i]), float(r[i]), N) for i in range(disks)]
+        out.append((prob, regs, probe_block(rng, n, l)))
+    return out

@@ -362,7 +362,9 @@ def test_indicator_is_zero_when_pf_is_at_rounding_level():
     m = o.moments(w.diagonal_linear(far), c, r, N, V)
     I = o.indicator_value(m.pf_N, m.pf_half, m.pf_abs)
     assert I == 0.0 and abs(I - 5.0 ** -32) < 1e-12
-    mu, a = _poles(rng, c, r, 3, 7)
+    # poles inside and just outside (|a| <= 1.8 at N = 32 keeps every component of P f resolved)
+    N = 32
+    mu, a = _poles(rng, c, r, 3, 7, rout=(1.3, 1.8))
     m = o.moments(w.diagonal_linear(mu), c, r, N, w.probe_block(rng, 10, 2))
     I_exact = np.linalg.norm(1.0 / (1.0 - a ** (N // 2))) / math.sqrt(10)
     assert o.indicator_value(m.pf_N, m.pf_half, m.pf_abs) == pytest.approx(I_exact, rel=1e-12)

@@ -287,6 +287,93 @@ def run_batched(args, world, rank, local):
     return 0
 
 
+def run_screen(args, world, rank, local):
+    """Learned screen on the damped mass-spring problem (n = 2048).
+
+    Untimed set-up: traces of small delay and quadratic problems (features
+    I_8, I_16, r and the full N = 64 decision) computed by the library, the
+    screen trained on the GPU, and its threshold set so every training
+    positive passes with margin. Timed: pmCIMb in the precision form on an
+    8 x 8 block of the 32 x 256 disk grid, without and with the screen."""
+    import torch
+    from paper_2312_13117_gb300 import pmcim
+    import workloads as w
+    # ---- traces and training (untimed) ----
+    t0 = time.perf_counter()
+    F, Y = [], []
+    for prob, regs, V in w.screen_trace_problems(range(args.trace_problems)):
+        h = pmcim.Problem(prob.n, prob.terms)
+        ind3, feats = h.screen_features(regs, V)
+        h.close()
+        F.append(feats)
+        Y.append(ind3[:, 2] > 0.1)
+    F = np.concatenate(F)
+    Y = np.concatenate(Y).astype(np.uint8)
+    t_traces = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    perm = rng.permutation(len(Y))
+    F, Y = F[perm], Y[perm]
+    W1 = rng.standard_normal((64, 3)) * np.sqrt(2.0 / 3)
+    W2 = rng.standard_normal((64, 64)) * np.sqrt(2.0 / 64)
+    W3 = rng.standard_normal(64) * np.sqrt(1.0 / 64)
+    p0 = np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), W3, [0.0]]).astype(np.float32)
+    t0 = time.perf_counter()
+    params, loss = pmcim.screen_train(F, Y, p0, epochs=args.epochs, batch=1024, lr=3e-3, pos_weight=8.0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    prob = pmcim.screen_apply(F, params)
+    thr = 0.5 * float(prob[Y == 1].min())
+    # ---- the mass-spring slice ----
+    W = w.mass_spring(l=args.ms_l)
+    cols, rows = range(24, 32), range(40, 48)
+    regs = [W.regions[i * 256 + j] for i in cols for j in rows]
+    h = pmcim.Problem(W.problem.n, W.problem.terms)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, kw in (("plain", {}), ("screened", {"screen_params": params, "screen_threshold": thr})):
+        o = pmcim.options(stream=stream.cuda_stream, precision=pmcim.PREC_FP32_IR, **kw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = h.solve(regs, W.V, opt=o, want_vecs=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": e0.elapsed_time(e1) / 1e3, "lam": r["lam"], "ind": r["ind"], "stats": r["stats"],
+                     "status": r["status"], "region_of": r["region_of"]}
+    h.close()
+    plain_cand = out["plain"]["ind"] > 0.1
+    passed = (out["screened"]["status"] & pmcim.RS_SCREENED) == 0
+    recall = float(np.mean(passed[plain_cand])) if plain_cand.any() else 1.0
+    with_eigs = np.zeros(len(regs), bool)
+    with_eigs[np.unique(out["plain"]["region_of"])] = True
+    recall_eig_disks = float(np.mean(passed[with_eigs])) if with_eigs.any() else 1.0
+    a, b = np.sort_complex(out["plain"]["lam"]), np.sort_complex(out["screened"]["lam"])
+    found = sum(1 for x in a if len(b) and np.min(np.abs(b - x)) <= 1e-12 * max(1.0, abs(x)))
+    eig_recall = found / len(a) if len(a) else 1.0
+    same = len(a) == len(b) and (len(a) == 0 or float(np.max(np.abs(a - b))) <= 1e-12)
+    R = len(regs)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "learned screen: subregions/s on the mass-spring NEP (n=2048)",
+            "value": R / out["screened"]["seconds"], "unit": "subregions/s", "n_gpus": world,
+            "higher_is_better": True, "dtype": "precision form (FP32 LU + FP64 IR); screen BF16/FP32",
+            "data": "synthetic",
+            "config": {"workload": "mass-spring z^2 I + z C + K, n=2048, l=%d, N=64; disks of grid columns 24-31 x "
+                                   "rows 40-47 of the 32 x 256 split of [-1,0] x [0,8]" % args.ms_l,
+                       "traces": int(len(Y)), "trace_positive_fraction": float(Y.mean()),
+                       "trace_seconds": t_traces, "train_seconds": t_train, "epochs": args.epochs,
+                       "final_loss": float(loss[-1]), "threshold": thr},
+            "plain_seconds": out["plain"]["seconds"], "screened_seconds": out["screened"]["seconds"],
+            "speedup": out["plain"]["seconds"] / out["screened"]["seconds"],
+            "eigenvalue_recall_vs_plain": eig_recall, "recall_disks_with_eigenvalues": recall_eig_disks,
+            "candidate_decision_recall_vs_plain": recall, "screened_out": out["screened"]["stats"]["screened_out"],
+            "candidates_plain": int(plain_cand.sum()), "eigenvalues_plain": len(a), "eigenvalues_screened": len(b),
+            "same_eigenvalues": same,
+            "solves_plain": out["plain"]["stats"]["solves"],
+            "solves_screened": out["screened"]["stats"]["solves"] + out["screened"]["stats"]["screen_solves"]}))
+    return 0
+
+
 def run_full(args, P, W, opt, opt_mixed, world, rank, local):
     """Time to all eigenvalues: one pmCIMb pass over the whole grid per form."""
     import torch
@@ -334,7 +421,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the precision-form measurement")
     ap.add_argument("--only-mixed", action="store_true", help="time only the precision form (profiling runs)")
-    ap.add_argument("--workload", default="delay", choices=["delay", "batched"])
+    ap.add_argument("--workload", default="delay", choices=["delay", "batched", "screen"])
+    ap.add_argument("--trace-problems", type=int, default=2100, help="screen traces: 48 disks per problem")
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--ms-l", type=int, default=48, help="probe columns on the mass-spring problem")
     ap.add_argument("--problems-per-step", type=int, default=4)
     ap.add_argument("--batched-fp64", action="store_true", help="also time the batched workload in plain FP64")
     ap.add_argument("--time-budget", type=float, default=240.0, help="seconds before remaining legs are skipped")
@@ -353,6 +443,8 @@ def main():
     pmcim.load()
     if args.workload == "batched":
         return run_batched(args, world, rank, local)
+    if args.workload == "screen":
+        return run_screen(args, world, rank, local)
     import workloads as w
 
     W = w.delay_large()

@@ -98,9 +98,10 @@ typedef struct {
   /* learned screen (pmcim_solve / pmcim_batch_solve): NULL = off; else the
      PMCIM_SCREEN_PARAMS trained parameters (host or device). Every disk first
      gets the coarse indicators of screen_N nodes (one probe column); a disk
-     whose screen probability is below screen_threshold skips the full
-     indicator and Beyn (status PMCIM_RS_SCREENED); every other disk goes on
-     exactly as without the screen. */
+     skips the full indicator and Beyn (status PMCIM_RS_SCREENED) only when
+     its screen probability is below screen_threshold and both coarse
+     indicators (8 and 16 nodes) are at or below tol_ind; every other disk
+     goes on exactly as without the screen. */
   const float* screen_params;
   double screen_threshold;
   int32_t screen_N;        /* coarse nodes, a multiple of 16 (default 16)            */

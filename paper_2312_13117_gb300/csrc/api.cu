@@ -923,9 +923,18 @@ int run_screen(Call& c, const std::vector<HostRegion>& top, std::vector<uint8_t>
   CU(screen_forward(R, ws.feats.as<float>(), ws.sparams.as<float>(), ws.sprob.as<float>(), ws.sscratch.p, s));
   prof_end(PMCIM_K_SCREEN, s);
   std::vector<float> prob(R);
+  std::vector<double> ind3((size_t)R * 3);
   CU(cudaMemcpyAsync(prob.data(), ws.sprob.p, R * sizeof(float), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(ind3.data(), ws.ind3.p, (size_t)R * 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
-  for (int g = 0; g < R; ++g) (*skip)[g] = (prob[g] < c.opt->screen_threshold) ? 1 : 0;
+  // skip only a confident negative: the network below its threshold AND both
+  // coarse indicators (Eq. 3.1 with 8 and 16 nodes) at or below tol_ind, so a
+  // disk the paper's own coarse screen would flag is never dropped
+  for (int g = 0; g < R; ++g)
+    (*skip)[g] = (prob[g] < c.opt->screen_threshold && !(ind3[3 * (size_t)g] > c.opt->tol_ind) &&
+                  !(ind3[3 * (size_t)g + 1] > c.opt->tol_ind))
+                     ? 1
+                     : 0;
   c.groups.resize(G);
   CHK(upload_problems(c));
   return PMCIM_OK;

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libpmcim.so")
 PMCIM_OK = 0
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ECAPACITY", -6: "ENOTSUP"}
 
-RS_CANDIDATE, RS_SATURATED, RS_SPLIT, RS_SINGULAR_NODE, RS_IR_FALLBACK, RS_NO_EIG = 1, 2, 4, 8, 16, 32
+RS_CANDIDATE, RS_SATURATED, RS_SPLIT, RS_SINGULAR_NODE, RS_IR_FALLBACK, RS_NO_EIG, RS_SCREENED = 1, 2, 4, 8, 16, 32, 64
 F_MONOMIAL, F_EXP_NEG = 0, 1
 PREC_FP64, PREC_FP32_IR, PREC_AUTO = 0, 1, 2
 

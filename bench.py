@@ -134,24 +134,32 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x: float, world: int) -> float:
+def disk_ids(step: int, rank: int, world: int, per_step: int, R: int, offset: int):
+    """Disks of one rank in one step: each rank takes its own consecutive block of
+    per_step disks, so the ranks' blocks are disjoint (weak scaling, no data-path
+    collective)."""
+    base = offset + (step * world + rank) * per_step
+    return [(base + i) % R for i in range(per_step)]
+
+
+def reduce_over_ranks(x: float, world: int, op: str) -> float:
+    """max or sum of a scalar over ranks (timings and counts only)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    return reduce_over_ranks(x, world, "max")
 
 
 def sum_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return reduce_over_ranks(x, world, "sum")
 
 
 # ---------------------------------------------------------------------------
@@ -453,9 +461,7 @@ def main():
     B = args.regions_per_step
 
     def batch(step):
-        # rank r takes its own disjoint batch of consecutive disks: weak scaling
-        base = args.region_offset + (step * world + rank) * B
-        return [W.regions[(base + i) % R] for i in range(B)]
+        return [W.regions[g] for g in disk_ids(step, rank, world, B, R, args.region_offset)]
 
     stream = torch.cuda.current_stream()
     opt = pmcim.options(stream=stream.cuda_stream)

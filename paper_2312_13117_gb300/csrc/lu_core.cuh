@@ -83,143 +83,164 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* red2) {
 // row swaps and elimination). piv[k] = row swapped with row k at step k.
 // Returns 0, or 1 + the first column whose pivot was exactly zero.
 // ---------------------------------------------------------------------------
+// Panel factorisation of columns k0..k0+kb-1 (rows k0..n-1), with the row swaps
+// applied across all ncols columns.
 template <typename T2>
-__device__ int cta_lu(T2* __restrict__ M, int n, int ncols, int* __restrict__ piv, LuSmemT<T2>& sm) {
+__device__ void cta_lu_panel(T2* __restrict__ M, int n, int ncols, int k0, int kb, int* __restrict__ piv,
+                             LuSmemT<T2>& sm) {
   const int tid = threadIdx.x;
   const size_t ld = (size_t)n;
-  if (tid == 0) sm.info_sh = 0;
-  __syncthreads();
+  const int kend = k0 + kb;
+  // ---- panel factorisation, columns k0..kend-1 ----
+  for (int j = k0; j < kend; ++j) {
+    T2* colj = M + (size_t)j * ld;
+    double bv = -1.0;
+    int bi = n;
+    for (int i = j + tid; i < n; i += THREADS) {
+      double v = l1abs(colj[i]);
+      if (v > bv) { bv = v; bi = i; }
+    }
+    warp_argmax(bv, bi);
+    if ((tid & 31) == 0) { sm.red_v[tid >> 5] = bv; sm.red_i[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double v = sm.red_v[0];
+      int ii = sm.red_i[0];
+      for (int w = 1; w < THREADS / 32; ++w) {
+        if (sm.red_v[w] > v || (sm.red_v[w] == v && sm.red_i[w] < ii)) { v = sm.red_v[w]; ii = sm.red_i[w]; }
+      }
+      if (ii >= n) ii = j;
+      sm.piv_sh = ii;
+      piv[j] = ii;
+    }
+    __syncthreads();
+    const int p = sm.piv_sh;
+    if (p != j) {
+      for (int c = tid; c < ncols; c += THREADS) {
+        T2* cc = M + (size_t)c * ld;
+        T2 t = cc[j];
+        cc[j] = cc[p];
+        cc[p] = t;
+      }
+    }
+    __syncthreads();
+    for (int c = j + 1 + tid; c < kend; c += THREADS) sm.prow[c - k0] = M[(size_t)c * ld + j];
+    const T2 pv = colj[j];
+    const bool zero = cis_zero(pv);
+    if (zero && tid == 0 && sm.info_sh == 0) sm.info_sh = j + 1;
+    __syncthreads();
+    if (!zero) {
+      const T2 rp = crecip(pv);
+      for (int i = j + 1 + tid; i < n; i += THREADS) {
+        T2 lij = cmul(colj[i], rp);
+        colj[i] = lij;
+        for (int c = j + 1; c < kend; ++c) cfms(M[(size_t)c * ld + i], lij, sm.prow[c - k0]);
+      }
+    }
+    __syncthreads();
+  }
+}
 
+// U12 = L11^{-1} A12 for rows k0..k0+kb-1, columns k0+kb..ncols-1.
+template <typename T2>
+__device__ void cta_lu_trsm(T2* __restrict__ M, int n, int ncols, int k0, int kb, LuSmemT<T2>& sm) {
+  const int tid = threadIdx.x;
+  const size_t ld = (size_t)n;
+  const int kend = k0 + kb;
+  // ---- U12 = L11^{-1} A12 (rows k0..kend-1, columns kend..ncols-1) ----
+  for (int e = tid; e < kb * kb; e += THREADS) {
+    int r = e % kb, c = e / kb;
+    sm.Ls[c * NB + r] = M[(size_t)(k0 + c) * ld + k0 + r];  // Ls[t*NB + i] = L11[i][t]
+  }
+  __syncthreads();
+  {
+    // one warp per column, lane i holds row k0+i (NB == warp size)
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int c = kend + wid; c < ncols; c += THREADS / 32) {
+      T2* cc = M + (size_t)c * ld + k0;
+      T2 x = (lane < kb) ? cc[lane] : czero<T2>();
+      for (int t = 0; t < kb - 1; ++t) {
+        T2 xt;
+        xt.x = __shfl_sync(0xffffffffu, x.x, t);
+        xt.y = __shfl_sync(0xffffffffu, x.y, t);
+        if (lane > t && lane < kb) cfms(x, sm.Ls[t * NB + lane], xt);
+      }
+      if (lane < kb) cc[lane] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// Trailing update A22 -= L21 U12 (rows and columns from k0+kb on), FMA pipes.
+template <typename T2>
+__device__ void cta_lu_update_simt(T2* __restrict__ M, int n, int ncols, int k0, int kb, LuSmemT<T2>& sm) {
+  const int tid = threadIdx.x;
+  const size_t ld = (size_t)n;
+  const int kend = k0 + kb;
+  // ---- trailing update A22 -= L21 U12 over TILE x TILE tiles ----
+  const int m_rows = n - kend, m_cols = ncols - kend;
+  const int mt = (m_rows + TILE - 1) / TILE, nt = (m_cols + TILE - 1) / TILE;
+  const int tx = tid & 15, ty = tid >> 4;
+  for (int ti = 0; ti < mt; ++ti) {
+    const int r0 = kend + ti * TILE;
+    for (int e = tid; e < NB * TILE; e += THREADS) {
+      int r = e % TILE, kk = e / TILE;
+      T2 v = czero<T2>();
+      if (kk < kb && r0 + r < n) v = M[(size_t)(k0 + kk) * ld + r0 + r];
+      sm.Ls[kk * TILE + r] = v;
+    }
+    for (int tj = 0; tj < nt; ++tj) {
+      const int c0 = kend + tj * TILE;
+      for (int e = tid; e < NB * TILE; e += THREADS) {
+        int kk = e % NB, c = e / NB;
+        T2 v = czero<T2>();
+        if (kk < kb && c0 + c < ncols) v = M[(size_t)(c0 + c) * ld + k0 + kk];
+        sm.Us[kk * US_LD + c] = v;
+      }
+      __syncthreads();
+      T2 acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int r = r0 + tx + 16 * i, c = c0 + ty + 16 * q;
+          acc[i][q] = (r < n && c < ncols) ? M[(size_t)c * ld + r] : czero<T2>();
+        }
+      for (int kk = 0; kk < kb; ++kk) {
+        T2 a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = sm.Ls[kk * TILE + tx + 16 * i];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[q] = sm.Us[kk * US_LD + ty + 16 * q];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cfms(acc[i][q], a[i], b[q]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int r = r0 + tx + 16 * i, c = c0 + ty + 16 * q;
+          if (r < n && c < ncols) M[(size_t)c * ld + r] = acc[i][q];
+        }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T2>
+__device__ int cta_lu(T2* __restrict__ M, int n, int ncols, int* __restrict__ piv, LuSmemT<T2>& sm) {
+  if (threadIdx.x == 0) sm.info_sh = 0;
+  __syncthreads();
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = min(NB, n - k0);
     const int kend = k0 + kb;
-
-    // ---- panel factorisation, columns k0..kend-1 ----
-    for (int j = k0; j < kend; ++j) {
-      T2* colj = M + (size_t)j * ld;
-      double bv = -1.0;
-      int bi = n;
-      for (int i = j + tid; i < n; i += THREADS) {
-        double v = l1abs(colj[i]);
-        if (v > bv) { bv = v; bi = i; }
-      }
-      warp_argmax(bv, bi);
-      if ((tid & 31) == 0) { sm.red_v[tid >> 5] = bv; sm.red_i[tid >> 5] = bi; }
-      __syncthreads();
-      if (tid == 0) {
-        double v = sm.red_v[0];
-        int ii = sm.red_i[0];
-        for (int w = 1; w < THREADS / 32; ++w) {
-          if (sm.red_v[w] > v || (sm.red_v[w] == v && sm.red_i[w] < ii)) { v = sm.red_v[w]; ii = sm.red_i[w]; }
-        }
-        if (ii >= n) ii = j;
-        sm.piv_sh = ii;
-        piv[j] = ii;
-      }
-      __syncthreads();
-      const int p = sm.piv_sh;
-      if (p != j) {
-        for (int c = tid; c < ncols; c += THREADS) {
-          T2* cc = M + (size_t)c * ld;
-          T2 t = cc[j];
-          cc[j] = cc[p];
-          cc[p] = t;
-        }
-      }
-      __syncthreads();
-      for (int c = j + 1 + tid; c < kend; c += THREADS) sm.prow[c - k0] = M[(size_t)c * ld + j];
-      const T2 pv = colj[j];
-      const bool zero = cis_zero(pv);
-      if (zero && tid == 0 && sm.info_sh == 0) sm.info_sh = j + 1;
-      __syncthreads();
-      if (!zero) {
-        const T2 rp = crecip(pv);
-        for (int i = j + 1 + tid; i < n; i += THREADS) {
-          T2 lij = cmul(colj[i], rp);
-          colj[i] = lij;
-          for (int c = j + 1; c < kend; ++c) cfms(M[(size_t)c * ld + i], lij, sm.prow[c - k0]);
-        }
-      }
-      __syncthreads();
-    }
-
+    cta_lu_panel(M, n, ncols, k0, kb, piv, sm);
     if (kend >= ncols) continue;
-
-    // ---- U12 = L11^{-1} A12 (rows k0..kend-1, columns kend..ncols-1) ----
-    for (int e = tid; e < kb * kb; e += THREADS) {
-      int r = e % kb, c = e / kb;
-      sm.Ls[c * NB + r] = M[(size_t)(k0 + c) * ld + k0 + r];  // Ls[t*NB + i] = L11[i][t]
-    }
-    __syncthreads();
-    {
-      // one warp per column, lane i holds row k0+i (NB == warp size)
-      const int lane = tid & 31, wid = tid >> 5;
-      for (int c = kend + wid; c < ncols; c += THREADS / 32) {
-        T2* cc = M + (size_t)c * ld + k0;
-        T2 x = (lane < kb) ? cc[lane] : czero<T2>();
-        for (int t = 0; t < kb - 1; ++t) {
-          T2 xt;
-          xt.x = __shfl_sync(0xffffffffu, x.x, t);
-          xt.y = __shfl_sync(0xffffffffu, x.y, t);
-          if (lane > t && lane < kb) cfms(x, sm.Ls[t * NB + lane], xt);
-        }
-        if (lane < kb) cc[lane] = x;
-      }
-    }
-    __syncthreads();
-
+    cta_lu_trsm(M, n, ncols, k0, kb, sm);
     if (kend >= n) continue;
-
-    // ---- trailing update A22 -= L21 U12 over TILE x TILE tiles ----
-    const int m_rows = n - kend, m_cols = ncols - kend;
-    const int mt = (m_rows + TILE - 1) / TILE, nt = (m_cols + TILE - 1) / TILE;
-    const int tx = tid & 15, ty = tid >> 4;
-    for (int ti = 0; ti < mt; ++ti) {
-      const int r0 = kend + ti * TILE;
-      for (int e = tid; e < NB * TILE; e += THREADS) {
-        int r = e % TILE, kk = e / TILE;
-        T2 v = czero<T2>();
-        if (kk < kb && r0 + r < n) v = M[(size_t)(k0 + kk) * ld + r0 + r];
-        sm.Ls[kk * TILE + r] = v;
-      }
-      for (int tj = 0; tj < nt; ++tj) {
-        const int c0 = kend + tj * TILE;
-        for (int e = tid; e < NB * TILE; e += THREADS) {
-          int kk = e % NB, c = e / NB;
-          T2 v = czero<T2>();
-          if (kk < kb && c0 + c < ncols) v = M[(size_t)(c0 + c) * ld + k0 + kk];
-          sm.Us[kk * US_LD + c] = v;
-        }
-        __syncthreads();
-        T2 acc[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            int r = r0 + tx + 16 * i, c = c0 + ty + 16 * q;
-            acc[i][q] = (r < n && c < ncols) ? M[(size_t)c * ld + r] : czero<T2>();
-          }
-        for (int kk = 0; kk < kb; ++kk) {
-          T2 a[4], b[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = sm.Ls[kk * TILE + tx + 16 * i];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) b[q] = sm.Us[kk * US_LD + ty + 16 * q];
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) cfms(acc[i][q], a[i], b[q]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            int r = r0 + tx + 16 * i, c = c0 + ty + 16 * q;
-            if (r < n && c < ncols) M[(size_t)c * ld + r] = acc[i][q];
-          }
-        __syncthreads();
-      }
-    }
+    cta_lu_update_simt(M, n, ncols, k0, kb, sm);
   }
   __syncthreads();
   return sm.info_sh;
@@ -277,6 +298,114 @@ __device__ void cta_perm_fwd_subst(T2* __restrict__ M, int n, int l, const int* 
     }
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------
+// Blocked triangular solves on the l columns n..n+l-1 of M (32-row blocks):
+// the 32 x 32 diagonal block is solved one warp per column (lane = row), then
+// the rows outside the block are updated by all threads (coalesced over rows).
+// Two barriers per block instead of two per row.
+// ---------------------------------------------------------------------------
+
+// Y[i, :] -= M[i, k0:k0+kb] * S where S (kb x l) sits in sm.Us ([t][c]);
+// columns in chunks of 8 kept in registers, so M is read once per chunk.
+template <typename T2>
+__device__ __forceinline__ void block_update_row(const T2* __restrict__ M, T2* __restrict__ Y, size_t ld, int i,
+                                                 int k0, int kb, int l, LuSmemT<T2>& sm) {
+  for (int c0 = 0; c0 < l; c0 += 8) {
+    T2 acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = (c0 + q < l) ? Y[(size_t)(c0 + q) * ld + i] : czero<T2>();
+    for (int t = 0; t < kb; ++t) {
+      const T2 m = M[(size_t)(k0 + t) * ld + i];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) cfms(acc[q], m, sm.Us[t * US_LD + c0 + q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (c0 + q < l) Y[(size_t)(c0 + q) * ld + i] = acc[q];
+  }
+}
+
+// L y = b, L unit lower (no row swaps here).
+template <typename T2>
+__device__ void cta_fwd_blocked(T2* __restrict__ M, int n, int l, LuSmemT<T2>& sm) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const size_t ld = (size_t)n;
+  T2* Y = M + (size_t)n * ld;
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = min(NB, n - k0);
+    for (int e = tid; e < kb * kb; e += THREADS) {
+      const int r = e % kb, c = e / kb;
+      sm.Ls[c * NB + r] = M[(size_t)(k0 + c) * ld + k0 + r];  // Ls[t*NB + i] = L[k0+i][k0+t]
+    }
+    __syncthreads();
+    for (int c = wid; c < l; c += THREADS / 32) {
+      T2* yc = Y + (size_t)c * ld + k0;
+      T2 y = (lane < kb) ? yc[lane] : czero<T2>();
+      for (int t = 0; t < kb - 1; ++t) {
+        T2 yt;
+        yt.x = __shfl_sync(0xffffffffu, y.x, t);
+        yt.y = __shfl_sync(0xffffffffu, y.y, t);
+        if (lane > t && lane < kb) cfms(y, sm.Ls[t * NB + lane], yt);
+      }
+      if (lane < kb) yc[lane] = y;
+      if (lane < kb) sm.Us[lane * US_LD + c] = y;  // solved block rows, [t][c]
+    }
+    __syncthreads();
+    for (int i = k0 + kb + tid; i < n; i += THREADS) block_update_row(M, Y, ld, i, k0, kb, l, sm);
+    __syncthreads();
+  }
+}
+
+// U x = y, U upper with its diagonal.
+template <typename T2>
+__device__ void cta_back_blocked(T2* __restrict__ M, int n, int l, LuSmemT<T2>& sm) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const size_t ld = (size_t)n;
+  T2* Y = M + (size_t)n * ld;
+  const int nblk = (n + NB - 1) / NB;
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int k0 = b * NB;
+    const int kb = min(NB, n - k0);
+    for (int e = tid; e < kb * kb; e += THREADS) {
+      const int r = e % kb, c = e / kb;
+      sm.Ls[c * NB + r] = M[(size_t)(k0 + c) * ld + k0 + r];  // Ls[t*NB + i] = U[k0+i][k0+t]
+    }
+    __syncthreads();
+    for (int c = wid; c < l; c += THREADS / 32) {
+      T2* yc = Y + (size_t)c * ld + k0;
+      T2 y = (lane < kb) ? yc[lane] : czero<T2>();
+      for (int t = kb - 1; t >= 0; --t) {
+        if (lane == t) y = cdiv(y, sm.Ls[t * NB + t]);
+        T2 xt;
+        xt.x = __shfl_sync(0xffffffffu, y.x, t);
+        xt.y = __shfl_sync(0xffffffffu, y.y, t);
+        if (lane < t) cfms(y, sm.Ls[t * NB + lane], xt);
+      }
+      if (lane < kb) yc[lane] = y;
+      if (lane < kb) sm.Us[lane * US_LD + c] = y;
+    }
+    __syncthreads();
+    for (int i = tid; i < k0; i += THREADS) block_update_row(M, Y, ld, i, k0, kb, l, sm);
+    __syncthreads();
+  }
+}
+
+// perm[i] = original row that ends up in row i after the swaps piv[0..n-1].
+__device__ inline void cta_pivots_to_perm(const int* __restrict__ piv, int* __restrict__ perm, int n) {
+  for (int i = threadIdx.x; i < n; i += THREADS) perm[i] = i;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < n; ++k) {
+      const int p = piv[k];
+      if (p != k) {
+        const int t = perm[k];
+        perm[k] = perm[p];
+        perm[p] = t;
+      }
+    }
+  __syncthreads();
 }
 
 }  // namespace lucore

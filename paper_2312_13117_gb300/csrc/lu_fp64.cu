@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_fp64(NodeArgs a) {
     __syncthreads();
 
     const int info = cta_lu(M, n, ncols, piv, sm.lu);
-    cta_back_subst(M, n, l, sm.lu);
+    cta_back_blocked(M, n, l, sm.lu);
 
     double2* Xo = a.X + rg.x_off + (size_t)it.j * n * l;
     for (size_t e = tid; e < (size_t)n * l; e += THREADS) Xo[e] = M[nn + e];

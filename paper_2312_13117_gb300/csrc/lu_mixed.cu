@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_mixed(NodeArgs a) {
     const int n = P.n, l = P.l, ncols = n + l;
     const size_t nn = (size_t)n * n, nl = (size_t)n * l;
     double2* R = reinterpret_cast<double2*>(slot + mixed_residual_offset(n, l));
+    int* perm = reinterpret_cast<int*>(slot + mixed_residual_offset(n, l) + nl * sizeof(double2));
     double2 z, w;
     node_weight(rg.cre, rg.cim, rg.r, rg.N, it.j, &z, &w);
     if (tid < P.K) sm.fz[tid] = eval_f(P.term[tid], z);
@@ -207,7 +208,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_mixed(NodeArgs a) {
     bool ok = (info == 0);
     int sweeps = 0;
     if (ok) {
-      cta_back_subst(M32, n, l, sm.u.lu32);
+      cta_back_blocked(M32, n, l, sm.u.lu32);
+      cta_pivots_to_perm(piv, perm, n);
       double xm = 0.0;
       for (size_t e = tid; e < nl; e += THREADS) {
         const float2 y = M32[nn + e];
@@ -228,11 +230,15 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_mixed(NodeArgs a) {
         rm = block_max(rm, sm.red);
         if (rm == 0.0) { conv = true; break; }
         const double inv = 1.0 / rm;
-        for (size_t e = tid; e < nl; e += THREADS)
-          M32[nn + e] = make_float2((float)(R[e].x * inv), (float)(R[e].y * inv));
+        // right-hand side P R / |R|max: the row swaps as one gather
+        for (size_t e = tid; e < nl; e += THREADS) {
+          const size_t c = e / n, i = e % n;
+          const double2 rv = R[c * n + perm[i]];
+          M32[nn + e] = make_float2((float)(rv.x * inv), (float)(rv.y * inv));
+        }
         __syncthreads();
-        cta_perm_fwd_subst(M32, n, l, piv, sm.u.lu32);
-        cta_back_subst(M32, n, l, sm.u.lu32);
+        cta_fwd_blocked(M32, n, l, sm.u.lu32);
+        cta_back_blocked(M32, n, l, sm.u.lu32);
         double dm = 0.0, xmx = 0.0;
         for (size_t e = tid; e < nl; e += THREADS) {
           const float2 d = M32[nn + e];
@@ -261,7 +267,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_mixed(NodeArgs a) {
       for (size_t e = tid; e < nl; e += THREADS) M64[nn + e] = P.V[e];
       __syncthreads();
       info = cta_lu(M64, n, ncols, piv, sm.u.lu64);
-      cta_back_subst(M64, n, l, sm.u.lu64);
+      cta_back_blocked(M64, n, l, sm.u.lu64);
       for (size_t e = tid; e < nl; e += THREADS) X[e] = M64[nn + e];
       pc.mark(5);
     }
@@ -272,11 +278,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_mixed(NodeArgs a) {
 
 }  // namespace
 
-// Slot layout: [FP32 matrix n x (n + l)] [FP64 residual n x l], or, after a
-// fallback, the FP64 matrix n x (n + l) over the whole slot.
+// Slot layout: [FP32 matrix n x (n + l)] [FP64 residual n x l] [row permutation n],
+// or, after a fallback, the FP64 matrix n x (n + l) over the whole slot.
 size_t mixed_slot_bytes(int n, int l) {
   const size_t fp64 = (size_t)n * (n + l) * sizeof(double2);
-  const size_t mixed = mixed_residual_offset(n, l) + (size_t)n * l * sizeof(double2);
+  const size_t mixed = mixed_residual_offset(n, l) + (size_t)n * l * sizeof(double2) + (size_t)n * sizeof(int);
   const size_t b = fp64 > mixed ? fp64 : mixed;
   return (b + 255) & ~(size_t)255;
 }

@@ -52,6 +52,10 @@ def _peaks():
         return {}
 
 
+# TF32 tensor peak: the measured dense bf16 burst x the nominal tf32 / bf16 ratio (1.1 / 2.25 PFLOP/s)
+TF32_PEAK_TFLOPS = float(_peaks().get("bf16_tflops", 1900.0)) * 1.1 / 2.25
+
+
 def fp64_peak_tflops(sm_max_mhz: float) -> float:
     """FP64 pipe peak: 2 DFMA / SM / clock x 2 flops x 152 SMs x max SM clock."""
     return FP64_DFMA_PER_SM_CLK * 2 * SM_COUNT * sm_max_mhz * 1e6 / 1e12
@@ -466,6 +470,7 @@ def main():
     stream = torch.cuda.current_stream()
     opt = pmcim.options(stream=stream.cuda_stream)
     opt_mixed = pmcim.options(stream=stream.cuda_stream, precision=pmcim.PREC_FP32_IR)
+    opt_tc = pmcim.options(stream=stream.cuda_stream, precision=pmcim.PREC_TF32X3_IR)
     P = pmcim.Problem(n, W.problem.terms)
     cap = 64 * l * B
 
@@ -500,38 +505,46 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
+    forms = [] if args.no_mixed else [("fp32ir", opt_mixed), ("tf32x3", opt_tc)]
     if args.only_mixed:
-        tm_ms, msolves, mfound, aggm, profm = timed(opt_mixed, args.steps, args.warmup)
+        for name, o in forms:
+            tm_ms, msolves, mfound, aggm, profm = timed(o, args.steps, args.warmup)
+            if rank == 0:
+                print(json.dumps({"form": name, "solves_per_s": msolves / (tm_ms / 1e3), "ms": tm_ms,
+                                  "stats": aggm, "kernels": profm}))
         clk = clocks.stop()
         if rank == 0:
-            print(json.dumps({"form": "precision", "solves_per_s": msolves / (tm_ms / 1e3), "ms": tm_ms,
-                              "stats": aggm, "kernels": profm, "clocks": clk}))
+            print(json.dumps({"clocks": clk}))
         P.close()
         return 0
     t_ms, solves, found, agg64, prof = timed(opt, args.steps, args.warmup)
-    mixed = None
-    if not args.no_mixed:
-        tm_ms, msolves, mfound, aggm, profm = timed(opt_mixed, args.steps, args.warmup)
+    runs = {name: timed(o, args.steps, args.warmup) for name, o in forms}
     clk = clocks.stop()
     t_max = max_over_ranks(t_ms, world)
     solves_all = sum_over_ranks(float(solves), world)
     value = solves_all / (t_max / 1e3)
     smax = clk.get("sm_max_mhz") or SM_MAX_MHZ
     peak64 = fp64_peak_tflops(smax)
-    if not args.no_mixed:
+    k_dense = sum(1 for t in W.problem.terms if not np.isscalar(t[0]))
+
+    def precision_record(name, run):
+        tm_ms, msolves, mfound, aggm, profm = run
         tm_max = max_over_ranks(tm_ms, world)
         fm = profm["factor_fp32"]
-        k_dense = sum(1 for t in W.problem.terms if not np.isscalar(t[0]))
         w64 = aggm["ir_sweeps"] * 8.0 * k_dense * n * n * l + aggm["ir_fallbacks"] * (8.0 * n ** 3 / 3 + 8.0 * n * n * l)
         w32 = msolves * (8.0 * n ** 3 / 3 + 8.0 * n * n * l) + aggm["ir_sweeps"] * 8.0 * n * n * l
         a64 = w64 / (fm["ms"] / 1e3) / 1e12 if fm["ms"] > 0 else None
         a32 = w32 / (fm["ms"] / 1e3) / 1e12 if fm["ms"] > 0 else None
-        mixed = {
-            "form": "FP32 LU + FP64 iterative refinement (residual R = V - T(z)X from the FP64 A_k)",
+        rec = {
+            "form": ("FP32 LU + FP64 iterative refinement (residual R = V - T(z)X from the FP64 A_k)"
+                     if name == "fp32ir" else
+                     "FP32 LU with 3xTF32 complex trailing updates on the tensor cores (tcgen05, TMEM "
+                     "accumulators) + FP64 iterative refinement"),
             "value": sum_over_ranks(float(msolves), world) / (tm_max / 1e3), "unit": UNIT,
             "ms_per_step": tm_max / args.steps, "speedup_vs_fp64": t_max / tm_max,
             "eigenvalues_found": mfound, "eigenvalues_found_fp64": found,
             "ir_sweeps_per_node": aggm["ir_sweeps"] / max(1, msolves), "ir_fallbacks": aggm["ir_fallbacks"],
+            "tc_timeouts": aggm.get("tc_timeouts", 0),
             "roofline": {"bound": "alu", "kernel": "k_factor_solve_mixed (FP64 pipe: refinement residuals)",
                          "achieved": a64, "peak": peak64, "unit": "TFLOP/s",
                          "frac": (a64 / peak64) if a64 else None,
@@ -539,6 +552,20 @@ def main():
                          "launches": fm["launches"], "share_of_step": fm["ms"] / tm_ms if tm_ms else None},
             "kernels": profm,
         }
+        if name == "tf32x3":
+            # tensor-pipe work of the trailing updates: 3 split products of the complex
+            # rank-32 updates, 8 real flops per complex multiply-add
+            upd = sum(8.0 * 32 * (n - k) * (n + l - k) for k in range(32, n, 32))
+            lu_share = profm["factor_fp32"].get("phase_share", {}).get("lu_fp32")
+            lu_s = fm["ms"] / 1e3 * lu_share if lu_share else None
+            tf = 3.0 * upd * msolves / lu_s / 1e12 if lu_s else None
+            rec["tensor"] = {"tf32_tflops_during_lu_phase": tf, "tf32_peak_tflops": TF32_PEAK_TFLOPS,
+                             "frac_during_lu_phase": tf / TF32_PEAK_TFLOPS if tf else None,
+                             "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
+        return rec
+
+    mixed = precision_record("fp32ir", runs["fp32ir"]) if "fp32ir" in runs else None
+    mixed_tc = precision_record("tf32x3", runs["tf32x3"]) if "tf32x3" in runs else None
 
     # ---- e2e: host buffers through the C ABI, copies inside the timed region
     e2e = None
@@ -617,7 +644,7 @@ def main():
                        "l2": "working set > L2 (304 x 16.3 MB factorisation slots)",
                        "eigenvalues_found": found},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "kernels": prof, "precision_form": mixed, "clocks": clk,
+            "kernels": prof, "precision_form": mixed, "precision_form_tc": mixed_tc, "clocks": clk,
         }
         print(json.dumps(line))
     P.close()

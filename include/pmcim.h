@@ -79,12 +79,16 @@ typedef struct {
 
 /* Arithmetic of the LU factorisation (the solves are always refined to FP64
    accuracy when a reduced precision is chosen). */
-#define PMCIM_PREC_FP64 0    /* plain FP64 LU                                    */
-#define PMCIM_PREC_FP32_IR 1 /* FP32 LU + FP64 iterative refinement              */
-#define PMCIM_PREC_AUTO 2    /* per problem, whichever of the two solves nodes
-                                faster on this device, measured on first use for
-                                each (n bucket, l, dense-term count) and kept for
-                                the process; both meet the same accuracy         */
+#define PMCIM_PREC_FP64 0      /* plain FP64 LU                                  */
+#define PMCIM_PREC_FP32_IR 1   /* FP32 LU + FP64 iterative refinement            */
+#define PMCIM_PREC_AUTO 2      /* per problem, whichever of the three forms solves
+                                  nodes fastest on this device, measured on first
+                                  use for each (n bucket, l, dense-term count) and
+                                  kept for the process; all meet the same accuracy */
+#define PMCIM_PREC_TF32X3_IR 3 /* FP32 LU whose trailing updates are complex
+                                  products on the tensor cores, each FP32 operand
+                                  split into two TF32 parts (3 products per real
+                                  product, FP32 accumulation), + FP64 refinement  */
 
 typedef struct {
   double tol_ind;          /* indicator threshold, paper default 0.1 (Sec. 3.1)        */
@@ -121,9 +125,12 @@ typedef struct {
   int32_t certified;       /* values accepted by the eigenvector certificate     */
   int32_t graphs;          /* CUDA graphs launched (one per level of disks)      */
   int32_t tuned_fp64;      /* problems the autotuner ran in FP64                 */
-  int32_t tuned_mixed;     /* problems the autotuner ran in the precision form   */
+  int32_t tuned_mixed;     /* problems the autotuner ran in PMCIM_PREC_FP32_IR    */
   int32_t screened_out;    /* disks the learned screen skipped                   */
   int32_t screen_solves;   /* coarse node solves spent on the screen             */
+  int32_t tuned_tc;        /* problems the autotuner ran in PMCIM_PREC_TF32X3_IR  */
+  int32_t tc_timeouts;     /* nodes whose tensor-core wait ran out (their LU was
+                              finished on the FMA pipes; results stay refined)  */
 } pmcim_stats;
 
 typedef struct pmcim_problem_s* pmcim_problem;
@@ -292,14 +299,16 @@ int pmcim_solve_points_noalloc(int32_t n, int32_t K, const pmcim_fterm* f, const
 #define PMCIM_K_FACTOR32 6 /* assembly + LU + solve at the nodes (FP32 LU)   */
 #define PMCIM_K_SCREEN 7   /* learned screen: MLP forward / training          */
 #define PMCIM_K_COUNT 8
+#define PMCIM_PHASE_COUNT 12
 
 typedef struct {
   int64_t launches[PMCIM_K_COUNT];
   double ms[PMCIM_K_COUNT]; /* summed event time; 0 unless timing was on */
   /* precision-form node kernel, with timing on: SM clock cycles summed over
-     CTAs per phase: assembly, FP32 LU, first solve, FP64 residual, correction
-     solves, FP64 fallback, node set-up, unused */
-  double mixed_phase_cycles[8];
+     CTAs per phase: assembly, LU panels, first solve, FP64 residual,
+     correction solves, FP64 fallback, node set-up, LU triangular solves
+     (U12), LU trailing updates, 3 unused */
+  double mixed_phase_cycles[PMCIM_PHASE_COUNT];
 } pmcim_profile;
 
 void pmcim_profile_enable(int on);

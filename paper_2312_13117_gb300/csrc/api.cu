@@ -117,7 +117,7 @@ struct Prof {
   bool on = false;
   int64_t launches[PMCIM_K_COUNT] = {};
   double ms[PMCIM_K_COUNT] = {};
-  double phase[8] = {};
+  double phase[PMCIM_PHASE_COUNT] = {};
   struct Pending {
     int kind;
     cudaEvent_t a, b;
@@ -162,7 +162,7 @@ void prof_add_phases(const unsigned long long* c, int slots) {
   Prof& P = prof();
   std::lock_guard<std::mutex> g(P.mu);
   for (int b = 0; b < slots; ++b)
-    for (int q = 0; q < 8; ++q) P.phase[q] += (double)c[(size_t)b * 8 + q];
+    for (int q = 0; q < PMCIM_PHASES; ++q) P.phase[q] += (double)c[(size_t)b * PMCIM_PHASES + q];
 }
 
 void prof_begin(int kind, cudaStream_t s) {
@@ -227,6 +227,7 @@ struct pmcim_problem_s {
   int n = 0, K = 0, n_dense = 0;
   TermDesc term[PMCIM_MAX_TERMS];
   double2* dA = nullptr;
+  float2* dA32 = nullptr;  // complex64 copy for the FP32 LU's assembly
   int device = 0;
   DevBuf V;  // probe block of the current call
   Workspace ws;
@@ -257,7 +258,7 @@ int call_stream(Workspace& ws, const pmcim_options* opt, cudaStream_t* out) {
 struct Group {
   pmcim_problem h;
   int l;
-  int form;  // PMCIM_PREC_FP64 or PMCIM_PREC_FP32_IR
+  int form;  // PMCIM_PREC_FP64, PMCIM_PREC_FP32_IR or PMCIM_PREC_TF32X3_IR
 };
 
 int check_options(const pmcim_options* opt) {
@@ -265,7 +266,7 @@ int check_options(const pmcim_options* opt) {
   if (!(opt->tol_ind >= 0.0) || !(opt->tol_svd >= 0.0) || !(opt->tol_verify >= 0.0))
     return fail(PMCIM_EINVAL, "tolerances must be non-negative");
   if (opt->precision != PMCIM_PREC_FP64 && opt->precision != PMCIM_PREC_FP32_IR &&
-      opt->precision != PMCIM_PREC_AUTO)
+      opt->precision != PMCIM_PREC_AUTO && opt->precision != PMCIM_PREC_TF32X3_IR)
     return fail(PMCIM_EINVAL, "unknown precision %d", opt->precision);
   if (opt->max_split_depth < 0 || opt->max_split_depth > 30) return fail(PMCIM_EINVAL, "max_split_depth out of range");
   if (opt->precision != PMCIM_PREC_FP64 && (opt->max_ir_sweeps < 1 || opt->max_ir_sweeps > 10))
@@ -324,6 +325,7 @@ int upload_problems(Call& c) {
     d.l = g.l;
     d.n_dense = g.h->n_dense;
     d.A = g.h->dA;
+    d.A32 = g.h->dA32;
     d.V = g.h->V.as<double2>();
     for (int k = 0; k < g.h->K; ++k) d.term[k] = g.h->term[k];
   }
@@ -333,8 +335,9 @@ int upload_problems(Call& c) {
 }
 
 // ===========================================================================
-// Autotuner: per (n-bucket, l, dense terms), FP64 or the precision form,
-// whichever solves nodes faster on this device (measured once per process).
+// Autotuner: per (n-bucket, l, dense terms), FP64 or one of the two precision
+// forms, whichever solves nodes fastest on this device (measured once per
+// process).
 // ===========================================================================
 struct TuneKey {
   int bucket, l, kd;
@@ -384,10 +387,11 @@ int tune_forms(Call& c) {
       std::vector<HostRegion> probe(1);
       probe[0] = HostRegion{50.0, 50.0, 1.0, 2 * num_sms(), 0, 0, (int)gi};
       // each form runs once untimed (workspace allocation, first launch), then timed
-      double t[2] = {0.0, 0.0};
+      const int forms[3] = {PMCIM_PREC_FP64, PMCIM_PREC_FP32_IR, PMCIM_PREC_TF32X3_IR};
+      double t[3] = {0.0, 0.0, 0.0};
       const pmcim_stats keep = c.st;
-      for (int f = 0; f < 2; ++f) {
-        std::vector<int> ov(c.groups.size(), f == 0 ? PMCIM_PREC_FP64 : PMCIM_PREC_FP32_IR);
+      for (int f = 0; f < 3; ++f) {
+        std::vector<int> ov(c.groups.size(), forms[f]);
         cudaEvent_t a, b;
         CU(cudaEventCreate(&a));
         CU(cudaEventCreate(&b));
@@ -404,13 +408,17 @@ int tune_forms(Call& c) {
         cudaEventDestroy(b);
       }
       c.st = keep;  // probe work is not part of the call's statistics
-      decided = (t[1] < t[0]) ? PMCIM_PREC_FP32_IR : PMCIM_PREC_FP64;
+      int best = 0;
+      for (int f = 1; f < 3; ++f)
+        if (t[f] < t[best]) best = f;
+      decided = forms[best];
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tune[key] = decided;
     }
     g.form = decided;
     if (decided == PMCIM_PREC_FP64) c.st.tuned_fp64 += 1;
-    else c.st.tuned_mixed += 1;
+    else if (decided == PMCIM_PREC_FP32_IR) c.st.tuned_mixed += 1;
+    else c.st.tuned_tc += 1;
   }
   return PMCIM_OK;
 }
@@ -442,6 +450,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
     d.prob = h.prob;
     d.node_off = (int32_t)total_nodes;
     d.gate = (h.depth > 0 || gate_top) ? 1 : 0;
+    d.lu_tc = form_of(h.prob) == PMCIM_PREC_TF32X3_IR ? 1 : 0;
     d.c_off = (int64_t)c_tot;
     d.p_off = (int64_t)p_tot;
     d.w_off = (int64_t)w_tot;
@@ -533,7 +542,8 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   CU(ws.X.ensure(std::max<size_t>(1, x_need)));
   CU(ws.items.ensure(std::max<size_t>(1, items.size()) * sizeof(NodeItem)));
   CU(ws.regions.ensure(R * sizeof(RegionDev)));
-  CU(ws.counters.ensure(std::max<size_t>(1, 3 * waves.size()) * sizeof(int)));
+  // 3 work counters per wave, then the mixed kernel's error flag
+  CU(ws.counters.ensure((3 * waves.size() + 1) * sizeof(int)));
   CU(cudaMemcpyAsync(ws.items.p, items.data(), items.size() * sizeof(NodeItem), cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(ws.regions.p, rd.data(), R * sizeof(RegionDev), cudaMemcpyHostToDevice, s));
 
@@ -548,15 +558,19 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
     CU(ws.piv64.ensure((size_t)slots64 * max_n * sizeof(int32_t)));
   }
   if (any32) {
+    // one CTA per SM, each cycling through mixed_slots_per_cta() slots
     slot32 = mixed_slot_bytes(max_n, max_l);
-    slots32 = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(2 * sms, kSlotBytes / slot32), total_nodes));
+    const size_t per = (size_t)mixed_slots_per_cta();
+    const size_t ctas = std::max<size_t>(1, std::min<size_t>(std::min<size_t>(sms, kSlotBytes / (per * slot32)),
+                                                             total_nodes));
+    slots32 = (int)(ctas * per);
     CU(ws.work32.ensure((size_t)slots32 * slot32));
     CU(ws.piv32.ensure((size_t)slots32 * max_n * sizeof(int32_t)));
   }
   const bool timed = prof_on();
   if (timed && any32) {
-    CU(ws.phase.ensure((size_t)slots32 * 8 * sizeof(unsigned long long)));
-    CU(cudaMemsetAsync(ws.phase.p, 0, (size_t)slots32 * 8 * sizeof(unsigned long long), s));
+    CU(ws.phase.ensure((size_t)slots32 * PMCIM_PHASES * sizeof(unsigned long long)));
+    CU(cudaMemsetAsync(ws.phase.p, 0, (size_t)slots32 * PMCIM_PHASES * sizeof(unsigned long long), s));
   }
 
   LevelArgs la;
@@ -592,7 +606,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   cudaGraph_t graph = nullptr;
   CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   auto capture = [&]() -> int {
-    CU(cudaMemsetAsync(ws.counters.p, 0, 3 * waves.size() * sizeof(int), s));
+    CU(cudaMemsetAsync(ws.counters.p, 0, (3 * waves.size() + 1) * sizeof(int), s));
     for (size_t wi = 0; wi < waves.size(); ++wi) {
       const Wave& wv = waves[wi];
       NodeArgs na;
@@ -604,6 +618,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
       na.max_n = max_n;
       na.max_sweeps = c.opt->max_ir_sweeps;
       na.tol_ir = kIrTol;
+      na.err = ws.counters.as<int32_t>() + 3 * waves.size();
       if (wv.n64) {
         na.items = ws.items.as<NodeItem>() + wv.items64_off;
         na.n_items = (int)wv.n64;
@@ -692,6 +707,9 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
     CU(cudaMemcpyAsync(out->cand.data(), ws.cand.p, R, cudaMemcpyDeviceToHost, s));
   }
   CU(cudaMemcpyAsync(out->node_info.data(), ws.node_info.p, total_nodes * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  int32_t handoff_err = 0;
+  CU(cudaMemcpyAsync(&handoff_err, ws.counters.as<int32_t>() + 3 * waves.size(), sizeof(int32_t),
+                     cudaMemcpyDeviceToHost, s));
   if (do_beyn) {
     out->p.resize(R);
     out->status.resize(R);
@@ -703,18 +721,21 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
     CU(cudaMemcpyAsync(out->kept.data(), ws.bkept.p, (size_t)R * PMCIM_MAX_L, cudaMemcpyDeviceToHost, s));
   }
   if (timed && any32) {
-    std::vector<unsigned long long> cyc((size_t)slots32 * 8);
+    std::vector<unsigned long long> cyc((size_t)slots32 * PMCIM_PHASES);
     CU(cudaMemcpyAsync(cyc.data(), ws.phase.p, cyc.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     prof_add_phases(cyc.data(), slots32);
   }
   CU(cudaStreamSynchronize(s));
+  if (handoff_err)
+    return fail(PMCIM_ETIMEOUT, "precision-form node kernel: a wait between its thread groups ran out");
   c.st.solves += (int64_t)total_nodes;
   c.st.regions += R;
   for (size_t i = 0; i < total_nodes; ++i) {
     const int v = out->node_info[i];
     if (v & (1 << 30)) c.st.ir_fallbacks += 1;
-    c.st.ir_sweeps += (v >> 24) & 63;
+    if (v & (1 << 29)) c.st.tc_timeouts += 1;
+    c.st.ir_sweeps += (v >> 24) & 31;
   }
   return PMCIM_OK;
 }
@@ -1057,7 +1078,7 @@ void pmcim_profile_reset(void) {
     P.launches[k] = 0;
     P.ms[k] = 0.0;
   }
-  for (int q = 0; q < 8; ++q) P.phase[q] = 0.0;
+  for (int q = 0; q < PMCIM_PHASE_COUNT; ++q) P.phase[q] = 0.0;
 }
 
 void pmcim_profile_read(pmcim_profile* out) {
@@ -1069,7 +1090,7 @@ void pmcim_profile_read(pmcim_profile* out) {
     out->launches[k] = P.launches[k];
     out->ms[k] = P.ms[k];
   }
-  for (int q = 0; q < 8; ++q) out->mixed_phase_cycles[q] = P.phase[q];
+  for (int q = 0; q < PMCIM_PHASE_COUNT; ++q) out->mixed_phase_cycles[q] = P.phase[q];
 }
 
 int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmcim_fterm* f, pmcim_problem* out) {
@@ -1118,6 +1139,15 @@ int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmc
         return fail(PMCIM_ECUDA, "coefficient upload: %s", cudaGetErrorString(e));
       }
     }
+    e = cudaMalloc(&p->dA32, (size_t)nd * nn * sizeof(float2));
+    if (e == cudaSuccess) e = round_coefficients_c64(p->dA, p->dA32, (size_t)nd * nn, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      cudaFree(p->dA);
+      if (p->dA32) cudaFree(p->dA32);
+      delete p;
+      return fail(PMCIM_ENOMEM, "coefficient copy: %s", cudaGetErrorString(e));
+    }
   }
   *out = p;
   return PMCIM_OK;
@@ -1127,6 +1157,7 @@ int pmcim_problem_destroy(pmcim_problem p) {
   if (!p) return PMCIM_OK;
   cudaDeviceSynchronize();
   if (p->dA) cudaFree(p->dA);
+  if (p->dA32) cudaFree(p->dA32);
   p->V.release();
   p->ws.release();
   delete p;

@@ -15,14 +15,21 @@
 namespace lucore {
 
 constexpr int THREADS = 256;
+
+// Thread groups. Every routine below runs on one group of THREADS threads and
+// synchronises only that group, through named barrier 1 + group: a CTA of
+// THREADS threads is one group (the barrier then spans the whole CTA), and the
+// precision-form kernel runs two groups side by side in one CTA.
+__device__ __forceinline__ int gtid() { return (int)(threadIdx.x & (THREADS - 1)); }
+__device__ __forceinline__ void gsync() {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / THREADS)), "n"(THREADS) : "memory");
+}
 constexpr int NB = 32;    // panel width
 constexpr int TILE = 64;  // trailing-update tile (TILE x TILE complex)
 constexpr int US_LD = TILE + 1;
 
 template <typename T2>
 struct LuSmemT {
-  T2 Ls[NB * TILE];        // L21 tile, [kk][row]; reused for L11 during the TRSM
-  T2 Us[NB * US_LD];       // U12 tile, [kk][col], padded
   T2 prow[NB];             // pivot row of the panel
   double red_v[THREADS / 32];
   int red_i[THREADS / 32];
@@ -30,12 +37,17 @@ struct LuSmemT {
   double2 fz[PMCIM_MAX_TERMS];
   int piv_sh;
   int info_sh;
+  // the tile buffers come last: a tensor-core update may stage its operands
+  // from here on, over the end of the struct
+  alignas(128) T2 Ls[NB * TILE];  // L21 tile, [kk][row]; reused for L11 during the TRSM
+  T2 Us[NB * US_LD];              // U12 tile, [kk][col], padded
 };
 using LuSmem = LuSmemT<double2>;
 
-__device__ __forceinline__ void warp_argmax(double& v, int& i) {
+template <typename R>
+__device__ __forceinline__ void warp_argmax(R& v, int& i) {
   for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_down_sync(0xffffffffu, v, o);
+    R ov = __shfl_down_sync(0xffffffffu, v, o);
     int oi = __shfl_down_sync(0xffffffffu, i, o);
     if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
   }
@@ -55,11 +67,11 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
 
 // Deterministic block sum (fixed tree); every thread gets the result.
 __device__ __forceinline__ double block_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = gtid() & 31, wid = gtid() >> 5;
   v = warp_sum(v);
-  __syncthreads();
+  gsync();
   if (lane == 0) red[wid] = v;
-  __syncthreads();
+  gsync();
   double t = 0.0;
   for (int k = 0; k < THREADS / 32; ++k) t += red[k];
   return t;
@@ -67,11 +79,11 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 // Block sum of a complex value; every thread gets the result.
 __device__ __forceinline__ double2 block_sum2(double2 v, double2* red2) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = gtid() & 31, wid = gtid() >> 5;
   v = warp_sum2(v);
-  __syncthreads();
+  gsync();
   if (lane == 0) red2[wid] = v;
-  __syncthreads();
+  gsync();
   double2 t = make_double2(0.0, 0.0);
   for (int k = 0; k < THREADS / 32; ++k) t = cadd(t, red2[k]);
   return t;
@@ -88,21 +100,25 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* red2) {
 template <typename T2>
 __device__ void cta_lu_panel(T2* __restrict__ M, int n, int ncols, int k0, int kb, int* __restrict__ piv,
                              LuSmemT<T2>& sm) {
-  const int tid = threadIdx.x;
+  const int tid = gtid();
   const size_t ld = (size_t)n;
   const int kend = k0 + kb;
   // ---- panel factorisation, columns k0..kend-1 ----
+  using R = decltype(l1abs(T2{}));  // pivot magnitudes in the matrix's own precision
+  // rows and columns a thread handles per batch: all loads of a batch are issued
+  // before its stores, so that each batch costs one memory round trip
+  constexpr int RB = sizeof(T2) == 8 ? 4 : 2, CB = RB;
   for (int j = k0; j < kend; ++j) {
     T2* colj = M + (size_t)j * ld;
-    double bv = -1.0;
+    R bv = R(-1);
     int bi = n;
     for (int i = j + tid; i < n; i += THREADS) {
-      double v = l1abs(colj[i]);
+      const R v = l1abs(colj[i]);
       if (v > bv) { bv = v; bi = i; }
     }
     warp_argmax(bv, bi);
-    if ((tid & 31) == 0) { sm.red_v[tid >> 5] = bv; sm.red_i[tid >> 5] = bi; }
-    __syncthreads();
+    if ((tid & 31) == 0) { sm.red_v[tid >> 5] = (double)bv; sm.red_i[tid >> 5] = bi; }
+    gsync();
     if (tid == 0) {
       double v = sm.red_v[0];
       int ii = sm.red_i[0];
@@ -113,38 +129,80 @@ __device__ void cta_lu_panel(T2* __restrict__ M, int n, int ncols, int k0, int k
       sm.piv_sh = ii;
       piv[j] = ii;
     }
-    __syncthreads();
+    gsync();
     const int p = sm.piv_sh;
     if (p != j) {
-      for (int c = tid; c < ncols; c += THREADS) {
-        T2* cc = M + (size_t)c * ld;
-        T2 t = cc[j];
-        cc[j] = cc[p];
-        cc[p] = t;
+      for (int c0 = tid; c0 < ncols; c0 += THREADS * RB) {
+        T2 a[RB], b[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+          const int c = c0 + u * THREADS;
+          if (c < ncols) {
+            a[u] = M[(size_t)c * ld + j];
+            b[u] = M[(size_t)c * ld + p];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+          const int c = c0 + u * THREADS;
+          if (c < ncols) {
+            M[(size_t)c * ld + j] = b[u];
+            M[(size_t)c * ld + p] = a[u];
+          }
+        }
       }
     }
-    __syncthreads();
+    gsync();
     for (int c = j + 1 + tid; c < kend; c += THREADS) sm.prow[c - k0] = M[(size_t)c * ld + j];
     const T2 pv = colj[j];
     const bool zero = cis_zero(pv);
     if (zero && tid == 0 && sm.info_sh == 0) sm.info_sh = j + 1;
-    __syncthreads();
+    gsync();
     if (!zero) {
       const T2 rp = crecip(pv);
-      for (int i = j + 1 + tid; i < n; i += THREADS) {
-        T2 lij = cmul(colj[i], rp);
-        colj[i] = lij;
-        for (int c = j + 1; c < kend; ++c) cfms(M[(size_t)c * ld + i], lij, sm.prow[c - k0]);
+      for (int i0 = j + 1 + tid; i0 < n; i0 += THREADS * RB) {
+        T2 lv[RB];  // multipliers l_ij of this thread's rows
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          const int i = i0 + r * THREADS;
+          lv[r] = i < n ? colj[i] : czero<T2>();
+        }
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          const int i = i0 + r * THREADS;
+          lv[r] = cmul(lv[r], rp);
+          if (i < n) colj[i] = lv[r];
+        }
+        for (int c = j + 1; c < kend; c += CB) {
+          T2 mv[CB][RB];
+#pragma unroll
+          for (int q = 0; q < CB; ++q)
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+              const int i = i0 + r * THREADS;
+              mv[q][r] = (c + q < kend && i < n) ? M[(size_t)(c + q) * ld + i] : czero<T2>();
+            }
+#pragma unroll
+          for (int q = 0; q < CB; ++q)
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+              const int i = i0 + r * THREADS;
+              if (c + q < kend && i < n) {
+                cfms(mv[q][r], lv[r], sm.prow[c + q - k0]);
+                M[(size_t)(c + q) * ld + i] = mv[q][r];
+              }
+            }
+        }
       }
     }
-    __syncthreads();
+    gsync();
   }
 }
 
 // U12 = L11^{-1} A12 for rows k0..k0+kb-1, columns k0+kb..ncols-1.
 template <typename T2>
 __device__ void cta_lu_trsm(T2* __restrict__ M, int n, int ncols, int k0, int kb, LuSmemT<T2>& sm) {
-  const int tid = threadIdx.x;
+  const int tid = gtid();
   const size_t ld = (size_t)n;
   const int kend = k0 + kb;
   // ---- U12 = L11^{-1} A12 (rows k0..kend-1, columns kend..ncols-1) ----
@@ -152,7 +210,7 @@ __device__ void cta_lu_trsm(T2* __restrict__ M, int n, int ncols, int k0, int kb
     int r = e % kb, c = e / kb;
     sm.Ls[c * NB + r] = M[(size_t)(k0 + c) * ld + k0 + r];  // Ls[t*NB + i] = L11[i][t]
   }
-  __syncthreads();
+  gsync();
   {
     // one warp per column, lane i holds row k0+i (NB == warp size)
     const int lane = tid & 31, wid = tid >> 5;
@@ -168,13 +226,13 @@ __device__ void cta_lu_trsm(T2* __restrict__ M, int n, int ncols, int k0, int kb
       if (lane < kb) cc[lane] = x;
     }
   }
-  __syncthreads();
+  gsync();
 }
 
 // Trailing update A22 -= L21 U12 (rows and columns from k0+kb on), FMA pipes.
 template <typename T2>
 __device__ void cta_lu_update_simt(T2* __restrict__ M, int n, int ncols, int k0, int kb, LuSmemT<T2>& sm) {
-  const int tid = threadIdx.x;
+  const int tid = gtid();
   const size_t ld = (size_t)n;
   const int kend = k0 + kb;
   // ---- trailing update A22 -= L21 U12 over TILE x TILE tiles ----
@@ -183,7 +241,10 @@ __device__ void cta_lu_update_simt(T2* __restrict__ M, int n, int ncols, int k0,
   const int tx = tid & 15, ty = tid >> 4;
   for (int ti = 0; ti < mt; ++ti) {
     const int r0 = kend + ti * TILE;
-    for (int e = tid; e < NB * TILE; e += THREADS) {
+    static_assert((NB * TILE) % THREADS == 0, "tile staging mapping");
+#pragma unroll
+    for (int u = 0; u < NB * TILE / THREADS; ++u) {  // unrolled: all loads in flight at once
+      const int e = tid + u * THREADS;
       int r = e % TILE, kk = e / TILE;
       T2 v = czero<T2>();
       if (kk < kb && r0 + r < n) v = M[(size_t)(k0 + kk) * ld + r0 + r];
@@ -191,13 +252,15 @@ __device__ void cta_lu_update_simt(T2* __restrict__ M, int n, int ncols, int k0,
     }
     for (int tj = 0; tj < nt; ++tj) {
       const int c0 = kend + tj * TILE;
-      for (int e = tid; e < NB * TILE; e += THREADS) {
+#pragma unroll
+      for (int u = 0; u < NB * TILE / THREADS; ++u) {
+        const int e = tid + u * THREADS;
         int kk = e % NB, c = e / NB;
         T2 v = czero<T2>();
         if (kk < kb && c0 + c < ncols) v = M[(size_t)(c0 + c) * ld + k0 + kk];
         sm.Us[kk * US_LD + c] = v;
       }
-      __syncthreads();
+      gsync();
       T2 acc[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
@@ -224,15 +287,15 @@ __device__ void cta_lu_update_simt(T2* __restrict__ M, int n, int ncols, int k0,
           int r = r0 + tx + 16 * i, c = c0 + ty + 16 * q;
           if (r < n && c < ncols) M[(size_t)c * ld + r] = acc[i][q];
         }
-      __syncthreads();
+      gsync();
     }
   }
 }
 
 template <typename T2>
 __device__ int cta_lu(T2* __restrict__ M, int n, int ncols, int* __restrict__ piv, LuSmemT<T2>& sm) {
-  if (threadIdx.x == 0) sm.info_sh = 0;
-  __syncthreads();
+  if (gtid() == 0) sm.info_sh = 0;
+  gsync();
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = min(NB, n - k0);
     const int kend = k0 + kb;
@@ -242,14 +305,14 @@ __device__ int cta_lu(T2* __restrict__ M, int n, int ncols, int* __restrict__ pi
     if (kend >= n) continue;
     cta_lu_update_simt(M, n, ncols, k0, kb, sm);
   }
-  __syncthreads();
+  gsync();
   return sm.info_sh;
 }
 
 // Back substitution U X = Y for the l columns n..n+l-1 of M, in place.
 template <typename T2>
 __device__ void cta_back_subst(T2* __restrict__ M, int n, int l, LuSmemT<T2>& sm) {
-  const int tid = threadIdx.x;
+  const int tid = gtid();
   const size_t ld = (size_t)n;
   T2* Y = M + (size_t)n * ld;
   for (int j = n - 1; j >= 0; --j) {
@@ -258,13 +321,13 @@ __device__ void cta_back_subst(T2* __restrict__ M, int n, int l, LuSmemT<T2>& sm
       Y[(size_t)tid * ld + j] = x;
       sm.bcast[tid] = x;
     }
-    __syncthreads();
+    gsync();
     const T2* uj = M + (size_t)j * ld;
     for (int i = tid; i < j; i += THREADS) {
       const T2 u = uj[i];
       for (int c = 0; c < l; ++c) cfms(Y[(size_t)c * ld + i], u, sm.bcast[c]);
     }
-    __syncthreads();
+    gsync();
   }
 }
 
@@ -273,7 +336,7 @@ __device__ void cta_back_subst(T2* __restrict__ M, int n, int l, LuSmemT<T2>& sm
 template <typename T2>
 __device__ void cta_perm_fwd_subst(T2* __restrict__ M, int n, int l, const int* __restrict__ piv,
                                    LuSmemT<T2>& sm) {
-  const int tid = threadIdx.x;
+  const int tid = gtid();
   const size_t ld = (size_t)n;
   T2* Y = M + (size_t)n * ld;
   if (tid < l) {
@@ -287,16 +350,16 @@ __device__ void cta_perm_fwd_subst(T2* __restrict__ M, int n, int l, const int* 
       }
     }
   }
-  __syncthreads();
+  gsync();
   for (int j = 0; j < n; ++j) {
     if (tid < l) sm.bcast[tid] = Y[(size_t)tid * ld + j];
-    __syncthreads();
+    gsync();
     const T2* lj = M + (size_t)j * ld;
     for (int i = j + 1 + tid; i < n; i += THREADS) {
       const T2 u = lj[i];
       for (int c = 0; c < l; ++c) cfms(Y[(size_t)c * ld + i], u, sm.bcast[c]);
     }
-    __syncthreads();
+    gsync();
   }
 }
 
@@ -330,7 +393,7 @@ __device__ __forceinline__ void block_update_row(const T2* __restrict__ M, T2* _
 // L y = b, L unit lower (no row swaps here).
 template <typename T2>
 __device__ void cta_fwd_blocked(T2* __restrict__ M, int n, int l, LuSmemT<T2>& sm) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = gtid(), lane = tid & 31, wid = tid >> 5;
   const size_t ld = (size_t)n;
   T2* Y = M + (size_t)n * ld;
   for (int k0 = 0; k0 < n; k0 += NB) {
@@ -339,7 +402,7 @@ __device__ void cta_fwd_blocked(T2* __restrict__ M, int n, int l, LuSmemT<T2>& s
       const int r = e % kb, c = e / kb;
       sm.Ls[c * NB + r] = M[(size_t)(k0 + c) * ld + k0 + r];  // Ls[t*NB + i] = L[k0+i][k0+t]
     }
-    __syncthreads();
+    gsync();
     for (int c = wid; c < l; c += THREADS / 32) {
       T2* yc = Y + (size_t)c * ld + k0;
       T2 y = (lane < kb) ? yc[lane] : czero<T2>();
@@ -352,16 +415,16 @@ __device__ void cta_fwd_blocked(T2* __restrict__ M, int n, int l, LuSmemT<T2>& s
       if (lane < kb) yc[lane] = y;
       if (lane < kb) sm.Us[lane * US_LD + c] = y;  // solved block rows, [t][c]
     }
-    __syncthreads();
+    gsync();
     for (int i = k0 + kb + tid; i < n; i += THREADS) block_update_row(M, Y, ld, i, k0, kb, l, sm);
-    __syncthreads();
+    gsync();
   }
 }
 
 // U x = y, U upper with its diagonal.
 template <typename T2>
 __device__ void cta_back_blocked(T2* __restrict__ M, int n, int l, LuSmemT<T2>& sm) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = gtid(), lane = tid & 31, wid = tid >> 5;
   const size_t ld = (size_t)n;
   T2* Y = M + (size_t)n * ld;
   const int nblk = (n + NB - 1) / NB;
@@ -372,7 +435,7 @@ __device__ void cta_back_blocked(T2* __restrict__ M, int n, int l, LuSmemT<T2>& 
       const int r = e % kb, c = e / kb;
       sm.Ls[c * NB + r] = M[(size_t)(k0 + c) * ld + k0 + r];  // Ls[t*NB + i] = U[k0+i][k0+t]
     }
-    __syncthreads();
+    gsync();
     for (int c = wid; c < l; c += THREADS / 32) {
       T2* yc = Y + (size_t)c * ld + k0;
       T2 y = (lane < kb) ? yc[lane] : czero<T2>();
@@ -386,17 +449,17 @@ __device__ void cta_back_blocked(T2* __restrict__ M, int n, int l, LuSmemT<T2>& 
       if (lane < kb) yc[lane] = y;
       if (lane < kb) sm.Us[lane * US_LD + c] = y;
     }
-    __syncthreads();
+    gsync();
     for (int i = tid; i < k0; i += THREADS) block_update_row(M, Y, ld, i, k0, kb, l, sm);
-    __syncthreads();
+    gsync();
   }
 }
 
 // perm[i] = original row that ends up in row i after the swaps piv[0..n-1].
 __device__ inline void cta_pivots_to_perm(const int* __restrict__ piv, int* __restrict__ perm, int n) {
-  for (int i = threadIdx.x; i < n; i += THREADS) perm[i] = i;
-  __syncthreads();
-  if (threadIdx.x == 0)
+  for (int i = gtid(); i < n; i += THREADS) perm[i] = i;
+  gsync();
+  if (gtid() == 0)
     for (int k = 0; k < n; ++k) {
       const int p = piv[k];
       if (p != k) {
@@ -405,7 +468,7 @@ __device__ inline void cta_pivots_to_perm(const int* __restrict__ piv, int* __re
         perm[p] = t;
       }
     }
-  __syncthreads();
+  gsync();
 }
 
 }  // namespace lucore

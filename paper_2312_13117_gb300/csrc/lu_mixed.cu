@@ -6,7 +6,7 @@
 // FP64 is kept for what needs it: the residual R = V - T(z_j) X, formed from
 // the FP64 coefficients A_k, and the accumulated solution X.
 //
-// Per node (one CTA, persistent grid):
+// Per node:
 //   1. assemble T(z_j) in FP64 and round to complex64, append V;
 //   2. FP32 blocked LU with partial pivoting (also eliminates V), back
 //      substitution -> X_0 (promoted to FP64);
@@ -16,66 +16,199 @@
 //      tol_ir |X| (max norms);
 //   4. no convergence within max sweeps (or growth) -> the node is solved
 //      again by the FP64 LU in the same workspace and flagged.
-// node_info: bits 0-23 = 0 or 1 + first zero-pivot column, bits 24-29 = sweeps
-// run, bit 30 = FP64 fallback.
-#include "lu_core.cuh"
+// Steps 1-2 are FP32 (or tensor-core) work, step 3 is FP64 work. One
+// persistent CTA per SM runs them in two warp-specialised groups of 256
+// threads: the factor group (warps 0-7) does steps 1-2 for node k+1 while the
+// refine group (warps 8-15) does steps 3-4 for node k, so the FP64 pipe and
+// the FP32 / tensor pipes of the SM work at the same time. Nodes pass between
+// the groups through two workspace slots per CTA, each guarded by a pair of
+// mbarriers (full: factor -> refine, empty: refine -> factor); every wait on
+// them is bounded and a wait that runs out ends both groups with an error.
+// The trailing updates of step 2 run on the FMA pipes, or, for regions marked
+// lu_tc, as 3xTF32 complex products on the tensor cores (tc_update.cuh).
+// node_info: bits 0-23 = 0 or 1 + first zero-pivot column, bits 24-28 = sweeps
+// run, bit 29 = a tensor-core wait ran out, bit 30 = FP64 fallback.
+#include "tc_update.cuh"
 
 namespace {
 
 using namespace lucore;
 
-// Residual tiles: 256 rows x 16 columns per pass, depth 16; thread (tx, ty) owns
-// rows tx + 64 i and columns ty + 4 q (i, q < 4) of the tile: a 4 x 4 complex
-// register block, the same shape as the LU's trailing update.
-constexpr int RT_ROWS = 256;
+// Residual tiles: 128 rows x 16 columns per pass, depth 16; thread (tx, ty) owns
+// rows tx + 64 i (i < 2) and columns ty + 4 q (q < 4) of the tile. The FP64
+// pipe issues so slowly that shared-memory traffic is no constraint here; the
+// small register block leaves room for the rest of the refinement loop.
+constexpr int RT_ROWS = 128;
 constexpr int RT_COLS = 16;
 constexpr int RT_K = 16;
+constexpr int RT_RI = RT_ROWS / 64;  // rows per thread
+static_assert(RT_K * RT_COLS == THREADS, "one X-slice element per thread");
+static_assert((RT_K * RT_ROWS) % THREADS == 0 && THREADS % RT_ROWS == 0, "tile copy mapping");
 
 struct ResSmem {
-  double2 As[RT_K * RT_ROWS];   // A_k tile [kk][row]
-  double2 Xs[RT_K * RT_COLS];   // f_k X tile [kk][col]
+  double2 As[2][RT_K * RT_ROWS];  // A_k tiles [kk][row], double-buffered
+  double2 Xs[RT_K * RT_COLS];     // f_k X tile [kk][col]
 };
 
-union MixedSmemU {
-  LuSmemT<float2> lu32;
-  LuSmemT<double2> lu64;
-  ResSmem res;
-};
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src, bool ok) {
+  // 16 bytes global -> shared; zero-filled (nothing read) when !ok
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(ok ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most the most recent group is still in flight
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-struct MixedSmem {
-  MixedSmemU u;
+// Issue the copies of A_k rows r0.., columns k0..k0+RT_K-1 into dst [kk][row];
+// thread (pr, pk) copies rows pr of columns pk + (THREADS / RT_ROWS) u. Out of
+// range elements are zero-filled from a valid address.
+__device__ __forceinline__ void res_tile_async(double2* dst, const double2* __restrict__ Ak, int n, int r0, int k0,
+                                               int pr, int pk) {
+#pragma unroll
+  for (int u = 0; u < RT_K * RT_ROWS / THREADS; ++u) {
+    const int kk = pk + (THREADS / RT_ROWS) * u;
+    const bool ok = r0 + pr < n && k0 + kk < n;
+    cp_async_16(dst + kk * RT_ROWS + pr, ok ? Ak + (size_t)(k0 + kk) * n + r0 + pr : Ak, ok);
+  }
+}
+
+constexpr int GROUPS = 2;                        // factor group, refine group
+constexpr int CTA_THREADS = GROUPS * THREADS;
+constexpr int SLOTS = 2;                         // node slots per CTA
+constexpr long long HANDOFF_WAIT_CYCLES = 1ll << 35;  // about 16 s at 2 GHz
+
+// A group's node context.
+struct NodeCtx {
   ProblemDev P;
   double2 fz[PMCIM_MAX_TERMS];
+  float2 fz32[PMCIM_MAX_TERMS];  // f_k(z) rounded to complex64
+  float2 fid32;                  // sum over identity terms of f_k(z) id_k, complex64
   double red[THREADS / 32];
   int item;
 };
 
+struct FactorSmem {
+  union {
+    LuSmemT<float2> lu32;
+    // lu32 followed by the tensor-core operand stage, which starts at lu32.Ls
+    unsigned char tc[offsetof(LuSmemT<float2>, Ls) + tcu::STAGE_BYTES];
+  } u;
+  NodeCtx c;
+};
+
+struct RefineSmem {
+  union {
+    LuSmemT<float2> lu32;   // correction solves
+    LuSmemT<double2> lu64;  // FP64 fallback
+    ResSmem res;            // residual tiles
+  } u;
+  NodeCtx c;
+};
+
+// What the factor group hands over with a slot.
+struct Slot {
+  int item;        // node item, or -1: no more nodes
+  int info;        // 0, or 1 + first zero-pivot column of the FP32 LU
+  int tc_timeout;  // a tensor-core wait ran out during the LU
+  double xm;       // max |X_0|
+};
+
+struct MixedSmem {
+  FactorSmem f;
+  RefineSmem r;
+  Slot slot[SLOTS];
+  uint64_t full[SLOTS];   // THREADS arrivals of the factor group
+  uint64_t empty[SLOTS];  // THREADS arrivals of the refine group
+  uint64_t mbar_tc[2];    // tensor-core completion, one per accumulator
+  uint32_t tmem_base;
+  int tc_bad;             // a tensor-core wait ran out: FMA pipes from then on
+};
+
+__device__ __forceinline__ void mbar_init_count(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tcu::smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Arrival with release semantics: this thread's earlier writes (shared and
+// global) are visible to a thread whose wait on the phase succeeds.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(tcu::smem_u32(bar))
+               : "memory");
+}
+
+// Phase clock: the group's thread 0 adds the cycles since the last mark to counter p.
+struct PhaseClock {
+  unsigned long long* c;
+  long long t;
+  __device__ explicit PhaseClock(unsigned long long* base) : c(base), t(0) { t = (long long)clock64(); }
+  __device__ void mark(int p) {
+    if (c && gtid() == 0) {
+      const long long u = (long long)clock64();
+      c[p] += (unsigned long long)(u - t);
+      t = u;
+    }
+  }
+};
+
+// Phase-clock slots. Factor group: assemble, LU panels / TRSM / updates, first
+// solve, set-up, waiting for a free slot; refine group: residual, correction
+// solves, fallback, waiting for a factored node.
+enum { PH_ASSEMBLE = 0, PH_PANEL = 1, PH_FIRST_SOLVE = 2, PH_RESIDUAL = 3, PH_CORRECTION = 4, PH_FALLBACK = 5,
+       PH_SETUP = 6, PH_TRSM = 7, PH_UPDATE = 8, PH_FACTOR_WAIT = 9, PH_REFINE_WAIT = 10 };
+
+// The FP32 blocked LU of lucore::cta_lu, with the trailing updates on the
+// tensor cores (use_tc, while no wait has run out) or on the FMA pipes.
+// Factor group only: its warps 0-7 are the TMEM lane owners.
+__device__ int cta_lu32(float2* __restrict__ M, int n, int ncols, int* __restrict__ piv, LuSmemT<float2>& sm,
+                        tcu::Ctx& cx, bool use_tc, PhaseClock& pc) {
+  if (gtid() == 0) sm.info_sh = 0;
+  gsync();
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = min(NB, n - k0);
+    const int kend = k0 + kb;
+    cta_lu_panel(M, n, ncols, k0, kb, piv, sm);
+    pc.mark(PH_PANEL);
+    if (kend >= ncols) continue;
+    cta_lu_trsm(M, n, ncols, k0, kb, sm);
+    pc.mark(PH_TRSM);
+    if (kend >= n) continue;
+    if (use_tc && !*cx.bad) tcu::update(M, n, ncols, k0, kb, cx);
+    else cta_lu_update_simt(M, n, ncols, k0, kb, sm);
+    pc.mark(PH_UPDATE);
+  }
+  gsync();
+  return sm.info_sh;
+}
+
 __device__ double block_max(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
+  gsync();
+  if ((gtid() & 31) == 0) red[gtid() >> 5] = v;
+  gsync();
   double t = 0.0;
   for (int k = 0; k < THREADS / 32; ++k) t = fmax(t, red[k]);
   return t;
 }
 
 // R = V - sum_k f_k(z) A_k X  (FP64), R and X column-major n x l.
-__device__ void residual_fp64(const double2* __restrict__ X, double2* __restrict__ R, MixedSmem& sm) {
-  const ProblemDev& P = sm.P;
+__device__ void residual_fp64(const double2* __restrict__ X, double2* __restrict__ R, const NodeCtx& cx,
+                              ResSmem& rs) {
+  const ProblemDev& P = cx.P;
   const int n = P.n, l = P.l;
-  const int tid = threadIdx.x;
+  const int tid = gtid();
   const size_t nn = (size_t)n * n;
   const int tx = tid & 63, ty = tid >> 6;
-  ResSmem& rs = sm.u.res;
+  const int pr = tid % RT_ROWS, pk = tid / RT_ROWS;  // tile element (row, k) this thread fetches first
+  const int xk = tid % RT_K, xc = tid / RT_K;        // X slice element (k, column)
   double2 idsum = make_double2(0.0, 0.0);  // sum of identity-term coefficients f_k id_k
   for (int k = 0; k < P.K; ++k)
-    if (!P.term[k].dense) idsum = cadd(idsum, cmul(sm.fz[k], P.term[k].id));
+    if (!P.term[k].dense) idsum = cadd(idsum, cmul(cx.fz[k], P.term[k].id));
   for (int c0 = 0; c0 < l; c0 += RT_COLS) {
     for (int r0 = 0; r0 < n; r0 += RT_ROWS) {
-      double2 acc[4][4];
+      double2 acc[RT_RI][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RT_RI; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int row = r0 + tx + 64 * i, c = c0 + ty + 4 * q;
@@ -90,38 +223,43 @@ __device__ void residual_fp64(const double2* __restrict__ X, double2* __restrict
         const TermDesc& t = P.term[k];
         if (!t.dense) continue;
         const double2* Ak = P.A + (size_t)t.mat_index * nn;
-        const double2 fk = sm.fz[k];
-        for (int k0 = 0; k0 < n; k0 += RT_K) {
-          __syncthreads();
-          for (int e = tid; e < RT_K * RT_ROWS; e += THREADS) {
-            const int r = e % RT_ROWS, kk = e / RT_ROWS;
-            double2 v = make_double2(0.0, 0.0);
-            if (r0 + r < n && k0 + kk < n) v = Ak[(size_t)(k0 + kk) * n + r0 + r];
-            rs.As[kk * RT_ROWS + r] = v;
+        const double2 fk = cx.fz[k];
+        // A_k tiles stream through two shared buffers with cp.async: the copy
+        // of the next tile is in flight while the current one is multiplied
+        const double2* xcol = X + (size_t)(c0 + xc) * n;
+        const bool xc_ok = c0 + xc < l;
+        double2 px = (xk < n && xc_ok) ? xcol[xk] : make_double2(0.0, 0.0);
+        gsync();  // both buffers are free
+        res_tile_async(rs.As[0], Ak, n, r0, 0, pr, pk);
+        cp_async_commit();
+        int b = 0;
+        for (int k0 = 0; k0 < n; k0 += RT_K, b ^= 1) {
+          gsync();  // the previous step's multiplications are done
+          rs.Xs[xk * RT_COLS + xc] = cmul(fk, px);
+          if (k0 + RT_K < n) {
+            res_tile_async(rs.As[b ^ 1], Ak, n, r0, k0 + RT_K, pr, pk);
+            px = (k0 + RT_K + xk < n && xc_ok) ? xcol[k0 + RT_K + xk] : make_double2(0.0, 0.0);
           }
-          {
-            const int kk = tid % RT_K, c = tid / RT_K;  // 256 threads = 16 x 16
-            double2 v = make_double2(0.0, 0.0);
-            if (k0 + kk < n && c0 + c < l) v = cmul(fk, X[(size_t)(c0 + c) * n + k0 + kk]);
-            rs.Xs[kk * RT_COLS + c] = v;
-          }
-          __syncthreads();
+          cp_async_commit();
+          cp_async_wait_prior();  // this tile's copies have landed (the next may be in flight)
+          gsync();
+          const double2* As = rs.As[b];
 #pragma unroll 4
           for (int kk = 0; kk < RT_K; ++kk) {
-            double2 av[4], xv[4];
+            double2 av[RT_RI], xv[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = rs.As[kk * RT_ROWS + tx + 64 * i];
+            for (int i = 0; i < RT_RI; ++i) av[i] = As[kk * RT_ROWS + tx + 64 * i];
 #pragma unroll
             for (int q = 0; q < 4; ++q) xv[q] = rs.Xs[kk * RT_COLS + ty + 4 * q];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < RT_RI; ++i)
 #pragma unroll
               for (int q = 0; q < 4; ++q) cfms(acc[i][q], av[i], xv[q]);
           }
         }
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RT_RI; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int row = r0 + tx + 64 * i, c = c0 + ty + 4 * q;
@@ -129,22 +267,49 @@ __device__ void residual_fp64(const double2* __restrict__ X, double2* __restrict
         }
     }
   }
-  __syncthreads();
+  cp_async_wait_all();
+  gsync();
+}
+
+// T(z_j) for the FP32 LU: FP32 arithmetic on the complex64 copy of the A_k
+// (the LU only has to approximate T(z_j) to FP32 accuracy; the refinement
+// residuals use the FP64 coefficients). It keeps the factor group off the FP64
+// pipe, which the refine group saturates.
+__device__ void assemble32(const NodeCtx& cx, float2* M32) {
+  const ProblemDev& P = cx.P;
+  const int n = P.n;
+  const size_t nn = (size_t)n * n;
+  const float2 fid = cx.fid32;
+  for (int col = 0; col < n; ++col) {
+    for (int row = gtid(); row < n; row += THREADS) {
+      const size_t e = (size_t)col * n + row;
+      float2 v = row == col ? fid : make_float2(0.f, 0.f);
+      for (int k = 0; k < P.K; ++k) {
+        const TermDesc& t = P.term[k];
+        if (t.dense) {
+          const float2 a = P.A32[(size_t)t.mat_index * nn + e], f = cx.fz32[k];
+          v.x = fmaf(f.x, a.x, fmaf(-f.y, a.y, v.x));
+          v.y = fmaf(f.x, a.y, fmaf(f.y, a.x, v.y));
+        }
+      }
+      M32[e] = v;
+    }
+  }
 }
 
 // T(z_j) into the FP32 matrix (rounded) or, for the fallback, the FP64 matrix.
-__device__ void assemble(MixedSmem& sm, float2* M32, double2* M64) {
-  const ProblemDev& P = sm.P;
+__device__ void assemble(const NodeCtx& cx, float2* M32, double2* M64) {
+  const ProblemDev& P = cx.P;
   const int n = P.n;
   const size_t nn = (size_t)n * n;
   for (int col = 0; col < n; ++col) {
-    for (int row = threadIdx.x; row < n; row += THREADS) {
+    for (int row = gtid(); row < n; row += THREADS) {
       const size_t e = (size_t)col * n + row;
       double2 v = make_double2(0.0, 0.0);
       for (int k = 0; k < P.K; ++k) {
         const TermDesc& t = P.term[k];
-        if (t.dense) cfma(v, sm.fz[k], P.A[(size_t)t.mat_index * nn + e]);
-        else if (row == col) cfma(v, sm.fz[k], t.id);
+        if (t.dense) cfma(v, cx.fz[k], P.A[(size_t)t.mat_index * nn + e]);
+        else if (row == col) cfma(v, cx.fz[k], t.id);
       }
       if (M32) M32[e] = make_float2((float)v.x, (float)v.y);
       else M64[e] = v;
@@ -152,93 +317,181 @@ __device__ void assemble(MixedSmem& sm, float2* M32, double2* M64) {
   }
 }
 
-// Phase clock: thread 0 adds the cycles since the last mark to counter p.
-struct PhaseClock {
-  unsigned long long* c;
-  long long t;
-  __device__ explicit PhaseClock(unsigned long long* base) : c(base), t(0) { t = (long long)clock64(); }
-  __device__ void mark(int p) {
-    if (c && threadIdx.x == 0) {
-      const long long u = (long long)clock64();
-      c[p] += (unsigned long long)(u - t);
-      t = u;
-    }
+// Node item -> problem, node point and weight in the group's context.
+__device__ void load_node(const NodeArgs& a, int idx, NodeCtx& c, RegionDev& rg, NodeItem& it) {
+  it = a.items[idx];
+  rg = a.regions[it.region];
+  {
+    const int* src = reinterpret_cast<const int*>(a.probs + rg.prob);
+    int* dst = reinterpret_cast<int*>(&c.P);
+    for (int i = gtid(); i < (int)(sizeof(ProblemDev) / sizeof(int)); i += THREADS) dst[i] = src[i];
   }
-};
+  gsync();
+  double2 z, w;
+  node_weight(rg.cre, rg.cim, rg.r, rg.N, it.j, &z, &w);
+  if (gtid() < c.P.K) {
+    const double2 f = eval_f(c.P.term[gtid()], z);
+    c.fz[gtid()] = f;
+    c.fz32[gtid()] = make_float2((float)f.x, (float)f.y);
+  }
+  gsync();
+  if (gtid() == 0) {
+    double2 id = make_double2(0.0, 0.0);
+    for (int k = 0; k < c.P.K; ++k)
+      if (!c.P.term[k].dense) id = cadd(id, cmul(c.fz[k], c.P.term[k].id));
+    c.fid32 = make_float2((float)id.x, (float)id.y);
+  }
+  gsync();
+}
 
-__global__ void __launch_bounds__(THREADS, 2) k_factor_solve_mixed(NodeArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  MixedSmem& sm = *reinterpret_cast<MixedSmem*>(smem_raw);
-  const int tid = threadIdx.x;
-  char* slot = a.work + (size_t)blockIdx.x * a.slot_bytes;
-  float2* M32 = reinterpret_cast<float2*>(slot);
-  double2* M64 = reinterpret_cast<double2*>(slot);  // fallback only; aliases M32
-  int* piv = a.piv + (size_t)blockIdx.x * a.max_n;
-  PhaseClock pc(a.phase ? a.phase + (size_t)blockIdx.x * PMCIM_PHASES : nullptr);
+// True in every thread of the group when v is true in every thread (a group barrier).
+__device__ __forceinline__ bool group_all(bool v) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, %3, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((int)v), "r"(1 + (int)(threadIdx.x / THREADS)), "n"(THREADS)
+      : "memory");
+  return r != 0;
+}
 
-  for (;;) {
-    // largest-first list, handed out by an atomic counter (no waiting on other CTAs)
-    if (tid == 0) sm.item = atomicAdd(a.counter, 1);
-    __syncthreads();
-    const int idx = sm.item;
-    if (idx >= a.n_items) break;
-    const NodeItem it = a.items[idx];
-    const RegionDev rg = a.regions[it.region];
-    load_problem(&sm.P, a.probs + rg.prob);
-    __syncthreads();
-    const ProblemDev& P = sm.P;
+// Bounded wait of the whole group on a hand-off barrier; the group agrees on
+// the outcome, so that it never splits at a timeout.
+__device__ bool handoff_wait(uint64_t* bar, uint32_t parity, int32_t* err) {
+  const bool ok = group_all(tcu::wait_parity(bar, parity, HANDOFF_WAIT_CYCLES));
+  if (!ok && gtid() == 0) atomicExch(err, 1);
+  return ok;
+}
+
+// Steps 1-2 for one node after another, into the CTA's slots in turn.
+__device__ void factor_group(const NodeArgs& a, MixedSmem& sm, tcu::Ctx& cx, PhaseClock& pc) {
+  const int tid = gtid();
+  NodeCtx& c = sm.f.c;
+  for (int k = 0;; ++k) {
+    const int s = k % SLOTS, use = k / SLOTS;
+    // the slot is free again once the refine group has finished its previous node
+    if (use > 0 && !handoff_wait(&sm.empty[s], (uint32_t)((use - 1) & 1), a.err)) return;
+    pc.mark(PH_FACTOR_WAIT);
+    if (tid == 0) c.item = atomicAdd(a.counter, 1);
+    gsync();
+    const int idx = c.item;
+    Slot& sl = sm.slot[s];
+    if (idx >= a.n_items) {
+      if (tid == 0) sl.item = -1;
+      mbar_arrive(&sm.full[s]);
+      return;
+    }
+    const size_t si = (size_t)blockIdx.x * SLOTS + s;
+    char* slot = a.work + si * a.slot_bytes;
+    float2* M32 = reinterpret_cast<float2*>(slot);
+    int* piv = a.piv + si * a.max_n;
+    NodeItem it;
+    RegionDev rg;
+    load_node(a, idx, c, rg, it);
+    const ProblemDev& P = c.P;
     const int n = P.n, l = P.l, ncols = n + l;
     const size_t nn = (size_t)n * n, nl = (size_t)n * l;
-    double2* R = reinterpret_cast<double2*>(slot + mixed_residual_offset(n, l));
     int* perm = reinterpret_cast<int*>(slot + mixed_residual_offset(n, l) + nl * sizeof(double2));
-    double2 z, w;
-    node_weight(rg.cre, rg.cim, rg.r, rg.N, it.j, &z, &w);
-    if (tid < P.K) sm.fz[tid] = eval_f(P.term[tid], z);
-    __syncthreads();
     double2* X = a.X + rg.x_off + (size_t)it.j * nl;
-    pc.mark(6);
-
-    // 1-2: FP32 factorisation and first solution
-    assemble(sm, M32, nullptr);
+    pc.mark(PH_SETUP);
+    assemble32(c, M32);
     for (size_t e = tid; e < nl; e += THREADS) M32[nn + e] = make_float2((float)P.V[e].x, (float)P.V[e].y);
-    __syncthreads();
-    pc.mark(0);
-    int info = cta_lu(M32, n, ncols, piv, sm.u.lu32);
-    pc.mark(1);
-    bool ok = (info == 0);
-    int sweeps = 0;
-    if (ok) {
-      cta_back_blocked(M32, n, l, sm.u.lu32);
+    gsync();
+    pc.mark(PH_ASSEMBLE);
+    const int bad_before = sm.tc_bad;
+    const int info = cta_lu32(M32, n, ncols, piv, sm.f.u.lu32, cx, rg.lu_tc != 0, pc);
+    double xm = 0.0;
+    if (info == 0) {
+      cta_back_blocked(M32, n, l, sm.f.u.lu32);
       cta_pivots_to_perm(piv, perm, n);
-      double xm = 0.0;
       for (size_t e = tid; e < nl; e += THREADS) {
         const float2 y = M32[nn + e];
         const double2 x = make_double2((double)y.x, (double)y.y);
         X[e] = x;
         xm = fmax(xm, fmax(fabs(x.x), fabs(x.y)));
       }
-      xm = block_max(xm, sm.red);
-      pc.mark(2);
-      double dprev = xm;
+      xm = block_max(xm, c.red);
+    }
+    pc.mark(PH_FIRST_SOLVE);
+    if (tid == 0) {
+      sl.item = idx;
+      sl.info = info;
+      sl.tc_timeout = sm.tc_bad != bad_before;
+      sl.xm = xm;
+    }
+    mbar_arrive(&sm.full[s]);
+  }
+}
+
+// Step 4: the node solved again by the FP64 LU in its slot. Kept out of line:
+// it is rare, and its registers should not weigh on the refinement loop.
+__device__ __noinline__ int fallback_fp64(const NodeCtx& c, double2* M64, int* piv, double2* X,
+                                          LuSmemT<double2>& lu) {
+  const ProblemDev& P = c.P;
+  const int n = P.n, l = P.l;
+  const size_t nn = (size_t)n * n, nl = (size_t)n * l;
+  gsync();
+  assemble(c, nullptr, M64);
+  for (size_t e = gtid(); e < nl; e += THREADS) M64[nn + e] = P.V[e];
+  gsync();
+  const int info = cta_lu(M64, n, n + l, piv, lu);
+  cta_back_blocked(M64, n, l, lu);
+  for (size_t e = gtid(); e < nl; e += THREADS) X[e] = M64[nn + e];
+  gsync();
+  return info;
+}
+
+// Steps 3-4 for the nodes the factor group hands over, in the same order.
+__device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
+  const int tid = gtid();
+  NodeCtx& c = sm.r.c;
+  for (int k = 0;; ++k) {
+    const int s = k % SLOTS, use = k / SLOTS;
+    if (!handoff_wait(&sm.full[s], (uint32_t)(use & 1), a.err)) return;
+    pc.mark(PH_REFINE_WAIT);
+    const Slot sl = sm.slot[s];
+    if (sl.item < 0) return;
+    const size_t si = (size_t)blockIdx.x * SLOTS + s;
+    char* slot = a.work + si * a.slot_bytes;
+    float2* M32 = reinterpret_cast<float2*>(slot);
+    double2* M64 = reinterpret_cast<double2*>(slot);  // fallback only; aliases M32
+    int* piv = a.piv + si * a.max_n;
+    NodeItem it;
+    RegionDev rg;
+    load_node(a, sl.item, c, rg, it);
+    const ProblemDev& P = c.P;
+    const int n = P.n, l = P.l, ncols = n + l;
+    const size_t nn = (size_t)n * n, nl = (size_t)n * l;
+    double2* R = reinterpret_cast<double2*>(slot + mixed_residual_offset(n, l));
+    const int* perm = reinterpret_cast<const int*>(slot + mixed_residual_offset(n, l) + nl * sizeof(double2));
+    double2* X = a.X + rg.x_off + (size_t)it.j * nl;
+    int info = sl.info;
+    bool ok = (info == 0);
+    int sweeps = 0;
+    if (ok) {
+      double dprev = sl.xm;
       bool conv = false;
-      // 3: refinement
-      for (int s = 1; s <= a.max_sweeps && ok; ++s) {
-        residual_fp64(X, R, sm);
-        pc.mark(3);
+      for (int sw = 1; sw <= a.max_sweeps && ok; ++sw) {
+        residual_fp64(X, R, c, sm.r.u.res);
+        pc.mark(PH_RESIDUAL);
         double rm = 0.0;
         for (size_t e = tid; e < nl; e += THREADS) rm = fmax(rm, fmax(fabs(R[e].x), fabs(R[e].y)));
-        rm = block_max(rm, sm.red);
-        if (rm == 0.0) { conv = true; break; }
+        rm = block_max(rm, c.red);
+        if (rm == 0.0) {
+          conv = true;
+          break;
+        }
         const double inv = 1.0 / rm;
         // right-hand side P R / |R|max: the row swaps as one gather
         for (size_t e = tid; e < nl; e += THREADS) {
-          const size_t c = e / n, i = e % n;
-          const double2 rv = R[c * n + perm[i]];
+          const size_t cc = e / n, i = e % n;
+          const double2 rv = R[cc * n + perm[i]];
           M32[nn + e] = make_float2((float)(rv.x * inv), (float)(rv.y * inv));
         }
-        __syncthreads();
-        cta_fwd_blocked(M32, n, l, sm.u.lu32);
-        cta_back_blocked(M32, n, l, sm.u.lu32);
+        gsync();
+        cta_fwd_blocked(M32, n, l, sm.r.u.lu32);
+        cta_back_blocked(M32, n, l, sm.r.u.lu32);
         double dm = 0.0, xmx = 0.0;
         for (size_t e = tid; e < nl; e += THREADS) {
           const float2 d = M32[nn + e];
@@ -250,29 +503,72 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_mixed(NodeArgs a) {
           dm = fmax(dm, fmax(fabs(dx), fabs(dy)));
           xmx = fmax(xmx, fmax(fabs(x.x), fabs(x.y)));
         }
-        dm = block_max(dm, sm.red);
-        xmx = block_max(xmx, sm.red);
-        pc.mark(4);
-        sweeps = s;
-        if (!(dm < dprev) && s > 1) { ok = false; break; }          // no contraction
-        if (dm * dm <= a.tol_ir * xmx * dprev) { conv = true; break; }
+        dm = block_max(dm, c.red);
+        xmx = block_max(xmx, c.red);
+        pc.mark(PH_CORRECTION);
+        sweeps = sw;
+        if (!(dm < dprev) && sw > 1) {  // no contraction
+          ok = false;
+          break;
+        }
+        if (dm * dm <= a.tol_ir * xmx * dprev) {
+          conv = true;
+          break;
+        }
         dprev = dm;
       }
       if (!conv) ok = false;
     }
     if (!ok) {
-      // 4: FP64 fallback in the same workspace
-      __syncthreads();
-      assemble(sm, nullptr, M64);
-      for (size_t e = tid; e < nl; e += THREADS) M64[nn + e] = P.V[e];
-      __syncthreads();
-      info = cta_lu(M64, n, ncols, piv, sm.u.lu64);
-      cta_back_blocked(M64, n, l, sm.u.lu64);
-      for (size_t e = tid; e < nl; e += THREADS) X[e] = M64[nn + e];
-      pc.mark(5);
+      info = fallback_fp64(c, M64, piv, X, sm.r.u.lu64);
+      pc.mark(PH_FALLBACK);
     }
-    if (tid == 0) a.node_info[rg.node_off + it.j] = info | (sweeps << 24) | (ok ? 0 : (1 << 30));
-    __syncthreads();
+    if (tid == 0)
+      a.node_info[rg.node_off + it.j] =
+          info | (sweeps << 24) | (sl.tc_timeout ? (1 << 29) : 0) | (ok ? 0 : (1 << 30));
+    gsync();
+    mbar_arrive(&sm.empty[s]);
+  }
+}
+
+__global__ void __launch_bounds__(CTA_THREADS, 1) k_factor_solve_mixed(NodeArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  MixedSmem& sm = *reinterpret_cast<MixedSmem*>(smem_raw);
+  const int tid = threadIdx.x;
+  PhaseClock pc(a.phase ? a.phase + (size_t)blockIdx.x * PMCIM_PHASES : nullptr);
+
+  // tensor memory (factor group's warp 0) and the barriers, for the whole persistent CTA
+  if (tid < 32) tcu::tmem_alloc(&sm.tmem_base);
+  if (tid == 0) {
+    for (int s = 0; s < SLOTS; ++s) {
+      mbar_init_count(&sm.full[s], THREADS);
+      mbar_init_count(&sm.empty[s], THREADS);
+    }
+    tcu::mbar_init(&sm.mbar_tc[0]);
+    tcu::mbar_init(&sm.mbar_tc[1]);
+    sm.tc_bad = 0;
+  }
+  tcu::fence_async_smem();
+  tcu::fence_before();
+  __syncthreads();
+  tcu::fence_after();
+
+  if (tid < THREADS) {
+    tcu::Ctx cx{sm.f.u.tc + offsetof(LuSmemT<float2>, Ls), sm.mbar_tc, sm.tmem_base, {0u, 0u}, &sm.tc_bad};
+    factor_group(a, sm, cx, pc);
+    // a commit whose wait ran out may still be in flight: wait once more (bounded)
+    // before the columns are given back
+    if (sm.tc_bad) {
+      // returns at once for a barrier with no commit outstanding
+      tcu::wait_parity(&sm.mbar_tc[0], cx.phase[0] ^ 1u, tcu::WAIT_CYCLES);
+      tcu::wait_parity(&sm.mbar_tc[1], cx.phase[1] ^ 1u, tcu::WAIT_CYCLES);
+    }
+    tcu::fence_before();
+    gsync();
+    tcu::fence_after();
+    if (tid < 32) tcu::tmem_dealloc(cx.tmem);
+  } else {
+    refine_group(a, sm, pc);
   }
 }
 
@@ -287,16 +583,37 @@ size_t mixed_slot_bytes(int n, int l) {
   return (b + 255) & ~(size_t)255;
 }
 
+static_assert(sizeof(MixedSmem) + 1024 <= 227 * 1024, "one CTA per SM");
+
 cudaError_t prepare_factor_mixed() {
   return cudaFuncSetAttribute(k_factor_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(MixedSmem));
 }
 
+int mixed_slots_per_cta() { return SLOTS; }
+
+namespace {
+__global__ void k_round_c64(const double2* __restrict__ src, float2* __restrict__ dst, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = make_float2((float)src[i].x, (float)src[i].y);
+}
+}  // namespace
+
+cudaError_t round_coefficients_c64(const double2* src, float2* dst, size_t count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const size_t blocks = (count + 255) / 256;
+  k_round_c64<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
 // Launch only; prepare_factor_mixed() must have set the shared-memory limit.
+// One CTA per a.slots / SLOTS workspace slots.
 cudaError_t launch_factor_solve_mixed(const NodeArgs& a, cudaStream_t s) {
   if (a.n_items <= 0) return cudaSuccess;
   const size_t smem = sizeof(MixedSmem);
-  int grid = a.slots < a.n_items ? a.slots : a.n_items;
-  k_factor_solve_mixed<<<grid, THREADS, smem, s>>>(a);
+  int grid = a.slots / SLOTS;
+  if (grid > a.n_items) grid = a.n_items;
+  if (grid < 1) return cudaErrorInvalidValue;
+  k_factor_solve_mixed<<<grid, CTA_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }

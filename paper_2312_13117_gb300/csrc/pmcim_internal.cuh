@@ -96,7 +96,7 @@ __host__ __device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
     return make_float2((a.x * t + a.y) / d, (a.y * t - a.x) / d);
   }
 }
-__device__ __forceinline__ double l1abs(float2 a) { return (double)(fabsf(a.x) + fabsf(a.y)); }
+__device__ __forceinline__ float l1abs(float2 a) { return fabsf(a.x) + fabsf(a.y); }
 template <typename T2> __device__ __forceinline__ T2 czero();
 template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.0f, 0.0f); }
@@ -152,8 +152,9 @@ __device__ __forceinline__ void node_weight(double cre, double cim, double r, in
 // ---------------------------------------------------------------------------
 struct ProblemDev {
   int32_t n, K, l, n_dense;
-  const double2* A;  // n_dense * n * n, column-major, in term order
-  const double2* V;  // n x l probe block
+  const double2* A;    // n_dense * n * n, column-major, in term order
+  const double2* V;    // n x l probe block
+  const float2* A32;   // the same coefficients rounded to complex64 (FP32 LU assembly)
   TermDesc term[PMCIM_MAX_TERMS];
 };
 
@@ -163,6 +164,7 @@ struct RegionDev {
   int32_t prob;      // index into the problem table
   int32_t node_off;  // index of node 0 in the launch's node_info array
   int32_t gate;      // 1: Beyn runs only when the indicator marks a candidate
+  int32_t lu_tc;     // 1: the precision form's trailing updates run on the tensor cores
   int64_t x_off;     // double2 offset of node 0's solution in X (node j at x_off + j n l)
   int64_t c_off;     // double2 offset of the disk's C0 / C1 blocks (n l)
   int64_t p_off;     // offset of the disk's P f blocks (n)
@@ -202,18 +204,24 @@ struct NodeArgs {
   int max_sweeps;
   double tol_ir;
   unsigned long long* phase;  // NULL, or slots * PMCIM_PHASES clock64 counters (mixed kernel)
+  int32_t* err;               // mixed kernel: set to 1 when a wait between its thread groups ran out
 };
 cudaError_t prepare_factor_fp64();   // shared-memory limits; call outside graph capture
 cudaError_t prepare_factor_mixed();
 cudaError_t launch_factor_solve_fp64(const NodeArgs& a, cudaStream_t s);
 cudaError_t launch_factor_solve_mixed(const NodeArgs& a, cudaStream_t s);
+int mixed_slots_per_cta();  // workspace slots each CTA of the mixed kernel cycles through
+// dst[i] = complex64(src[i]), i < count (the FP32 copy of the coefficients)
+cudaError_t round_coefficients_c64(const double2* src, float2* dst, size_t count, cudaStream_t s);
 // warp-per-node FP64 kernel for small problems (lu_small.cu)
 bool small_kernel_fits(int n, int l);
 cudaError_t prepare_factor_small();
 cudaError_t launch_factor_solve_small(const NodeArgs& a, cudaStream_t s);
 int factor_slots_fp64(int n, int l);
 // Phases of the precision-form node kernel timed with clock64 when profiling.
-#define PMCIM_PHASES 8  // assemble, LU, first solve, residual, correction solve, fallback, set-up, unused
+// assemble, LU panels, first solve, residual, correction solves, fallback, set-up,
+// LU triangular solves, LU trailing updates, 3 unused
+#define PMCIM_PHASES PMCIM_PHASE_COUNT
 __host__ __device__ inline size_t mixed_residual_offset(int n, int l) {
   return (((size_t)n * (n + l) * 8) + 255) & ~(size_t)255;
 }

@@ -22,7 +22,7 @@ STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: 
 
 RS_CANDIDATE, RS_SATURATED, RS_SPLIT, RS_SINGULAR_NODE, RS_IR_FALLBACK, RS_NO_EIG, RS_SCREENED = 1, 2, 4, 8, 16, 32, 64
 F_MONOMIAL, F_EXP_NEG = 0, 1
-PREC_FP64, PREC_FP32_IR, PREC_AUTO = 0, 1, 2
+PREC_FP64, PREC_FP32_IR, PREC_AUTO, PREC_TF32X3_IR = 0, 1, 2, 3
 
 EXPORTS = ["pmcim_default_options", "pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments",
            "pmcim_indicator", "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_status_string",
@@ -57,7 +57,7 @@ class pmcim_batch_item(C.Structure):
 
 
 class pmcim_profile(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8), ("mixed_phase_cycles", C.c_double * 8)]
+    _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8), ("mixed_phase_cycles", C.c_double * 12)]
 
 
 class pmcim_stats(C.Structure):
@@ -65,7 +65,8 @@ class pmcim_stats(C.Structure):
                 ("splits", C.c_int32), ("unverified", C.c_int32), ("ir_fallbacks", C.c_int32),
                 ("singular_nodes", C.c_int32), ("ir_sweeps", C.c_int64), ("certified", C.c_int32),
                 ("graphs", C.c_int32), ("tuned_fp64", C.c_int32), ("tuned_mixed", C.c_int32),
-                ("screened_out", C.c_int32), ("screen_solves", C.c_int32)]
+                ("screened_out", C.c_int32), ("screen_solves", C.c_int32), ("tuned_tc", C.c_int32),
+                ("tc_timeouts", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -171,9 +172,17 @@ def pmcim_profile_read() -> dict:
     cyc = [float(x) for x in pr.mixed_phase_cycles]
     tot = sum(cyc)
     if tot > 0:
-        names = ["assemble", "lu_fp32", "first_solve", "residual_fp64", "correction_solve", "fp64_fallback",
-                 "node_setup", "unused"]
-        out["factor_fp32"]["phase_share"] = {nm: c / tot for nm, c in zip(names, cyc) if c > 0}
+        # the node kernel runs two thread groups side by side: each phase is given
+        # as a share of its own group's clock
+        names = ["assemble", "lu_panel", "first_solve", "residual_fp64", "correction_solve", "fp64_fallback",
+                 "node_setup", "lu_trsm", "lu_update", "factor_wait", "refine_wait", "unused11"]
+        factor = {0, 1, 2, 6, 7, 8, 9}
+        tot_f = sum(c for i, c in enumerate(cyc) if i in factor) or 1.0
+        tot_r = sum(c for i, c in enumerate(cyc) if i not in factor) or 1.0
+        share = {nm: c / (tot_f if i in factor else tot_r) for i, (nm, c) in enumerate(zip(names, cyc)) if c > 0}
+        share["lu_fp32"] = sum(share.get(k, 0.0) for k in ("lu_panel", "lu_trsm", "lu_update"))
+        out["factor_fp32"]["phase_share"] = share
+        out["factor_fp32"]["phase_cycles"] = {nm: c for nm, c in zip(names, cyc) if c > 0}
     return out
 
 

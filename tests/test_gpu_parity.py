@@ -310,15 +310,20 @@ def test_full_size_delay_sampled_regions(pm):
 # a5: precision form (FP32 LU + FP64 refinement) against the FP64 oracle
 # ---------------------------------------------------------------------------
 
-def _mixed_opt(pm, **kw):
-    return pm.options(precision=pm.PREC_FP32_IR, **kw)
+MIXED_FORMS = ["fp32ir", "tf32x3"]
 
 
-def test_mixed_moments_close_to_oracle(pm):
+def _mixed_opt(pm, form="fp32ir", **kw):
+    prec = {"fp32ir": pm.PREC_FP32_IR, "tf32x3": pm.PREC_TF32X3_IR}[form]
+    return pm.options(precision=prec, **kw)
+
+
+@pytest.mark.parametrize("form", MIXED_FORMS)
+def test_mixed_moments_close_to_oracle(pm, form):
     """Refined solutions: |dX| <= 1e-9 |X| per node is the contract of the refinement stop."""
     W = w.quadratic_small(seed=2, n=72, l=6, N=16)
     P = pm.Problem(W.problem.n, W.problem.terms)
-    C0, C1, _, _ = P.moments(W.regions[:6], W.V, opt=_mixed_opt(pm))
+    C0, C1, _, _ = P.moments(W.regions[:6], W.V, opt=_mixed_opt(pm, form))
     for g, reg in enumerate(W.regions[:6]):
         m = o.moments(W.problem, reg.c, reg.r, reg.N, W.V)
         z, wts = o.nodes_weights(reg.c, reg.r, reg.N)
@@ -330,26 +335,64 @@ def test_mixed_moments_close_to_oracle(pm):
     P.close()
 
 
-def test_mixed_solve_quadratic_n64(pm):
+@pytest.mark.parametrize("form", MIXED_FORMS)
+def test_mixed_solve_quadratic_n64(pm, form):
     W = w.quadratic_small()
     P = pm.Problem(W.problem.n, W.problem.terms)
-    res = P.solve(W.regions, W.V, opt=_mixed_opt(pm))
+    res = P.solve(W.regions, W.V, opt=_mixed_opt(pm, form))
     ref = o.pmcimb(W.problem, W.regions, W.V)
     assert _match_lam(res["lam"], ref.lam) <= LAM_TOL
     assert res["stats"]["ir_sweeps"] >= res["stats"]["solves"]
+    assert res["stats"]["tc_timeouts"] == 0
     P.close()
 
 
-def test_mixed_solve_delay_small(pm):
+@pytest.mark.parametrize("form", MIXED_FORMS)
+def test_mixed_solve_delay_small(pm, form):
     W = w.delay_large(n=64, l=8, N=32, nx=4, ny=12)
     P = pm.Problem(W.problem.n, W.problem.terms)
-    res = P.solve(W.regions, W.V, opt=_mixed_opt(pm))
+    res = P.solve(W.regions, W.V, opt=_mixed_opt(pm, form))
     ref = o.pmcimb(W.problem, W.regions, W.V)
     assert _match_lam(res["lam"], ref.lam) <= LAM_TOL
     P.close()
 
 
-def test_mixed_fallback_path(pm):
+def test_tc_moments_ragged_tiles(pm):
+    """Tensor-core trailing updates over several 128-row and 32-column tiles with ragged
+    edges (n = 291: 3 row tiles at the first panel, the last one 35 rows; n + l = 296
+    columns). T(z) = A - zI with a prescribed spectrum: 3 + 2 eigenvalues inside the two
+    disks, the rest at |z| >= 3, so every node is well conditioned and the refinement must
+    converge without the FP64 fallback. Moments and eigenvalues against the oracle."""
+    rng = np.random.default_rng(31)
+    n, l, N = 291, 5, 16
+    regs = [w.Region(0.3 + 0.2j, 0.4, N), w.Region(-1.1 - 0.5j, 0.6, N)]
+    inside = [0.3 + 0.2j + 0.2 * np.exp(2j * np.pi * k / 3) for k in range(3)]
+    inside += [-1.1 - 0.5j + 0.25 * np.exp(2j * np.pi * k / 2 + 0.4j) for k in range(2)]
+    far = (3.0 + 2.0 * rng.random(n - 5)) * np.exp(2j * np.pi * rng.random(n - 5))
+    prob, _ = w.similarity_linear(np.concatenate([inside, far]), seed=8)
+    V = w.probe_block(rng, n, l)
+    P = pm.Problem(n, prob.terms)
+    opt = _mixed_opt(pm, "tf32x3")
+    C0, C1, _, _ = P.moments(regs, V, opt=opt)
+    for g, reg in enumerate(regs):
+        m = o.moments(prob, reg.c, reg.r, reg.N, V)
+        z, wts = o.nodes_weights(reg.c, reg.r, reg.N)
+        X = o.solve_nodes(prob, z, V)
+        scale = sum(abs(wts[j]) * np.linalg.norm(X[j]) for j in range(reg.N))
+        b0, b1, _ = _moment_bound(prob, reg, V)
+        assert np.linalg.norm(C0[g] - m.C0) <= b0 + 1e-9 * scale
+        assert np.linalg.norm(C1[g] - m.C1) <= b1 + 1e-9 * scale * (abs(reg.c) + reg.r)
+    res = P.solve(regs, V, opt=opt)
+    ref = o.pmcimb(prob, regs, V)
+    assert len(ref.lam) == 5
+    assert _match_lam(res["lam"], ref.lam) <= LAM_TOL
+    assert res["stats"]["ir_fallbacks"] == 0
+    assert res["stats"]["tc_timeouts"] == 0
+    P.close()
+
+
+@pytest.mark.parametrize("form", MIXED_FORMS)
+def test_mixed_fallback_path(pm, form):
     """An eigenvalue 1e-7 from node 0 makes T(z_0) too ill-conditioned for FP32 (kappa u32 ~ 1):
     refinement cannot converge there, so that node is re-solved in FP64 and flagged; the
     moments still agree with the FP64 form."""
@@ -361,10 +404,10 @@ def test_mixed_fallback_path(pm):
     V = w.probe_block(rng, n, 4)
     reg = [w.Region(c, r, N)]
     P = pm.Problem(n, prob.terms)
-    res = P.solve(reg, V, opt=_mixed_opt(pm))
+    res = P.solve(reg, V, opt=_mixed_opt(pm, form))
     assert res["stats"]["ir_fallbacks"] >= 1
     assert res["status"][0] & pm.RS_IR_FALLBACK
-    Cm0, Cm1, _, _ = P.moments(reg, V, opt=_mixed_opt(pm))
+    Cm0, Cm1, _, _ = P.moments(reg, V, opt=_mixed_opt(pm, form))
     Cd0, Cd1, _, _ = P.moments(reg, V)
     z, wts = o.nodes_weights(c, r, N)
     X = o.solve_nodes(prob, z, V)
@@ -374,16 +417,18 @@ def test_mixed_fallback_path(pm):
     P.close()
 
 
-def test_mixed_full_size_delay_sampled(pm):
-    """n = 1024 delay problem: eigenvalues of two disks through the precision form."""
+@pytest.mark.parametrize("form", MIXED_FORMS)
+def test_mixed_full_size_delay_sampled(pm, form):
+    """n = 1024 delay problem: eigenvalues of two disks through the precision forms."""
     W = w.delay_large()
     regs = [W.regions[300], W.regions[517]]
     P = pm.Problem(W.problem.n, W.problem.terms)
-    res = P.solve(regs, W.V, opt=_mixed_opt(pm))
+    res = P.solve(regs, W.V, opt=_mixed_opt(pm, form))
     ref = o.pmcimb(W.problem, regs, W.V)
     assert len(ref.lam) >= 2
     assert _match_lam(res["lam"], ref.lam) <= LAM_TOL
     assert res["stats"]["ir_fallbacks"] == 0
+    assert res["stats"]["tc_timeouts"] == 0
     P.close()
 
 
@@ -407,16 +452,18 @@ def _small_batch(count=6, seed0=1000):
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32ir", "auto"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32ir", "tf32x3", "auto"])
 def test_batch_matches_oracle_per_problem(pm, precision):
-    prec = {"fp64": pm.PREC_FP64, "fp32ir": pm.PREC_FP32_IR, "auto": pm.PREC_AUTO}[precision]
+    prec = {"fp64": pm.PREC_FP64, "fp32ir": pm.PREC_FP32_IR, "tf32x3": pm.PREC_TF32X3_IR,
+            "auto": pm.PREC_AUTO}[precision]
     batch = _small_batch()
     handles = [pm.Problem(p.n, p.terms) for (p, _, _) in batch]
     res = pm.batch_solve(handles, [r for (_, r, _) in batch], [V for (_, _, V) in batch],
                          opt=pm.options(precision=prec))
     assert res["stats"]["graphs"] >= 1
     if precision == "auto":
-        assert res["stats"]["tuned_fp64"] + res["stats"]["tuned_mixed"] == len(batch)
+        st = res["stats"]
+        assert st["tuned_fp64"] + st["tuned_mixed"] + st["tuned_tc"] == len(batch)
     for q, (prob, regs, V) in enumerate(batch):
         ref = o.pmcimb(prob, regs, V)
         got = res["lam"][res["problem_of"] == q]

@@ -40,6 +40,8 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes per node of k_factor_solve_fp64, from one ncu capture of a 64-node launch at n = 1024, l = 16
 # (dram__bytes_read.sum + dram__bytes_write.sum = 28.59 GB); scaled to a launch by its node count.
 FACTOR_FP64_TRAFFIC_PER_NODE = 28.59e9 / 64
+# DRAM bytes per node of k_factor_solve_mixed (tensor-core form), from one ncu capture; None until measured
+MIXED_TRAFFIC_PER_NODE = None
 # FP32 pipe: 128 FFMA / SM / clock (measured 73.3 TFLOP/s at ~2.0 GHz); at the 2.07 GHz maximum:
 FP32_PEAK_TFLOPS = 128 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
 
@@ -87,11 +89,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -99,22 +101,31 @@ class ClockSampler:
             self.proc.kill()
         if self.t:
             self.t.join(timeout=2)
-        sm, smax, reasons = [], [], set()
+
+    def window(self, t0=None, t1=None):
+        """Median SM clock, its minimum, peak power and throttle reasons of the samples
+        taken between monotonic times t0 and t1 (all samples when None)."""
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if (t0 is not None and ts < t0) or (t1 is not None and ts > t1):
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
             try:
                 sm.append(float(parts[0]))
                 smax.append(float(parts[1]))
+                pw.append(float(parts[2]))
             except ValueError:
                 continue
             for nm, v in zip(names, parts[4:8]):
                 if v.lower() == "active":
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_min_mhz": min(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "power_w_max": max(pw) if pw else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
@@ -387,7 +398,8 @@ def run_screen(args, world, rank, local):
 
 
 def run_full(args, P, W, opt, opt_mixed, world, rank, local):
-    """Time to all eigenvalues: one pmCIMb pass over the whole grid per form."""
+    """Time to all eigenvalues: one pmCIMb pass over the whole grid per form
+    (opt_mixed: the tensor-core precision form)."""
     import torch
     from paper_2312_13117_gb300 import pmcim
     R = len(W.regions)
@@ -422,11 +434,11 @@ def run_full(args, P, W, opt, opt_mixed, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--regions-per-step", type=int, default=19,
-                    help="disks per step; 19 x 64 nodes = 1216 = 4 x 304 factorisation slots")
+    ap.add_argument("--regions-per-step", type=int, default=38,
+                    help="disks per step; 38 x 64 nodes = 2432 = 8 x 304 FP64 factorisation slots")
     ap.add_argument("--region-offset", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-regions", type=int, default=2)
@@ -489,6 +501,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        w0 = time.monotonic()
         solves, found = 0, 0
         agg = {}
         for k in range(steps):
@@ -499,73 +512,105 @@ def main():
                 agg[key] = agg.get(key, 0) + v
         e1.record(stream)
         torch.cuda.synchronize()
+        w1 = time.monotonic()
         barrier(world)
         pmcim.pmcim_profile_enable(False)
-        return e0.elapsed_time(e1), solves, found, agg, pmcim.pmcim_profile_read()
+        return e0.elapsed_time(e1), solves, found, agg, pmcim.pmcim_profile_read(), (w0, w1)
 
+    # forms: the headline is the fastest form at FP64 accuracy (the FP32 LU on the
+    # FMA pipes with FP64 refinement); the tensor-core precision form and plain
+    # FP64 are measured on the same disks beside it
+    forms = [("fp64", opt)] if args.no_mixed else [("fp32ir", opt_mixed), ("tf32x3", opt_tc), ("fp64", opt)]
+    head_name, head_opt = forms[0]
     clocks = ClockSampler(local)
     clocks.start()
-    forms = [] if args.no_mixed else [("fp32ir", opt_mixed), ("tf32x3", opt_tc)]
     if args.only_mixed:
-        for name, o in forms:
-            tm_ms, msolves, mfound, aggm, profm = timed(o, args.steps, args.warmup)
+        for name, o in forms[:-1] if len(forms) > 1 else forms:
+            tm_ms, msolves, mfound, aggm, profm, win = timed(o, args.steps, args.warmup)
             if rank == 0:
                 print(json.dumps({"form": name, "solves_per_s": msolves / (tm_ms / 1e3), "ms": tm_ms,
                                   "stats": aggm, "kernels": profm}))
-        clk = clocks.stop()
+        clocks.stop()
         if rank == 0:
-            print(json.dumps({"clocks": clk}))
+            print(json.dumps({"clocks": clocks.window()}))
         P.close()
         return 0
-    t_ms, solves, found, agg64, prof = timed(opt, args.steps, args.warmup)
     runs = {name: timed(o, args.steps, args.warmup) for name, o in forms}
-    clk = clocks.stop()
-    t_max = max_over_ranks(t_ms, world)
-    solves_all = sum_over_ranks(float(solves), world)
-    value = solves_all / (t_max / 1e3)
+    clocks.stop()
+    clk = clocks.window(*runs[head_name][5])  # the headline's timed region
     smax = clk.get("sm_max_mhz") or SM_MAX_MHZ
     peak64 = fp64_peak_tflops(smax)
     k_dense = sum(1 for t in W.problem.terms if not np.isscalar(t[0]))
+    t_fp64 = max_over_ranks(runs["fp64"][0], world)
+    found_fp64 = runs["fp64"][2]
+
+    def fp64_record(run):
+        t_ms, solves, found, agg, prof, win = run
+        t_max = max_over_ranks(t_ms, world)
+        fac = prof["factor_fp64"]
+        flops_per_node = 8.0 * n ** 3 / 3.0 + 8.0 * n * n * l
+        achieved = (flops_per_node * solves) / (fac["ms"] / 1e3) / 1e12 if fac["ms"] > 0 else None
+        roof = {"bound": "alu", "kernel": "k_factor_solve_fp64 (FP64 pipe)",
+                "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                "frac": (achieved / peak64) if achieved else None,
+                "traffic": FACTOR_FP64_TRAFFIC_PER_NODE * solves / max(1, fac["launches"]),
+                "traffic_note": "ncu DRAM bytes of a 64-node capture, scaled by nodes per launch",
+                "peak_source": "2 DFMA/SM/clk x 152 SMs x max SM clock (probe: 1.20 TFLOP/s at 2.0 GHz)",
+                "launches": fac["launches"], "avg_launch_ms": fac["ms"] / max(1, fac["launches"]),
+                "share_of_step": fac["ms"] / t_ms if t_ms else None}
+        return {"form": "plain FP64 LU", "value": sum_over_ranks(float(solves), world) / (t_max / 1e3),
+                "unit": UNIT, "ms_per_step": t_max / args.steps, "eigenvalues_found": found,
+                "roofline": roof, "kernels": prof, "clocks": clocks.window(*win)}
 
     def precision_record(name, run):
-        tm_ms, msolves, mfound, aggm, profm = run
+        tm_ms, msolves, mfound, aggm, profm, win = run
         tm_max = max_over_ranks(tm_ms, world)
         fm = profm["factor_fp32"]
         w64 = aggm["ir_sweeps"] * 8.0 * k_dense * n * n * l + aggm["ir_fallbacks"] * (8.0 * n ** 3 / 3 + 8.0 * n * n * l)
         w32 = msolves * (8.0 * n ** 3 / 3 + 8.0 * n * n * l) + aggm["ir_sweeps"] * 8.0 * n * n * l
         a64 = w64 / (fm["ms"] / 1e3) / 1e12 if fm["ms"] > 0 else None
         a32 = w32 / (fm["ms"] / 1e3) / 1e12 if fm["ms"] > 0 else None
+        roof = {"bound": "alu", "kernel": "k_factor_solve_mixed (FP64 pipe: refinement residuals)",
+                "achieved": a64, "peak": peak64, "unit": "TFLOP/s",
+                "frac": (a64 / peak64) if a64 else None,
+                "traffic": MIXED_TRAFFIC_PER_NODE * msolves / max(1, fm["launches"]) if MIXED_TRAFFIC_PER_NODE else None,
+                "traffic_note": "ncu DRAM bytes of a small capture, scaled by nodes per launch",
+                "peak_source": "2 DFMA/SM/clk x 152 SMs x max SM clock",
+                "fp32_work_tflops": a32, "fp32_peak_tflops": FP32_PEAK_TFLOPS,
+                "launches": fm["launches"], "avg_launch_ms": fm["ms"] / max(1, fm["launches"]),
+                "share_of_step": fm["ms"] / tm_ms if tm_ms else None}
+        cyc = fm.get("phase_cycles", {})
+        if cyc.get("residual_fp64"):
+            # SM clock cycles of the refine group inside the residual phase, summed over CTAs
+            # (one CTA per SM): the FP64 pipe's rate while the residual runs
+            roof["residual_dfma_per_sm_clock"] = aggm["ir_sweeps"] * 4.0 * k_dense * n * n * l / cyc["residual_fp64"]
+            roof["peak_dfma_per_sm_clock"] = FP64_DFMA_PER_SM_CLK
         rec = {
             "form": ("FP32 LU + FP64 iterative refinement (residual R = V - T(z)X from the FP64 A_k)"
                      if name == "fp32ir" else
                      "FP32 LU with 3xTF32 complex trailing updates on the tensor cores (tcgen05, TMEM "
                      "accumulators) + FP64 iterative refinement"),
             "value": sum_over_ranks(float(msolves), world) / (tm_max / 1e3), "unit": UNIT,
-            "ms_per_step": tm_max / args.steps, "speedup_vs_fp64": t_max / tm_max,
-            "eigenvalues_found": mfound, "eigenvalues_found_fp64": found,
+            "ms_per_step": tm_max / args.steps, "speedup_vs_fp64": t_fp64 / tm_max,
+            "eigenvalues_found": mfound, "eigenvalues_found_fp64": found_fp64,
             "ir_sweeps_per_node": aggm["ir_sweeps"] / max(1, msolves), "ir_fallbacks": aggm["ir_fallbacks"],
             "tc_timeouts": aggm.get("tc_timeouts", 0),
-            "roofline": {"bound": "alu", "kernel": "k_factor_solve_mixed (FP64 pipe: refinement residuals)",
-                         "achieved": a64, "peak": peak64, "unit": "TFLOP/s",
-                         "frac": (a64 / peak64) if a64 else None,
-                         "fp32_achieved_tflops": a32, "fp32_peak_tflops": FP32_PEAK_TFLOPS,
-                         "launches": fm["launches"], "share_of_step": fm["ms"] / tm_ms if tm_ms else None},
-            "kernels": profm,
+            "roofline": roof, "kernels": profm, "clocks": clocks.window(*win),
         }
         if name == "tf32x3":
             # tensor-pipe work of the trailing updates: 3 split products of the complex
             # rank-32 updates, 8 real flops per complex multiply-add
             upd = sum(8.0 * 32 * (n - k) * (n + l - k) for k in range(32, n, 32))
-            lu_share = profm["factor_fp32"].get("phase_share", {}).get("lu_fp32")
-            lu_s = fm["ms"] / 1e3 * lu_share if lu_share else None
-            tf = 3.0 * upd * msolves / lu_s / 1e12 if lu_s else None
-            rec["tensor"] = {"tf32_tflops_during_lu_phase": tf, "tf32_peak_tflops": TF32_PEAK_TFLOPS,
-                             "frac_during_lu_phase": tf / TF32_PEAK_TFLOPS if tf else None,
+            lu_cyc = sum(cyc.get(k, 0.0) for k in ("lu_update",))
+            tf = 3.0 * upd * msolves / (lu_cyc / (152 * smax * 1e6)) / 1e12 if lu_cyc else None
+            rec["tensor"] = {"tf32_tflops_during_update_phase": tf, "tf32_peak_tflops": TF32_PEAK_TFLOPS,
+                             "frac_during_update_phase": tf / TF32_PEAK_TFLOPS if tf else None,
                              "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
         return rec
 
-    mixed = precision_record("fp32ir", runs["fp32ir"]) if "fp32ir" in runs else None
-    mixed_tc = precision_record("tf32x3", runs["tf32x3"]) if "tf32x3" in runs else None
+    plain = fp64_record(runs["fp64"])
+    head = plain if head_name == "fp64" else precision_record(head_name, runs[head_name])
+    other = precision_record("tf32x3", runs["tf32x3"]) if "tf32x3" in runs else None
 
     # ---- e2e: host buffers through the C ABI, copies inside the timed region
     e2e = None
@@ -584,7 +629,7 @@ def main():
 
         def e2e_step(step):
             regs = pmcim.regions_array(batch(step))
-            rc = lib.pmcim_solve(P.handle, ctypes.byref(opt), B, regs, l, Vh.data_ptr(), cap, lam_h.data_ptr(),
+            rc = lib.pmcim_solve(P.handle, ctypes.byref(head_opt), B, regs, l, Vh.data_ptr(), cap, lam_h.data_ptr(),
                                  vec_h.data_ptr(), sig_h.data_ptr(), rof_h.data_ptr(), cnt_h.data_ptr(),
                                  ind_h.data_ptr(), st_h.data_ptr(), ctypes.byref(stats))
             assert rc == 0, pmcim.load().pmcim_last_error()
@@ -608,22 +653,7 @@ def main():
         te = max_over_ranks(te, world)
         es_all = sum_over_ranks(float(es), world)
         e2e = {"value": es_all / te, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
-               "d2h_bytes_per_step": d2h // args.steps}
-
-    # ---- roofline of the dominant kernel (FP64 node factorisation)
-    fac = prof["factor_fp64"]
-    flops_per_node = 8.0 * n ** 3 / 3.0 + 8.0 * n * n * l
-    factor_nodes = solves  # every node solve is one unit of the factorisation kernel
-    achieved = (flops_per_node * factor_nodes) / (fac["ms"] / 1e3) / 1e12 if fac["ms"] > 0 else None
-    peak = peak64
-    roofline = {"bound": "alu", "kernel": "k_factor_solve_fp64 (FP64 pipe)",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None,
-                "traffic": FACTOR_FP64_TRAFFIC_PER_NODE * factor_nodes / max(1, fac["launches"]),
-                "traffic_note": "ncu DRAM bytes of a 64-node capture, scaled by nodes per launch",
-                "peak_source": "2 DFMA/SM/clk x 152 SMs x max SM clock (probe: 1.20 TFLOP/s at 2.0 GHz)",
-                "launches": fac["launches"], "avg_launch_ms": fac["ms"] / max(1, fac["launches"]),
-                "share_of_step": fac["ms"] / t_ms if t_ms else None}
+               "d2h_bytes_per_step": d2h // args.steps, "form": head_name}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -632,20 +662,29 @@ def main():
         cpu = {"value": s / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": "%d disks (%d node solves) through the full oracle pmCIMb, %.1f s" % (len(ids), s, dt)}
 
+    prof = head["kernels"]
     launches = sum(v["launches"] for v in prof.values())
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if head_name == "fp64" else "f32 LU + f64 refinement",
+            "data": "synthetic",
             "config": {"workload": "delay NEP T(z)=-zI+A0+A1 exp(-z), n=1024, l=16, N=64, "
                                    "Omega=[-3,1]x[-6,6] split 16x48; %d disks per step per GPU" % B,
-                       "form": "plain FP64", "regions_per_step": B, "n": n, "l": l, "N": 64,
-                       "l2": "working set > L2 (304 x 16.3 MB factorisation slots)",
-                       "eigenvalues_found": found},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "kernels": prof, "precision_form": mixed, "precision_form_tc": mixed_tc, "clocks": clk,
+                       "form": head["form"], "regions_per_step": B, "n": n, "l": l, "N": 64,
+                       "l2": "working set > L2 (one 17 MB factorisation slot per CTA and slot)",
+                       "eigenvalues_found": head["eigenvalues_found"],
+                       "eigenvalues_found_fp64": found_fp64},
+            "speedup_vs_plain_fp64": (head["value"] / plain["value"]) if head is not plain else 1.0,
+            "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "kernels": prof, "plain_fp64": plain if head is not plain else None,
+            "precision_form_tc": other, "clocks": clk,
         }
+        for key in ("tensor", "ir_sweeps_per_node", "ir_fallbacks", "tc_timeouts"):
+            if key in head:
+                line[key] = head[key]
         print(json.dumps(line))
     P.close()
     if world > 1:

@@ -38,10 +38,11 @@ FP64_DFMA_PER_SM_CLK = 2          # measured: 1.19-1.20 TFLOP/s at ~2.0 GHz on 1
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes per node of k_factor_solve_fp64, from one ncu capture of a 64-node launch at n = 1024, l = 16
-# (dram__bytes_read.sum + dram__bytes_write.sum = 28.59 GB); scaled to a launch by its node count.
-FACTOR_FP64_TRAFFIC_PER_NODE = 28.59e9 / 64
-# DRAM bytes per node of k_factor_solve_mixed (tensor-core form), from one ncu capture; None until measured
-MIXED_TRAFFIC_PER_NODE = None
+# (dram__bytes_read.sum + dram__bytes_write.sum = 15.16 + 13.45 GB); scaled to a launch by its node count.
+FACTOR_FP64_TRAFFIC_PER_NODE = 28.61e9 / 64
+# DRAM bytes per node of k_factor_solve_mixed (FP32 form), from one ncu capture of a 320-node launch
+# (dram__bytes_read.sum + dram__bytes_write.sum = 49.91 + 35.55 GB); scaled to a launch by its node count
+MIXED_TRAFFIC_PER_NODE = 85.45e9 / 320
 # FP32 pipe: 128 FFMA / SM / clock (measured 73.3 TFLOP/s at ~2.0 GHz); at the 2.07 GHz maximum:
 FP32_PEAK_TFLOPS = 128 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
 

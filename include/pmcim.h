@@ -110,6 +110,10 @@ typedef struct {
   double screen_threshold;
   int32_t screen_N;        /* coarse nodes, a multiple of 16 (default 16)            */
   int32_t reserved2;
+  /* refinement stop (reduced precisions): a node's sweeps end when the estimated
+     remaining error |delta_s|^2 / |delta_{s-1}| is at most tol_ir |X| (max
+     norms); 0 = the default 1e-11. Must lie in [1e-15, 1e-6]. */
+  double tol_ir;
 } pmcim_options;
 
 /* Statistics of one pmcim_solve call. */

@@ -271,6 +271,8 @@ int check_options(const pmcim_options* opt) {
   if (opt->max_split_depth < 0 || opt->max_split_depth > 30) return fail(PMCIM_EINVAL, "max_split_depth out of range");
   if (opt->precision != PMCIM_PREC_FP64 && (opt->max_ir_sweeps < 1 || opt->max_ir_sweeps > 10))
     return fail(PMCIM_EINVAL, "max_ir_sweeps must be 1..10");
+  if (opt->tol_ir != 0.0 && !(opt->tol_ir >= 1e-15 && opt->tol_ir <= 1e-6))
+    return fail(PMCIM_EINVAL, "tol_ir must be 0 (default) or in [1e-15, 1e-6]");
   return PMCIM_OK;
 }
 
@@ -617,7 +619,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
       na.node_info = ws.node_info.as<int32_t>();
       na.max_n = max_n;
       na.max_sweeps = c.opt->max_ir_sweeps;
-      na.tol_ir = kIrTol;
+      na.tol_ir = c.opt->tol_ir > 0.0 ? c.opt->tol_ir : kIrTol;
       na.err = ws.counters.as<int32_t>() + 3 * waves.size();
       if (wv.n64) {
         na.items = ws.items.as<NodeItem>() + wv.items64_off;
@@ -1047,6 +1049,7 @@ void pmcim_default_options(pmcim_options* opt) {
   opt->screen_params = nullptr;
   opt->screen_threshold = 0.0;
   opt->screen_N = 16;
+  opt->tol_ir = kIrTol;
 }
 
 const char* pmcim_status_string(int code) {

@@ -109,7 +109,14 @@ typedef struct {
   const float* screen_params;
   double screen_threshold;
   int32_t screen_N;        /* coarse nodes, a multiple of 16 (default 16)            */
-  int32_t reserved2;
+  /* pmcim_solve / pmcim_batch_solve / pmcim_beyn: 0 = one N per disk serves the
+     indicator and Beyn; > 0 = the paper's two-pass schedule (Appendix pmCIMb
+     driver): the indicator gates each disk on an indicator_N-node rule (even;
+     every disk's N a multiple of it), then Beyn runs on the candidates with the
+     disk's N, reusing the indicator pass's solves (its nodes are every
+     (N / indicator_N)-th node of the full rule). Disks the indicator does not
+     gate (depth-0 disks of pmcim_beyn) go straight to Beyn. */
+  int32_t indicator_N;
   /* refinement stop (reduced precisions): a node's sweeps end when the estimated
      remaining error |delta_s|^2 / |delta_{s-1}| is at most tol_ir |X| (max
      norms); 0 = the default 1e-11. Must lie in [1e-15, 1e-6]. */

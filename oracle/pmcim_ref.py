@@ -258,10 +258,16 @@ class PmcimbResult:
 
 
 def pmcimb(problem, regions: Sequence, V: np.ndarray, tol_ind: float = 0.1,
-           tol_svd: float = 1e-6, tol_verify: float = 1e-6, max_depth: int = 8) -> PmcimbResult:
+           tol_svd: float = 1e-6, tol_verify: float = 1e-6, max_depth: int = 8,
+           indicator_N: int = 0) -> PmcimbResult:
     """pmCIMb steps 1-3 over the given disks, with saturated disks split and re-run.
 
-    One N per disk serves both the indicator and Beyn's moments.
+    indicator_N = 0: one N per disk serves both the indicator and Beyn's moments.
+    indicator_N > 0: the paper's two-pass schedule (Appendix, pmCIMb driver; Sec. 3.2
+    remark that N = 16 suffices for the indicator and N = 64 for Beyn): step 1
+    screens each disk with the indicator on an indicator_N-node rule, step 2 runs
+    Beyn with the disk's N on the candidates. Split children go through both steps
+    again. Each disk's N must be a multiple of indicator_N.
     """
     n = problem.n
     records: List[RegionRecord] = []
@@ -270,8 +276,15 @@ def pmcimb(problem, regions: Sequence, V: np.ndarray, tol_ind: float = 0.1,
     while level:
         nxt = []
         for (c, r, N, depth) in level:
-            m = moments(problem, c, r, N, V)
-            I = indicator_value(m.pf_N, m.pf_half, m.pf_abs)
+            if indicator_N:
+                if N % indicator_N:
+                    raise ValueError("N = %d is not a multiple of indicator_N = %d" % (N, indicator_N))
+                mi = moments(problem, c, r, indicator_N, V)
+                I = indicator_value(mi.pf_N, mi.pf_half, mi.pf_abs)
+                m = moments(problem, c, r, N, V) if I > tol_ind else None
+            else:
+                m = moments(problem, c, r, N, V)
+                I = indicator_value(m.pf_N, m.pf_half, m.pf_abs)
             rec = RegionRecord(c, r, N, depth, I, I > tol_ind)
             if rec.candidate:
                 b = beyn_extract(m.C0, m.C1, tol_svd)

@@ -99,6 +99,8 @@ struct DevBuf {
 constexpr size_t kWaveBytes = size_t(16) << 30;
 // Upper bound on the per-CTA factorisation workspaces of one form.
 constexpr size_t kSlotBytes = size_t(24) << 30;
+// indicator-pass solutions kept for reuse by the two-pass schedule, per chunk of disks
+constexpr size_t kKeepBytes = size_t(8) << 30;
 // Refinement stops when the estimated remaining error of X (max norm) is below
 // this fraction of |X|: 1e-11 keeps Beyn's eigenvalues within about 1e-14 of
 // the FP64 ones on the delay workload (simulated FP32 LU + FP64 refinement).
@@ -206,6 +208,7 @@ struct Workspace {
   DevBuf bwork, bsigma, bp, blam, bvecs, bkept, bstatus;
   DevBuf vlam, vprob, voff, vsig, vacc, vwork, vvec, vpiv;
   DevBuf gitems, gdst, gperm;
+  DevBuf Xkeep, citems;  // two-pass schedule: indicator-pass solutions, copy list
   DevBuf ind3, feats, sprob, sparams, sscratch;
   // the library's own stream: graphs cannot be captured on the legacy default stream
   cudaStream_t stream = nullptr;
@@ -218,7 +221,8 @@ struct Workspace {
     DevBuf* b[] = {&probs, &regions, &items, &counters, &node_info, &X, &work64, &piv64, &work32, &piv32,
                    &phase, &C0, &C1, &pf_half, &pf_abs, &ind, &pf_norm, &pf_scale, &cand, &bwork, &bsigma,
                    &bp, &blam, &bvecs, &bkept, &bstatus, &vlam, &vprob, &voff, &vsig, &vacc, &vwork,
-                   &vvec, &vpiv, &gitems, &gdst, &gperm, &ind3, &feats, &sprob, &sparams, &sscratch};
+                   &vvec, &vpiv, &gitems, &gdst, &gperm, &ind3, &feats, &sprob, &sparams, &sscratch, &Xkeep,
+                   &citems};
     for (DevBuf* x : b) x->release();
   }
 };
@@ -273,6 +277,8 @@ int check_options(const pmcim_options* opt) {
     return fail(PMCIM_EINVAL, "max_ir_sweeps must be 1..10");
   if (opt->tol_ir != 0.0 && !(opt->tol_ir >= 1e-15 && opt->tol_ir <= 1e-6))
     return fail(PMCIM_EINVAL, "tol_ir must be 0 (default) or in [1e-15, 1e-6]");
+  if (opt->indicator_N != 0 && (opt->indicator_N < 2 || opt->indicator_N > 4096 || (opt->indicator_N & 1)))
+    return fail(PMCIM_EINVAL, "indicator_N = %d must be 0 or even, 2..4096", opt->indicator_N);
   return PMCIM_OK;
 }
 
@@ -363,8 +369,21 @@ struct LevelOut {
   std::vector<RegionDev> rd;
 };
 
+// Node solutions a level takes over from an earlier pass instead of solving
+// them: for region g with src[g] >= 0, node j = m * stride[g] (m = 0, 1, ...)
+// is copied from X + src[g] + m n l.
+struct LevelReuse {
+  const double2* X = nullptr;
+  std::vector<int64_t> src;
+  std::vector<int> stride;
+};
+
+// gate_top: the indicator gates Beyn for depth-0 disks too (deeper ones always);
+// no_gate: Beyn runs on every disk; keep_x: all solutions of the level stay in
+// ws.Xkeep (one wave), at rd[g].x_off, for a later pass to reuse.
 int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool do_beyn, LevelOut* out,
-              const std::vector<int>* form_override = nullptr, bool screen_features = false);
+              const std::vector<int>* form_override = nullptr, bool screen_features = false,
+              const LevelReuse* reuse = nullptr, bool keep_x = false, bool no_gate = false);
 
 int tune_forms(Call& c) {
   if (c.opt->precision != PMCIM_PREC_AUTO) {
@@ -429,7 +448,8 @@ int tune_forms(Call& c) {
 // One level: node solves (waves), reduction, indicator, Beyn (gated)
 // ===========================================================================
 int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool do_beyn, LevelOut* out,
-              const std::vector<int>* form_override, bool screen_features) {
+              const std::vector<int>* form_override, bool screen_features, const LevelReuse* reuse, bool keep_x,
+              bool no_gate) {
   Workspace& ws = *c.ws;
   cudaStream_t s = c.s;
   const int R = (int)regs.size();
@@ -451,7 +471,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
     d.N = h.N;
     d.prob = h.prob;
     d.node_off = (int32_t)total_nodes;
-    d.gate = (h.depth > 0 || gate_top) ? 1 : 0;
+    d.gate = no_gate ? 0 : ((h.depth > 0 || gate_top) ? 1 : 0);
     d.lu_tc = form_of(h.prob) == PMCIM_PREC_TF32X3_IR ? 1 : 0;
     d.c_off = (int64_t)c_tot;
     d.p_off = (int64_t)p_tot;
@@ -492,10 +512,13 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   struct Wave {
     int g0, g1;
     size_t items64_off, n64, items32_off, n32, itemsS_off, nS;
+    size_t copies_off, n_copies;  // reused solutions copied into this wave's X
+    int max_copy;
   };
   std::vector<Wave> waves;
   std::vector<NodeItem> items;  // all waves: FP64 items then mixed items per wave
-  size_t x_need = 0;
+  std::vector<VecItem> copies;  // all waves
+  size_t x_need = 0, reused_nodes = 0;
   bool any64 = false, any32 = false, anyS = false;
   {
     int g0 = 0;
@@ -505,7 +528,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
       while (g1 < R && g1 - g0 < 65535) {
         const ProblemDev& P = c.pd[regs[g1].prob];
         const size_t b = (size_t)regs[g1].N * P.n * P.l * sizeof(double2);
-        if (g1 > g0 && xb + b > kWaveBytes) break;
+        if (g1 > g0 && xb + b > kWaveBytes && !keep_x) break;
         rd[g1].x_off = (int64_t)(xb / sizeof(double2));
         xb += b;
         ++g1;
@@ -514,11 +537,24 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
       // largest n first: the atomic work counter then hands out the long jobs early
       // small problems (n <= 32, l <= 16) go to the warp-per-node kernel whatever the form
       std::vector<NodeItem> it64, it32, itS;
+      const size_t copies_off = copies.size();
+      int max_copy = 0;
       for (int g = g0; g < g1; ++g) {
         const ProblemDev& P = c.pd[regs[g].prob];
         std::vector<NodeItem>& dst = small_kernel_fits(P.n, P.l) ? itS
                                      : (form_of(regs[g].prob) == PMCIM_PREC_FP64 ? it64 : it32);
-        for (int j = 0; j < regs[g].N; ++j) dst.push_back(NodeItem{g, j});
+        const bool re = reuse && reuse->src[g] >= 0;
+        const int nl = P.n * P.l;
+        for (int j = 0; j < regs[g].N; ++j) {
+          if (re && j % reuse->stride[g] == 0) {
+            copies.push_back(VecItem{reuse->src[g] + (int64_t)(j / reuse->stride[g]) * nl,
+                                     rd[g].x_off + (int64_t)j * nl, nl, 0});
+            max_copy = std::max(max_copy, nl);
+            ++reused_nodes;
+          } else {
+            dst.push_back(NodeItem{g, j});
+          }
+        }
       }
       auto by_n = [&](const NodeItem& a, const NodeItem& b) {
         const int na = c.pd[regs[a.region].prob].n, nb = c.pd[regs[b.region].prob].n;
@@ -528,7 +564,8 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
       };
       std::stable_sort(it64.begin(), it64.end(), by_n);
       std::stable_sort(it32.begin(), it32.end(), by_n);
-      Wave wv{g0, g1, items.size(), it64.size(), 0, it32.size(), 0, itS.size()};
+      Wave wv{g0, g1, items.size(), it64.size(), 0, it32.size(), 0, itS.size(), copies_off,
+              copies.size() - copies_off, max_copy};
       items.insert(items.end(), it64.begin(), it64.end());
       wv.items32_off = items.size();
       items.insert(items.end(), it32.begin(), it32.end());
@@ -541,7 +578,12 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
       g0 = g1;
     }
   }
-  CU(ws.X.ensure(std::max<size_t>(1, x_need)));
+  DevBuf& xbuf = keep_x ? ws.Xkeep : ws.X;
+  CU(xbuf.ensure(std::max<size_t>(1, x_need)));
+  if (!copies.empty()) {
+    CU(ws.citems.ensure(copies.size() * sizeof(VecItem)));
+    CU(cudaMemcpyAsync(ws.citems.p, copies.data(), copies.size() * sizeof(VecItem), cudaMemcpyHostToDevice, s));
+  }
   CU(ws.items.ensure(std::max<size_t>(1, items.size()) * sizeof(NodeItem)));
   CU(ws.regions.ensure(R * sizeof(RegionDev)));
   // 3 work counters per wave, then the mixed kernel's error flag
@@ -581,7 +623,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   la.regions = ws.regions.as<RegionDev>();
   la.R = R;
   la.max_nl = max_nl;
-  la.X = ws.X.as<double2>();
+  la.X = xbuf.as<double2>();
   la.C0 = ws.C0.as<double2>();
   la.C1 = ws.C1.as<double2>();
   la.pf_half = ws.pf_half.as<double2>();
@@ -615,7 +657,15 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
       std::memset(&na, 0, sizeof(na));
       na.probs = la.probs;
       na.regions = la.regions;
-      na.X = ws.X.as<double2>();
+      na.X = xbuf.as<double2>();
+      // solutions taken over from an earlier pass
+      for (size_t q0 = 0; q0 < wv.n_copies; q0 += 65535) {
+        const int cnt = (int)std::min<size_t>(65535, wv.n_copies - q0);
+        prof_begin(PMCIM_K_GATHER, s);
+        CU(launch_gather_vecs(reuse->X, xbuf.as<double2>(), ws.citems.as<VecItem>() + wv.copies_off + q0, cnt,
+                              wv.max_copy, s));
+        prof_end(PMCIM_K_GATHER, s);
+      }
       na.node_info = ws.node_info.as<int32_t>();
       na.max_n = max_n;
       na.max_sweeps = c.opt->max_ir_sweeps;
@@ -731,8 +781,15 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   CU(cudaStreamSynchronize(s));
   if (handoff_err)
     return fail(PMCIM_ETIMEOUT, "precision-form node kernel: a wait between its thread groups ran out");
-  c.st.solves += (int64_t)total_nodes;
-  c.st.regions += R;
+  if (reuse)  // reused nodes were not solved here: their info words are stale
+    for (int g = 0; g < R; ++g)
+      if (reuse->src[g] >= 0)
+        for (int j = 0; j < regs[g].N; j += reuse->stride[g]) out->node_info[rd[g].node_off + j] = 0;
+  c.st.solves += (int64_t)(total_nodes - reused_nodes);
+  int recount = 0;  // disks already counted by the pass their solutions come from
+  if (reuse)
+    for (int g = 0; g < R; ++g) recount += reuse->src[g] >= 0 ? 1 : 0;
+  c.st.regions += R - recount;
   for (size_t i = 0; i < total_nodes; ++i) {
     const int v = out->node_info[i];
     if (v & (1 << 30)) c.st.ir_fallbacks += 1;
@@ -754,23 +811,44 @@ struct EigOut {
 
 int run_beyn_levels(Call& c, const std::vector<HostRegion>& top, bool gate_top, EigOut* out,
                     std::vector<int>* root_status, std::vector<double>* top_ind, size_t n_roots = 0) {
+  if (c.opt->indicator_N > 0)
+    for (const HostRegion& h : top)
+      if (h.N % c.opt->indicator_N)
+        return fail(PMCIM_EINVAL, "N = %d is not a multiple of indicator_N = %d", h.N, c.opt->indicator_N);
   Workspace& ws = *c.ws;
   cudaStream_t s = c.s;
   std::vector<HostRegion> level = top;
   if (n_roots < top.size()) n_roots = top.size();
   root_status->assign(n_roots, 0);
   if (top_ind) top_ind->assign(n_roots, 0.0);
+  const int Ni = c.opt->indicator_N;
   while (!level.empty()) {
-    const int R = (int)level.size();
-    LevelOut lo;
-    CHK(run_level(c, level, gate_top, true, &lo));
     std::vector<HostRegion> next;
     std::vector<VecItem> vi;
-    const size_t vec_before = out->vec_used;
+    size_t vec_before = out->vec_used;
     int max_vn = 0;
-    for (int g = 0; g < R; ++g) {
-      const HostRegion& h = level[g];
-      const RegionDev& d = lo.rd[g];
+    // eigenvectors of the last Beyn pass, from its scratch to the call's output
+    // buffer (before the next pass overwrites the scratch)
+    auto flush_vecs = [&]() -> int {
+      if (vi.empty()) return PMCIM_OK;
+      CU(ws.gdst.grow_keep(out->vec_used * sizeof(double2), vec_before * sizeof(double2), s));
+      CU(ws.gitems.ensure(vi.size() * sizeof(VecItem)));
+      CU(cudaMemcpyAsync(ws.gitems.p, vi.data(), vi.size() * sizeof(VecItem), cudaMemcpyHostToDevice, s));
+      for (size_t q0 = 0; q0 < vi.size(); q0 += 65535) {
+        const int cnt = (int)std::min<size_t>(65535, vi.size() - q0);
+        prof_begin(PMCIM_K_GATHER, s);
+        CU(launch_gather_vecs(ws.bvecs.as<double2>(), ws.gdst.as<double2>(), ws.gitems.as<VecItem>() + q0, cnt,
+                              max_vn, s));
+        prof_end(PMCIM_K_GATHER, s);
+      }
+      CU(cudaStreamSynchronize(s));
+      vi.clear();
+      vec_before = out->vec_used;
+      max_vn = 0;
+      return PMCIM_OK;
+    };
+    // node flags of the solves that ran
+    auto node_flags = [&](const HostRegion& h, const RegionDev& d, const LevelOut& lo) {
       int& rs = (*root_status)[h.root];
       for (int j = 0; j < h.N; ++j) {
         const int v = lo.node_info[d.node_off + j];
@@ -780,9 +858,11 @@ int run_beyn_levels(Call& c, const std::vector<HostRegion>& top, bool gate_top, 
         }
         if (v & (1 << 30)) rs |= PMCIM_RS_IR_FALLBACK;
       }
-      if (h.depth == 0 && top_ind) (*top_ind)[h.root] = lo.ind[g];
-      if (lo.cand[g]) rs |= PMCIM_RS_CANDIDATE;
-      if (lo.p[g] < 0) continue;  // gated out
+    };
+    // Beyn's results of a disk: split it, or keep its filtered eigenvalues
+    auto beyn_results = [&](const HostRegion& h, const RegionDev& d, const LevelOut& lo, int g) {
+      int& rs = (*root_status)[h.root];
+      if (lo.p[g] < 0) return;  // gated out
       c.st.candidates += 1;
       const int bits = lo.status[g];
       if ((bits & PMCIM_RS_SATURATED) && h.depth < c.opt->max_split_depth) {
@@ -792,7 +872,7 @@ int run_beyn_levels(Call& c, const std::vector<HostRegion>& top, bool gate_top, 
         const int sx[4] = {1, -1, 1, -1}, sy[4] = {1, 1, -1, -1};
         for (int q = 0; q < 4; ++q)
           next.push_back(HostRegion{h.cre + sx[q] * dd, h.cim + sy[q] * dd, rc, h.N, h.depth + 1, h.root, h.prob});
-        continue;
+        return;
       }
       rs |= bits;
       const int n = c.pd[h.prob].n;
@@ -806,19 +886,81 @@ int run_beyn_levels(Call& c, const std::vector<HostRegion>& top, bool gate_top, 
         out->vec_used += (size_t)n;
         max_vn = std::max(max_vn, n);
       }
-    }
-    if (!vi.empty()) {
-      CU(ws.gdst.grow_keep(out->vec_used * sizeof(double2), vec_before * sizeof(double2), s));
-      CU(ws.gitems.ensure(vi.size() * sizeof(VecItem)));
-      CU(cudaMemcpyAsync(ws.gitems.p, vi.data(), vi.size() * sizeof(VecItem), cudaMemcpyHostToDevice, s));
-      for (size_t q0 = 0; q0 < vi.size(); q0 += 65535) {
-        const int cnt = (int)std::min<size_t>(65535, vi.size() - q0);
-        prof_begin(PMCIM_K_GATHER, s);
-        CU(launch_gather_vecs(ws.bvecs.as<double2>(), ws.gdst.as<double2>(), ws.gitems.as<VecItem>() + q0, cnt,
-                              max_vn, s));
-        prof_end(PMCIM_K_GATHER, s);
+    };
+    if (Ni <= 0) {
+      // one N per disk: the level's solves feed the indicator and Beyn
+      LevelOut lo;
+      CHK(run_level(c, level, gate_top, true, &lo));
+      for (int g = 0; g < (int)level.size(); ++g) {
+        const HostRegion& h = level[g];
+        node_flags(h, lo.rd[g], lo);
+        if (h.depth == 0 && top_ind) (*top_ind)[h.root] = lo.ind[g];
+        if (lo.cand[g]) (*root_status)[h.root] |= PMCIM_RS_CANDIDATE;
+        beyn_results(h, lo.rd[g], lo, g);
       }
-      CU(cudaStreamSynchronize(s));
+      CHK(flush_vecs());
+    } else {
+      // two passes (Appendix pmCIMb driver): the indicator on an Ni-node rule,
+      // whose nodes are every (N / Ni)-th node of the disk's rule, then Beyn on the
+      // candidates with the full rule, reusing the indicator pass's solutions.
+      // Disks that the indicator does not gate (depth 0 without gate_top) go
+      // straight to Beyn. Chunks bound the kept solutions.
+      for (size_t q0 = 0; q0 < level.size();) {
+        size_t q1 = q0, bytes = 0;
+        while (q1 < level.size() && q1 - q0 < 65535) {
+          const ProblemDev& P = c.pd[level[q1].prob];
+          const size_t b = (size_t)Ni * P.n * P.l * sizeof(double2);
+          if (q1 > q0 && bytes + b > kKeepBytes) break;
+          bytes += b;
+          ++q1;
+        }
+        std::vector<HostRegion> A;
+        std::vector<size_t> a_of;
+        for (size_t q = q0; q < q1; ++q)
+          if (level[q].depth > 0 || gate_top) {
+            A.push_back(level[q]);
+            A.back().N = Ni;
+            a_of.push_back(q);
+          }
+        LevelOut la;
+        if (!A.empty()) CHK(run_level(c, A, false, false, &la, nullptr, false, nullptr, true));
+        std::vector<HostRegion> B;
+        LevelReuse ru;
+        ru.X = ws.Xkeep.as<double2>();
+        size_t ai = 0;
+        for (size_t q = q0; q < q1; ++q) {
+          const HostRegion& h = level[q];
+          if (ai < a_of.size() && a_of[ai] == q) {
+            const int g = (int)ai++;
+            node_flags(A[g], la.rd[g], la);
+            if (h.depth == 0 && top_ind) (*top_ind)[h.root] = la.ind[g];
+            if (!la.cand[g]) continue;
+            (*root_status)[h.root] |= PMCIM_RS_CANDIDATE;
+            B.push_back(h);
+            ru.src.push_back(la.rd[g].x_off);
+            ru.stride.push_back(h.N / Ni);
+          } else {
+            B.push_back(h);
+            ru.src.push_back(-1);
+            ru.stride.push_back(1);
+          }
+        }
+        if (!B.empty()) {
+          LevelOut lb;
+          CHK(run_level(c, B, false, true, &lb, nullptr, false, &ru, false, true));
+          for (int g = 0; g < (int)B.size(); ++g) {
+            const HostRegion& h = B[g];
+            node_flags(h, lb.rd[g], lb);
+            if (ru.src[g] < 0) {
+              if (h.depth == 0 && top_ind) (*top_ind)[h.root] = lb.ind[g];
+              if (lb.cand[g]) (*root_status)[h.root] |= PMCIM_RS_CANDIDATE;
+            }
+            beyn_results(h, lb.rd[g], lb, g);
+          }
+          CHK(flush_vecs());
+        }
+        q0 = q1;
+      }
     }
     level.swap(next);
   }

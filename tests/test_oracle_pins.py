@@ -368,3 +368,42 @@ def test_indicator_is_zero_when_pf_is_at_rounding_level():
     m = o.moments(w.diagonal_linear(mu), c, r, N, w.probe_block(rng, 10, 2))
     I_exact = np.linalg.norm(1.0 / (1.0 - a ** (N // 2))) / math.sqrt(10)
     assert o.indicator_value(m.pf_N, m.pf_half, m.pf_abs) == pytest.approx(I_exact, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Two-pass schedule (Appendix pmCIMb driver: the indicator on 16 nodes, Beyn on
+# 64 nodes of the candidates).  For T = diag(z - mu) and f with no zero entry,
+# P f|_N ./ P f|_{N/2} has entries (1 + a^{N/2}) / (1 - a^N) = 1 / (1 - a^{N/2}),
+# so the coarse indicator is || 1 / (1 - a^{Ni/2}) ||_2 / sqrt(n) with Ni the
+# indicator's node count (P1's sums).
+# ---------------------------------------------------------------------------
+
+def test_two_pass_schedule_decisions_and_eigenvalues():
+    # 3 x 3 squares of side 1 on [-1.5, 1.5]^2, circumscribed disks, N = 64, indicator on 16 nodes
+    regs = w.grid_regions(-1.5, 1.5, -1.5, 1.5, 3, 3, 64)
+    mu = np.array([-1.0 + 0.9j, -0.8 + 1.1j, 0.1 - 0.05j, 1.05 - 1.0j,    # inside squares
+                   -1.0 - 1.0j + 1.2 * 0.7071 * np.exp(0.3j),                 # |a| = 1.2 from the (-1,-1) disk
+                   3.5 + 0.2j, -0.3 - 3.0j])                                  # outside the grid
+    P = w.diagonal_linear(mu)
+    V = w.probe_block(np.random.default_rng(41), len(mu), 4)
+    Ni, tol = 16, 0.1
+    res2 = o.pmcimb(P, regs, V, indicator_N=Ni)
+    res1 = o.pmcimb(P, regs, V)
+    tops = [rec for rec in res2.records if rec.depth == 0]
+    assert len(tops) == len(regs)
+    coarse_only = 0
+    for rec in tops:
+        a = (mu - rec.c) / rec.r
+        q = 1.0 / (1.0 - a ** (Ni // 2))
+        I_exact = np.linalg.norm(q) / math.sqrt(len(mu))
+        assert rec.candidate == (I_exact > tol)
+        if np.max(np.abs(q)) > 1e-3:
+            assert rec.I == pytest.approx(I_exact, rel=1e-8)
+        fine = np.linalg.norm(1.0 / (1.0 - a ** 32)) / math.sqrt(len(mu))
+        coarse_only += int(rec.candidate and not fine > tol)
+    assert coarse_only >= 1   # the |a| = 1.2 pole: a candidate on 16 nodes, not on 64
+    inside = mu[(np.abs(mu.real) < 1.5) & (np.abs(mu.imag) < 1.5)]
+    for lam in (res2.lam, res1.lam):
+        assert len(lam) == len(inside)
+        k, err = _match(inside, lam)
+        assert k == len(inside) and err < 1e-10

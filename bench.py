@@ -258,6 +258,13 @@ def run_batched(args, world, rank, local):
     forms = [("auto", pmcim.PREC_AUTO), ("fp32ir", pmcim.PREC_FP32_IR), ("unbatched_auto", pmcim.PREC_AUTO)]
     if args.batched_fp64:
         forms.append(("fp64", pmcim.PREC_FP64))
+    # the autotuner measures each (n bucket, l, dense terms) on first use: let it do so
+    # for every timed problem before timing (one disk each)
+    o_auto = pmcim.options(stream=stream.cuda_stream, precision=pmcim.PREC_AUTO)
+    for k in steps:
+        hs, W = prepared[k]
+        pmcim.batch_solve(hs, [x.regions[:1] for x in W], [x.V for x in W], opt=o_auto)
+    torch.cuda.synchronize()
     t_start = time.perf_counter()
     for name, prec in forms:
         if time.perf_counter() - t_start > args.time_budget:
@@ -293,12 +300,12 @@ def run_batched(args, world, rank, local):
         res[name] = {"solves_per_s": sum_over_ranks(float(agg["solves"]), world) / (t_max / 1e3),
                      "ms_per_step": t_max / args.steps, "solves": agg["solves"], "splits": agg["splits"],
                      "graphs": agg["graphs"], "tuned_fp64": agg["tuned_fp64"], "tuned_mixed": agg["tuned_mixed"],
-                     "ir_fallbacks": agg["ir_fallbacks"]}
+                     "tuned_tc": agg.get("tuned_tc", 0), "ir_fallbacks": agg["ir_fallbacks"]}
     if rank == 0:
         ns = [x.problem.n for k in steps if k >= 0 for x in prepared[k][1]]
         print(json.dumps({"metric": "solves/s, batched quadratic NEPs", "value": res["auto"]["solves_per_s"],
                           "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                          "higher_is_better": True, "scaling": "weak", "dtype": "f64 (auto: FP64 or FP32+FP64 IR)",
+                          "higher_is_better": True, "scaling": "weak", "dtype": "auto: per problem FP64, FP32 LU + FP64 IR or tensor-core LU + FP64 IR",
                           "data": "synthetic",
                           "config": {"workload": "batched quadratic NEPs, seeds 1..512, %d problems per step" % per,
                                      "n_range": [min(ns), max(ns)], "l": 8},
@@ -354,7 +361,10 @@ def run_screen(args, world, rank, local):
     h = pmcim.Problem(W.problem.n, W.problem.terms)
     stream = torch.cuda.current_stream()
     out = {}
-    for name, kw in (("plain", {}), ("screened", {"screen_params": params, "screen_threshold": thr})):
+    legs = (("plain", {}), ("screened", {"screen_params": params, "screen_threshold": thr}),
+            ("two_pass", {"indicator_N": args.indicator_n}),
+            ("two_pass_screened", {"screen_params": params, "screen_threshold": thr, "indicator_N": args.indicator_n}))
+    for name, kw in legs:
         o = pmcim.options(stream=stream.cuda_stream, precision=pmcim.PREC_FP32_IR, **kw)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -394,20 +404,41 @@ def run_screen(args, world, rank, local):
             "candidates_plain": int(plain_cand.sum()), "eigenvalues_plain": len(a), "eigenvalues_screened": len(b),
             "same_eigenvalues": same,
             "solves_plain": out["plain"]["stats"]["solves"],
-            "solves_screened": out["screened"]["stats"]["solves"] + out["screened"]["stats"]["screen_solves"]}))
+            "solves_screened": out["screened"]["stats"]["solves"] + out["screened"]["stats"]["screen_solves"],
+            "two_pass": {name: {"seconds": out[name]["seconds"],
+                                "solves": out[name]["stats"]["solves"] + out[name]["stats"]["screen_solves"],
+                                "speedup_vs_plain": out["plain"]["seconds"] / out[name]["seconds"],
+                                "same_eigenvalues_as_plain": _same_lams(out["plain"]["lam"], out[name]["lam"])}
+                         for name in ("two_pass", "two_pass_screened")},
+            "indicator_N": args.indicator_n}))
     return 0
+
+
+def _same_lams(a, b, tol=1e-10):
+    """Both eigenvalue lists hold the same values (relative tol), matched one to one."""
+    a, b = np.asarray(a), np.asarray(b)
+    if len(a) != len(b):
+        return False
+    if len(a) == 0:
+        return True
+    from scipy.optimize import linear_sum_assignment
+    ri, ci = linear_sum_assignment(np.abs(a[:, None] - b[None, :]))
+    return bool(np.max(np.abs(a[ri] - b[ci]) / np.maximum(1.0, np.abs(a[ri]))) <= tol)
 
 
 def run_full(args, P, W, opt, opt_mixed, world, rank, local):
     """Time to all eigenvalues: one pmCIMb pass over the whole grid per form
-    (opt_mixed: the tensor-core precision form)."""
+    (opt_mixed: the FP32-LU precision form), each also with the two-pass schedule."""
     import torch
     from paper_2312_13117_gb300 import pmcim
     R = len(W.regions)
     mine = [W.regions[g] for g in range(rank, R, world)]
     out = {}
     lams = {}
-    for name, o in (("precision_form", opt_mixed), ("fp64", opt)):
+    o2 = pmcim.options(stream=opt_mixed.cuda_stream, precision=opt_mixed.precision, indicator_N=args.indicator_n)
+    f2 = pmcim.options(stream=opt.cuda_stream, precision=opt.precision, indicator_N=args.indicator_n)
+    for name, o in (("precision_form", opt_mixed), ("precision_form_two_pass", o2), ("fp64", opt),
+                    ("fp64_two_pass", f2)):
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
@@ -427,7 +458,12 @@ def run_full(args, P, W, opt, opt_mixed, world, rank, local):
         print(json.dumps({"metric": "full pmCIMb time (all %d disks)" % R, "unit": "s", "n_gpus": world,
                           "workload": "delay NEP n=1024, l=16, N=64, Omega=[-3,1]x[-6,6] 16x48",
                           "forms": out, "max_rel_lambda_diff_fp64_vs_precision_form": err,
-                          "speedup": out["fp64"]["seconds"] / out["precision_form"]["seconds"]}))
+                          "speedup": out["fp64"]["seconds"] / out["precision_form"]["seconds"],
+                          "indicator_N": args.indicator_n,
+                          "speedup_two_pass_precision_vs_fp64": out["fp64"]["seconds"] /
+                          out["precision_form_two_pass"]["seconds"],
+                          "two_pass_same_eigenvalues": {k: _same_lams(lams["fp64"], lams[k])
+                                                        for k in ("precision_form_two_pass", "fp64_two_pass")}}))
     P.close()
     return 0
 
@@ -453,6 +489,8 @@ def main():
     ap.add_argument("--problems-per-step", type=int, default=4)
     ap.add_argument("--batched-fp64", action="store_true", help="also time the batched workload in plain FP64")
     ap.add_argument("--time-budget", type=float, default=240.0, help="seconds before remaining legs are skipped")
+    ap.add_argument("--indicator-n", type=int, default=16,
+                    help="coarse indicator rule of the two-pass legs (--full, --workload screen)")
     ap.add_argument("--full", action="store_true",
                     help="time pmCIMb over all 768 disks (time to all eigenvalues), FP64 and precision form")
     args = ap.parse_args()

@@ -197,6 +197,23 @@ int pmcim_beyn(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim
 int pmcim_verify(pmcim_problem p, const pmcim_options* opt, int32_t m, const double* lambda,
                  double* sigma_min, uint8_t* accept);
 
+/* pmCIMa (Sec. 3.1): the spectral indicator alone, level by level. Each level
+   computes the indicator (Eq. 3.1, the disk's N nodes, probe column V, n x 1)
+   of every disk; a candidate (I > tol_ind) is quadrisected into four disks of
+   half the radius centred at the centres of its square's quarters, until the
+   disk's level count L = ceil(log2(r / tol_eps)) + 2 (the Appendix listing's
+   count; the last disks' radius is at most tol_eps / 2). The last level's
+   candidate centres approximate the eigenvalues (step 1.c); centres closer than
+   tol_eps are merged into their mean (the remark after the algorithm). Step 2:
+   sigma_min of T(lambda) and its unit right singular vector, by FP64 LU and
+   inverse iteration as in pmcim_verify. Outputs: lambda (cap complex, sorted by
+   real then imaginary part), vecs (n x cap, may be NULL), sigma_min (cap, may
+   be NULL), *count; stats may be NULL. ECAPACITY when more than cap values
+   (*count holds the number), or when a level exceeds 2^20 disks. */
+int pmcim_pmcima(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim_region* reg,
+                 const double* V, double tol_eps, int32_t cap, double* lambda, double* vecs,
+                 double* sigma_min, int32_t* count, pmcim_stats* stats);
+
 /* Whole pmCIMb (steps 1-3) over R disks with one N per disk for both the
    indicator and the moments: one LU per node serves both. Outputs the verified
    eigenvalues (sorted by real, then imaginary part) with eigenvectors (may be

@@ -45,7 +45,7 @@ __all__ = [
     "MONOMIAL", "EXP_NEG", "scalar_f", "assemble_T", "nodes_weights", "solve_nodes",
     "Moments", "moments", "indicator_value", "indicator", "BeynResult", "beyn_extract",
     "square_filter", "normalise_vectors", "sigma_min", "verify", "split4",
-    "pmcimb", "PmcimbResult",
+    "pmcimb", "PmcimbResult", "pmcima", "PmcimaResult", "pmcima_levels", "merge_centres",
 ]
 
 MONOMIAL = 0
@@ -305,3 +305,81 @@ def pmcimb(problem, regions: Sequence, V: np.ndarray, tol_ind: float = 0.1,
     order = np.lexsort((lam.imag, lam.real))
     lam, vecs, sig, acc = lam[order], vecs[:, order], sig[order], acc[order]
     return PmcimbResult(lam[acc], vecs[:, acc], sig[acc], lam, sig, acc, records)
+
+
+# ---------------------------------------------------------------------------
+# pmCIMa (Sec. 3.1): the indicator alone, level by level, then one linear
+# eigenproblem per value
+# ---------------------------------------------------------------------------
+
+def pmcima_levels(r: float, tol_eps: float) -> int:
+    """Levels of pmCIMa for a disk of radius r: ceil(log2(r / tol_eps)) + 2.
+
+    Step 1.a gives ceil(log2(r / tol_eps)); the Appendix listing adds 2, which makes
+    the last disks' radius r / 2^(L-1) at most tol_eps / 2, so that neighbouring
+    final squares around one eigenvalue have centres within tol_eps of each other
+    and the merge of the remark after the algorithm joins them. Taken as written in
+    the listing."""
+    return max(1, int(math.ceil(math.log2(r / tol_eps))) + 2)
+
+
+def merge_centres(z: np.ndarray, tol_eps: float) -> np.ndarray:
+    """The merge of the remark after pmCIMa: in order, each not yet merged centre
+    takes every not yet merged centre within tol_eps of it (itself included, once)
+    and is replaced by their mean."""
+    z = np.asarray(z, dtype=np.complex128)
+    used = np.zeros(len(z), dtype=bool)
+    out = []
+    for i in range(len(z)):
+        if used[i]:
+            continue
+        grp = [j for j in range(len(z)) if not used[j] and abs(z[i] - z[j]) < tol_eps]
+        used[grp] = True
+        out.append(np.mean(z[grp]))
+    return np.array(out, dtype=np.complex128)
+
+
+@dataclasses.dataclass
+class PmcimaResult:
+    lam: np.ndarray      # merged approximate eigenvalues, sorted by (Re, Im)
+    vecs: np.ndarray     # n x m: right singular vector of T(lam) for sigma_min (unit norm)
+    sigma: np.ndarray    # sigma_min(T(lam))
+    centres: np.ndarray  # the last level's candidate centres, before the merge
+    regions: int         # indicator evaluations over all levels
+
+
+def pmcima(problem, regions: Sequence, V: np.ndarray, tol_ind: float = 0.1,
+           tol_eps: float = 1e-6) -> PmcimaResult:
+    """pmCIMa. Step 1: each level computes the indicator (Eq. 3.1, the disk's N
+    nodes, probe column f = V[:, 0]) of every disk; candidates (I > tol_ind) are
+    quadrisected (split4) until the disk's level count is reached, and the last
+    level's candidate centres approximate the eigenvalues (1.c), merged as in the
+    remark. Step 2: for each value, the eigenvector of T(lambda) is taken as the
+    right singular vector of its smallest singular value (the reading used for
+    verification in pmCIMb)."""
+    f = np.asarray(V)[:, :1]
+    centres = []
+    evaluated = 0
+    level = [(complex(g.c), float(g.r), int(g.N), pmcima_levels(float(g.r), tol_eps), 0) for g in regions]
+    while level:
+        nxt = []
+        for (c, r, N, L, depth) in level:
+            m = moments(problem, c, r, N, f)
+            evaluated += 1
+            if indicator_value(m.pf_N, m.pf_half, m.pf_abs) <= tol_ind:
+                continue
+            if depth + 1 < L:
+                nxt += [(cc, rr, N, L, depth + 1) for (cc, rr) in split4(c, r)]
+            else:
+                centres.append(c)
+        level = nxt
+    centres = np.array(centres, dtype=np.complex128)
+    lam = merge_centres(centres, tol_eps)
+    lam = lam[np.lexsort((lam.imag, lam.real))] if len(lam) else lam
+    vecs = np.zeros((problem.n, len(lam)), dtype=np.complex128)
+    sig = np.zeros(len(lam))
+    for i, z in enumerate(lam):
+        _, s, vh = np.linalg.svd(assemble_T(problem, z))
+        sig[i] = s[-1]
+        vecs[:, i] = vh[-1].conj()
+    return PmcimaResult(lam, vecs, sig, centres, evaluated)

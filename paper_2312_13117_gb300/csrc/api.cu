@@ -101,6 +101,8 @@ constexpr size_t kWaveBytes = size_t(16) << 30;
 constexpr size_t kSlotBytes = size_t(24) << 30;
 // indicator-pass solutions kept for reuse by the two-pass schedule, per chunk of disks
 constexpr size_t kKeepBytes = size_t(8) << 30;
+// largest pmCIMa level (disks); beyond it the indicator is marking noise
+constexpr size_t kMaxPmcimaRegions = size_t(1) << 20;
 // Refinement stops when the estimated remaining error of X (max norm) is below
 // this fraction of |X|: 1e-11 keeps Beyn's eigenvalues within about 1e-14 of
 // the FP64 ones on the delay workload (simulated FP32 LU + FP64 refinement).
@@ -209,6 +211,7 @@ struct Workspace {
   DevBuf vlam, vprob, voff, vsig, vacc, vwork, vvec, vpiv;
   DevBuf gitems, gdst, gperm;
   DevBuf Xkeep, citems;  // two-pass schedule: indicator-pass solutions, copy list
+  DevBuf vout;           // verification's singular vectors (pmCIMa)
   DevBuf ind3, feats, sprob, sparams, sscratch;
   // the library's own stream: graphs cannot be captured on the legacy default stream
   cudaStream_t stream = nullptr;
@@ -222,7 +225,7 @@ struct Workspace {
                    &phase, &C0, &C1, &pf_half, &pf_abs, &ind, &pf_norm, &pf_scale, &cand, &bwork, &bsigma,
                    &bp, &blam, &bvecs, &bkept, &bstatus, &vlam, &vprob, &voff, &vsig, &vacc, &vwork,
                    &vvec, &vpiv, &gitems, &gdst, &gperm, &ind3, &feats, &sprob, &sparams, &sscratch, &Xkeep,
-                   &citems};
+                   &citems, &vout};
     for (DevBuf* x : b) x->release();
   }
 };
@@ -969,7 +972,7 @@ int run_beyn_levels(Call& c, const std::vector<HostRegion>& top, bool gate_top, 
 
 // sigma_min (full) for the given values; slots sized for the largest n among them.
 int run_verify(Call& c, const std::vector<double2>& lam, const std::vector<int>& prob, std::vector<double>* sig,
-               std::vector<uint8_t>* acc) {
+               std::vector<uint8_t>* acc, std::vector<double2>* vecs = nullptr, int* vec_stride = nullptr) {
   Workspace& ws = *c.ws;
   cudaStream_t s = c.s;
   const int m = (int)lam.size();
@@ -1004,11 +1007,20 @@ int run_verify(Call& c, const std::vector<double2>& lam, const std::vector<int>&
   va.piv = ws.vpiv.as<int32_t>();
   va.slots = slots;
   va.max_n = max_n;
+  if (vecs) {
+    CU(ws.vout.ensure((size_t)m * max_n * sizeof(double2)));
+    va.vec_out = ws.vout.as<double2>();
+  }
   prof_begin(PMCIM_K_VERIFY, s);
   CU(launch_verify_fp64(va, s));
   prof_end(PMCIM_K_VERIFY, s);
   CU(cudaMemcpyAsync(sig->data(), ws.vsig.p, m * sizeof(double), cudaMemcpyDeviceToHost, s));
   CU(cudaMemcpyAsync(acc->data(), ws.vacc.p, m, cudaMemcpyDeviceToHost, s));
+  if (vecs) {
+    vecs->resize((size_t)m * max_n);
+    *vec_stride = max_n;
+    CU(cudaMemcpyAsync(vecs->data(), ws.vout.p, (size_t)m * max_n * sizeof(double2), cudaMemcpyDeviceToHost, s));
+  }
   CU(cudaStreamSynchronize(s));
   return PMCIM_OK;
 }
@@ -1388,6 +1400,87 @@ int pmcim_verify(pmcim_problem p, const pmcim_options* opt, int32_t m, const dou
   CHK(run_verify(c, lam, std::vector<int>(m, 0), &sig, &acc));
   CHK(copy_out(sigma_min, sig.data(), m * sizeof(double)));
   if (accept) CHK(copy_out(accept, acc.data(), m));
+  return PMCIM_OK;
+}
+
+int pmcim_pmcima(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim_region* reg, const double* V,
+                 double tol_eps, int32_t cap, double* lambda, double* vecs, double* sigma_min, int32_t* count,
+                 pmcim_stats* stats) {
+  if (!p) return fail(PMCIM_EINVAL, "problem is NULL");
+  CHK(check_options(opt));
+  CHK(check_regions(R, reg, 1));
+  if (!(tol_eps > 0.0) || !std::isfinite(tol_eps)) return fail(PMCIM_EINVAL, "tol_eps must be positive");
+  if (!count || cap < 0 || (cap > 0 && !lambda)) return fail(PMCIM_EINVAL, "bad output arguments");
+  Call c;
+  CHK(single_call(c, p, opt, 1, V));
+  CHK(tune_forms(c));
+  // step 1: levels of indicators; candidates are quadrisected until the disk's level count
+  std::vector<int> levels(R);
+  for (int g = 0; g < R; ++g) levels[g] = std::max(1, (int)std::ceil(std::log2(reg[g].r / tol_eps)) + 2);
+  std::vector<HostRegion> level = to_host_regions(R, reg, 0);
+  std::vector<double2> centres;
+  while (!level.empty()) {
+    if (level.size() > kMaxPmcimaRegions)
+      return fail(PMCIM_ECAPACITY, "pmCIMa level of %zu disks: the indicator marks too many disks",
+                  level.size());
+    LevelOut lo;
+    CHK(run_level(c, level, false, false, &lo));
+    std::vector<HostRegion> next;
+    for (size_t g = 0; g < level.size(); ++g) {
+      if (!lo.cand[g]) continue;
+      const HostRegion& h = level[g];
+      c.st.candidates += 1;
+      if (h.depth + 1 < levels[h.root]) {
+        const double rc = h.r / 2.0, dd = rc / std::sqrt(2.0);
+        const int sx[4] = {1, -1, 1, -1}, sy[4] = {1, 1, -1, -1};
+        for (int q = 0; q < 4; ++q)
+          next.push_back(HostRegion{h.cre + sx[q] * dd, h.cim + sy[q] * dd, rc, h.N, h.depth + 1, h.root, h.prob});
+      } else {
+        centres.push_back(make_double2(h.cre, h.cim));
+      }
+    }
+    level.swap(next);
+  }
+  // merge: in order, each free centre takes the free centres within tol_eps (itself once), mean
+  std::vector<double2> lam;
+  std::vector<uint8_t> used(centres.size(), 0);
+  for (size_t i = 0; i < centres.size(); ++i) {
+    if (used[i]) continue;
+    double sr = 0.0, si = 0.0;
+    int k = 0;
+    for (size_t j = 0; j < centres.size(); ++j) {
+      if (used[j] || std::hypot(centres[i].x - centres[j].x, centres[i].y - centres[j].y) >= tol_eps) continue;
+      used[j] = 1;
+      sr += centres[j].x;
+      si += centres[j].y;
+      ++k;
+    }
+    lam.push_back(make_double2(sr / k, si / k));
+  }
+  std::sort(lam.begin(), lam.end(), [](const double2& a, const double2& b) {
+    return a.x != b.x ? a.x < b.x : a.y < b.y;
+  });
+  const int m = (int)lam.size();
+  *count = m;
+  if (stats) *stats = c.st;
+  if (m > cap) return fail(PMCIM_ECAPACITY, "%d values, capacity %d", m, cap);
+  // step 2: sigma_min of T(lambda) and its right singular vector
+  std::vector<double> sig;
+  std::vector<uint8_t> acc;
+  std::vector<double2> vv;
+  int stride = 0;
+  CHK(run_verify(c, lam, std::vector<int>(m, 0), &sig, &acc, vecs ? &vv : nullptr, vecs ? &stride : nullptr));
+  if (m > 0) {
+    CHK(copy_out(lambda, lam.data(), m * sizeof(double2)));
+    if (sigma_min) CHK(copy_out(sigma_min, sig.data(), m * sizeof(double)));
+    if (vecs) {
+      std::vector<double2> packed((size_t)m * p->n);
+      for (int i = 0; i < m; ++i)
+        std::memcpy(packed.data() + (size_t)i * p->n, vv.data() + (size_t)i * stride, p->n * sizeof(double2));
+      CHK(copy_out(vecs, packed.data(), packed.size() * sizeof(double2)));
+    }
+  }
+  if (stats) *stats = c.st;
   return PMCIM_OK;
 }
 

@@ -238,6 +238,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_verify_fp64(ValueArgs a) {
       double thr = a.tol_verify * fmax(1.0, fro / sqrt((double)n));
       a.accept[it] = (smin <= thr) ? 1 : 0;
     }
+    if (a.vec_out)  // the inverse iteration's last unit vector (zero when the LU met an exact zero pivot)
+      for (int i = tid; i < n; i += THREADS)
+        a.vec_out[(size_t)it * a.max_n + i] = info == 0 ? x[i] : make_double2(0.0, 0.0);
     __syncthreads();
   }
 }

@@ -271,6 +271,7 @@ struct ValueArgs {
   int32_t* piv;             // verify: slots * max_n
   int slots;
   int max_n;
+  double2* vec_out;         // verify: NULL, or m * max_n: the unit right singular vector for sigma_min
 };
 cudaError_t launch_certify(const ValueArgs& a, cudaStream_t s);
 cudaError_t launch_verify_fp64(const ValueArgs& a, cudaStream_t s);

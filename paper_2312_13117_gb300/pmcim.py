@@ -28,7 +28,7 @@ EXPORTS = ["pmcim_default_options", "pmcim_problem_create", "pmcim_problem_destr
            "pmcim_indicator", "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_status_string",
            "pmcim_last_error", "pmcim_profile_enable", "pmcim_profile_reset", "pmcim_profile_read",
            "pmcim_solve_points_noalloc", "pmcim_batch_solve", "pmcim_screen_features", "pmcim_screen_train",
-           "pmcim_screen_apply", "pmcim_screen_gradient"]
+           "pmcim_screen_apply", "pmcim_screen_gradient", "pmcim_pmcima"]
 
 KERNELS = ["factor_fp64", "reduce", "indicator", "beyn", "verify", "gather", "factor_fp32", "screen"]
 SCREEN_PARAMS = 4481
@@ -115,9 +115,12 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pmcim_screen_gradient.argtypes = [I32, F, VP, D, F, F, VP, VP]
     lib.pmcim_batch_solve.argtypes = [I32, C.POINTER(pmcim_batch_item), C.POINTER(pmcim_options), I32, VP, VP, VP,
                                       VP, VP, C.POINTER(pmcim_stats)]
+    lib.pmcim_pmcima.argtypes = [P, C.POINTER(pmcim_options), I32, C.POINTER(pmcim_region), VP, D, I32, VP, VP, VP,
+                                 VP, C.POINTER(pmcim_stats)]
     for name in ("pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments", "pmcim_indicator",
                  "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_solve_points_noalloc", "pmcim_batch_solve",
-                 "pmcim_screen_features", "pmcim_screen_train", "pmcim_screen_apply", "pmcim_screen_gradient"):
+                 "pmcim_screen_features", "pmcim_screen_train", "pmcim_screen_apply", "pmcim_screen_gradient",
+                 "pmcim_pmcima"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -393,6 +396,29 @@ class Problem:
         opt = opt or options()
         _check(lib.pmcim_verify(self.handle, C.byref(opt), m, _ptr(lam), _ptr(sig), _ptr(acc)), "pmcim_verify")
         return sig[:m], acc[:m].astype(bool)
+
+    def pmcima(self, regions, V, tol_eps=1e-6, cap=None, opt=None, want_vecs=True):
+        """pmCIMa with probe column V[:, 0]: returns dict(lam, vecs, sigma_min, stats)."""
+        lib = load()
+        f = _colmajor_c128(np.asarray(V).reshape(self.n, -1)[:, :1])
+        R = len(regions)
+        cap = cap if cap is not None else max(64, 8 * R)
+        while True:
+            lam = np.zeros(cap, np.complex128)
+            vecs = np.zeros((cap, self.n), np.complex128) if want_vecs else None
+            sig = np.zeros(cap)
+            cnt = np.zeros(1, np.int32)
+            st = pmcim_stats()
+            o = opt or options()
+            rc = lib.pmcim_pmcima(self.handle, C.byref(o), R, regions_array(regions), _ptr(f), float(tol_eps), cap,
+                                  _ptr(lam), _ptr(vecs), _ptr(sig), _ptr(cnt), C.byref(st))
+            if rc == -5 and int(cnt[0]) > cap:
+                cap = int(cnt[0])
+                continue
+            _check(rc, "pmcim_pmcima", cnt)
+            k = int(cnt[0])
+            return dict(lam=lam[:k], vecs=(vecs[:k].T if want_vecs else None), sigma_min=sig[:k],
+                        stats=st.as_dict())
 
     def solve(self, regions, V, cap=None, opt=None, want_vecs=True):
         """Whole pmCIMb: returns dict(lam, vecs, sigma_min, region_of, ind, status, stats)."""

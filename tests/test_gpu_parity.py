@@ -547,3 +547,34 @@ def test_two_pass_rejects_bad_indicator_rule(pm):
     with pytest.raises(RuntimeError):
         P.solve(W.regions[:2], W.V, opt=pm.options(indicator_N=7))    # odd
     P.close()
+
+
+# ---------------------------------------------------------------------------
+# pmCIMa: levels of indicators with quadrisection, merge, sigma_min vectors
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32ir"])
+def test_pmcima_matches_oracle(pm, precision):
+    """Prescribed spectrum (A = Q diag(mu) Q^-1): the GPU's merged values equal the oracle's
+    (same decisions at every level, same merge) to rounding, are within tol_eps of the
+    eigenvalues inside Omega, and come with unit vectors v with ||T(lambda) v|| = sigma_min."""
+    mu = np.array([0.12 + 0.31j, -0.27 - 0.05j, 0.33 - 0.38j, 0.9 + 0.9j, -0.8 + 0.6j, 1.3 - 0.2j])
+    prob, _ = w.similarity_linear(mu, seed=4)
+    V = w.probe_block(np.random.default_rng(3), len(mu), 2)
+    regs = w.grid_regions(-0.5, 0.5, -0.5, 0.5, 2, 2, 16)
+    prec = {"fp64": pm.PREC_FP64, "fp32ir": pm.PREC_FP32_IR}[precision]
+    P = pm.Problem(prob.n, prob.terms)
+    res = P.pmcima(regs, V, tol_eps=1e-6, opt=pm.options(precision=prec))
+    ref = o.pmcima(prob, regs, V, tol_eps=1e-6)
+    assert len(res["lam"]) == len(ref.lam) == 3
+    assert np.max(np.abs(res["lam"] - ref.lam)) <= 1e-12
+    inside = mu[(np.abs(mu.real) < 0.5) & (np.abs(mu.imag) < 0.5)]
+    assert _match_lam(res["lam"], inside) < 1e-6
+    for i, lam in enumerate(res["lam"]):
+        v = res["vecs"][:, i]
+        T = o.assemble_T(prob, lam)
+        assert abs(np.linalg.norm(v) - 1.0) < 1e-10
+        assert np.linalg.norm(T @ v) == pytest.approx(res["sigma_min"][i], rel=1e-6)
+        assert res["sigma_min"][i] == pytest.approx(ref.sigma[i], rel=1e-6)
+    assert res["stats"]["solves"] == 16 * ref.regions
+    P.close()

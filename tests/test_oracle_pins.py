@@ -407,3 +407,38 @@ def test_two_pass_schedule_decisions_and_eigenvalues():
         assert len(lam) == len(inside)
         k, err = _match(inside, lam)
         assert k == len(inside) and err < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# pmCIMa (Sec. 3.1): T(z) = A - zI with a prescribed spectrum (A = Q diag(mu) Q^-1, so
+# every component of P f carries each pole's residue). The merged last-level centres
+# must be the eigenvalues inside Omega, one each, within tol_eps; the vectors are unit
+# null vectors of T(lambda) to sigma_min.
+# ---------------------------------------------------------------------------
+
+def test_pmcima_finds_prescribed_eigenvalues():
+    mu = np.array([0.12 + 0.31j, -0.27 - 0.05j, 0.33 - 0.38j, 0.9 + 0.9j, -0.8 + 0.6j, 1.3 - 0.2j])
+    P, _ = w.similarity_linear(mu, seed=4)
+    V = w.probe_block(np.random.default_rng(3), len(mu), 2)
+    regs = w.grid_regions(-0.5, 0.5, -0.5, 0.5, 2, 2, 16)
+    tol_eps = 1e-6
+    L = o.pmcima_levels(regs[0].r, tol_eps)
+    assert regs[0].r / 2 ** (L - 1) <= tol_eps / 2      # the last disks are below the merge radius
+    res = o.pmcima(P, regs, V, tol_eps=tol_eps)
+    inside = mu[(np.abs(mu.real) < 0.5) & (np.abs(mu.imag) < 0.5)]
+    assert len(res.lam) == len(inside) == 3
+    k, err = _match(inside, res.lam)
+    assert k == 3 and err < tol_eps
+    T = [o.assemble_T(P, z) for z in res.lam]
+    for i in range(len(res.lam)):
+        v = res.vecs[:, i]
+        assert abs(np.linalg.norm(v) - 1.0) < 1e-12
+        assert np.linalg.norm(T[i] @ v) == pytest.approx(res.sigma[i], rel=1e-6)
+        assert res.sigma[i] < 10 * tol_eps * np.linalg.norm(T[i], 2)
+
+
+def test_merge_centres_groups_within_tol():
+    z = np.array([0.0, 0.4e-6, 0.9e-6, 5e-6, 5.3e-6, 1.0])
+    m = o.merge_centres(z, 1e-6)
+    # the first centre takes the two within 1e-6 of it; the next free one takes its neighbour
+    assert np.allclose(m, [np.mean(z[:3]), np.mean(z[3:5]), 1.0], atol=1e-15)

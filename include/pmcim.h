@@ -97,7 +97,12 @@ typedef struct {
   int32_t precision;       /* PMCIM_PREC_*                                             */
   int32_t max_ir_sweeps;   /* refinement sweeps for reduced precision (default 3)      */
   int32_t max_split_depth; /* splits of saturated disks (default 8)                    */
-  int32_t reserved;
+  /* moment pairs of Beyn's step (default 1, Eq. 2.8 on C0 and C1). K > 1
+     (at most 8, K l <= 64): the block Hankel matrices of the 2K moments
+     M_p = sum_j w_j ((z_j - c)/r)^p X_j (Beyn's higher moments) take C0's and
+     C1's places, so a disk holds up to K l eigenvalues before it is saturated
+     and split. */
+  int32_t beyn_K;
   void* cuda_stream;       /* cudaStream_t the call is ordered after; NULL = default   */
   /* learned screen (pmcim_solve / pmcim_batch_solve): NULL = off; else the
      PMCIM_SCREEN_PARAMS trained parameters (host or device). Every disk first

@@ -45,7 +45,7 @@ __all__ = [
     "MONOMIAL", "EXP_NEG", "scalar_f", "assemble_T", "nodes_weights", "solve_nodes",
     "Moments", "moments", "indicator_value", "indicator", "BeynResult", "beyn_extract",
     "square_filter", "normalise_vectors", "sigma_min", "verify", "split4",
-    "pmcimb", "PmcimbResult", "pmcima", "PmcimaResult", "pmcima_levels", "merge_centres",
+    "hankel_moments", "beyn_extract_hankel", "pmcimb", "PmcimbResult", "pmcima", "PmcimaResult", "pmcima_levels", "merge_centres",
 ]
 
 MONOMIAL = 0
@@ -190,6 +190,42 @@ def beyn_extract(C0: np.ndarray, C1: np.ndarray, tol_svd: float = 1e-6) -> BeynR
     return BeynResult(s, p, saturated, lam, normalise_vectors(V0 @ S))
 
 
+def hankel_moments(problem, c: complex, r: float, N: int, V: np.ndarray, K: int):
+    """Scaled moments M_p = sum_j w_j ((z_j - c)/r)^p X_j, p = 0..2K-1, of one disk.
+
+    The higher moments of Beyn's method (the pointer to Beyn's Remark 3.5 in
+    Sec. 2.2) in the variable (z - c)/r, whose powers on the nodes are the unit
+    phases e^{i p theta_j}: the contour integrals of z^p T^{-1} V would grow like
+    |c|^p instead."""
+    z, w = nodes_weights(c, r, N)
+    X = solve_nodes(problem, z, V)
+    zeta = np.exp(1j * 2.0 * np.pi * np.arange(N) / N)
+    return [sum(w[j] * zeta[j] ** p * X[j] for j in range(N)) for p in range(2 * K)]
+
+
+def beyn_extract_hankel(M, c: complex, r: float, tol_svd: float = 1e-6) -> BeynResult:
+    """Beyn's extraction from the block Hankel matrices of the scaled moments.
+
+    B0 = [M_{i+j}] and B1 = [M_{i+j+1}] (i, j < K; K n x K l). SVD B0 = V Sigma W^H,
+    keep sigma > tol_svd, D = V0^H B1 W0 Sigma0^{-1}, eig(D) = mu, lambda = c + r mu.
+    B0's left factor has block rows v, v mu, ..., v mu^{K-1}, so an eigenvector is
+    the first n-block of V0 s. With K = 1 this is Eq. 2.8 in the variable (z - c)/r."""
+    K = len(M) // 2
+    n, l = M[0].shape
+    B0 = np.block([[M[i + j] for j in range(K)] for i in range(K)])
+    B1 = np.block([[M[i + j + 1] for j in range(K)] for i in range(K)])
+    Vs, s, Wh = np.linalg.svd(B0, full_matrices=False)
+    p = int(np.sum(s > tol_svd))
+    saturated = p >= min(K * n, K * l)
+    if p == 0:
+        return BeynResult(s, 0, False, np.zeros(0, np.complex128), np.zeros((n, 0), np.complex128))
+    V0 = Vs[:, :p]
+    W0 = Wh.conj().T[:, :p]
+    D = V0.conj().T @ B1 @ W0 @ np.diag(1.0 / s[:p])
+    mu, S = np.linalg.eig(D)
+    return BeynResult(s, p, saturated, c + r * mu, normalise_vectors((V0 @ S)[:n]))
+
+
 def square_filter(lam: np.ndarray, c: complex, r: float) -> np.ndarray:
     """Step 2.f: keep lambda inside the square inscribed in the disk (half-open)."""
     h = r / math.sqrt(2.0)
@@ -259,7 +295,7 @@ class PmcimbResult:
 
 def pmcimb(problem, regions: Sequence, V: np.ndarray, tol_ind: float = 0.1,
            tol_svd: float = 1e-6, tol_verify: float = 1e-6, max_depth: int = 8,
-           indicator_N: int = 0) -> PmcimbResult:
+           indicator_N: int = 0, beyn_K: int = 1) -> PmcimbResult:
     """pmCIMb steps 1-3 over the given disks, with saturated disks split and re-run.
 
     indicator_N = 0: one N per disk serves both the indicator and Beyn's moments.
@@ -268,6 +304,9 @@ def pmcimb(problem, regions: Sequence, V: np.ndarray, tol_ind: float = 0.1,
     screens each disk with the indicator on an indicator_N-node rule, step 2 runs
     Beyn with the disk's N on the candidates. Split children go through both steps
     again. Each disk's N must be a multiple of indicator_N.
+    beyn_K > 1: Beyn's step uses the block Hankel matrices of 2 beyn_K scaled
+    moments (beyn_extract_hankel); a disk is saturated, and split, only when
+    p reaches min(K n, K l).
     """
     n = problem.n
     records: List[RegionRecord] = []
@@ -287,7 +326,10 @@ def pmcimb(problem, regions: Sequence, V: np.ndarray, tol_ind: float = 0.1,
                 I = indicator_value(m.pf_N, m.pf_half, m.pf_abs)
             rec = RegionRecord(c, r, N, depth, I, I > tol_ind)
             if rec.candidate:
-                b = beyn_extract(m.C0, m.C1, tol_svd)
+                if beyn_K > 1:
+                    b = beyn_extract_hankel(hankel_moments(problem, c, r, N, V, beyn_K), c, r, tol_svd)
+                else:
+                    b = beyn_extract(m.C0, m.C1, tol_svd)
                 rec.p, rec.saturated, rec.sigma, rec.lam = b.p, b.saturated, b.sigma, b.lam
                 if b.saturated and depth < max_depth:
                     rec.split = True

@@ -212,6 +212,7 @@ struct Workspace {
   DevBuf gitems, gdst, gperm;
   DevBuf Xkeep, citems;  // two-pass schedule: indicator-pass solutions, copy list
   DevBuf vout;           // verification's singular vectors (pmCIMa)
+  DevBuf Cm;             // scaled moments of the block Hankel form of Beyn's step
   DevBuf ind3, feats, sprob, sparams, sscratch;
   // the library's own stream: graphs cannot be captured on the legacy default stream
   cudaStream_t stream = nullptr;
@@ -225,7 +226,7 @@ struct Workspace {
                    &phase, &C0, &C1, &pf_half, &pf_abs, &ind, &pf_norm, &pf_scale, &cand, &bwork, &bsigma,
                    &bp, &blam, &bvecs, &bkept, &bstatus, &vlam, &vprob, &voff, &vsig, &vacc, &vwork,
                    &vvec, &vpiv, &gitems, &gdst, &gperm, &ind3, &feats, &sprob, &sparams, &sscratch, &Xkeep,
-                   &citems, &vout};
+                   &citems, &vout, &Cm};
     for (DevBuf* x : b) x->release();
   }
 };
@@ -282,6 +283,8 @@ int check_options(const pmcim_options* opt) {
     return fail(PMCIM_EINVAL, "tol_ir must be 0 (default) or in [1e-15, 1e-6]");
   if (opt->indicator_N != 0 && (opt->indicator_N < 2 || opt->indicator_N > 4096 || (opt->indicator_N & 1)))
     return fail(PMCIM_EINVAL, "indicator_N = %d must be 0 or even, 2..4096", opt->indicator_N);
+  if (opt->beyn_K < 0 || opt->beyn_K > PMCIM_MAX_BEYN_K)
+    return fail(PMCIM_EINVAL, "beyn_K = %d outside 0..%d", opt->beyn_K, PMCIM_MAX_BEYN_K);
   return PMCIM_OK;
 }
 
@@ -461,8 +464,10 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   auto form_of = [&](int prob) { return form_override ? (*form_override)[prob] : c.groups[prob].form; };
 
   // ---- offsets of every disk's blocks ----
+  // K > 1: Beyn on the block Hankel matrices of 2K scaled moments (K l columns)
+  const int K = do_beyn ? std::max(1, c.opt->beyn_K) : 1;
   int max_n = 0, max_l = 0, max_nl = 0;
-  size_t c_tot = 0, p_tot = 0, w_tot = 0, total_nodes = 0;
+  size_t c_tot = 0, p_tot = 0, w_tot = 0, v_tot = 0, total_nodes = 0;
   std::vector<RegionDev>& rd = out->rd;
   for (int g = 0; g < R; ++g) {
     const HostRegion& h = regs[g];
@@ -479,10 +484,14 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
     d.c_off = (int64_t)c_tot;
     d.p_off = (int64_t)p_tot;
     d.w_off = (int64_t)w_tot;
-    d.v_off = (int64_t)c_tot;
+    d.v_off = (int64_t)v_tot;
+    if (K * P.l > PMCIM_MAX_L)
+      return fail(PMCIM_EINVAL, "beyn_K = %d with l = %d exceeds %d Beyn columns", K, P.l, PMCIM_MAX_L);
+    const size_t rows = (size_t)K * P.n, cols = (size_t)K * P.l;
     c_tot += (size_t)P.n * P.l;
     p_tot += (size_t)P.n;
-    w_tot += 2 * (size_t)P.n * P.l + 4 * (size_t)P.l * P.l;
+    v_tot += (size_t)P.n * cols;
+    w_tot += (K == 1 ? 2 : 3) * rows * cols + 4 * cols * cols;
     total_nodes += (size_t)h.N;
     max_n = std::max(max_n, P.n);
     max_l = std::max(max_l, P.l);
@@ -503,7 +512,8 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   }
   if (do_beyn) {
     CU(ws.bwork.ensure(w_tot * sizeof(double2)));
-    CU(ws.bvecs.ensure(c_tot * sizeof(double2)));
+    CU(ws.bvecs.ensure(v_tot * sizeof(double2)));
+    if (K > 1) CU(ws.Cm.ensure((size_t)2 * K * c_tot * sizeof(double2)));
     CU(ws.bsigma.ensure((size_t)R * PMCIM_MAX_L * sizeof(double)));
     CU(ws.blam.ensure((size_t)R * PMCIM_MAX_L * sizeof(double2)));
     CU(ws.bkept.ensure((size_t)R * PMCIM_MAX_L));
@@ -629,6 +639,8 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   la.X = xbuf.as<double2>();
   la.C0 = ws.C0.as<double2>();
   la.C1 = ws.C1.as<double2>();
+  la.K = K;
+  la.Cm = K > 1 ? ws.Cm.as<double2>() : nullptr;
   la.pf_half = ws.pf_half.as<double2>();
   la.pf_abs = ws.pf_abs.as<double>();
   la.tol_ind = c.opt->tol_ind;
@@ -1204,6 +1216,7 @@ void pmcim_default_options(pmcim_options* opt) {
   opt->screen_threshold = 0.0;
   opt->screen_N = 16;
   opt->tol_ir = kIrTol;
+  opt->beyn_K = 1;
 }
 
 const char* pmcim_status_string(int code) {

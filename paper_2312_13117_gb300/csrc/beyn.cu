@@ -12,6 +12,11 @@
 //   5. eigenvectors v = V0 s, unit 2-norm, largest-modulus entry real positive;
 //   6. square filter: keep c - h <= Re, Im < c + h with h = r / sqrt(2).
 // Steps 1, 3 and 5 are spread over the CTA; step 4 (p <= 64) runs on one thread.
+// With K > 1 moment pairs the same steps run on the block Hankel matrices of the
+// scaled moments M_p (reduce.cu): C0 -> B0 = [M_{i+j}], C1 -> B1 = [M_{i+j+1}]
+// (i, j < K; K n x K l); eig(D) then gives mu = (lambda - c) / r, and an
+// eigenvector is the first n-block of V0 s (B0's left factor has block rows
+// v, v mu, ..., v mu^{K-1}).
 #include "pmcim_internal.cuh"
 
 namespace {
@@ -229,19 +234,35 @@ __global__ void __launch_bounds__(BT) k_beyn(LevelArgs a) {
     }
     return;
   }
-  const int n = a.probs[rg.prob].n, l = a.probs[rg.prob].l;
+  const int nv = a.probs[rg.prob].n, lp = a.probs[rg.prob].l;  // eigenvector length, probes
+  const int K = a.K;
+  const int n = K * nv, l = K * lp;  // rows and columns of the matrix the SVD runs on
   const size_t nl = (size_t)n * l;
-  const double2* C0 = a.C0 + rg.c_off;
-  const double2* C1 = a.C1 + rg.c_off;
-  // per-disk scratch: Acol (n x l) | B (n x l) | W (l x l) | H | Z | Y (p x p each, p <= l)
+  // per-disk scratch: Acol (n x l) | B (n x l) | W (l x l) | H | Z | Y (p x p each, p <= l),
+  // then, for K > 1, B1 (n x l)
   double2* Ac = a.bwork + rg.w_off;
   double2* B = Ac + nl;
   double2* W = B + nl;
   double2* H = W + (size_t)l * l;
   double2* Z = H + (size_t)l * l;
   double2* Y = Z + (size_t)l * l;
-
-  for (size_t e = tid; e < nl; e += BT) Ac[e] = C0[e];
+  const double2* C1;
+  if (K == 1) {
+    const double2* C0 = a.C0 + rg.c_off;
+    C1 = a.C1 + rg.c_off;
+    for (size_t e = tid; e < nl; e += BT) Ac[e] = C0[e];
+  } else {
+    double2* B1 = Y + (size_t)l * l;
+    const double2* Mm = a.Cm + (size_t)2 * K * rg.c_off;
+    const size_t blk = (size_t)nv * lp;
+    for (size_t e = tid; e < nl; e += BT) {
+      const int row = (int)(e % n), col = (int)(e / n);
+      const int ib = row / nv, ir = row % nv, jb = col / lp, jc = col % lp;
+      Ac[e] = Mm[(size_t)(ib + jb) * blk + (size_t)jc * nv + ir];
+      B1[e] = Mm[(size_t)(ib + jb + 1) * blk + (size_t)jc * nv + ir];
+    }
+    C1 = B1;
+  }
   for (int e = tid; e < l * l; e += BT) W[e] = make_double2((e % l) == (e / l) ? 1.0 : 0.0, 0.0);
   __syncthreads();
 
@@ -369,17 +390,19 @@ __global__ void __launch_bounds__(BT) k_beyn(LevelArgs a) {
   if (tid == 0 && p > 0) {
     int fail = small_eig(H, Z, Y, p, sm.lam, sm);
     (void)fail;
+    if (K > 1)  // mu = (lambda - c) / r
+      for (int k = 0; k < p; ++k) sm.lam[k] = make_double2(rg.cre + rg.r * sm.lam[k].x, rg.cim + rg.r * sm.lam[k].y);
   }
   __syncthreads();
 
   // ---- 5. eigenvectors v = V0 s, normalised ----
   for (int k = 0; k < p; ++k) {
-    double2* vk = a.vecs + rg.v_off + (size_t)k * n;
+    double2* vk = a.vecs + rg.v_off + (size_t)k * nv;
     const double2* sk = Y + (size_t)k * p;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     double best = -1.0;
-    int bi = n;
-    for (int i = tid; i < n; i += BT) {
+    int bi = nv;
+    for (int i = tid; i < nv; i += BT) {
       double2 s = make_double2(0.0, 0.0);
       for (int m = 0; m < p; ++m) cfma(s, Ac[(size_t)m * n + i], sk[m]);
       vk[i] = s;
@@ -414,7 +437,7 @@ __global__ void __launch_bounds__(BT) k_beyn(LevelArgs a) {
     const double2 rot = ab > 0.0 ? make_double2(big.x / (ab * nrm), -big.y / (ab * nrm))
                                  : make_double2(1.0 / nrm, 0.0);
     __syncthreads();
-    for (int i = tid; i < n; i += BT) vk[i] = cmul(vk[i], rot);
+    for (int i = tid; i < nv; i += BT) vk[i] = cmul(vk[i], rot);
     __syncthreads();
   }
 

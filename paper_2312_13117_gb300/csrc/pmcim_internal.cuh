@@ -10,6 +10,7 @@
 // ||P f|_N|| at or below this fraction of ||sum_j |w_j| |x_j||| counts as zero
 constexpr double kPfFloor = 1e-10;
 #define PMCIM_MAX_L 64
+#define PMCIM_MAX_BEYN_K 8  // moment pairs of the block Hankel form of Beyn's step
 
 // ---------------------------------------------------------------------------
 // Complex helpers on double2 / float2 (re, im). Division uses Smith's scaling
@@ -235,6 +236,8 @@ struct LevelArgs {
   const double2* X;
   double2* C0;
   double2* C1;
+  int K;                    // 1: Beyn on C0, C1 (Eq. 2.8); > 1: block Hankel of 2K scaled moments
+  double2* Cm;              // K > 1: per disk 2K blocks n x l at 2K c_off: M_p = sum_j w_j e^{i p theta_j} X_j
   double2* pf_half;
   double* pf_abs;
   double tol_ind;

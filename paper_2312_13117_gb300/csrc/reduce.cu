@@ -5,6 +5,9 @@
 //   P f|_N = C0[:,0],  P f|_{N/2} = sum_{j odd} 2 w_j X_j[:,0]  (Eq. 3.1; the
 //   1-based even nodes x_2, x_4, ..., x_N are the 0-based odd ones)
 //   I = || P f|_N ./ P f|_{N/2} ||_2 / sqrt(n)                  (Eq. 3.1)
+// With K > 1 moment pairs it also forms the scaled moments of the block Hankel
+// form of Beyn's step, M_p = sum_j w_j ((z_j - c)/r)^p X_j, p < 2K; on the nodes
+// ((z_j - c)/r)^p = e^{i p theta_j}, taken from the integer phase p j mod N.
 // Nodes are summed in index order by one thread per output element, so the
 // result is deterministic. The kernel streams X once: it is HBM-bound.
 #include "pmcim_internal.cuh"
@@ -38,6 +41,31 @@ __global__ void __launch_bounds__(RT) k_reduce_moments(LevelArgs a) {
   }
   a.C0[rg.c_off + e] = c0;
   a.C1[rg.c_off + e] = c1;
+  if (a.K > 1) {
+    // M_0 = C0; M_p for 1 <= p < 2K, all p in one pass over the nodes
+    double2 m[2 * PMCIM_MAX_BEYN_K - 1];
+#pragma unroll
+    for (int q = 0; q < 2 * PMCIM_MAX_BEYN_K - 1; ++q) m[q] = make_double2(0.0, 0.0);
+    const double wr = rg.r / rg.N;
+    for (int j = 0; j < rg.N; ++j) {
+      const double2 x = Xg[(size_t)j * nl];
+#pragma unroll
+      for (int q = 0; q < 2 * PMCIM_MAX_BEYN_K - 1; ++q) {
+        if (q + 1 < 2 * a.K) {
+          // w_j e^{i (q+1) theta_j} = (r / N) e^{i (q+2) theta_j}
+          const int ph = (int)(((long long)(q + 2) * j) % rg.N);
+          double sn, cs;
+          sincospi(2.0 * ph / rg.N, &sn, &cs);
+          cfma(m[q], make_double2(wr * cs, wr * sn), x);
+        }
+      }
+    }
+    double2* Cm = a.Cm + (size_t)2 * a.K * rg.c_off + e;
+    Cm[0] = c0;
+#pragma unroll
+    for (int q = 0; q < 2 * PMCIM_MAX_BEYN_K - 1; ++q)
+      if (q + 1 < 2 * a.K) Cm[(size_t)(q + 1) * nl] = m[q];
+  }
   if (first_col) {
     a.pf_half[rg.p_off + e] = ph;
     a.pf_abs[rg.p_off + e] = pa;

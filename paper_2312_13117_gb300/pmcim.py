@@ -47,7 +47,7 @@ class pmcim_region(C.Structure):
 class pmcim_options(C.Structure):
     _fields_ = [("tol_ind", C.c_double), ("tol_svd", C.c_double), ("tol_verify", C.c_double),
                 ("precision", C.c_int32), ("max_ir_sweeps", C.c_int32), ("max_split_depth", C.c_int32),
-                ("reserved", C.c_int32), ("cuda_stream", C.c_void_p), ("screen_params", C.c_void_p),
+                ("beyn_K", C.c_int32), ("cuda_stream", C.c_void_p), ("screen_params", C.c_void_p),
                 ("screen_threshold", C.c_double), ("screen_N", C.c_int32), ("indicator_N", C.c_int32),
                 ("tol_ir", C.c_double)]
 
@@ -227,9 +227,10 @@ _screen_keep = []
 
 def options(tol_ind=0.1, tol_svd=1e-6, tol_verify=1e-6, precision=PREC_FP64, max_ir_sweeps=3,
             max_split_depth=8, stream=None, screen_params=None, screen_threshold=0.0,
-            screen_N=16, tol_ir=None, indicator_N=0) -> pmcim_options:
+            screen_N=16, tol_ir=None, indicator_N=0, beyn_K=1) -> pmcim_options:
     o = pmcim_default_options()
     o.indicator_N = int(indicator_N)
+    o.beyn_K = int(beyn_K)
     o.tol_ind, o.tol_svd, o.tol_verify = tol_ind, tol_svd, tol_verify
     if tol_ir is not None:
         o.tol_ir = float(tol_ir)

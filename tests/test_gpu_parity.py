@@ -578,3 +578,60 @@ def test_pmcima_matches_oracle(pm, precision):
         assert res["sigma_min"][i] == pytest.approx(ref.sigma[i], rel=1e-6)
     assert res["stats"]["solves"] == 16 * ref.regions
     P.close()
+
+
+# ---------------------------------------------------------------------------
+# Beyn's higher moments (block Hankel of 2K scaled moments)
+# ---------------------------------------------------------------------------
+
+def test_hankel_beyn_resolves_poles_without_split(pm):
+    """10 poles in one disk, l = 3 probes: K = 1 must split the disk, K = 4 (K l = 12) returns
+    all 10 from the disk itself, as the oracle does."""
+    rng = np.random.default_rng(52)
+    c, r, N = 0.0, 1.0, 64
+    ain = rng.uniform(0.1, 0.6, 10) * np.exp(2j * np.pi * rng.random(10))
+    aout = rng.uniform(1.5, 3.0, 5) * np.exp(2j * np.pi * rng.random(5))
+    mu = c + r * np.concatenate([ain, aout])
+    prob = w.diagonal_linear(mu)
+    V = w.probe_block(rng, len(mu), 3)
+    reg = [w.Region(c, r * np.sqrt(2.0), N)]      # the disk circumscribing the square of side 2
+    P = pm.Problem(prob.n, prob.terms)
+    k4 = P.solve(reg, V, opt=pm.options(beyn_K=4, tol_svd=1e-10))
+    ref = o.pmcimb(prob, reg, V, tol_svd=1e-10, beyn_K=4)
+    inside = mu[(np.abs(mu.real) < 1.0) & (np.abs(mu.imag) < 1.0)]
+    assert k4["stats"]["splits"] == 0
+    assert _match_lam(k4["lam"], inside) <= LAM_TOL
+    assert _match_lam(k4["lam"], ref.lam) <= LAM_TOL
+    k1 = P.solve(reg, V, opt=pm.options(tol_svd=1e-10))
+    assert k1["stats"]["splits"] >= 1
+    assert _match_lam(k1["lam"], inside) <= LAM_TOL
+    P.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32ir"])
+def test_hankel_quadratic_matches_oracle(pm, precision):
+    """n = 64 quadratic (up to 31 eigenvalues per disk at l = 8): K = 2 halves the saturation
+    of K = 1, so fewer disks split; eigenvalues equal the oracle's with the same K. Against
+    K = 1 they agree to the quadrature's accuracy only: with fewer splits a value may come from
+    a larger disk, where an eigenvalue near its circle carries a larger |a|^N error."""
+    W = w.quadratic_small()
+    prec = {"fp64": pm.PREC_FP64, "fp32ir": pm.PREC_FP32_IR}[precision]
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    k2 = P.solve(W.regions, W.V, opt=pm.options(precision=prec, beyn_K=2))
+    k1 = P.solve(W.regions, W.V, opt=pm.options(precision=prec))
+    ref = o.pmcimb(W.problem, W.regions, W.V, beyn_K=2)
+    assert _match_lam(k2["lam"], ref.lam) <= LAM_TOL
+    assert _match_lam(k2["lam"], k1["lam"]) <= 1e-5
+    assert k2["stats"]["splits"] < k1["stats"]["splits"]
+    assert k2["stats"]["solves"] < k1["stats"]["solves"]
+    P.close()
+
+
+def test_hankel_rejects_too_many_columns(pm):
+    W = w.quadratic_small()
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    with pytest.raises(RuntimeError):
+        P.solve(W.regions[:2], W.V, opt=pm.options(beyn_K=9))      # above 8
+    with pytest.raises(RuntimeError):
+        P.solve(W.regions[:2], np.hstack([W.V] * 3), opt=pm.options(beyn_K=3))   # K l = 72 > 64
+    P.close()

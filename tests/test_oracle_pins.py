@@ -442,3 +442,50 @@ def test_merge_centres_groups_within_tol():
     m = o.merge_centres(z, 1e-6)
     # the first centre takes the two within 1e-6 of it; the next free one takes its neighbour
     assert np.allclose(m, [np.mean(z[:3]), np.mean(z[3:5]), 1.0], atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Higher moments (block Hankel Beyn).  For T = diag(z - mu) the scaled moments are
+# M_p = diag(a^p / (1 - a^N)) V (P1's sums with the extra phase e^{i p theta_j}), so
+# B0 factors as [a^{i} ...] blocks and eig(D) returns every pole inside once K l
+# reaches their number, with no split.
+# ---------------------------------------------------------------------------
+
+def test_hankel_moments_exact_sums():
+    rng = np.random.default_rng(51)
+    c, r, N, K = 0.2 - 0.1j, 0.8, 32, 3
+    mu, a = _poles(rng, c, r, 4, 3)
+    V = w.probe_block(rng, 7, 2)
+    M = o.hankel_moments(w.diagonal_linear(mu), c, r, N, V, K)
+    for p in range(2 * K):
+        assert _rel(M[p], (a ** p / (1.0 - a ** N))[:, None] * V) < 1e-12
+
+
+def test_hankel_beyn_resolves_more_poles_than_probes():
+    rng = np.random.default_rng(52)
+    c, r, N = 0.0, 1.0, 64
+    mu, a = _poles(rng, c, r, 10, 5, rin=(0.1, 0.7), rout=(1.5, 3.0))
+    P = w.diagonal_linear(mu)
+    V = w.probe_block(rng, 15, 3)
+    m = o.moments(P, c, r, N, V)
+    b1 = o.beyn_extract(m.C0, m.C1, tol_svd=1e-10)
+    assert b1.p == 3 and b1.saturated                       # l = 3 probes cannot hold 10 poles
+    b4 = o.beyn_extract_hankel(o.hankel_moments(P, c, r, N, V, 4), c, r, tol_svd=1e-10)
+    assert b4.p == 10 and not b4.saturated                  # K l = 12 >= 10
+    k, err = _match(mu[:10], b4.lam)
+    assert k == 10 and err < 1e-10
+    for i in range(10):                                     # eigenvectors: e_i up to phase
+        j = int(np.argmin(np.abs(b4.lam - mu[i])))
+        assert abs(abs(b4.vecs[i, j]) - 1.0) < 1e-8
+
+
+def test_hankel_with_one_moment_pair_is_beyn():
+    rng = np.random.default_rng(53)
+    W = w.quadratic_small(seed=5, n=12, l=6, N=32)
+    reg = W.regions[5]
+    m = o.moments(W.problem, reg.c, reg.r, reg.N, W.V)
+    b = o.beyn_extract(m.C0, m.C1, tol_svd=1e-8)
+    h = o.beyn_extract_hankel(o.hankel_moments(W.problem, reg.c, reg.r, reg.N, W.V, 1), reg.c, reg.r, tol_svd=1e-8)
+    assert b.p == h.p > 0
+    k, err = _match(b.lam, h.lam)
+    assert k == b.p and err < 1e-9

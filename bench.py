@@ -255,7 +255,8 @@ def run_batched(args, world, rank, local):
     prepared = {k: make(k) for k in steps}          # coefficients resident before timing
     stream = torch.cuda.current_stream()
     res = {}
-    forms = [("auto", pmcim.PREC_AUTO), ("fp32ir", pmcim.PREC_FP32_IR), ("unbatched_auto", pmcim.PREC_AUTO)]
+    forms = [("auto", pmcim.PREC_AUTO), ("fp32ir", pmcim.PREC_FP32_IR), ("unbatched_auto", pmcim.PREC_AUTO),
+             ("auto_hankel", pmcim.PREC_AUTO)]
     if args.batched_fp64:
         forms.append(("fp64", pmcim.PREC_FP64))
     # the autotuner measures each (n bucket, l, dense terms) on first use: let it do so
@@ -270,7 +271,8 @@ def run_batched(args, world, rank, local):
         if time.perf_counter() - t_start > args.time_budget:
             sys.stderr.write("skipping %s: time budget spent\n" % name)
             continue
-        o = pmcim.options(stream=stream.cuda_stream, precision=prec)
+        o = pmcim.options(stream=stream.cuda_stream, precision=prec,
+                          beyn_K=args.beyn_k if name.endswith("hankel") else 1)
         agg = {}
         t_ms = 0.0
         for k in steps:
@@ -311,7 +313,10 @@ def run_batched(args, world, rank, local):
                                      "n_range": [min(ns), max(ns)], "l": 8},
                           "forms": res,
                           "speedup_batched_vs_unbatched": (res["unbatched_auto"]["ms_per_step"] / res["auto"]["ms_per_step"]
-                                                           if "unbatched_auto" in res else None)}))
+                                                           if "unbatched_auto" in res else None),
+                          "beyn_K_of_hankel_leg": args.beyn_k,
+                          "speedup_hankel_vs_auto": (res["auto"]["ms_per_step"] / res["auto_hankel"]["ms_per_step"]
+                                                     if "auto_hankel" in res else None)}))
     for k in steps:
         for h in prepared[k][0]:
             h.close()
@@ -414,16 +419,22 @@ def run_screen(args, world, rank, local):
     return 0
 
 
-def _same_lams(a, b, tol=1e-10):
-    """Both eigenvalue lists hold the same values (relative tol), matched one to one."""
+def _max_rel_diff(a, b):
+    """Largest relative difference of two eigenvalue lists matched one to one (None when the counts differ)."""
     a, b = np.asarray(a), np.asarray(b)
     if len(a) != len(b):
-        return False
+        return None
     if len(a) == 0:
-        return True
+        return 0.0
     from scipy.optimize import linear_sum_assignment
     ri, ci = linear_sum_assignment(np.abs(a[:, None] - b[None, :]))
-    return bool(np.max(np.abs(a[ri] - b[ci]) / np.maximum(1.0, np.abs(a[ri]))) <= tol)
+    return float(np.max(np.abs(a[ri] - b[ci]) / np.maximum(1.0, np.abs(a[ri]))))
+
+
+def _same_lams(a, b, tol=1e-10):
+    """Both eigenvalue lists hold the same values (relative tol), matched one to one."""
+    d = _max_rel_diff(a, b)
+    return d is not None and d <= tol
 
 
 def run_full(args, P, W, opt, opt_mixed, world, rank, local):
@@ -437,8 +448,10 @@ def run_full(args, P, W, opt, opt_mixed, world, rank, local):
     lams = {}
     o2 = pmcim.options(stream=opt_mixed.cuda_stream, precision=opt_mixed.precision, indicator_N=args.indicator_n)
     f2 = pmcim.options(stream=opt.cuda_stream, precision=opt.precision, indicator_N=args.indicator_n)
-    for name, o in (("precision_form", opt_mixed), ("precision_form_two_pass", o2), ("fp64", opt),
-                    ("fp64_two_pass", f2)):
+    o3 = pmcim.options(stream=opt_mixed.cuda_stream, precision=opt_mixed.precision, indicator_N=args.indicator_n,
+                       beyn_K=2)
+    for name, o in (("precision_form", opt_mixed), ("precision_form_two_pass", o2),
+                    ("precision_form_two_pass_hankel2", o3), ("fp64", opt), ("fp64_two_pass", f2)):
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
@@ -463,7 +476,11 @@ def run_full(args, P, W, opt, opt_mixed, world, rank, local):
                           "speedup_two_pass_precision_vs_fp64": out["fp64"]["seconds"] /
                           out["precision_form_two_pass"]["seconds"],
                           "two_pass_same_eigenvalues": {k: _same_lams(lams["fp64"], lams[k])
-                                                        for k in ("precision_form_two_pass", "fp64_two_pass")}}))
+                                                        for k in ("precision_form_two_pass", "fp64_two_pass")},
+                          "max_rel_lambda_diff_hankel2_vs_fp64": _max_rel_diff(
+                              lams["fp64"], lams["precision_form_two_pass_hankel2"]),
+                          "speedup_two_pass_hankel2_vs_fp64": out["fp64"]["seconds"] /
+                          out["precision_form_two_pass_hankel2"]["seconds"]}))
     P.close()
     return 0
 
@@ -489,6 +506,8 @@ def main():
     ap.add_argument("--problems-per-step", type=int, default=4)
     ap.add_argument("--batched-fp64", action="store_true", help="also time the batched workload in plain FP64")
     ap.add_argument("--time-budget", type=float, default=240.0, help="seconds before remaining legs are skipped")
+    ap.add_argument("--beyn-k", type=int, default=4,
+                    help="moment pairs of the block Hankel Beyn legs (--workload batched: 4, --full: 2)")
     ap.add_argument("--indicator-n", type=int, default=16,
                     help="coarse indicator rule of the two-pass legs (--full, --workload screen)")
     ap.add_argument("--full", action="store_true",

@@ -635,3 +635,19 @@ def test_hankel_rejects_too_many_columns(pm):
     with pytest.raises(RuntimeError):
         P.solve(W.regions[:2], np.hstack([W.V] * 3), opt=pm.options(beyn_K=3))   # K l = 72 > 64
     P.close()
+
+
+def test_beyn_api_two_pass_and_hankel(pm):
+    """pmcim_beyn runs Beyn on the given disks without the indicator gate; with the two-pass
+    schedule only the split children are gated, on the coarse rule. The verified values equal
+    those of the plain call; with beyn_K = 2 too, to the quadrature's accuracy."""
+    W = w.quadratic_small()
+    regs = W.regions[4:8]
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    lam1, _, _, st1 = P.beyn(regs, W.V)
+    lam2, _, _, st2 = P.beyn(regs, W.V, opt=pm.options(indicator_N=8))
+    lam3, _, _, st3 = P.beyn(regs, W.V, opt=pm.options(indicator_N=8, beyn_K=2))
+    acc = [o.verify(W.problem, lam)[1] for lam in (lam1, lam2, lam3)]
+    assert _match_lam(lam2[acc[1]], lam1[acc[0]]) <= LAM_TOL
+    assert _match_lam(lam3[acc[2]], lam1[acc[0]]) <= 1e-5
+    P.close()

@@ -651,3 +651,16 @@ def test_beyn_api_two_pass_and_hankel(pm):
     assert _match_lam(lam2[acc[1]], lam1[acc[0]]) <= LAM_TOL
     assert _match_lam(lam3[acc[2]], lam1[acc[0]]) <= 1e-5
     P.close()
+
+
+def test_paper_quadratic_two_pass_matches_oracle(pm):
+    """The paper's quadratic experiment (n = 100, T_j uniform [0,1), 225 disks on [-0.5,0.5]^2)
+    with the Appendix's schedule (indicator on 16 nodes, Beyn on 64, l = 10): the oracle's
+    eigenvalues, all 34 in Omega by the companion pencil."""
+    W = w.paper_quadratic()
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    res = P.solve(W.regions, W.V, opt=pm.options(indicator_N=16))
+    ref = o.pmcimb(W.problem, W.regions, W.V, indicator_N=16)
+    assert len(ref.lam) == 34
+    assert _match_lam(res["lam"], ref.lam) <= LAM_TOL
+    P.close()

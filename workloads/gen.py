@@ -27,7 +27,7 @@ EXP_NEG = 1
 __all__ = [
     "MONOMIAL", "EXP_NEG", "Problem", "Region", "Workload",
     "complex_gaussian", "probe_block", "grid_regions",
-    "quadratic_small", "delay_large", "batched_quadratics", "mass_spring",
+    "quadratic_small", "paper_quadratic", "delay_large", "batched_quadratics", "mass_spring",
     "diagonal_linear", "similarity_linear", "diagonal_delay", "paper_n4_example",
     "diagonal_quadratic", "screen_trace_problems",
 ]
@@ -109,6 +109,19 @@ def quadratic_small(seed: int = 0, n: int = 64, l: int = 8, N: int = 32) -> Work
     prob = Problem(n, [(np.asfortranarray(A[d]), MONOMIAL, d, 0.0) for d in range(3)])
     return Workload("quadratic_n%d" % n, prob, grid_regions(-2, 2, -2, 2, 4, 4, N), V,
                     omega=(-2, 2, -2, 2))
+
+
+def paper_quadratic(seed: int = 0, n: int = 100, m: int = 15, l: int = 10, N: int = 64) -> Workload:
+    """The paper's quadratic experiment (Sec. 4.1) with seeded inputs: T(z) = T0 + z T1 + z^2 T2
+    with real T_j of uniform [0, 1) entries (the shape and distribution of MATLAB rand),
+    n = 100, Omega = [-0.5, 0.5]^2 split m x m = 15 x 15, N = 64 nodes for Beyn, l = 10 probes
+    (the Appendix listing's numEig)."""
+    rng = np.random.default_rng(seed)
+    T = [np.asfortranarray(rng.random((n, n)).astype(np.complex128)) for _ in range(3)]
+    V = probe_block(rng, n, l)
+    prob = Problem(n, [(T[d], MONOMIAL, d, 0.0) for d in range(3)])
+    return Workload("paper_quadratic_n%d" % n, prob, grid_regions(-0.5, 0.5, -0.5, 0.5, m, m, N), V,
+                    omega=(-0.5, 0.5, -0.5, 0.5))
 
 
 def delay_large(seed: int = 0, n: int = 1024, l: int = 16, N: int = 64,

@@ -269,16 +269,21 @@ __device__ void cta_lu_update_simt(T2* __restrict__ M, int n, int ncols, int k0,
           int r = r0 + tx + 16 * i, c = c0 + ty + 16 * q;
           acc[i][q] = (r < n && c < ncols) ? M[(size_t)c * ld + r] : czero<T2>();
         }
-      for (int kk = 0; kk < kb; ++kk) {
-        T2 a[4], b[4];
+      // a thread whose rows (tx + 16 i) or columns (ty + 16 q) all lie past the matrix has
+      // nothing to update: on the ragged last tiles (most of each tile when n is small) it skips
+      // the multiply instead of running it on padding
+      if (r0 + tx < n && c0 + ty < ncols) {
+        for (int kk = 0; kk < kb; ++kk) {
+          T2 a[4], b[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = sm.Ls[kk * TILE + tx + 16 * i];
+          for (int i = 0; i < 4; ++i) a[i] = sm.Ls[kk * TILE + tx + 16 * i];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) b[q] = sm.Us[kk * US_LD + ty + 16 * q];
+          for (int q = 0; q < 4; ++q) b[q] = sm.Us[kk * US_LD + ty + 16 * q];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) cfms(acc[i][q], a[i], b[q]);
+            for (int q = 0; q < 4; ++q) cfms(acc[i][q], a[i], b[q]);
+        }
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i)

@@ -205,7 +205,7 @@ void prof_flush() {
 // Device workspaces, reused across calls on one handle.
 struct Workspace {
   DevBuf probs, regions, items, counters, node_info, X;
-  DevBuf work64, piv64, work32, piv32, phase;
+  DevBuf work64, piv64, work32, piv32, t64, phase;
   DevBuf C0, C1, pf_half, pf_abs, ind, pf_norm, pf_scale, cand;
   DevBuf bwork, bsigma, bp, blam, bvecs, bkept, bstatus;
   DevBuf vlam, vprob, voff, vsig, vacc, vwork, vvec, vpiv;
@@ -222,7 +222,7 @@ struct Workspace {
     if (ordered) cudaEventDestroy(ordered);
     stream = nullptr;
     ordered = nullptr;
-    DevBuf* b[] = {&probs, &regions, &items, &counters, &node_info, &X, &work64, &piv64, &work32, &piv32,
+    DevBuf* b[] = {&probs, &regions, &items, &counters, &node_info, &X, &work64, &piv64, &work32, &piv32, &t64,
                    &phase, &C0, &C1, &pf_half, &pf_abs, &ind, &pf_norm, &pf_scale, &cand, &bwork, &bsigma,
                    &bp, &blam, &bvecs, &bkept, &bstatus, &vlam, &vprob, &voff, &vsig, &vacc, &vwork,
                    &vvec, &vpiv, &gitems, &gdst, &gperm, &ind3, &feats, &sprob, &sparams, &sscratch, &Xkeep,
@@ -533,6 +533,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   std::vector<VecItem> copies;  // all waves
   size_t x_need = 0, reused_nodes = 0;
   bool any64 = false, any32 = false, anyS = false;
+  int t64_n = 0;  // largest n of a precision-form problem with two or more dense terms
   {
     int g0 = 0;
     while (g0 < R) {
@@ -556,6 +557,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
         const ProblemDev& P = c.pd[regs[g].prob];
         std::vector<NodeItem>& dst = small_kernel_fits(P.n, P.l) ? itS
                                      : (form_of(regs[g].prob) == PMCIM_PREC_FP64 ? it64 : it32);
+        if (&dst == &it32 && P.n_dense >= 2) t64_n = std::max(t64_n, P.n);
         const bool re = reuse && reuse->src[g] >= 0;
         const int nl = P.n * P.l;
         for (int j = 0; j < regs[g].N; ++j) {
@@ -607,7 +609,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   // ---- factorisation workspaces, one slot per resident CTA ----
   const int sms = num_sms();
   int slots64 = 0, slots32 = 0;
-  size_t slot64 = 0, slot32 = 0;
+  size_t slot64 = 0, slot32 = 0, t64_stride = 0;
   if (any64) {
     slot64 = (size_t)max_n * (max_n + max_l) * sizeof(double2);
     slots64 = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(2 * sms, kSlotBytes / slot64), total_nodes));
@@ -618,11 +620,14 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
     // one CTA per SM, each cycling through mixed_slots_per_cta() slots
     slot32 = mixed_slot_bytes(max_n, max_l);
     const size_t per = (size_t)mixed_slots_per_cta();
-    const size_t ctas = std::max<size_t>(1, std::min<size_t>(std::min<size_t>(sms, kSlotBytes / (per * slot32)),
+    t64_stride = (size_t)t64_n * t64_n;  // the refine group's FP64 T(z_j)
+    const size_t cta_bytes = per * slot32 + t64_stride * sizeof(double2);
+    const size_t ctas = std::max<size_t>(1, std::min<size_t>(std::min<size_t>(sms, kSlotBytes / cta_bytes),
                                                              total_nodes));
     slots32 = (int)(ctas * per);
     CU(ws.work32.ensure((size_t)slots32 * slot32));
     CU(ws.piv32.ensure((size_t)slots32 * max_n * sizeof(int32_t)));
+    if (t64_stride) CU(ws.t64.ensure(ctas * t64_stride * sizeof(double2)));
   }
   const bool timed = prof_on();
   if (timed && any32) {
@@ -707,6 +712,8 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
         na.slot_bytes = slot32;
         na.piv = ws.piv32.as<int32_t>();
         na.slots = slots32;
+        na.t64 = t64_stride ? ws.t64.as<double2>() : nullptr;
+        na.t64_stride = t64_stride;
         na.phase = timed ? ws.phase.as<unsigned long long>() : nullptr;
         prof_begin(PMCIM_K_FACTOR32, s);
         CU(launch_factor_solve_mixed(na, s));

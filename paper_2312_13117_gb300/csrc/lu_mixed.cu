@@ -192,18 +192,18 @@ __device__ double block_max(double v, double* red) {
 }
 
 // R = V - sum_k f_k(z) A_k X  (FP64), R and X column-major n x l.
+// R = V - id X - f_M M X in FP64 (the refinement residual), M an n x n column-major
+// matrix (NULL: none). With two or more dense terms M is T(z_j) itself, assembled
+// once per node (f_M = 1, id = 0), so that a sweep multiplies X by one matrix
+// instead of one per term; with a single dense term M is that term's A_k.
 __device__ void residual_fp64(const double2* __restrict__ X, double2* __restrict__ R, const NodeCtx& cx,
-                              ResSmem& rs) {
+                              ResSmem& rs, const double2* __restrict__ M, double2 fM, double2 id) {
   const ProblemDev& P = cx.P;
   const int n = P.n, l = P.l;
   const int tid = gtid();
-  const size_t nn = (size_t)n * n;
   const int tx = tid & 63, ty = tid >> 6;
   const int pr = tid % RT_ROWS, pk = tid / RT_ROWS;  // tile element (row, k) this thread fetches first
   const int xk = tid % RT_K, xc = tid / RT_K;        // X slice element (k, column)
-  double2 idsum = make_double2(0.0, 0.0);  // sum of identity-term coefficients f_k id_k
-  for (int k = 0; k < P.K; ++k)
-    if (!P.term[k].dense) idsum = cadd(idsum, cmul(cx.fz[k], P.term[k].id));
   for (int c0 = 0; c0 < l; c0 += RT_COLS) {
     for (int r0 = 0; r0 < n; r0 += RT_ROWS) {
       double2 acc[RT_RI][4];
@@ -215,29 +215,25 @@ __device__ void residual_fp64(const double2* __restrict__ X, double2* __restrict
           double2 v = make_double2(0.0, 0.0);
           if (row < n && c < l) {
             v = P.V[(size_t)c * n + row];
-            cfms(v, idsum, X[(size_t)c * n + row]);
+            cfms(v, id, X[(size_t)c * n + row]);
           }
           acc[i][q] = v;
         }
-      for (int k = 0; k < P.K; ++k) {
-        const TermDesc& t = P.term[k];
-        if (!t.dense) continue;
-        const double2* Ak = P.A + (size_t)t.mat_index * nn;
-        const double2 fk = cx.fz[k];
-        // A_k tiles stream through two shared buffers with cp.async: the copy
+      if (M) {
+        // tiles of M stream through two shared buffers with cp.async: the copy
         // of the next tile is in flight while the current one is multiplied
         const double2* xcol = X + (size_t)(c0 + xc) * n;
         const bool xc_ok = c0 + xc < l;
         double2 px = (xk < n && xc_ok) ? xcol[xk] : make_double2(0.0, 0.0);
         gsync();  // both buffers are free
-        res_tile_async(rs.As[0], Ak, n, r0, 0, pr, pk);
+        res_tile_async(rs.As[0], M, n, r0, 0, pr, pk);
         cp_async_commit();
         int b = 0;
         for (int k0 = 0; k0 < n; k0 += RT_K, b ^= 1) {
           gsync();  // the previous step's multiplications are done
-          rs.Xs[xk * RT_COLS + xc] = cmul(fk, px);
+          rs.Xs[xk * RT_COLS + xc] = cmul(fM, px);
           if (k0 + RT_K < n) {
-            res_tile_async(rs.As[b ^ 1], Ak, n, r0, k0 + RT_K, pr, pk);
+            res_tile_async(rs.As[b ^ 1], M, n, r0, k0 + RT_K, pr, pk);
             px = (k0 + RT_K + xk < n && xc_ok) ? xcol[k0 + RT_K + xk] : make_double2(0.0, 0.0);
           }
           cp_async_commit();
@@ -268,6 +264,30 @@ __device__ void residual_fp64(const double2* __restrict__ X, double2* __restrict
     }
   }
   cp_async_wait_all();
+  gsync();
+}
+
+// T(z_j) in FP64 into T (n x n, column-major) for the refinement residuals: the
+// dense terms in one pass over the elements, then the identity terms on the
+// diagonal.
+__device__ void assemble_t64(const NodeCtx& cx, double2* __restrict__ T) {
+  const ProblemDev& P = cx.P;
+  const int n = P.n;
+  const size_t nn = (size_t)n * n;
+  double2 id = make_double2(0.0, 0.0);
+  for (int k = 0; k < P.K; ++k)
+    if (!P.term[k].dense) id = cadd(id, cmul(cx.fz[k], P.term[k].id));
+#pragma unroll 4
+  for (size_t e = gtid(); e < nn; e += THREADS) {
+    double2 v = make_double2(0.0, 0.0);
+    for (int k = 0; k < P.K; ++k) {
+      const TermDesc& t = P.term[k];
+      if (t.dense) cfma(v, cx.fz[k], P.A[(size_t)t.mat_index * nn + e]);
+    }
+    T[e] = v;
+  }
+  gsync();
+  for (int i = gtid(); i < n; i += THREADS) T[(size_t)i * n + i] = cadd(T[(size_t)i * n + i], id);
   gsync();
 }
 
@@ -470,10 +490,29 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
     bool ok = (info == 0);
     int sweeps = 0;
     if (ok) {
+      // the matrix each residual multiplies: T(z_j) assembled once, or the one dense term
+      const double2* M = nullptr;
+      double2 fM = make_double2(0.0, 0.0), id = make_double2(0.0, 0.0);
+      if (P.n_dense >= 2) {
+        double2* T = a.t64 + (size_t)blockIdx.x * a.t64_stride;
+        assemble_t64(c, T);
+        M = T;
+        fM = make_double2(1.0, 0.0);
+      } else {
+        for (int k = 0; k < P.K; ++k) {
+          const TermDesc& t = P.term[k];
+          if (t.dense) {
+            M = P.A + (size_t)t.mat_index * nn;
+            fM = c.fz[k];
+          } else {
+            id = cadd(id, cmul(c.fz[k], t.id));
+          }
+        }
+      }
       double dprev = sl.xm;
       bool conv = false;
       for (int sw = 1; sw <= a.max_sweeps && ok; ++sw) {
-        residual_fp64(X, R, c, sm.r.u.res);
+        residual_fp64(X, R, c, sm.r.u.res, M, fM, id);
         pc.mark(PH_RESIDUAL);
         double rm = 0.0;
         for (size_t e = tid; e < nl; e += THREADS) rm = fmax(rm, fmax(fabs(R[e].x), fabs(R[e].y)));

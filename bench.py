@@ -40,9 +40,10 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes per node of k_factor_solve_fp64, from one ncu capture of a 64-node launch at n = 1024, l = 16
 # (dram__bytes_read.sum + dram__bytes_write.sum = 15.16 + 13.45 GB); scaled to a launch by its node count.
 FACTOR_FP64_TRAFFIC_PER_NODE = 28.61e9 / 64
-# DRAM bytes per node of k_factor_solve_mixed (FP32 form), from one ncu capture of a 320-node launch
-# (dram__bytes_read.sum + dram__bytes_write.sum = 49.91 + 35.55 GB); scaled to a launch by its node count
-MIXED_TRAFFIC_PER_NODE = 85.45e9 / 320
+# DRAM bytes per node of k_factor_solve_mixed, from one ncu capture of a 320-node launch per form
+# (dram__bytes_read.sum + dram__bytes_write.sum); scaled to a launch by its node count. None: no
+# capture of the kernel as it stands
+MIXED_TRAFFIC_PER_NODE = {"fp32ir": (62.38e9 + 41.47e9) / 320, "tf32x3": None}
 # FP32 pipe: 128 FFMA / SM / clock (measured 73.3 TFLOP/s at ~2.0 GHz); at the 2.07 GHz maximum:
 FP32_PEAK_TFLOPS = 128 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
 
@@ -552,7 +553,8 @@ def main():
     ap.add_argument("--cpu-sample-regions", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the precision-form measurement")
-    ap.add_argument("--only-mixed", action="store_true", help="time only the precision form (profiling runs)")
+    ap.add_argument("--only-mixed", action="store_true", help="time only the precision forms (profiling runs)")
+    ap.add_argument("--mixed-forms", default="fp32ir,tf32x3", help="precision forms --only-mixed times, in order")
     ap.add_argument("--workload", default="delay", choices=["delay", "batched", "screen", "paper_quadratic"])
     ap.add_argument("--trace-problems", type=int, default=2100, help="screen traces: 48 disks per problem")
     ap.add_argument("--epochs", type=int, default=40)
@@ -631,15 +633,17 @@ def main():
         pmcim.pmcim_profile_enable(False)
         return e0.elapsed_time(e1), solves, found, agg, pmcim.pmcim_profile_read(), (w0, w1)
 
-    # forms: the headline is the fastest form at FP64 accuracy (the FP32 LU on the
-    # FMA pipes with FP64 refinement); the tensor-core precision form and plain
-    # FP64 are measured on the same disks beside it
+    # forms: the headline is the faster of the two precision forms (FP32 LU with its
+    # trailing updates on the tensor cores or on the FMA pipes, FP64 refinement),
+    # both at FP64 accuracy; the other form and plain FP64 are measured on the same
+    # disks beside it
     forms = [("fp64", opt)] if args.no_mixed else [("fp32ir", opt_mixed), ("tf32x3", opt_tc), ("fp64", opt)]
     head_name, head_opt = forms[0]
     clocks = ClockSampler(local)
     clocks.start()
     if args.only_mixed:
-        for name, o in forms[:-1] if len(forms) > 1 else forms:
+        by_name = dict(forms)
+        for name, o in [(nm, by_name[nm]) for nm in args.mixed_forms.split(",")]:
             tm_ms, msolves, mfound, aggm, profm, win = timed(o, args.steps, args.warmup)
             if rank == 0:
                 print(json.dumps({"form": name, "solves_per_s": msolves / (tm_ms / 1e3), "ms": tm_ms,
@@ -651,6 +655,12 @@ def main():
         return 0
     runs = {name: timed(o, args.steps, args.warmup) for name, o in forms}
     clocks.stop()
+    if not args.no_mixed:
+        # the headline is the faster precision form on these disks (same work in both; the
+        # max over ranks, so that every rank picks the same one)
+        t_form = {nm: max_over_ranks(runs[nm][0], world) for nm in ("fp32ir", "tf32x3")}
+        head_name = min(t_form, key=t_form.get)
+        head_opt = opt_mixed if head_name == "fp32ir" else opt_tc
     clk = clocks.window(*runs[head_name][5])  # the headline's timed region
     smax = clk.get("sm_max_mhz") or SM_MAX_MHZ
     peak64 = fp64_peak_tflops(smax)
@@ -691,7 +701,8 @@ def main():
         roof = {"bound": "alu", "kernel": "k_factor_solve_mixed (FP64 pipe: refinement residuals)",
                 "achieved": a64, "peak": peak64, "unit": "TFLOP/s",
                 "frac": (a64 / peak64) if a64 else None,
-                "traffic": MIXED_TRAFFIC_PER_NODE * msolves / max(1, fm["launches"]) if MIXED_TRAFFIC_PER_NODE else None,
+                "traffic": (MIXED_TRAFFIC_PER_NODE[name] * msolves / max(1, fm["launches"])
+                            if MIXED_TRAFFIC_PER_NODE.get(name) else None),
                 "traffic_note": "ncu DRAM bytes of a small capture, scaled by nodes per launch",
                 "peak_source": "2 DFMA/SM/clk x 152 SMs x max SM clock",
                 "fp32_work_tflops": a32, "fp32_peak_tflops": FP32_PEAK_TFLOPS,
@@ -728,7 +739,8 @@ def main():
 
     plain = fp64_record(runs["fp64"])
     head = plain if head_name == "fp64" else precision_record(head_name, runs[head_name])
-    other = precision_record("tf32x3", runs["tf32x3"]) if "tf32x3" in runs else None
+    other_name = {"fp32ir": "tf32x3", "tf32x3": "fp32ir"}.get(head_name)
+    other = precision_record(other_name, runs[other_name]) if other_name in runs else None
 
     # ---- e2e: host buffers through the C ABI, copies inside the timed region
     e2e = None
@@ -787,7 +799,8 @@ def main():
             "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if head_name == "fp64" else "f32 LU + f64 refinement",
+            "dtype": {"fp64": "f64", "fp32ir": "f32 LU + f64 refinement",
+                      "tf32x3": "f32 LU (3xTF32 tensor-core updates) + f64 refinement"}[head_name],
             "data": "synthetic",
             "config": {"workload": "delay NEP T(z)=-zI+A0+A1 exp(-z), n=1024, l=16, N=64, "
                                    "Omega=[-3,1]x[-6,6] split 16x48; %d disks per step per GPU" % B,
@@ -798,7 +811,7 @@ def main():
             "speedup_vs_plain_fp64": (head["value"] / plain["value"]) if head is not plain else 1.0,
             "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "kernels": prof, "plain_fp64": plain if head is not plain else None,
-            "precision_form_tc": other, "clocks": clk,
+            "other_precision_form": other, "clocks": clk,
         }
         for key in ("tensor", "ir_sweeps_per_node", "ir_fallbacks", "tc_timeouts"):
             if key in head:

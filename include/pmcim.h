@@ -95,7 +95,7 @@ typedef struct {
   double tol_svd;          /* absolute singular-value threshold, 1e-6 (Sec. 3.2)        */
   double tol_verify;       /* sigma_min acceptance, 1e-6 (pmCIMb step 3.b)              */
   int32_t precision;       /* PMCIM_PREC_*                                             */
-  int32_t max_ir_sweeps;   /* refinement sweeps for reduced precision (default 3)      */
+  int32_t max_ir_sweeps;   /* refinement sweeps for reduced precision (default 6)      */
   int32_t max_split_depth; /* splits of saturated disks (default 8)                    */
   /* moment pairs of Beyn's step (default 1, Eq. 2.8 on C0 and C1). K > 1
      (at most 8, K l <= 64): the block Hankel matrices of the 2K moments
@@ -340,7 +340,9 @@ typedef struct {
   /* precision-form node kernel, with timing on: SM clock cycles summed over
      CTAs per phase: assembly, LU panels, first solve, FP64 residual,
      correction solves, FP64 fallback, node set-up, LU triangular solves
-     (U12), LU trailing updates, 3 unused */
+     (U12), LU trailing updates, factor group waiting for a free slot, refine
+     group waiting for a factored node; the last entry is the CTAs' lifetimes
+     in ns (globaltimer), summed */
   double mixed_phase_cycles[PMCIM_PHASE_COUNT];
 } pmcim_profile;
 

@@ -1216,7 +1216,7 @@ void pmcim_default_options(pmcim_options* opt) {
   opt->tol_svd = 1e-6;
   opt->tol_verify = 1e-6;
   opt->precision = PMCIM_PREC_FP64;
-  opt->max_ir_sweeps = 3;
+  opt->max_ir_sweeps = 6;
   opt->max_split_depth = 8;
   opt->cuda_stream = nullptr;
   opt->screen_params = nullptr;

@@ -375,22 +375,31 @@ __device__ void cta_perm_fwd_subst(T2* __restrict__ M, int n, int l, const int* 
 // Two barriers per block instead of two per row.
 // ---------------------------------------------------------------------------
 
-// Y[i, :] -= M[i, k0:k0+kb] * S where S (kb x l) sits in sm.Us ([t][c]);
-// columns in chunks of 8 kept in registers, so M is read once per chunk.
+// Y[i, :] -= M[i, k0:k0+kb] * S where S (kb x l) sits in sm.Us ([t][c]).
+// Columns in register chunks (16 complex64 or 8 complex128), so M is read once
+// per chunk; the M elements of 8 steps are loaded before they are used, so that
+// their memory latencies overlap instead of adding up.
 template <typename T2>
 __device__ __forceinline__ void block_update_row(const T2* __restrict__ M, T2* __restrict__ Y, size_t ld, int i,
                                                  int k0, int kb, int l, LuSmemT<T2>& sm) {
-  for (int c0 = 0; c0 < l; c0 += 8) {
-    T2 acc[8];
+  constexpr int CH = sizeof(T2) == 8 ? 16 : 8;
+  for (int c0 = 0; c0 < l; c0 += CH) {
+    T2 acc[CH];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = (c0 + q < l) ? Y[(size_t)(c0 + q) * ld + i] : czero<T2>();
-    for (int t = 0; t < kb; ++t) {
-      const T2 m = M[(size_t)(k0 + t) * ld + i];
+    for (int q = 0; q < CH; ++q) acc[q] = (c0 + q < l) ? Y[(size_t)(c0 + q) * ld + i] : czero<T2>();
+    for (int t0 = 0; t0 < kb; t0 += 8) {
+      T2 m[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) cfms(acc[q], m, sm.Us[t * US_LD + c0 + q]);
+      for (int u = 0; u < 8; ++u) m[u] = (t0 + u < kb) ? M[(size_t)(k0 + t0 + u) * ld + i] : czero<T2>();
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (t0 + u < kb) {  // rows of S past kb hold stale values
+#pragma unroll
+          for (int q = 0; q < CH; ++q) cfms(acc[q], m[u], sm.Us[(t0 + u) * US_LD + c0 + q]);
+        }
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
+    for (int q = 0; q < CH; ++q)
       if (c0 + q < l) Y[(size_t)(c0 + q) * ld + i] = acc[q];
   }
 }

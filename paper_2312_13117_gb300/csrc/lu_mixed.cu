@@ -155,7 +155,15 @@ struct PhaseClock {
 // solve, set-up, waiting for a free slot; refine group: residual, correction
 // solves, fallback, waiting for a factored node.
 enum { PH_ASSEMBLE = 0, PH_PANEL = 1, PH_FIRST_SOLVE = 2, PH_RESIDUAL = 3, PH_CORRECTION = 4, PH_FALLBACK = 5,
-       PH_SETUP = 6, PH_TRSM = 7, PH_UPDATE = 8, PH_FACTOR_WAIT = 9, PH_REFINE_WAIT = 10 };
+       PH_SETUP = 6, PH_TRSM = 7, PH_UPDATE = 8, PH_FACTOR_WAIT = 9, PH_REFINE_WAIT = 10,
+       PH_CTA_WALL_NS = 11 };  // the last holds ns of CTA lifetime, not cycles
+static_assert(PH_CTA_WALL_NS < PMCIM_PHASES, "phase slots");
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // The FP32 blocked LU of lucore::cta_lu, with the trailing updates on the
 // tensor cores (use_tc, while no wait has run out) or on the FMA pipes.
@@ -575,6 +583,8 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_factor_solve_mixed(NodeArgs 
   MixedSmem& sm = *reinterpret_cast<MixedSmem*>(smem_raw);
   const int tid = threadIdx.x;
   PhaseClock pc(a.phase ? a.phase + (size_t)blockIdx.x * PMCIM_PHASES : nullptr);
+  unsigned long long t_start = 0;
+  if (a.phase && tid == 0) t_start = global_ns();
 
   // tensor memory (factor group's warp 0) and the barriers, for the whole persistent CTA
   if (tid < 32) tcu::tmem_alloc(&sm.tmem_base);
@@ -608,6 +618,10 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_factor_solve_mixed(NodeArgs 
     if (tid < 32) tcu::tmem_dealloc(cx.tmem);
   } else {
     refine_group(a, sm, pc);
+  }
+  if (a.phase) {  // the CTA's lifetime, for cycles per ns
+    __syncthreads();
+    if (tid == 0) a.phase[(size_t)blockIdx.x * PMCIM_PHASES + PH_CTA_WALL_NS] += global_ns() - t_start;
   }
 }
 

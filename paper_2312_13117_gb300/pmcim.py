@@ -174,12 +174,14 @@ def pmcim_profile_read() -> dict:
     load().pmcim_profile_read(C.byref(pr))
     out = {k: {"launches": int(pr.launches[i]), "ms": float(pr.ms[i])} for i, k in enumerate(KERNELS)}
     cyc = [float(x) for x in pr.mixed_phase_cycles]
+    wall_ns = cyc[11]  # slot 11: CTA lifetimes in ns (globaltimer), not cycles
+    cyc[11] = 0.0
     tot = sum(cyc)
     if tot > 0:
         # the node kernel runs two thread groups side by side: each phase is given
         # as a share of its own group's clock
         names = ["assemble", "lu_panel", "first_solve", "residual_fp64", "correction_solve", "fp64_fallback",
-                 "node_setup", "lu_trsm", "lu_update", "factor_wait", "refine_wait", "unused11"]
+                 "node_setup", "lu_trsm", "lu_update", "factor_wait", "refine_wait", "cta_wall"]
         factor = {0, 1, 2, 6, 7, 8, 9}
         tot_f = sum(c for i, c in enumerate(cyc) if i in factor) or 1.0
         tot_r = sum(c for i, c in enumerate(cyc) if i not in factor) or 1.0
@@ -187,6 +189,11 @@ def pmcim_profile_read() -> dict:
         share["lu_fp32"] = sum(share.get(k, 0.0) for k in ("lu_panel", "lu_trsm", "lu_update"))
         out["factor_fp32"]["phase_share"] = share
         out["factor_fp32"]["phase_cycles"] = {nm: c for nm, c in zip(names, cyc) if c > 0}
+        if wall_ns > 0:
+            # SM cycles the refine group accounted for per ns of CTA lifetime: the
+            # effective SM clock the node kernel ran at, in GHz
+            out["factor_fp32"]["cta_wall_ns"] = wall_ns
+            out["factor_fp32"]["effective_clock_ghz"] = tot_r / wall_ns
     return out
 
 
@@ -225,7 +232,7 @@ def regions_array(regions: Sequence) -> C.Array:
 _screen_keep = []
 
 
-def options(tol_ind=0.1, tol_svd=1e-6, tol_verify=1e-6, precision=PREC_FP64, max_ir_sweeps=3,
+def options(tol_ind=0.1, tol_svd=1e-6, tol_verify=1e-6, precision=PREC_FP64, max_ir_sweeps=6,
             max_split_depth=8, stream=None, screen_params=None, screen_threshold=0.0,
             screen_N=16, tol_ir=None, indicator_N=0, beyn_K=1) -> pmcim_options:
     o = pmcim_default_options()

@@ -40,7 +40,7 @@ def test_status_strings_and_defaults(lib):
     o = pmcim.pmcim_default_options()
     assert (o.tol_ind, o.tol_svd, o.tol_verify) == (0.1, 1e-6, 1e-6)
     assert o.max_split_depth == 8 and o.precision == pmcim.PREC_FP64
-    assert o.tol_ir == 1e-11 and o.indicator_N == 0 and o.max_ir_sweeps == 3
+    assert o.tol_ir == 1e-11 and o.indicator_N == 0 and o.max_ir_sweeps == 6
     # the binding's struct has the header's size: the last field lands where the library writes it
     assert ctypes.sizeof(pmcim.pmcim_options) == pmcim.pmcim_options.tol_ir.offset + 8
     lib.pmcim_status_string.restype = ctypes.c_char_p

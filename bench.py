@@ -43,7 +43,7 @@ FACTOR_FP64_TRAFFIC_PER_NODE = 28.61e9 / 64
 # DRAM bytes per node of k_factor_solve_mixed, from one ncu capture of a 320-node launch per form
 # (dram__bytes_read.sum + dram__bytes_write.sum); scaled to a launch by its node count. None: no
 # capture of the kernel as it stands
-MIXED_TRAFFIC_PER_NODE = {"fp32ir": (62.38e9 + 41.47e9) / 320, "tf32x3": None}
+MIXED_TRAFFIC_PER_NODE = {"fp32ir": (62.38e9 + 41.47e9) / 320, "tf32x3": (60.83e9 + 41.60e9) / 320}
 # FP32 pipe: 128 FFMA / SM / clock (measured 73.3 TFLOP/s at ~2.0 GHz); at the 2.07 GHz maximum:
 FP32_PEAK_TFLOPS = 128 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
 
@@ -492,21 +492,23 @@ def run_paper_quadratic(args, world, rank, local):
     return 0
 
 
-def run_full(args, P, W, opt, opt_mixed, world, rank, local):
-    """Time to all eigenvalues: one pmCIMb pass over the whole grid per form
-    (opt_mixed: the FP32-LU precision form), each also with the two-pass schedule."""
+def run_full(args, P, W, opt, opt_mixed, opt_tc, world, rank, local):
+    """Time to all eigenvalues: one pmCIMb pass over the whole grid per form (opt_tc: the
+    precision form with tensor-core trailing updates, opt_mixed: the same on the FMA pipes,
+    opt: plain FP64), the tensor-core and FP64 forms also with the two-pass schedule."""
     import torch
     from paper_2312_13117_gb300 import pmcim
     R = len(W.regions)
     mine = [W.regions[g] for g in range(rank, R, world)]
     out = {}
     lams = {}
-    o2 = pmcim.options(stream=opt_mixed.cuda_stream, precision=opt_mixed.precision, indicator_N=args.indicator_n)
+    o2 = pmcim.options(stream=opt_tc.cuda_stream, precision=opt_tc.precision, indicator_N=args.indicator_n)
     f2 = pmcim.options(stream=opt.cuda_stream, precision=opt.precision, indicator_N=args.indicator_n)
-    o3 = pmcim.options(stream=opt_mixed.cuda_stream, precision=opt_mixed.precision, indicator_N=args.indicator_n,
+    o3 = pmcim.options(stream=opt_tc.cuda_stream, precision=opt_tc.precision, indicator_N=args.indicator_n,
                        beyn_K=2)
-    for name, o in (("precision_form", opt_mixed), ("precision_form_two_pass", o2),
-                    ("precision_form_two_pass_hankel2", o3), ("fp64", opt), ("fp64_two_pass", f2)):
+    for name, o in (("precision_form", opt_tc), ("precision_form_fma_pipes", opt_mixed),
+                    ("precision_form_two_pass", o2), ("precision_form_two_pass_hankel2", o3), ("fp64", opt),
+                    ("fp64_two_pass", f2)):
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
@@ -527,6 +529,10 @@ def run_full(args, P, W, opt, opt_mixed, world, rank, local):
                           "workload": "delay NEP n=1024, l=16, N=64, Omega=[-3,1]x[-6,6] 16x48",
                           "forms": out, "max_rel_lambda_diff_fp64_vs_precision_form": err,
                           "speedup": out["fp64"]["seconds"] / out["precision_form"]["seconds"],
+                          "speedup_fma_pipes_form": out["fp64"]["seconds"] /
+                          out["precision_form_fma_pipes"]["seconds"],
+                          "max_rel_lambda_diff_fp64_vs_fma_pipes_form": _max_rel_diff(
+                              lams["fp64"], lams["precision_form_fma_pipes"]),
                           "indicator_N": args.indicator_n,
                           "speedup_two_pass_precision_vs_fp64": out["fp64"]["seconds"] /
                           out["precision_form_two_pass"]["seconds"],
@@ -603,7 +609,7 @@ def main():
     cap = 64 * l * B
 
     if args.full:
-        return run_full(args, P, W, opt, opt_mixed, world, rank, local)
+        return run_full(args, P, W, opt, opt_mixed, opt_tc, world, rank, local)
 
     def timed(o, steps, warmup):
         """Warm up, then time `steps` steps on the library's stream; returns (ms, solves, found, stats, prof)."""

@@ -697,7 +697,7 @@ def main():
         tm_max = max_over_ranks(tm_ms, world)
         fm = profm["factor_fp32"]
         # FP64 work: per sweep one residual product T(z)X (T(z) assembled in FP64 once per node
-        # when the problem has two or more dense terms), plus the fallback solves
+        # by the factor group when the problem has two or more dense terms), plus the fallback solves
         w_asm = msolves * 8.0 * k_dense * n * n if k_dense >= 2 else 0.0
         w_res = aggm["ir_sweeps"] * 8.0 * n * n * l
         w64 = w_res + w_asm + aggm["ir_fallbacks"] * (8.0 * n ** 3 / 3 + 8.0 * n * n * l)
@@ -718,7 +718,7 @@ def main():
         if cyc.get("residual_fp64"):
             # SM clock cycles of the refine group inside the residual phase, summed over CTAs
             # (one CTA per SM): the FP64 pipe's rate while the residual runs
-            roof["residual_dfma_per_sm_clock"] = (w_res + w_asm) / 2.0 / cyc["residual_fp64"]
+            roof["residual_dfma_per_sm_clock"] = w_res / 2.0 / cyc["residual_fp64"]
             roof["peak_dfma_per_sm_clock"] = FP64_DFMA_PER_SM_CLK
         rec = {
             "form": ("FP32 LU + FP64 iterative refinement (residual R = V - T(z)X, T(z) assembled in FP64)"

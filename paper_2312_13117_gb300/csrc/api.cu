@@ -620,14 +620,14 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
     // one CTA per SM, each cycling through mixed_slots_per_cta() slots
     slot32 = mixed_slot_bytes(max_n, max_l);
     const size_t per = (size_t)mixed_slots_per_cta();
-    t64_stride = (size_t)t64_n * t64_n;  // the refine group's FP64 T(z_j)
-    const size_t cta_bytes = per * slot32 + t64_stride * sizeof(double2);
+    t64_stride = (size_t)t64_n * t64_n;  // FP64 T(z_j) of each slot
+    const size_t cta_bytes = per * (slot32 + t64_stride * sizeof(double2));
     const size_t ctas = std::max<size_t>(1, std::min<size_t>(std::min<size_t>(sms, kSlotBytes / cta_bytes),
                                                              total_nodes));
     slots32 = (int)(ctas * per);
     CU(ws.work32.ensure((size_t)slots32 * slot32));
     CU(ws.piv32.ensure((size_t)slots32 * max_n * sizeof(int32_t)));
-    if (t64_stride) CU(ws.t64.ensure(ctas * t64_stride * sizeof(double2)));
+    if (t64_stride) CU(ws.t64.ensure((size_t)slots32 * t64_stride * sizeof(double2)));
   }
   const bool timed = prof_on();
   if (timed && any32) {

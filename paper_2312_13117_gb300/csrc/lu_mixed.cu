@@ -202,8 +202,9 @@ __device__ double block_max(double v, double* red) {
 // R = V - sum_k f_k(z) A_k X  (FP64), R and X column-major n x l.
 // R = V - id X - f_M M X in FP64 (the refinement residual), M an n x n column-major
 // matrix (NULL: none). With two or more dense terms M is T(z_j) itself, assembled
-// once per node (f_M = 1, id = 0), so that a sweep multiplies X by one matrix
-// instead of one per term; with a single dense term M is that term's A_k.
+// in FP64 once per node by the factor group (f_M = 1, id = 0), so that a sweep
+// multiplies X by one matrix instead of one per term; with a single dense term M
+// is that term's A_k.
 __device__ void residual_fp64(const double2* __restrict__ X, double2* __restrict__ R, const NodeCtx& cx,
                               ResSmem& rs, const double2* __restrict__ M, double2 fM, double2 id) {
   const ProblemDev& P = cx.P;
@@ -275,27 +276,51 @@ __device__ void residual_fp64(const double2* __restrict__ X, double2* __restrict
   gsync();
 }
 
-// T(z_j) in FP64 into T (n x n, column-major) for the refinement residuals: the
-// dense terms in one pass over the elements, then the identity terms on the
-// diagonal.
-__device__ void assemble_t64(const NodeCtx& cx, double2* __restrict__ T) {
+// T(z_j) in FP64 into T (n x n, column-major), the matrix of the refinement
+// residuals, and rounded to complex64 into M32 (leading dimension n), the FP32
+// LU's matrix: the dense terms in one pass over the elements, four elements per
+// thread at a time so that their coefficient loads overlap, then the identity
+// terms on the diagonal.
+__device__ void assemble_fp64(const NodeCtx& cx, double2* __restrict__ T, float2* __restrict__ M32) {
   const ProblemDev& P = cx.P;
   const int n = P.n;
   const size_t nn = (size_t)n * n;
   double2 id = make_double2(0.0, 0.0);
   for (int k = 0; k < P.K; ++k)
     if (!P.term[k].dense) id = cadd(id, cmul(cx.fz[k], P.term[k].id));
-#pragma unroll 4
-  for (size_t e = gtid(); e < nn; e += THREADS) {
-    double2 v = make_double2(0.0, 0.0);
+  for (size_t e0 = gtid(); e0 < nn; e0 += 4 * (size_t)THREADS) {
+    double2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = make_double2(0.0, 0.0);
     for (int k = 0; k < P.K; ++k) {
       const TermDesc& t = P.term[k];
-      if (t.dense) cfma(v, cx.fz[k], P.A[(size_t)t.mat_index * nn + e]);
+      if (!t.dense) continue;
+      const double2* __restrict__ A = P.A + (size_t)t.mat_index * nn;
+      double2 a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const size_t e = e0 + (size_t)u * THREADS;
+        a[u] = e < nn ? A[e] : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) cfma(v[u], cx.fz[k], a[u]);
     }
-    T[e] = v;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const size_t e = e0 + (size_t)u * THREADS;
+      if (e < nn) {
+        T[e] = v[u];
+        M32[e] = make_float2((float)v[u].x, (float)v[u].y);
+      }
+    }
   }
   gsync();
-  for (int i = gtid(); i < n; i += THREADS) T[(size_t)i * n + i] = cadd(T[(size_t)i * n + i], id);
+  for (int i = gtid(); i < n; i += THREADS) {
+    const size_t e = (size_t)i * n + i;
+    const double2 t = cadd(T[e], id);
+    T[e] = t;
+    M32[e] = make_float2((float)t.x, (float)t.y);
+  }
   gsync();
 }
 
@@ -423,7 +448,10 @@ __device__ void factor_group(const NodeArgs& a, MixedSmem& sm, tcu::Ctx& cx, Pha
     int* perm = reinterpret_cast<int*>(slot + mixed_residual_offset(n, l) + nl * sizeof(double2));
     double2* X = a.X + rg.x_off + (size_t)it.j * nl;
     pc.mark(PH_SETUP);
-    assemble32(c, M32);
+    if (P.n_dense >= 2)  // T(z_j) in FP64 for the refine group, and rounded for the LU
+      assemble_fp64(c, a.t64 + si * a.t64_stride, M32);
+    else
+      assemble32(c, M32);
     for (size_t e = tid; e < nl; e += THREADS) M32[nn + e] = make_float2((float)P.V[e].x, (float)P.V[e].y);
     gsync();
     pc.mark(PH_ASSEMBLE);
@@ -501,10 +529,8 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
       // the matrix each residual multiplies: T(z_j) assembled once, or the one dense term
       const double2* M = nullptr;
       double2 fM = make_double2(0.0, 0.0), id = make_double2(0.0, 0.0);
-      if (P.n_dense >= 2) {
-        double2* T = a.t64 + (size_t)blockIdx.x * a.t64_stride;
-        assemble_t64(c, T);
-        M = T;
+      if (P.n_dense >= 2) {  // assembled by the factor group with the slot
+        M = a.t64 + si * a.t64_stride;
         fM = make_double2(1.0, 0.0);
       } else {
         for (int k = 0; k < P.K; ++k) {

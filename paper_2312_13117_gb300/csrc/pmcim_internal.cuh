@@ -206,8 +206,8 @@ struct NodeArgs {
   double tol_ir;
   unsigned long long* phase;  // NULL, or slots * PMCIM_PHASES clock64 counters (mixed kernel)
   int32_t* err;               // mixed kernel: set to 1 when a wait between its thread groups ran out
-  double2* t64;               // mixed kernel: per CTA, T(z_j) in FP64 for the residuals (problems
-  size_t t64_stride;          // with two or more dense terms); double2 elements per CTA
+  double2* t64;               // mixed kernel: per slot, T(z_j) in FP64 for the residuals (problems
+  size_t t64_stride;          // with two or more dense terms); double2 elements per slot
 };
 cudaError_t prepare_factor_fp64();   // shared-memory limits; call outside graph capture
 cudaError_t prepare_factor_mixed();

@@ -336,38 +336,6 @@ __device__ void cta_back_subst(T2* __restrict__ M, int n, int l, LuSmemT<T2>& sm
   }
 }
 
-// Row swaps of the factorisation applied to the l columns n..n+l-1 of M, then
-// forward substitution with the unit lower factor L, in place.
-template <typename T2>
-__device__ void cta_perm_fwd_subst(T2* __restrict__ M, int n, int l, const int* __restrict__ piv,
-                                   LuSmemT<T2>& sm) {
-  const int tid = gtid();
-  const size_t ld = (size_t)n;
-  T2* Y = M + (size_t)n * ld;
-  if (tid < l) {
-    T2* y = Y + (size_t)tid * ld;
-    for (int k = 0; k < n; ++k) {
-      const int p = piv[k];
-      if (p != k) {
-        T2 t = y[k];
-        y[k] = y[p];
-        y[p] = t;
-      }
-    }
-  }
-  gsync();
-  for (int j = 0; j < n; ++j) {
-    if (tid < l) sm.bcast[tid] = Y[(size_t)tid * ld + j];
-    gsync();
-    const T2* lj = M + (size_t)j * ld;
-    for (int i = j + 1 + tid; i < n; i += THREADS) {
-      const T2 u = lj[i];
-      for (int c = 0; c < l; ++c) cfms(Y[(size_t)c * ld + i], u, sm.bcast[c]);
-    }
-    gsync();
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Blocked triangular solves on the l columns n..n+l-1 of M (32-row blocks):
 // the 32 x 32 diagonal block is solved one warp per column (lane = row), then

@@ -25,7 +25,6 @@ __host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return 
 __host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 __host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
-__device__ __forceinline__ double cabs_(double2 a) { return hypot(a.x, a.y); }
 // acc -= a * b
 __device__ __forceinline__ void cfms(double2& acc, double2 a, double2 b) {
   acc.x = fma(-a.x, b.x, acc.x);

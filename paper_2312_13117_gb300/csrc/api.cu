@@ -97,8 +97,9 @@ struct DevBuf {
 
 // Upper bound on the node solutions kept before one reduction (one HBM wave).
 constexpr size_t kWaveBytes = size_t(16) << 30;
-// Upper bound on the per-CTA factorisation workspaces of one form.
-constexpr size_t kSlotBytes = size_t(24) << 30;
+// Upper bound on the per-CTA factorisation workspaces of one form: at n = 2048 the
+// precision form's 152 CTAs need 41 GB (two complex64 slots and two FP64 T(z_j) each).
+constexpr size_t kSlotBytes = size_t(48) << 30;
 // indicator-pass solutions kept for reuse by the two-pass schedule, per chunk of disks
 constexpr size_t kKeepBytes = size_t(8) << 30;
 // largest pmCIMa level (disks); beyond it the indicator is marking noise

@@ -152,7 +152,8 @@ typedef struct {
 typedef struct pmcim_problem_s* pmcim_problem;
 
 /* Fill *opt with the paper's parameters (tol_ind 0.1, tol_svd 1e-6,
-   tol_verify 1e-6), FP64, 3 refinement sweeps, split depth 8, default stream. */
+   tol_verify 1e-6), FP64, up to 6 refinement sweeps, split depth 8, default
+   stream. */
 void pmcim_default_options(pmcim_options* opt);
 
 /* Create a problem handle for T(z) = sum_{k<K} f_k(z) A_k  (Sec. 1).

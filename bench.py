@@ -432,6 +432,22 @@ def _max_rel_diff(a, b):
     return float(np.max(np.abs(a[ri] - b[ci]) / np.maximum(1.0, np.abs(a[ri]))))
 
 
+def _oracle_golden():
+    """Verified eigenvalues of the CPU oracle on every disk of the n = 1024 delay workload
+    (tol_svd = 1e-6), by disk, from the stored results tests/golden/make_oracle_golden.py
+    wrote; None when the file is absent."""
+    path = os.path.join(ROOT, "tests", "golden", "delay_n1024_oracle.json")
+    try:
+        with open(path) as fh:
+            run = json.load(fh)["runs"][repr(1e-6)]
+    except (OSError, KeyError, ValueError):
+        return None
+    out = {}
+    for (re_, im_, _sig, g) in run["lam"]:
+        out.setdefault(int(g), []).append(complex(re_, im_))
+    return out
+
+
 def _same_lams(a, b, tol=1e-10):
     """Both eigenvalue lists hold the same values (relative tol), matched one to one."""
     d = _max_rel_diff(a, b)
@@ -572,6 +588,8 @@ def main():
                     help="moment pairs of the block Hankel Beyn legs (--workload batched: 4, --full: 2)")
     ap.add_argument("--indicator-n", type=int, default=16,
                     help="coarse indicator rule of the two-pass legs (--full, --workload screen)")
+    ap.add_argument("--no-time-to-all", action="store_true",
+                    help="skip the passes over every disk (time to all eigenvalues; about 3 minutes)")
     ap.add_argument("--full", action="store_true",
                     help="time pmCIMb over all 768 disks (time to all eigenvalues), FP64 and precision form")
     args = ap.parse_args()
@@ -626,8 +644,10 @@ def main():
         w0 = time.monotonic()
         solves, found = 0, 0
         agg = {}
+        per_step = []
         for k in range(steps):
             res = P.solve(batch(k), W.V, cap=cap, opt=o)
+            per_step.append((k, res["lam"], res["region_of"]))
             solves += res["stats"]["solves"]
             found += len(res["lam"])
             for key, v in res["stats"].items():
@@ -637,20 +657,29 @@ def main():
         w1 = time.monotonic()
         barrier(world)
         pmcim.pmcim_profile_enable(False)
-        return e0.elapsed_time(e1), solves, found, agg, pmcim.pmcim_profile_read(), (w0, w1)
+        # eigenvalues of the timed steps by grid disk (first visit of a disk only)
+        by_disk = {}
+        for k, lam, rof in per_step:
+            ids = disk_ids(k, rank, world, B, R, args.region_offset)
+            step = {}
+            for x, q in zip(lam, rof):
+                step.setdefault(ids[int(q)], []).append(complex(x))
+            for g in ids:
+                by_disk.setdefault(g, step.get(g, []))
+        return e0.elapsed_time(e1), solves, found, agg, pmcim.pmcim_profile_read(), (w0, w1), by_disk
 
     # forms: the headline is the faster of the two precision forms (FP32 LU with its
     # trailing updates on the tensor cores or on the FMA pipes, FP64 refinement),
     # both at FP64 accuracy; the other form and plain FP64 are measured on the same
     # disks beside it
-    forms = [("fp64", opt)] if args.no_mixed else [("fp32ir", opt_mixed), ("tf32x3", opt_tc), ("fp64", opt)]
+    forms = [("fp64", opt)] if args.no_mixed else [("fp32ir", opt_mixed), ("tf32x3", opt_tc)]
     head_name, head_opt = forms[0]
     clocks = ClockSampler(local)
     clocks.start()
     if args.only_mixed:
         by_name = dict(forms)
         for name, o in [(nm, by_name[nm]) for nm in args.mixed_forms.split(",")]:
-            tm_ms, msolves, mfound, aggm, profm, win = timed(o, args.steps, args.warmup)
+            tm_ms, msolves, mfound, aggm, profm, win, _ = timed(o, args.steps, args.warmup)
             if rank == 0:
                 print(json.dumps({"form": name, "solves_per_s": msolves / (tm_ms / 1e3), "ms": tm_ms,
                                   "stats": aggm, "kernels": profm}))
@@ -660,7 +689,6 @@ def main():
         P.close()
         return 0
     runs = {name: timed(o, args.steps, args.warmup) for name, o in forms}
-    clocks.stop()
     if not args.no_mixed:
         # the headline is the faster precision form on these disks (same work in both; the
         # max over ranks, so that every rank picks the same one)
@@ -671,13 +699,55 @@ def main():
     smax = clk.get("sm_max_mhz") or SM_MAX_MHZ
     peak64 = fp64_peak_tflops(smax)
     k_dense = sum(1 for t in W.problem.terms if not np.isscalar(t[0]))
-    t_fp64 = max_over_ranks(runs["fp64"][0], world)
-    found_fp64 = runs["fp64"][2]
 
-    def fp64_record(run):
-        t_ms, solves, found, agg, prof, win = run
-        t_max = max_over_ranks(t_ms, world)
-        fac = prof["factor_fp64"]
+    # ---- time to all eigenvalues: one pmCIMb pass over every disk of the grid (this
+    # rank's share), in the headline form, in its two-pass schedule and in plain FP64
+    mine = list(range(rank, R, world))
+
+    def full_pass(o):
+        torch.cuda.synchronize()
+        pmcim.pmcim_profile_reset()
+        pmcim.pmcim_profile_enable(True)
+        barrier(world)
+        w0 = time.monotonic()
+        t0 = time.perf_counter()
+        res = P.solve([W.regions[g] for g in mine], W.V, cap=64 * l * len(mine), opt=o)
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+        w1 = time.monotonic()
+        pmcim.pmcim_profile_enable(False)
+        by_disk = {g: [] for g in mine}
+        for x, q in zip(res["lam"], res["region_of"]):
+            by_disk[mine[int(q)]].append(complex(x))
+        return {"seconds": dt, "res": res, "by_disk": by_disk, "clocks": clocks.window(w0, w1),
+                "kernels": pmcim.pmcim_profile_read()}
+
+    tta = {}
+    if not args.no_time_to_all:
+        o2 = pmcim.options(stream=stream.cuda_stream, precision=head_opt.precision, indicator_N=args.indicator_n)
+        legs = [(head_name, head_opt)] if head_name != "fp64" else []
+        legs += [(head_name + "_two_pass", o2), ("fp64", opt)]
+        for name, o in legs:
+            tta[name] = full_pass(o)
+    clocks.stop()
+
+    gold = _oracle_golden()
+
+    def lam_diff(a_by_disk, b_by_disk, disks):
+        """Largest relative eigenvalue difference over the given disks (one-to-one match
+        per disk; None when a disk's counts differ)."""
+        worst = 0.0
+        for g in disks:
+            d = _max_rel_diff(a_by_disk.get(g, []), b_by_disk.get(g, []))
+            if d is None:
+                return None
+            worst = max(worst, d)
+        return worst
+
+    def fp64_record(fp):
+        res = fp["res"]
+        solves = res["stats"]["solves"]
+        fac = fp["kernels"]["factor_fp64"]
         flops_per_node = 8.0 * n ** 3 / 3.0 + 8.0 * n * n * l
         achieved = (flops_per_node * solves) / (fac["ms"] / 1e3) / 1e12 if fac["ms"] > 0 else None
         roof = {"bound": "alu", "kernel": "k_factor_solve_fp64 (FP64 pipe)",
@@ -686,14 +756,14 @@ def main():
                 "traffic": FACTOR_FP64_TRAFFIC_PER_NODE * solves / max(1, fac["launches"]),
                 "traffic_note": "ncu DRAM bytes of a 64-node capture, scaled by nodes per launch",
                 "peak_source": "2 DFMA/SM/clk x 152 SMs x max SM clock (probe: 1.20 TFLOP/s at 2.0 GHz)",
-                "launches": fac["launches"], "avg_launch_ms": fac["ms"] / max(1, fac["launches"]),
-                "share_of_step": fac["ms"] / t_ms if t_ms else None}
-        return {"form": "plain FP64 LU", "value": sum_over_ranks(float(solves), world) / (t_max / 1e3),
-                "unit": UNIT, "ms_per_step": t_max / args.steps, "eigenvalues_found": found,
-                "roofline": roof, "kernels": prof, "clocks": clocks.window(*win)}
+                "launches": fac["launches"], "avg_launch_ms": fac["ms"] / max(1, fac["launches"])}
+        return {"form": "plain FP64 LU (all disks of the grid, one pmCIMb pass)",
+                "value": sum_over_ranks(float(solves), world) / fp["seconds"], "unit": UNIT,
+                "seconds": fp["seconds"], "eigenvalues_found": len(res["lam"]),
+                "roofline": roof, "kernels": fp["kernels"], "clocks": fp["clocks"]}
 
     def precision_record(name, run):
-        tm_ms, msolves, mfound, aggm, profm, win = run
+        tm_ms, msolves, mfound, aggm, profm, win, _ = run
         tm_max = max_over_ranks(tm_ms, world)
         fm = profm["factor_fp32"]
         # FP64 work: per sweep one residual product T(z)X (T(z) assembled in FP64 once per node
@@ -726,10 +796,10 @@ def main():
                      "FP32 LU with 3xTF32 complex trailing updates on the tensor cores (tcgen05, TMEM "
                      "accumulators) + FP64 iterative refinement"),
             "value": sum_over_ranks(float(msolves), world) / (tm_max / 1e3), "unit": UNIT,
-            "ms_per_step": tm_max / args.steps, "speedup_vs_fp64": t_fp64 / tm_max,
-            "eigenvalues_found": mfound, "eigenvalues_found_fp64": found_fp64,
+            "ms_per_step": tm_max / args.steps, "eigenvalues_found": mfound,
             "ir_sweeps_per_node": aggm["ir_sweeps"] / max(1, msolves), "ir_fallbacks": aggm["ir_fallbacks"],
-            "tc_timeouts": aggm.get("tc_timeouts", 0),
+            "tc_timeouts": aggm.get("tc_timeouts", 0), "certified": aggm.get("certified", 0),
+            "unverified": aggm.get("unverified", 0),
             "roofline": roof, "kernels": profm, "clocks": clocks.window(*win),
         }
         if name == "tf32x3":
@@ -743,10 +813,53 @@ def main():
                              "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
         return rec
 
-    plain = fp64_record(runs["fp64"])
-    head = plain if head_name == "fp64" else precision_record(head_name, runs[head_name])
+    plain = fp64_record(tta["fp64"]) if "fp64" in tta else None
+    head = precision_record(head_name, runs[head_name]) if head_name != "fp64" else None
+    if head is None:   # --no-mixed: plain FP64 steps only
+        tm_ms, msolves, mfound, aggm, profm, win, _ = runs["fp64"]
+        tm_max = max_over_ranks(tm_ms, world)
+        head = {"form": "plain FP64 LU", "value": sum_over_ranks(float(msolves), world) / (tm_max / 1e3),
+                "unit": UNIT, "ms_per_step": tm_max / args.steps, "eigenvalues_found": mfound,
+                "roofline": None, "kernels": profm, "clocks": clocks.window(*win)}
     other_name = {"fp32ir": "tf32x3", "tf32x3": "fp32ir"}.get(head_name)
     other = precision_record(other_name, runs[other_name]) if other_name in runs else None
+    if plain is not None:
+        for rec in (head, other):
+            if rec is not None and rec is not plain:
+                rec["speedup_vs_fp64_solves_per_s"] = rec["value"] / plain["value"]
+
+    # ---- the accuracy qualifier of the metric, computed in this run: eigenvalues of the
+    # timed steps against plain FP64 and against the stored oracle results on the same disks
+    head_by_disk = runs[head_name][6]
+    step_disks = sorted(head_by_disk)
+    lam_err = {"bound": 1e-10,
+               "measure": "max |d lambda| / max(1, |lambda|) over one-to-one matched eigenvalues per disk"}
+    if "fp64" in tta:
+        lam_err["timed_steps_vs_fp64"] = lam_diff(head_by_disk, tta["fp64"]["by_disk"], step_disks)
+    if gold is not None:
+        lam_err["timed_steps_vs_oracle"] = lam_diff(head_by_disk, gold, step_disks)
+    for name, fp in tta.items():
+        if "fp64" in tta and name != "fp64":
+            lam_err["all_disks_%s_vs_fp64" % name] = lam_diff(fp["by_disk"], tta["fp64"]["by_disk"], mine)
+        if gold is not None:
+            lam_err["all_disks_%s_vs_oracle" % name] = lam_diff(fp["by_disk"], gold, mine)
+    checks = [v for k, v in lam_err.items() if k.startswith(("timed_steps", "all_disks"))]
+    lam_err["within_bound"] = bool(checks) and all(v is not None and v <= 1e-10 for v in checks)
+
+    time_to_all = None
+    if tta:
+        time_to_all = {name: {"seconds": fp["seconds"], "solves": fp["res"]["stats"]["solves"],
+                              "eigenvalues": len(fp["res"]["lam"]), "splits": fp["res"]["stats"]["splits"],
+                              "ir_fallbacks": fp["res"]["stats"]["ir_fallbacks"],
+                              "certified": fp["res"]["stats"]["certified"],
+                              "unverified": fp["res"]["stats"]["unverified"],
+                              "kernels_ms": {k: v["ms"] for k, v in fp["kernels"].items()},
+                              "clocks": fp["clocks"]} for name, fp in tta.items()}
+        time_to_all["disks"] = len(mine) * world
+        if "fp64" in tta:
+            for name in tta:
+                if name != "fp64":
+                    time_to_all["speedup_%s_vs_fp64" % name] = tta["fp64"]["seconds"] / tta[name]["seconds"]
 
     # ---- e2e: host buffers through the C ABI, copies inside the timed region
     e2e = None
@@ -813,13 +926,15 @@ def main():
                        "form": head["form"], "regions_per_step": B, "n": n, "l": l, "N": 64,
                        "l2": "working set > L2 (one 17 MB factorisation slot per CTA and slot)",
                        "eigenvalues_found": head["eigenvalues_found"],
-                       "eigenvalues_found_fp64": found_fp64},
-            "speedup_vs_plain_fp64": (head["value"] / plain["value"]) if head is not plain else 1.0,
+                       "lambda_err_max_vs_fp64": lam_err.get("timed_steps_vs_fp64"),
+                       "lambda_err_max_vs_oracle": lam_err.get("timed_steps_vs_oracle")},
+            "lambda_err": lam_err, "time_to_all_eigenvalues": time_to_all,
+            "speedup_vs_plain_fp64": head.get("speedup_vs_fp64_solves_per_s"),
             "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "kernels": prof, "plain_fp64": plain if head is not plain else None,
+            "kernels": prof, "plain_fp64": plain,
             "other_precision_form": other, "clocks": clk,
         }
-        for key in ("tensor", "ir_sweeps_per_node", "ir_fallbacks", "tc_timeouts"):
+        for key in ("tensor", "ir_sweeps_per_node", "ir_fallbacks", "tc_timeouts", "certified", "unverified"):
             if key in head:
                 line[key] = head[key]
         print(json.dumps(line))

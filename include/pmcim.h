@@ -311,10 +311,13 @@ const char* pmcim_last_error(void);
    Workspace: a fixed 32 MiB array compiled into the library, held by every GPU
    that loads it until the process exits. A problem whose one-CTA workspace,
    n (n + l) * 16 + n * 4 bytes, exceeds 32 MiB (n above about 1440 at l = 16)
-   is rejected with PMCIM_ENOTSUP. The first call on each device looks up the
-   array's device address with that device current. Every call shares the
-   array, so calls that overlap on the GPU race; nothing in it needs clearing
-   between calls. Synchronous on cuda_stream. No cudaMalloc, no cudaFree. */
+   is rejected with PMCIM_ENOTSUP. Every call looks up the array's device
+   address (cudaGetSymbolAddress, which allocates nothing) with the calling
+   thread's current device, so the address stays right after the host
+   application resets the device and its context is created again. Every call
+   shares the array, so calls that overlap on the GPU race; nothing in it needs
+   clearing between calls. Synchronous on cuda_stream. No cudaMalloc, no
+   cudaFree. */
 int pmcim_solve_points_noalloc(int32_t n, int32_t K, const pmcim_fterm* f, const uint8_t* dense,
                                const double* A, int32_t m, const double* z, int32_t l, const double* V,
                                double* X, int32_t* info, void* cuda_stream);
@@ -350,6 +353,21 @@ typedef struct {
 void pmcim_profile_enable(int on);
 void pmcim_profile_reset(void);
 void pmcim_profile_read(pmcim_profile* out);
+
+/* Limits, in SM clock cycles, of the two kinds of bounded device waits in the
+   precision-form node kernel (no counterpart in the paper; for testing the
+   paths taken when a wait runs out). tc_wait_cycles bounds each wait for a
+   tensor-core commit inside the LU's trailing update: when one runs out the
+   node's LU is finished on the FMA pipes, the node is counted in
+   stats.tc_timeouts, and its refinement (or its FP64 re-solve) still delivers
+   an FP64-accurate solution. handoff_wait_cycles bounds each wait between the
+   kernel's two thread groups: when one runs out both groups end and the call
+   returns PMCIM_ETIMEOUT; the handle stays usable. 0 restores a default
+   (2^30 and 2^35 cycles, about 0.5 s and 16 s at 2 GHz). Process-wide; takes
+   effect for launches prepared after the call. The final wait for a commit in
+   flight before the kernel frees its tensor memory always uses the default.
+   EINVAL for a negative limit. */
+int pmcim_debug_wait_limits(int64_t tc_wait_cycles, int64_t handoff_wait_cycles);
 
 #ifdef __cplusplus
 }

@@ -108,6 +108,13 @@ constexpr size_t kMaxPmcimaRegions = size_t(1) << 20;
 // this fraction of |X|: 1e-11 keeps Beyn's eigenvalues within about 1e-14 of
 // the FP64 ones on the delay workload (simulated FP32 LU + FP64 refinement).
 constexpr double kIrTol = 1e-11;
+// Default limits of the precision-form kernel's bounded waits (clock64 cycles):
+// a tensor-core commit (about half a second at 2 GHz) and a hand-off between its
+// thread groups (about 16 s, longer than any node at n <= 4096).
+constexpr long long kTcWaitCycles = 1ll << 30;
+constexpr long long kHandoffWaitCycles = 1ll << 35;
+std::mutex g_wait_mu;
+long long g_tc_wait = kTcWaitCycles, g_handoff_wait = kHandoffWaitCycles;
 
 // Copy results to a caller buffer that may live on the host or the device.
 int copy_out(void* dst, const void* src, size_t bytes) {
@@ -201,6 +208,15 @@ void prof_flush() {
     P.pool.push_back(q.b);
   }
   P.pending.clear();
+}
+
+long long wait_limit_tc() {
+  std::lock_guard<std::mutex> g(g_wait_mu);
+  return g_tc_wait;
+}
+long long wait_limit_handoff() {
+  std::lock_guard<std::mutex> g(g_wait_mu);
+  return g_handoff_wait;
 }
 
 // Device workspaces, reused across calls on one handle.
@@ -692,6 +708,8 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
       na.max_sweeps = c.opt->max_ir_sweeps;
       na.tol_ir = c.opt->tol_ir > 0.0 ? c.opt->tol_ir : kIrTol;
       na.err = ws.counters.as<int32_t>() + 3 * waves.size();
+      na.tc_wait_cycles = wait_limit_tc();
+      na.handoff_wait_cycles = wait_limit_handoff();
       if (wv.n64) {
         na.items = ws.items.as<NodeItem>() + wv.items64_off;
         na.n_items = (int)wv.n64;
@@ -1723,6 +1741,14 @@ int pmcim_screen_gradient(int32_t M, const float* feats, const uint8_t* labels, 
   CU(cudaMemcpyAsync(grad, g.p, PMCIM_SCREEN_PARAMS * sizeof(float), cudaMemcpyDefault, s));
   if (loss) CU(cudaMemcpyAsync(loss, l.p, sizeof(double), cudaMemcpyDefault, s));
   CU(cudaStreamSynchronize(s));
+  return PMCIM_OK;
+}
+
+int pmcim_debug_wait_limits(int64_t tc_wait_cycles, int64_t handoff_wait_cycles) {
+  if (tc_wait_cycles < 0 || handoff_wait_cycles < 0) return fail(PMCIM_EINVAL, "negative wait limit");
+  std::lock_guard<std::mutex> g(g_wait_mu);
+  g_tc_wait = tc_wait_cycles ? (long long)tc_wait_cycles : kTcWaitCycles;
+  g_handoff_wait = handoff_wait_cycles ? (long long)handoff_wait_cycles : kHandoffWaitCycles;
   return PMCIM_OK;
 }
 

@@ -16,8 +16,6 @@
 //
 // Pivot rule: the row maximising |Re| + |Im| in the column, lowest row index on
 // ties (the BLAS izamax convention of LAPACK zgetrf).
-#include <mutex>
-
 #include "lu_core.cuh"
 
 namespace {
@@ -330,17 +328,16 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_points_fp64(PointAr
     if (tid < P.K) sm.fz[tid] = eval_f(P.term[tid], z);
     __syncthreads();
     const size_t nn = (size_t)n * n;
-    for (int col = 0; col < n; ++col) {
-      for (int row = tid; row < n; row += THREADS) {
-        const size_t e = (size_t)col * n + row;
-        double2 v = make_double2(0.0, 0.0);
-        for (int k = 0; k < P.K; ++k) {
-          const TermDesc& t = P.term[k];
-          if (t.dense) cfma(v, sm.fz[k], a.A[(size_t)t.mat_index * nn + e]);
-          else if (row == col) cfma(v, sm.fz[k], t.id);
-        }
-        M[e] = v;
+    // the flattened element index keeps every thread busy for any n
+    for (size_t e = tid; e < nn; e += THREADS) {
+      const size_t row = e % n, col = e / n;
+      double2 v = make_double2(0.0, 0.0);
+      for (int k = 0; k < P.K; ++k) {
+        const TermDesc& t = P.term[k];
+        if (t.dense) cfma(v, sm.fz[k], a.A[(size_t)t.mat_index * nn + e]);
+        else if (row == col) cfma(v, sm.fz[k], t.id);
       }
+      M[e] = v;
     }
     for (size_t e = tid; e < (size_t)n * l; e += THREADS) M[nn + e] = a.V[e];
     __syncthreads();
@@ -352,9 +349,6 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_points_fp64(PointAr
     __syncthreads();
   }
 }
-
-std::mutex g_noalloc_mu;
-void* g_noalloc_addr[64] = {};
 
 }  // namespace
 
@@ -385,19 +379,12 @@ extern "C" int pmcim_solve_points_noalloc(int32_t n, int32_t K, const pmcim_fter
   if (nd > 0 && !A) return PMCIM_EINVAL;
   if (m == 0) return PMCIM_OK;
 
-  // set-up, once per device, with that device current: the device address of the array
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PMCIM_ECUDA;
+  // The device address of the array, looked up on every call with the calling
+  // thread's device current. The lookup allocates nothing; it is not cached,
+  // because a context torn down and created again (cudaDeviceReset by the host
+  // application) can place the array at a new address.
   void* base = nullptr;
-  {
-    std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-      void* ptr = nullptr;
-      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return PMCIM_ECUDA;
-      g_noalloc_addr[dev] = ptr;
-    }
-    base = g_noalloc_addr[dev];
-  }
+  if (cudaGetSymbolAddress(&base, g_noalloc_scratch) != cudaSuccess || !base) return PMCIM_ECUDA;
   int slots = factor_slots_fp64(n, l);
   const size_t fit = kNoAllocScratchBytes / slot_bytes;
   if ((size_t)slots > fit) slots = (int)fit;

@@ -77,7 +77,6 @@ __device__ __forceinline__ void res_tile_async(double2* dst, const double2* __re
 constexpr int GROUPS = 2;                        // factor group, refine group
 constexpr int CTA_THREADS = GROUPS * THREADS;
 constexpr int SLOTS = 2;                         // node slots per CTA
-constexpr long long HANDOFF_WAIT_CYCLES = 1ll << 35;  // about 16 s at 2 GHz
 
 // A group's node context.
 struct NodeCtx {
@@ -411,8 +410,8 @@ __device__ __forceinline__ bool group_all(bool v) {
 
 // Bounded wait of the whole group on a hand-off barrier; the group agrees on
 // the outcome, so that it never splits at a timeout.
-__device__ bool handoff_wait(uint64_t* bar, uint32_t parity, int32_t* err) {
-  const bool ok = group_all(tcu::wait_parity(bar, parity, HANDOFF_WAIT_CYCLES));
+__device__ bool handoff_wait(uint64_t* bar, uint32_t parity, int32_t* err, long long limit) {
+  const bool ok = group_all(tcu::wait_parity(bar, parity, limit));
   if (!ok && gtid() == 0) atomicExch(err, 1);
   return ok;
 }
@@ -424,7 +423,7 @@ __device__ void factor_group(const NodeArgs& a, MixedSmem& sm, tcu::Ctx& cx, Pha
   for (int k = 0;; ++k) {
     const int s = k % SLOTS, use = k / SLOTS;
     // the slot is free again once the refine group has finished its previous node
-    if (use > 0 && !handoff_wait(&sm.empty[s], (uint32_t)((use - 1) & 1), a.err)) return;
+    if (use > 0 && !handoff_wait(&sm.empty[s], (uint32_t)((use - 1) & 1), a.err, a.handoff_wait_cycles)) return;
     pc.mark(PH_FACTOR_WAIT);
     if (tid == 0) c.item = atomicAdd(a.counter, 1);
     gsync();
@@ -504,7 +503,7 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
   NodeCtx& c = sm.r.c;
   for (int k = 0;; ++k) {
     const int s = k % SLOTS, use = k / SLOTS;
-    if (!handoff_wait(&sm.full[s], (uint32_t)(use & 1), a.err)) return;
+    if (!handoff_wait(&sm.full[s], (uint32_t)(use & 1), a.err, a.handoff_wait_cycles)) return;
     pc.mark(PH_REFINE_WAIT);
     const Slot sl = sm.slot[s];
     if (sl.item < 0) return;
@@ -629,10 +628,11 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_factor_solve_mixed(NodeArgs 
   tcu::fence_after();
 
   if (tid < THREADS) {
-    tcu::Ctx cx{sm.f.u.tc + offsetof(LuSmemT<float2>, Ls), sm.mbar_tc, sm.tmem_base, {0u, 0u}, &sm.tc_bad};
+    tcu::Ctx cx{sm.f.u.tc + offsetof(LuSmemT<float2>, Ls), sm.mbar_tc, sm.tmem_base, {0u, 0u}, &sm.tc_bad,
+                a.tc_wait_cycles};
     factor_group(a, sm, cx, pc);
-    // a commit whose wait ran out may still be in flight: wait once more (bounded)
-    // before the columns are given back
+    // a commit whose wait ran out may still be in flight: wait once more, with the
+    // default limit whatever the update's own limit was, before the columns are given back
     if (sm.tc_bad) {
       // returns at once for a barrier with no commit outstanding
       tcu::wait_parity(&sm.mbar_tc[0], cx.phase[0] ^ 1u, tcu::WAIT_CYCLES);

@@ -207,7 +207,13 @@ struct NodeArgs {
   int32_t* err;               // mixed kernel: set to 1 when a wait between its thread groups ran out
   double2* t64;               // mixed kernel: per slot, T(z_j) in FP64 for the residuals (problems
   size_t t64_stride;          // with two or more dense terms); double2 elements per slot
+  long long tc_wait_cycles;       // mixed kernel: limit of a wait for a tensor-core commit
+  long long handoff_wait_cycles;  // mixed kernel: limit of a wait between its thread groups
 };
+// Limits of the precision-form kernel's bounded waits (clock64 cycles): the
+// defaults, or the values a test set with pmcim_debug_wait_limits.
+long long wait_limit_tc();
+long long wait_limit_handoff();
 cudaError_t prepare_factor_fp64();   // shared-memory limits; call outside graph capture
 cudaError_t prepare_factor_mixed();
 cudaError_t launch_factor_solve_fp64(const NodeArgs& a, cudaStream_t s);

@@ -60,6 +60,7 @@ struct Ctx {
   uint32_t tmem;         // TMEM address of the TMEM_COLS allocated columns
   uint32_t phase[2];     // parity of each barrier's next commit (the same in every thread)
   int* bad;              // shared flag: a wait ran out
+  long long wait_cycles; // limit of one completion wait inside update()
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -298,7 +299,7 @@ __device__ void update(float2* __restrict__ M, int n, int ncols, int k0, int kb,
         const int col = c0 + 16 * half + c;
         cv[c] = (row < n && col < ncols) ? M[(size_t)col * ld + row] : make_float2(0.f, 0.f);
       }
-      const bool ok = wait_parity(cx.mbar + b, cx.phase[b]);
+      const bool ok = wait_parity(cx.mbar + b, cx.phase[b], cx.wait_cycles);
       cx.phase[b] ^= 1u;
       if (!ok) atomicExch(cx.bad, 1);
       stage_barrier();  // tile t+1 staged; tile t-1's accumulator read by every thread

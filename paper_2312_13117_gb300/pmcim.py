@@ -28,7 +28,7 @@ EXPORTS = ["pmcim_default_options", "pmcim_problem_create", "pmcim_problem_destr
            "pmcim_indicator", "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_status_string",
            "pmcim_last_error", "pmcim_profile_enable", "pmcim_profile_reset", "pmcim_profile_read",
            "pmcim_solve_points_noalloc", "pmcim_batch_solve", "pmcim_screen_features", "pmcim_screen_train",
-           "pmcim_screen_apply", "pmcim_screen_gradient", "pmcim_pmcima"]
+           "pmcim_screen_apply", "pmcim_screen_gradient", "pmcim_pmcima", "pmcim_debug_wait_limits"]
 
 KERNELS = ["factor_fp64", "reduce", "indicator", "beyn", "verify", "gather", "factor_fp32", "screen"]
 SCREEN_PARAMS = 4481
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pmcim_profile_reset.restype = None
     lib.pmcim_profile_read.argtypes = [C.POINTER(pmcim_profile)]
     lib.pmcim_profile_read.restype = None
+    lib.pmcim_debug_wait_limits.argtypes = [C.c_int64, C.c_int64]
     lib.pmcim_solve_points_noalloc.argtypes = [I32, I32, C.POINTER(pmcim_fterm), C.POINTER(C.c_uint8), VP, I32,
                                                VP, I32, VP, VP, VP, VP]
     F = C.c_void_p
@@ -120,7 +121,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     for name in ("pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments", "pmcim_indicator",
                  "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_solve_points_noalloc", "pmcim_batch_solve",
                  "pmcim_screen_features", "pmcim_screen_train", "pmcim_screen_apply", "pmcim_screen_gradient",
-                 "pmcim_pmcima"):
+                 "pmcim_pmcima", "pmcim_debug_wait_limits"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -167,6 +168,11 @@ def pmcim_profile_enable(on: bool):
 
 def pmcim_profile_reset():
     load().pmcim_profile_reset()
+
+
+def debug_wait_limits(tc_wait_cycles: int = 0, handoff_wait_cycles: int = 0):
+    """Limits of the precision-form kernel's bounded waits (0 = default); for tests."""
+    _check(load().pmcim_debug_wait_limits(int(tc_wait_cycles), int(handoff_wait_cycles)), "pmcim_debug_wait_limits")
 
 
 def pmcim_profile_read() -> dict:

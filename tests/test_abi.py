@@ -56,3 +56,13 @@ def test_no_cpu_fallback_without_gpu():
     with pytest.raises(pmcim.PmcimError) as e:
         pmcim.Problem(4, [(np.eye(4), 0, 0, 0.0)])
     assert e.value.code == -3  # PMCIM_ECUDA
+
+
+def test_debug_wait_limits_reject_negative(lib):
+    """The wait-limit setter validates on the host (no device call)."""
+    from paper_2312_13117_gb300 import pmcim
+    pmcim.load()
+    with pytest.raises(pmcim.PmcimError) as e:
+        pmcim.debug_wait_limits(-1, 0)
+    assert e.value.code == -1   # PMCIM_EINVAL
+    pmcim.debug_wait_limits(0, 0)

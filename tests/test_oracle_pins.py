@@ -489,3 +489,61 @@ def test_hankel_with_one_moment_pair_is_beyn():
     assert b.p == h.p > 0
     k, err = _match(b.lam, h.lam)
     assert k == b.p and err < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Eigenvector normalisation: unit 2-norm, largest-modulus entry real and
+# positive. The rule fixes a vector's free complex factor, so any s e^{i phi}
+# multiple of a vector must map to one and the same output.
+# ---------------------------------------------------------------------------
+
+def _phase_rule_holds(fn):
+    rng = np.random.default_rng(93)
+    n, k = 7, 3
+    base = w.complex_gaussian(rng, (n, k))
+    imax = [2, 5, 0]
+    for j, i in enumerate(imax):                  # a unique largest entry, real positive
+        base[:, j] *= 0.5 / np.max(np.abs(base[:, j]))
+        base[i, j] = 1.0
+    want = base / np.linalg.norm(base, axis=0, keepdims=True)
+    ok = True
+    for phi in (0.0, 0.7, 2.9, -1.4):
+        for s in (1e-3, 1.0, 40.0):
+            got = fn(s * np.exp(1j * phi) * base)
+            ok &= bool(np.allclose(got, want, rtol=0, atol=1e-14))
+    return ok
+
+
+def test_normalise_vectors_phase_rule():
+    """Every s e^{i phi} multiple of a vector whose largest entry is real positive maps back to
+    that unit vector; on a diagonal problem Beyn's eigenvector of pole mu_i is e_i itself."""
+    assert _phase_rule_holds(o.normalise_vectors)
+    rng = np.random.default_rng(94)
+    mu, a = _poles(rng, 0.0, 1.0, 3, 2, rout=(1.6, 2.5))
+    V = w.probe_block(rng, 5, 4)
+    m = o.moments(w.diagonal_linear(mu), 0.0, 1.0, 64, V)
+    b = o.beyn_extract(m.C0, m.C1, tol_svd=1e-9)
+    assert b.p == 3
+    for k in range(b.p):
+        i = int(np.argmin(np.abs(mu - b.lam[k])))
+        e = np.zeros(5, np.complex128)
+        e[i] = 1.0
+        assert np.max(np.abs(b.vecs[:, k] - e)) < 1e-9
+
+
+@pytest.mark.parametrize("mistake", ["no_rotation", "conjugate_rotation", "no_scaling"])
+def test_pin_catches_wrong_phase_rule(mistake):
+    def broken(Vc):
+        out = np.array(Vc, dtype=np.complex128, copy=True)
+        for k in range(out.shape[1]):
+            v = out[:, k]
+            if mistake != "no_scaling":
+                v = v / np.linalg.norm(v)
+            i = int(np.argmax(np.abs(v)))
+            if mistake == "conjugate_rotation":
+                v = v * (v[i] / abs(v[i]))
+            elif mistake == "no_scaling":
+                v = v * (abs(v[i]) / v[i])
+            out[:, k] = v
+        return out
+    assert not _phase_rule_holds(broken)

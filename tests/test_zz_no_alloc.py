@@ -2,10 +2,12 @@
 
 It serves callers that cannot allocate while they run (their own pool owns the
 device memory, or cudaFree's device-wide synchronisation is not acceptable).
-Its solutions, summed with the trapezoid weights, must equal the moments that
-the regular entry point pmcim_moments returns for the same disk, within the
-bound the other parity tests use; checked on two calls in a row, so the second
-call runs on the array the first one left behind.
+Each solution must equal the CPU oracle's LAPACK solve at the same point within
+the backward-error bound of two LU solves, and the solutions summed with the
+trapezoid weights must equal the moments that the regular entry point
+pmcim_moments returns for the same disk, within the bound the other parity
+tests use; checked on two calls in a row, so the second call runs on the array
+the first one left behind.
 """
 import ctypes
 
@@ -17,6 +19,19 @@ import workloads as w
 from tests.test_gpu_parity import _moment_bound
 
 pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+
+
+def _solve_bound(prob, zj, V, c=4.0):
+    """c u (n kappa_1(T(z_j)) + 4) ||X_j||, kappa from LAPACK's condition estimate."""
+    import scipy.linalg as sla
+    from scipy.linalg.lapack import zgecon
+    T = o.assemble_T(prob, zj)
+    lu, piv = sla.lu_factor(T)
+    X = sla.lu_solve((lu, piv), V)
+    rcond, _ = zgecon(lu, np.max(np.sum(np.abs(T), axis=0)), norm="1")
+    return c * U64 * (prob.n / max(rcond, 1e-300) + 4) * np.linalg.norm(X)
 
 
 def _call_noalloc(pm, prob, z, V):
@@ -60,6 +75,9 @@ def test_noalloc_matches_moments_two_calls():
         C0, C1, _, _ = P.moments([reg], W.V)
         z, wts = o.nodes_weights(reg.c, reg.r, reg.N)
         X = _call_noalloc(pmcim, W.problem, z, W.V)
+        Xo = o.solve_nodes(W.problem, z, W.V)
+        for j in range(reg.N):
+            assert np.linalg.norm(X[j] - Xo[j]) <= _solve_bound(W.problem, z[j], W.V), j
         C0_na = np.einsum("j,jnl->nl", wts, X)
         C1_na = np.einsum("j,jnl->nl", wts * z, X)
         b0, b1, _ = _moment_bound(W.problem, reg, W.V)

@@ -588,6 +588,8 @@ def main():
                     help="moment pairs of the block Hankel Beyn legs (--workload batched: 4, --full: 2)")
     ap.add_argument("--indicator-n", type=int, default=16,
                     help="coarse indicator rule of the two-pass legs (--full, --workload screen)")
+    ap.add_argument("--no-fp64-residual-leg", action="store_true",
+                    help="skip the leg with the refinement residuals on the FP64 pipe")
     ap.add_argument("--no-time-to-all", action="store_true",
                     help="skip the passes over every disk (time to all eigenvalues; about 3 minutes)")
     ap.add_argument("--full", action="store_true",
@@ -623,6 +625,8 @@ def main():
     opt = pmcim.options(stream=stream.cuda_stream)
     opt_mixed = pmcim.options(stream=stream.cuda_stream, precision=pmcim.PREC_FP32_IR)
     opt_tc = pmcim.options(stream=stream.cuda_stream, precision=pmcim.PREC_TF32X3_IR)
+    # the same form with its refinement residuals on the FP64 pipe (the tensor-core residual's A/B leg)
+    opt_tc64 = pmcim.options(stream=stream.cuda_stream, precision=pmcim.PREC_TF32X3_IR, residual_fp64=True)
     P = pmcim.Problem(n, W.problem.terms)
     cap = 64 * l * B
 
@@ -673,6 +677,8 @@ def main():
     # both at FP64 accuracy; the other form and plain FP64 are measured on the same
     # disks beside it
     forms = [("fp64", opt)] if args.no_mixed else [("fp32ir", opt_mixed), ("tf32x3", opt_tc)]
+    if not args.no_mixed and not args.no_fp64_residual_leg:
+        forms.append(("tf32x3_fp64res", opt_tc64))
     head_name, head_opt = forms[0]
     clocks = ClockSampler(local)
     clocks.start()
@@ -791,10 +797,13 @@ def main():
             roof["residual_dfma_per_sm_clock"] = w_res / 2.0 / cyc["residual_fp64"]
             roof["peak_dfma_per_sm_clock"] = FP64_DFMA_PER_SM_CLK
         rec = {
-            "form": ("FP32 LU + FP64 iterative refinement (residual R = V - T(z)X, T(z) assembled in FP64)"
-                     if name == "fp32ir" else
-                     "FP32 LU with 3xTF32 complex trailing updates on the tensor cores (tcgen05, TMEM "
-                     "accumulators) + FP64 iterative refinement"),
+            "form": {"fp32ir": "FP32 LU + FP64-accurate iterative refinement, residuals on the tensor cores "
+                               "(exact BF16 digit products)",
+                     "tf32x3": "FP32 LU with 3xTF32 complex trailing updates on the tensor cores (tcgen05, TMEM "
+                               "accumulators) + FP64-accurate iterative refinement, residuals on the tensor "
+                               "cores (exact BF16 digit products)",
+                     "tf32x3_fp64res": "FP32 LU with 3xTF32 tensor-core trailing updates + FP64 iterative "
+                                       "refinement, residuals on the FP64 pipe (T(z) assembled in FP64)"}[name],
             "value": sum_over_ranks(float(msolves), world) / (tm_max / 1e3), "unit": UNIT,
             "ms_per_step": tm_max / args.steps, "eigenvalues_found": mfound,
             "ir_sweeps_per_node": aggm["ir_sweeps"] / max(1, msolves), "ir_fallbacks": aggm["ir_fallbacks"],
@@ -802,7 +811,7 @@ def main():
             "unverified": aggm.get("unverified", 0),
             "roofline": roof, "kernels": profm, "clocks": clocks.window(*win),
         }
-        if name == "tf32x3":
+        if name.startswith("tf32x3"):
             # tensor-pipe work of the trailing updates: 3 split products of the complex
             # rank-32 updates, 8 real flops per complex multiply-add
             upd = sum(8.0 * 32 * (n - k) * (n + l - k) for k in range(32, n, 32))
@@ -823,6 +832,7 @@ def main():
                 "roofline": None, "kernels": profm, "clocks": clocks.window(*win)}
     other_name = {"fp32ir": "tf32x3", "tf32x3": "fp32ir"}.get(head_name)
     other = precision_record(other_name, runs[other_name]) if other_name in runs else None
+    fp64res = precision_record("tf32x3_fp64res", runs["tf32x3_fp64res"]) if "tf32x3_fp64res" in runs else None
     if plain is not None:
         for rec in (head, other):
             if rec is not None and rec is not plain:
@@ -932,7 +942,10 @@ def main():
             "speedup_vs_plain_fp64": head.get("speedup_vs_fp64_solves_per_s"),
             "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "kernels": prof, "plain_fp64": plain,
-            "other_precision_form": other, "clocks": clk,
+            "other_precision_form": other, "residual_on_fp64_pipe": fp64res,
+            "speedup_tensor_core_residual": (runs["tf32x3_fp64res"][0] / runs["tf32x3"][0]
+                                             if "tf32x3_fp64res" in runs else None),
+            "clocks": clk,
         }
         for key in ("tensor", "ir_sweeps_per_node", "ir_fallbacks", "tc_timeouts", "certified", "unverified"):
             if key in head:

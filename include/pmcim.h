@@ -126,6 +126,12 @@ typedef struct {
      remaining error |delta_s|^2 / |delta_{s-1}| is at most tol_ir |X| (max
      norms); 0 = the default 1e-11. Must lie in [1e-15, 1e-6]. */
   double tol_ir;
+  /* reduced precisions: where the refinement residuals R = V - T(z_j) X are
+     formed. 0 (default): on the tensor cores, from exact BF16 digits of the
+     coefficients and of f_k(z_j) X (7 digits of 7 bits each per number, the
+     digit products accumulated exactly in FP32 and combined in FP64; about the
+     accuracy of an FP64 product, see pmcim_residual). 1: on the FP64 pipe. */
+  int32_t residual_fp64;
 } pmcim_options;
 
 /* Statistics of one pmcim_solve call. */
@@ -196,6 +202,18 @@ int pmcim_indicator(pmcim_problem p, const pmcim_options* opt, int32_t R, const 
 int pmcim_beyn(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim_region* reg,
                int32_t l, const double* V, int32_t cap, double* lambda, double* vecs,
                int32_t* region_of, int32_t* count, int32_t* region_status);
+
+/* The residuals of m linear systems T(z_j) X_j = V (Eq. 2.4), R_j = V - T(z_j) X_j,
+   formed as the precision forms' refinement forms them on the tensor cores
+   (exact products of BF16 digits: every row of each dense A_k and every column
+   of f_k(z_j) X_j is written as 48 bits in 7 digits of 7 bits, the digit pairs
+   of total order <= 9 are multiplied with exact FP32 accumulation, and the
+   results are combined in FP64; the error is of the order of 2^-47 of
+   sum_i |A_k||f_k X|, comparable with an FP64 product). z: m complex points;
+   V: n x l; X and R: m blocks of n x l (column-major, complex). ETIMEOUT if a
+   bounded wait of the kernel ran out (R not valid). */
+int pmcim_residual(pmcim_problem p, const pmcim_options* opt, int32_t m, const double* z, int32_t l,
+                   const double* V, const double* X, double* R);
 
 /* pmCIMb step 3: sigma_min[i] = smallest singular value of T(lambda_i) by LU and
    inverse iteration on (T^H T)^{-1}; accept[i] = sigma_min <= tol_verify *

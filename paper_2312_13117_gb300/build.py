@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(LIBDIR, "libpmcim.so")
-SOURCES = ["api.cu", "lu_fp64.cu", "lu_mixed.cu", "reduce.cu", "beyn.cu", "screen.cu", "lu_small.cu"]
+SOURCES = ["api.cu", "lu_fp64.cu", "lu_mixed.cu", "reduce.cu", "beyn.cu", "screen.cu", "lu_small.cu", "ozaki.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]

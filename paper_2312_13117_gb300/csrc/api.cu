@@ -231,6 +231,10 @@ struct Workspace {
   DevBuf vout;           // verification's singular vectors (pmCIMa)
   DevBuf Cm;             // scaled moments of the block Hankel form of Beyn's step
   DevBuf ind3, feats, sprob, sparams, sscratch;
+  // verification's inverse-iteration step: per-value problem table, pseudo-disks, items, solutions
+  DevBuf iprobs, iregions, iitems, iX, iinfo, icounters;
+  DevBuf ysl;                        // per slot: digits of f_k X for the tensor-core residual
+  DevBuf rz, rX, rR, rstat, rysl;    // pmcim_residual: points, solutions, residuals, status, scratch
   // the library's own stream: graphs cannot be captured on the legacy default stream
   cudaStream_t stream = nullptr;
   cudaEvent_t ordered = nullptr;
@@ -243,7 +247,8 @@ struct Workspace {
                    &phase, &C0, &C1, &pf_half, &pf_abs, &ind, &pf_norm, &pf_scale, &cand, &bwork, &bsigma,
                    &bp, &blam, &bvecs, &bkept, &bstatus, &vlam, &vprob, &voff, &vsig, &vacc, &vwork,
                    &vvec, &vpiv, &gitems, &gdst, &gperm, &ind3, &feats, &sprob, &sparams, &sscratch, &Xkeep,
-                   &citems, &vout, &Cm};
+                   &citems, &vout, &Cm, &iprobs, &iregions, &iitems, &iX, &iinfo, &icounters, &ysl, &rz,
+                   &rX, &rR, &rstat, &rysl};
     for (DevBuf* x : b) x->release();
   }
 };
@@ -253,6 +258,10 @@ struct pmcim_problem_s {
   TermDesc term[PMCIM_MAX_TERMS];
   double2* dA = nullptr;
   float2* dA32 = nullptr;  // complex64 copy for the FP32 LU's assembly
+  // exact BF16 digits of the dense coefficients and their row exponents, made on
+  // the first call that refines with residuals on the tensor cores
+  DevBuf dig, dexp;
+  bool dig_ok = false;
   int device = 0;
   DevBuf V;  // probe block of the current call
   Workspace ws;
@@ -300,6 +309,8 @@ int check_options(const pmcim_options* opt) {
     return fail(PMCIM_EINVAL, "tol_ir must be 0 (default) or in [1e-15, 1e-6]");
   if (opt->indicator_N != 0 && (opt->indicator_N < 2 || opt->indicator_N > 4096 || (opt->indicator_N & 1)))
     return fail(PMCIM_EINVAL, "indicator_N = %d must be 0 or even, 2..4096", opt->indicator_N);
+  if (opt->residual_fp64 != 0 && opt->residual_fp64 != 1)
+    return fail(PMCIM_EINVAL, "residual_fp64 = %d must be 0 or 1", opt->residual_fp64);
   if (opt->beyn_K < 0 || opt->beyn_K > PMCIM_MAX_BEYN_K)
     return fail(PMCIM_EINVAL, "beyn_K = %d outside 0..%d", opt->beyn_K, PMCIM_MAX_BEYN_K);
   return PMCIM_OK;
@@ -345,7 +356,24 @@ struct Call {
   pmcim_stats st{};
 };
 
+// The coefficient digits of a handle for the tensor-core residuals (ozaki.cuh),
+// made once; ordered before later work on stream s.
+int ensure_digits(pmcim_problem h, cudaStream_t s) {
+  if (h->dig_ok || h->n_dense == 0) return PMCIM_OK;
+  const int RB = (h->n + 127) / 128;
+  CU(h->dexp.ensure((size_t)h->n_dense * RB * 128 * sizeof(int32_t)));
+  CU(h->dig.ensure(coefficient_digit_bytes(h->n, h->n_dense)));
+  CU(make_coefficient_digits(h->dA, h->n, h->n_dense, h->dexp.as<int32_t>(), h->dig.as<unsigned char>(), s));
+  h->dig_ok = true;
+  return PMCIM_OK;
+}
+
+// Residuals of the precision forms on the tensor cores (default) or the FP64 pipe.
+bool tc_residual(const pmcim_options* opt) { return opt->residual_fp64 == 0; }
+
 int upload_problems(Call& c) {
+  if (c.opt->precision != PMCIM_PREC_FP64 && tc_residual(c.opt))
+    for (const Group& g : c.groups) CHK(ensure_digits(g.h, c.s));
   c.pd.resize(c.groups.size());
   for (size_t i = 0; i < c.groups.size(); ++i) {
     const Group& g = c.groups[i];
@@ -357,6 +385,8 @@ int upload_problems(Call& c) {
     d.n_dense = g.h->n_dense;
     d.A = g.h->dA;
     d.A32 = g.h->dA32;
+    d.Adig = g.h->dig_ok ? g.h->dig.as<unsigned char>() : nullptr;
+    d.Aexp = g.h->dig_ok ? g.h->dexp.as<int32_t>() : nullptr;
     d.V = g.h->V.as<double2>();
     for (int k = 0; k < g.h->K; ++k) d.term[k] = g.h->term[k];
   }
@@ -551,6 +581,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   size_t x_need = 0, reused_nodes = 0;
   bool any64 = false, any32 = false, anyS = false;
   int t64_n = 0;  // largest n of a precision-form problem with two or more dense terms
+  int ysl_n = 0, ysl_nd = 0;  // largest n and dense-term count of the tensor-core residuals
   {
     int g0 = 0;
     while (g0 < R) {
@@ -574,7 +605,11 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
         const ProblemDev& P = c.pd[regs[g].prob];
         std::vector<NodeItem>& dst = small_kernel_fits(P.n, P.l) ? itS
                                      : (form_of(regs[g].prob) == PMCIM_PREC_FP64 ? it64 : it32);
-        if (&dst == &it32 && P.n_dense >= 2) t64_n = std::max(t64_n, P.n);
+        if (&dst == &it32 && P.n_dense >= 2 && !tc_residual(c.opt)) t64_n = std::max(t64_n, P.n);
+        if (&dst == &it32 && tc_residual(c.opt)) {
+          ysl_n = std::max(ysl_n, P.n);
+          ysl_nd = std::max(ysl_nd, P.n_dense);
+        }
         const bool re = reuse && reuse->src[g] >= 0;
         const int nl = P.n * P.l;
         for (int j = 0; j < regs[g].N; ++j) {
@@ -626,7 +661,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   // ---- factorisation workspaces, one slot per resident CTA ----
   const int sms = num_sms();
   int slots64 = 0, slots32 = 0;
-  size_t slot64 = 0, slot32 = 0, t64_stride = 0;
+  size_t slot64 = 0, slot32 = 0, t64_stride = 0, ysl_stride = 0;
   if (any64) {
     slot64 = (size_t)max_n * (max_n + max_l) * sizeof(double2);
     slots64 = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(2 * sms, kSlotBytes / slot64), total_nodes));
@@ -645,6 +680,8 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
     CU(ws.work32.ensure((size_t)slots32 * slot32));
     CU(ws.piv32.ensure((size_t)slots32 * max_n * sizeof(int32_t)));
     if (t64_stride) CU(ws.t64.ensure((size_t)slots32 * t64_stride * sizeof(double2)));
+    ysl_stride = y_digit_scratch_bytes(ysl_n, ysl_nd);
+    if (ysl_stride) CU(ws.ysl.ensure((size_t)slots32 * ysl_stride));
   }
   const bool timed = prof_on();
   if (timed && any32) {
@@ -733,6 +770,9 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
         na.slots = slots32;
         na.t64 = t64_stride ? ws.t64.as<double2>() : nullptr;
         na.t64_stride = t64_stride;
+        na.oz = tc_residual(c.opt) ? 1 : 0;
+        na.ysl = ysl_stride ? ws.ysl.as<unsigned char>() : nullptr;
+        na.ysl_stride = ysl_stride;
         na.phase = timed ? ws.phase.as<unsigned long long>() : nullptr;
         prof_begin(PMCIM_K_FACTOR32, s);
         CU(launch_factor_solve_mixed(na, s));
@@ -1100,6 +1140,194 @@ int run_certify(Call& c, const EigOut& e, std::vector<double>* cert, std::vector
   return PMCIM_OK;
 }
 
+// One step of inverse iteration from Beyn's eigenvector, for the values whose
+// first certificate ||T(lambda) v|| did not accept them: x = T(lambda)^-1 v by
+// the node kernel of the value's arithmetic form (the precision forms refine x
+// to FP64 accuracy), then the certificate ||T(lambda) x|| / ||x||, evaluated in
+// FP64 from the coefficients. sigma_min <= ||T y|| / ||y|| for every y != 0, so a
+// value whose certificate is at or below the acceptance threshold is accepted
+// exactly as the sigma_min rule would accept it. Each value is a pseudo-disk
+// with one node z_0 = lambda (centre lambda, radius 0) and its own one-column
+// problem entry whose probe column is v; the values run in parallel, one per CTA.
+int run_inverse_step(Call& c, const EigOut& e, const std::vector<int>& idx, std::vector<double>* cert,
+                     std::vector<uint8_t>* ok) {
+  Workspace& ws = *c.ws;
+  cudaStream_t s = c.s;
+  const int m = (int)idx.size();
+  cert->assign(m, 0.0);
+  ok->assign(m, 0);
+  if (m == 0) return PMCIM_OK;
+  std::vector<ProblemDev> pdv(m);
+  std::vector<RegionDev> rdv(m);
+  std::vector<NodeItem> it64, it32, itS;
+  std::vector<int32_t> prob_of(m);
+  std::vector<int64_t> x_off(m);
+  std::vector<double2> lam(m);
+  size_t x_tot = 0;
+  int max_n = 1, t64_n = 0, ysl_n = 0, ysl_nd = 0;
+  bool any_tc = false;
+  for (int i = 0; i < m; ++i) {
+    const int v = idx[i], q = e.prob[v];
+    pdv[i] = c.pd[q];
+    pdv[i].l = 1;
+    pdv[i].V = ws.gdst.as<double2>() + e.vec_off[v];
+    const int n = pdv[i].n, form = c.groups[q].form;
+    RegionDev& d = rdv[i];
+    std::memset(&d, 0, sizeof(d));
+    d.cre = e.lam[v].x;
+    d.cim = e.lam[v].y;
+    d.r = 0.0;
+    d.N = 1;
+    d.prob = i;
+    d.node_off = i;
+    d.lu_tc = form == PMCIM_PREC_TF32X3_IR ? 1 : 0;
+    d.x_off = (int64_t)x_tot;
+    x_off[i] = (int64_t)x_tot;
+    x_tot += (size_t)n;
+    prob_of[i] = q;
+    lam[i] = e.lam[v];
+    max_n = std::max(max_n, n);
+    if (small_kernel_fits(n, 1)) {
+      itS.push_back(NodeItem{i, 0});
+    } else if (form == PMCIM_PREC_FP64) {
+      it64.push_back(NodeItem{i, 0});
+    } else {
+      it32.push_back(NodeItem{i, 0});
+      any_tc |= d.lu_tc != 0;
+      if (pdv[i].n_dense >= 2 && !tc_residual(c.opt)) t64_n = std::max(t64_n, n);
+      if (tc_residual(c.opt)) {
+        ysl_n = std::max(ysl_n, n);
+        ysl_nd = std::max(ysl_nd, pdv[i].n_dense);
+      }
+    }
+  }
+  auto by_n = [&](const NodeItem& a, const NodeItem& b) {
+    return pdv[a.region].n != pdv[b.region].n ? pdv[a.region].n > pdv[b.region].n : a.region < b.region;
+  };
+  std::stable_sort(it64.begin(), it64.end(), by_n);
+  std::stable_sort(it32.begin(), it32.end(), by_n);
+  std::vector<NodeItem> items(it64);
+  items.insert(items.end(), it32.begin(), it32.end());
+  items.insert(items.end(), itS.begin(), itS.end());
+  CU(ws.iprobs.ensure(m * sizeof(ProblemDev)));
+  CU(ws.iregions.ensure(m * sizeof(RegionDev)));
+  CU(ws.iitems.ensure(items.size() * sizeof(NodeItem)));
+  CU(ws.iX.ensure(x_tot * sizeof(double2)));
+  CU(ws.iinfo.ensure(m * sizeof(int32_t)));
+  CU(ws.icounters.ensure(4 * sizeof(int32_t)));
+  CU(cudaMemcpyAsync(ws.iprobs.p, pdv.data(), m * sizeof(ProblemDev), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(ws.iregions.p, rdv.data(), m * sizeof(RegionDev), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(ws.iitems.p, items.data(), items.size() * sizeof(NodeItem), cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(ws.icounters.p, 0, 4 * sizeof(int32_t), s));
+  NodeArgs na;
+  std::memset(&na, 0, sizeof(na));
+  na.probs = ws.iprobs.as<ProblemDev>();
+  na.regions = ws.iregions.as<RegionDev>();
+  na.X = ws.iX.as<double2>();
+  na.node_info = ws.iinfo.as<int32_t>();
+  na.max_n = max_n;
+  na.max_sweeps = c.opt->max_ir_sweeps;
+  na.tol_ir = c.opt->tol_ir > 0.0 ? c.opt->tol_ir : kIrTol;
+  na.err = ws.icounters.as<int32_t>() + 3;
+  na.tc_wait_cycles = wait_limit_tc();
+  na.handoff_wait_cycles = wait_limit_handoff();
+  const int sms = num_sms();
+  if (!it64.empty()) {
+    const size_t slot64 = (size_t)max_n * (max_n + 1) * sizeof(double2);
+    const int slots64 = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(2 * sms, kSlotBytes / slot64),
+                                                                  it64.size()));
+    CU(ws.work64.ensure((size_t)slots64 * slot64));
+    CU(ws.piv64.ensure((size_t)slots64 * max_n * sizeof(int32_t)));
+    CU(prepare_factor_fp64());
+    na.items = ws.iitems.as<NodeItem>();
+    na.n_items = (int)it64.size();
+    na.counter = ws.icounters.as<int>();
+    na.work = ws.work64.as<char>();
+    na.slot_bytes = slot64;
+    na.piv = ws.piv64.as<int32_t>();
+    na.slots = slots64;
+    prof_begin(PMCIM_K_FACTOR, s);
+    CU(launch_factor_solve_fp64(na, s));
+    prof_end(PMCIM_K_FACTOR, s);
+  }
+  if (!it32.empty()) {
+    const size_t slot32 = mixed_slot_bytes(max_n, 1);
+    const size_t per = (size_t)mixed_slots_per_cta();
+    const size_t t64_stride = (size_t)t64_n * t64_n;
+    const size_t cta_bytes = per * (slot32 + t64_stride * sizeof(double2));
+    const size_t ctas = std::max<size_t>(1, std::min<size_t>(std::min<size_t>(sms, kSlotBytes / cta_bytes),
+                                                             (it32.size() + per - 1) / per));
+    const int slots32 = (int)(ctas * per);
+    CU(ws.work32.ensure((size_t)slots32 * slot32));
+    CU(ws.piv32.ensure((size_t)slots32 * max_n * sizeof(int32_t)));
+    if (t64_stride) CU(ws.t64.ensure((size_t)slots32 * t64_stride * sizeof(double2)));
+    const size_t ysl_stride = y_digit_scratch_bytes(ysl_n, ysl_nd);
+    if (ysl_stride) CU(ws.ysl.ensure((size_t)slots32 * ysl_stride));
+    CU(prepare_factor_mixed());
+    na.oz = tc_residual(c.opt) ? 1 : 0;
+    na.ysl = ysl_stride ? ws.ysl.as<unsigned char>() : nullptr;
+    na.ysl_stride = ysl_stride;
+    na.items = ws.iitems.as<NodeItem>() + it64.size();
+    na.n_items = (int)it32.size();
+    na.counter = ws.icounters.as<int>() + 1;
+    na.work = ws.work32.as<char>();
+    na.slot_bytes = slot32;
+    na.piv = ws.piv32.as<int32_t>();
+    na.slots = slots32;
+    na.t64 = t64_stride ? ws.t64.as<double2>() : nullptr;
+    na.t64_stride = t64_stride;
+    na.phase = nullptr;
+    prof_begin(PMCIM_K_FACTOR32, s);
+    CU(launch_factor_solve_mixed(na, s));
+    prof_end(PMCIM_K_FACTOR32, s);
+  }
+  if (!itS.empty()) {
+    CU(prepare_factor_small());
+    na.items = ws.iitems.as<NodeItem>() + it64.size() + it32.size();
+    na.n_items = (int)itS.size();
+    na.counter = ws.icounters.as<int>() + 2;
+    prof_begin(PMCIM_K_FACTOR, s);
+    CU(launch_factor_solve_small(na, s));
+    prof_end(PMCIM_K_FACTOR, s);
+  }
+  (void)any_tc;
+  // the certificate of x, against the call's own problem table
+  CU(ws.vlam.ensure(m * sizeof(double2)));
+  CU(ws.vprob.ensure(m * sizeof(int32_t)));
+  CU(ws.voff.ensure(m * sizeof(int64_t)));
+  CU(ws.vsig.ensure(m * sizeof(double)));
+  CU(ws.vacc.ensure(m));
+  CU(cudaMemcpyAsync(ws.vlam.p, lam.data(), m * sizeof(double2), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(ws.vprob.p, prob_of.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(ws.voff.p, x_off.data(), m * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  ValueArgs va;
+  std::memset(&va, 0, sizeof(va));
+  va.probs = ws.probs.as<ProblemDev>();
+  va.prob_of = ws.vprob.as<int32_t>();
+  va.lam = ws.vlam.as<double2>();
+  va.vec_off = ws.voff.as<int64_t>();
+  va.vecs = ws.iX.as<double2>();
+  va.m = m;
+  va.tol_verify = c.opt->tol_verify;
+  va.sigma = ws.vsig.as<double>();
+  va.accept = ws.vacc.as<uint8_t>();
+  prof_begin(PMCIM_K_VERIFY, s);
+  CU(launch_certify(va, s));
+  prof_end(PMCIM_K_VERIFY, s);
+  int32_t handoff_err = 0;
+  CU(cudaMemcpyAsync(cert->data(), ws.vsig.p, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(ok->data(), ws.vacc.p, m, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(&handoff_err, ws.icounters.as<int32_t>() + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (handoff_err)
+    return fail(PMCIM_ETIMEOUT, "precision-form node kernel: a wait between its thread groups ran out");
+  // a value whose certificate is not finite (e.g. an exactly singular T(lambda)) is left
+  // to the full sigma_min computation
+  for (int i = 0; i < m; ++i)
+    if (!std::isfinite((*cert)[i])) (*ok)[i] = 0;
+  return PMCIM_OK;
+}
+
 // Steps 1-3 for all groups of a call. Outputs in call order (not sorted).
 struct Verified {
   std::vector<double> sig;
@@ -1186,6 +1414,28 @@ int run_pmcimb(Call& c, const std::vector<HostRegion>& top_in, EigOut* e, Verifi
       idx.push_back((int)i);
     }
   }
+  // second certificate: one refined inverse-iteration step from Beyn's vector
+  {
+    std::vector<double> cert2;
+    std::vector<uint8_t> ok2;
+    CHK(run_inverse_step(c, *e, idx, &cert2, &ok2));
+    std::vector<double2> rest2;
+    std::vector<int> rest2_prob, idx2;
+    for (size_t k = 0; k < idx.size(); ++k) {
+      if (ok2[k]) {
+        v->sig[idx[k]] = cert2[k];
+        v->acc[idx[k]] = 1;
+        c.st.certified += 1;
+      } else {
+        rest2.push_back(rest[k]);
+        rest2_prob.push_back(rest_prob[k]);
+        idx2.push_back(idx[k]);
+      }
+    }
+    rest.swap(rest2);
+    rest_prob.swap(rest2_prob);
+    idx.swap(idx2);
+  }
   std::vector<double> sig2;
   std::vector<uint8_t> acc2;
   CHK(run_verify(c, rest, rest_prob, &sig2, &acc2));
@@ -1243,6 +1493,7 @@ void pmcim_default_options(pmcim_options* opt) {
   opt->screen_N = 16;
   opt->tol_ir = kIrTol;
   opt->beyn_K = 1;
+  opt->residual_fp64 = 0;
 }
 
 const char* pmcim_status_string(int code) {
@@ -1354,6 +1605,8 @@ int pmcim_problem_destroy(pmcim_problem p) {
   cudaDeviceSynchronize();
   if (p->dA) cudaFree(p->dA);
   if (p->dA32) cudaFree(p->dA32);
+  p->dig.release();
+  p->dexp.release();
   p->V.release();
   p->ws.release();
   delete p;
@@ -1415,6 +1668,44 @@ int pmcim_beyn(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim
   CHK(copy_out(lambda, out.lam.data(), cnt * sizeof(double2)));
   if (region_of) CHK(copy_out(region_of, out.root.data(), cnt * sizeof(int32_t)));
   if (vecs && cnt > 0) CHK(copy_out(vecs, p->ws.gdst.p, (size_t)cnt * p->n * sizeof(double2)));
+  return PMCIM_OK;
+}
+
+int pmcim_residual(pmcim_problem p, const pmcim_options* opt, int32_t m, const double* z, int32_t l,
+                   const double* V, const double* X, double* R) {
+  if (!p) return fail(PMCIM_EINVAL, "problem is NULL");
+  CHK(check_options(opt));
+  if (m < 0 || l < 1 || l > PMCIM_MAX_L) return fail(PMCIM_EINVAL, "m = %d or l = %d out of range", m, l);
+  if (m > 0 && (!z || !V || !X || !R)) return fail(PMCIM_EINVAL, "NULL buffer");
+  if (m == 0) return PMCIM_OK;
+  Call c;
+  c.opt = opt;
+  c.ws = &p->ws;
+  CHK(call_stream(p->ws, opt, &c.s));
+  c.groups = {Group{p, l, PMCIM_PREC_FP32_IR}};
+  CHK(upload_V(p, l, V, c.s));
+  CHK(ensure_digits(p, c.s));
+  CHK(upload_problems(c));
+  Workspace& ws = p->ws;
+  const size_t nl = (size_t)p->n * l;
+  CU(ws.rz.ensure(m * sizeof(double2)));
+  CU(ws.rX.ensure((size_t)m * nl * sizeof(double2)));
+  CU(ws.rR.ensure((size_t)m * nl * sizeof(double2)));
+  CU(ws.rstat.ensure(m * sizeof(int32_t)));
+  const int ctas = std::min(num_sms(), (int)m);
+  const size_t stride = y_digit_scratch_bytes(p->n, std::max(1, p->n_dense));
+  CU(ws.rysl.ensure((size_t)ctas * stride));
+  CU(cudaMemcpyAsync(ws.rz.p, z, m * sizeof(double2), cudaMemcpyDefault, c.s));
+  CU(cudaMemcpyAsync(ws.rX.p, X, (size_t)m * nl * sizeof(double2), cudaMemcpyDefault, c.s));
+  CU(launch_residual_points(ws.probs.as<ProblemDev>(), ws.rz.as<double2>(), m, ws.rX.as<double2>(),
+                            ws.rR.as<double2>(), ws.rysl.as<unsigned char>(), stride, ctas, ws.rstat.as<int32_t>(),
+                            wait_limit_tc(), c.s));
+  std::vector<int32_t> st(m);
+  CU(cudaMemcpyAsync(R, ws.rR.p, (size_t)m * nl * sizeof(double2), cudaMemcpyDefault, c.s));
+  CU(cudaMemcpyAsync(st.data(), ws.rstat.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
+  CU(cudaStreamSynchronize(c.s));
+  for (int i = 0; i < m; ++i)
+    if (st[i]) return fail(PMCIM_ETIMEOUT, "residual at point %d: a tensor-core wait ran out", i);
   return PMCIM_OK;
 }
 

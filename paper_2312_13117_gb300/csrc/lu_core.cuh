@@ -24,6 +24,17 @@ __device__ __forceinline__ int gtid() { return (int)(threadIdx.x & (THREADS - 1)
 __device__ __forceinline__ void gsync() {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / THREADS)), "n"(THREADS) : "memory");
 }
+// True in every thread of the group when v is true in every thread (a group barrier).
+__device__ __forceinline__ bool group_all_sync(bool v) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, %3, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((int)v), "r"(1 + (int)(threadIdx.x / THREADS)), "n"(THREADS)
+      : "memory");
+  return r != 0;
+}
 constexpr int NB = 32;    // panel width
 constexpr int TILE = 64;  // trailing-update tile (TILE x TILE complex)
 constexpr int US_LD = TILE + 1;

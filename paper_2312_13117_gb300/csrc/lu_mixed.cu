@@ -28,7 +28,7 @@
 // lu_tc, as 3xTF32 complex products on the tensor cores (tc_update.cuh).
 // node_info: bits 0-23 = 0 or 1 + first zero-pivot column, bits 24-28 = sweeps
 // run, bit 29 = a tensor-core wait ran out, bit 30 = FP64 fallback.
-#include "tc_update.cuh"
+#include "ozaki.cuh"
 
 namespace {
 
@@ -101,9 +101,12 @@ struct RefineSmem {
   union {
     LuSmemT<float2> lu32;   // correction solves
     LuSmemT<double2> lu64;  // FP64 fallback
-    ResSmem res;            // residual tiles
+    ResSmem res;            // residual tiles (FP64 pipe)
+    ozk::Smem oz;           // residual operand stages (tensor cores)
   } u;
   NodeCtx c;
+  int ozg[PMCIM_MAX_TERMS * ozk::LC];  // column exponents of the digits of f_k X
+  double ozred[THREADS];
 };
 
 // What the factor group hands over with a slot.
@@ -121,7 +124,8 @@ struct MixedSmem {
   uint64_t full[SLOTS];   // THREADS arrivals of the factor group
   uint64_t empty[SLOTS];  // THREADS arrivals of the refine group
   uint64_t mbar_tc[2];    // tensor-core completion, one per accumulator
-  uint32_t tmem_base;
+  ozk::Bars ozb;          // the refine group's tensor-core residual: stage rings, drains
+  uint32_t tmem_base;     // TMEM_ALL columns: the factor group's from 0, the refine group's from 256
   int tc_bad;             // a tensor-core wait ran out: FMA pipes from then on
 };
 
@@ -416,6 +420,10 @@ __device__ bool handoff_wait(uint64_t* bar, uint32_t parity, int32_t* err, long 
   return ok;
 }
 
+constexpr uint32_t TMEM_ALL = 512;
+constexpr uint32_t TMEM_REFINE = 256;  // first column of the refine group's accumulators
+static_assert(tcu::TMEM_COLS <= TMEM_REFINE && TMEM_REFINE + ozk::TMEM_COLS <= TMEM_ALL, "TMEM split");
+
 // Steps 1-2 for one node after another, into the CTA's slots in turn.
 __device__ void factor_group(const NodeArgs& a, MixedSmem& sm, tcu::Ctx& cx, PhaseClock& pc) {
   const int tid = gtid();
@@ -447,7 +455,7 @@ __device__ void factor_group(const NodeArgs& a, MixedSmem& sm, tcu::Ctx& cx, Pha
     int* perm = reinterpret_cast<int*>(slot + mixed_residual_offset(n, l) + nl * sizeof(double2));
     double2* X = a.X + rg.x_off + (size_t)it.j * nl;
     pc.mark(PH_SETUP);
-    if (P.n_dense >= 2)  // T(z_j) in FP64 for the refine group, and rounded for the LU
+    if (P.n_dense >= 2 && !a.oz)  // T(z_j) in FP64 for the refine group's FP64 residual, and rounded
       assemble_fp64(c, a.t64 + si * a.t64_stride, M32);
     else
       assemble32(c, M32);
@@ -523,12 +531,22 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
     double2* X = a.X + rg.x_off + (size_t)it.j * nl;
     int info = sl.info;
     bool ok = (info == 0);
+    bool tc_lost = sl.tc_timeout != 0;
     int sweeps = 0;
+    // residuals on the tensor cores (exact digit products), unless a wait of that
+    // path ran out earlier in this CTA; then the node is solved in FP64 below
+    const bool use_oz = a.oz && P.Adig != nullptr;
+    if (use_oz && sm.ozb.bad) {
+      ok = false;
+      tc_lost = true;
+    }
     if (ok) {
       // the matrix each residual multiplies: T(z_j) assembled once, or the one dense term
       const double2* M = nullptr;
       double2 fM = make_double2(0.0, 0.0), id = make_double2(0.0, 0.0);
-      if (P.n_dense >= 2) {  // assembled by the factor group with the slot
+      if (use_oz) {
+        // every dense term through the digit products; nothing to set up here
+      } else if (P.n_dense >= 2) {  // assembled by the factor group with the slot
         M = a.t64 + si * a.t64_stride;
         fM = make_double2(1.0, 0.0);
       } else {
@@ -545,7 +563,16 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
       double dprev = sl.xm;
       bool conv = false;
       for (int sw = 1; sw <= a.max_sweeps && ok; ++sw) {
-        residual_fp64(X, R, c, sm.r.u.res, M, fM, id);
+        if (use_oz) {
+          if (!ozk::residual(P, c.fz, X, R, sm.r.u.oz, sm.ozb, a.ysl + si * a.ysl_stride,
+                             sm.tmem_base + TMEM_REFINE, sm.r.ozg, sm.r.ozred, a.tc_wait_cycles)) {
+            ok = false;
+            tc_lost = true;
+            break;
+          }
+        } else {
+          residual_fp64(X, R, c, sm.r.u.res, M, fM, id);
+        }
         pc.mark(PH_RESIDUAL);
         double rm = 0.0;
         for (size_t e = tid; e < nl; e += THREADS) rm = fmax(rm, fmax(fabs(R[e].x), fabs(R[e].y)));
@@ -597,7 +624,7 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
     }
     if (tid == 0)
       a.node_info[rg.node_off + it.j] =
-          info | (sweeps << 24) | (sl.tc_timeout ? (1 << 29) : 0) | (ok ? 0 : (1 << 30));
+          info | (sweeps << 24) | (tc_lost ? (1 << 29) : 0) | (ok ? 0 : (1 << 30));
     gsync();
     mbar_arrive(&sm.empty[s]);
   }
@@ -611,9 +638,10 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_factor_solve_mixed(NodeArgs 
   unsigned long long t_start = 0;
   if (a.phase && tid == 0) t_start = global_ns();
 
-  // tensor memory (factor group's warp 0) and the barriers, for the whole persistent CTA
-  if (tid < 32) tcu::tmem_alloc(&sm.tmem_base);
+  // tensor memory (all of it: one CTA per SM) and the barriers, for the whole persistent CTA
+  if (tid < 32) tcu::tmem_alloc_cols(&sm.tmem_base, TMEM_ALL);
   if (tid == 0) {
+    ozk::init_bars(sm.ozb);
     for (int s = 0; s < SLOTS; ++s) {
       mbar_init_count(&sm.full[s], THREADS);
       mbar_init_count(&sm.empty[s], THREADS);
@@ -638,17 +666,16 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_factor_solve_mixed(NodeArgs 
       tcu::wait_parity(&sm.mbar_tc[0], cx.phase[0] ^ 1u, tcu::WAIT_CYCLES);
       tcu::wait_parity(&sm.mbar_tc[1], cx.phase[1] ^ 1u, tcu::WAIT_CYCLES);
     }
-    tcu::fence_before();
-    gsync();
-    tcu::fence_after();
-    if (tid < 32) tcu::tmem_dealloc(cx.tmem);
   } else {
     refine_group(a, sm, pc);
   }
-  if (a.phase) {  // the CTA's lifetime, for cycles per ns
-    __syncthreads();
-    if (tid == 0) a.phase[(size_t)blockIdx.x * PMCIM_PHASES + PH_CTA_WALL_NS] += global_ns() - t_start;
-  }
+  // both groups are done with tensor memory before it is given back
+  tcu::fence_before();
+  __syncthreads();
+  tcu::fence_after();
+  if (tid < 32) tcu::tmem_dealloc_cols(sm.tmem_base, TMEM_ALL);
+  if (a.phase && tid == 0)  // the CTA's lifetime, for cycles per ns
+    a.phase[(size_t)blockIdx.x * PMCIM_PHASES + PH_CTA_WALL_NS] += global_ns() - t_start;
 }
 
 }  // namespace

@@ -155,6 +155,10 @@ struct ProblemDev {
   const double2* A;    // n_dense * n * n, column-major, in term order
   const double2* V;    // n x l probe block
   const float2* A32;   // the same coefficients rounded to complex64 (FP32 LU assembly)
+  // the coefficients as exact BF16 digits for the tensor-core refinement residual
+  // (ozaki.cuh; NULL until made), and the row exponents [dense term][row blocks x 128]
+  const unsigned char* Adig;
+  const int32_t* Aexp;
   TermDesc term[PMCIM_MAX_TERMS];
 };
 
@@ -207,6 +211,9 @@ struct NodeArgs {
   int32_t* err;               // mixed kernel: set to 1 when a wait between its thread groups ran out
   double2* t64;               // mixed kernel: per slot, T(z_j) in FP64 for the residuals (problems
   size_t t64_stride;          // with two or more dense terms); double2 elements per slot
+  int oz;                     // mixed kernel: 1 = refinement residuals on the tensor cores
+  unsigned char* ysl;         // mixed kernel: per slot, the digits of f_k X (ozaki.cuh)
+  size_t ysl_stride;          // bytes per slot
   long long tc_wait_cycles;       // mixed kernel: limit of a wait for a tensor-core commit
   long long handoff_wait_cycles;  // mixed kernel: limit of a wait between its thread groups
 };
@@ -221,6 +228,19 @@ cudaError_t launch_factor_solve_mixed(const NodeArgs& a, cudaStream_t s);
 int mixed_slots_per_cta();  // workspace slots each CTA of the mixed kernel cycles through
 // dst[i] = complex64(src[i]), i < count (the FP32 copy of the coefficients)
 cudaError_t round_coefficients_c64(const double2* src, float2* dst, size_t count, cudaStream_t s);
+// Exact BF16 digits of the n_dense dense coefficients (ozaki.cu): row exponents
+// into exps ([n_dense][row blocks x 128]) and digit tiles into dig.
+cudaError_t make_coefficient_digits(const double2* A, int n, int n_dense, int32_t* exps, unsigned char* dig,
+                                    cudaStream_t s);
+// Bytes of the coefficient digits of a problem, and of one slot's digits of f_k X.
+size_t coefficient_digit_bytes(int n, int n_dense);
+size_t y_digit_scratch_bytes(int n, int n_dense);
+// R_j = V - T(z_j) X_j for m points, one node per CTA, on the tensor cores
+// (ozaki.cu). ysl: per-CTA Y-digit scratch of ysl_stride bytes for `ctas` CTAs;
+// status[j] = 0, or 1 when a wait ran out (R_j not valid).
+cudaError_t launch_residual_points(const ProblemDev* prob, const double2* z, int m, const double2* X, double2* R,
+                                   unsigned char* ysl, size_t ysl_stride, int ctas, int32_t* status,
+                                   long long wait_cycles, cudaStream_t s);
 // warp-per-node FP64 kernel for small problems (lu_small.cu)
 bool small_kernel_fits(int n, int l);
 cudaError_t prepare_factor_small();

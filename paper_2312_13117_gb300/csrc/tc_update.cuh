@@ -162,6 +162,17 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t tmem) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// The same for a given column count (a power of two, 32..512).
+__device__ __forceinline__ void tmem_alloc_cols(uint32_t* dst_smem, uint32_t cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(cols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_cols(uint32_t tmem, uint32_t cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols) : "memory");
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -273,7 +284,7 @@ __device__ __forceinline__ void stage_barrier() {
 // the group call it; it returns with the group synchronised and no MMA in
 // flight, unless a wait ran out (then *cx.bad is set and the rest of the
 // panel's update is skipped).
-__device__ void update(float2* __restrict__ M, int n, int ncols, int k0, int kb, Ctx& cx) {
+__device__ inline void update(float2* __restrict__ M, int n, int ncols, int k0, int kb, Ctx& cx) {
   const int tid = lucore::gtid(), warp = tid >> 5, lane = tid & 31;
   const size_t ld = (size_t)n;
   const int kend = k0 + kb;

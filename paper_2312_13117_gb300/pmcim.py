@@ -28,7 +28,8 @@ EXPORTS = ["pmcim_default_options", "pmcim_problem_create", "pmcim_problem_destr
            "pmcim_indicator", "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_status_string",
            "pmcim_last_error", "pmcim_profile_enable", "pmcim_profile_reset", "pmcim_profile_read",
            "pmcim_solve_points_noalloc", "pmcim_batch_solve", "pmcim_screen_features", "pmcim_screen_train",
-           "pmcim_screen_apply", "pmcim_screen_gradient", "pmcim_pmcima", "pmcim_debug_wait_limits"]
+           "pmcim_screen_apply", "pmcim_screen_gradient", "pmcim_pmcima", "pmcim_debug_wait_limits",
+           "pmcim_residual"]
 
 KERNELS = ["factor_fp64", "reduce", "indicator", "beyn", "verify", "gather", "factor_fp32", "screen"]
 SCREEN_PARAMS = 4481
@@ -49,7 +50,7 @@ class pmcim_options(C.Structure):
                 ("precision", C.c_int32), ("max_ir_sweeps", C.c_int32), ("max_split_depth", C.c_int32),
                 ("beyn_K", C.c_int32), ("cuda_stream", C.c_void_p), ("screen_params", C.c_void_p),
                 ("screen_threshold", C.c_double), ("screen_N", C.c_int32), ("indicator_N", C.c_int32),
-                ("tol_ir", C.c_double)]
+                ("tol_ir", C.c_double), ("residual_fp64", C.c_int32)]
 
 
 class pmcim_batch_item(C.Structure):
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pmcim_profile_read.argtypes = [C.POINTER(pmcim_profile)]
     lib.pmcim_profile_read.restype = None
     lib.pmcim_debug_wait_limits.argtypes = [C.c_int64, C.c_int64]
+    lib.pmcim_residual.argtypes = [P, C.POINTER(pmcim_options), I32, VP, I32, VP, VP, VP]
     lib.pmcim_solve_points_noalloc.argtypes = [I32, I32, C.POINTER(pmcim_fterm), C.POINTER(C.c_uint8), VP, I32,
                                                VP, I32, VP, VP, VP, VP]
     F = C.c_void_p
@@ -121,7 +123,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     for name in ("pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments", "pmcim_indicator",
                  "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_solve_points_noalloc", "pmcim_batch_solve",
                  "pmcim_screen_features", "pmcim_screen_train", "pmcim_screen_apply", "pmcim_screen_gradient",
-                 "pmcim_pmcima", "pmcim_debug_wait_limits"):
+                 "pmcim_pmcima", "pmcim_debug_wait_limits", "pmcim_residual"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -240,8 +242,9 @@ _screen_keep = []
 
 def options(tol_ind=0.1, tol_svd=1e-6, tol_verify=1e-6, precision=PREC_FP64, max_ir_sweeps=6,
             max_split_depth=8, stream=None, screen_params=None, screen_threshold=0.0,
-            screen_N=16, tol_ir=None, indicator_N=0, beyn_K=1) -> pmcim_options:
+            screen_N=16, tol_ir=None, indicator_N=0, beyn_K=1, residual_fp64=False) -> pmcim_options:
     o = pmcim_default_options()
+    o.residual_fp64 = 1 if residual_fp64 else 0
     o.indicator_N = int(indicator_N)
     o.beyn_K = int(beyn_K)
     o.tol_ind, o.tol_svd, o.tol_verify = tol_ind, tol_svd, tol_verify
@@ -410,6 +413,24 @@ class Problem:
         opt = opt or options()
         _check(lib.pmcim_verify(self.handle, C.byref(opt), m, _ptr(lam), _ptr(sig), _ptr(acc)), "pmcim_verify")
         return sig[:m], acc[:m].astype(bool)
+
+    def residual(self, z, V, X, opt=None):
+        """R_j = V - T(z_j) X_j on the tensor cores; X is m x n x l (or n x l for one point)."""
+        lib = load()
+        z = np.ascontiguousarray(np.atleast_1d(np.asarray(z, np.complex128)))
+        X = np.asarray(X, np.complex128)
+        one = X.ndim == 2
+        if one:
+            X = X[None]
+        m, n, l = X.shape
+        Xc = np.ascontiguousarray(X.transpose(0, 2, 1))          # column-major blocks
+        Vc = np.ascontiguousarray(np.asarray(V, np.complex128).T)
+        R = np.zeros_like(Xc)
+        opt = opt or options()
+        _check(lib.pmcim_residual(self.handle, C.byref(opt), m, _ptr(z), l, _ptr(Vc), _ptr(Xc), _ptr(R)),
+               "pmcim_residual")
+        R = R.transpose(0, 2, 1)
+        return R[0] if one else R
 
     def pmcima(self, regions, V, tol_eps=1e-6, cap=None, opt=None, want_vecs=True):
         """pmCIMa with probe column V[:, 0]: returns dict(lam, vecs, sigma_min, stats)."""

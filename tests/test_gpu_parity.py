@@ -678,3 +678,15 @@ def test_paper_quadratic_two_pass_matches_oracle(pm):
     assert len(ref.lam) == 34
     assert _match_lam(res["lam"], ref.lam) <= LAM_TOL
     P.close()
+
+
+@pytest.mark.parametrize("form", MIXED_FORMS)
+def test_mixed_residual_on_fp64_pipe(pm, form):
+    """The precision forms with their refinement residuals on the FP64 pipe (option
+    residual_fp64) instead of the tensor cores: the same eigenvalues as the oracle."""
+    W = w.delay_large(n=64, l=8, N=32, nx=4, ny=12)
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    res = P.solve(W.regions, W.V, opt=_mixed_opt(pm, form, residual_fp64=True))
+    ref = o.pmcimb(W.problem, W.regions, W.V)
+    assert _match_lam(res["lam"], ref.lam) <= LAM_TOL
+    P.close()

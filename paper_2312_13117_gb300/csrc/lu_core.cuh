@@ -223,18 +223,28 @@ __device__ void cta_lu_trsm(T2* __restrict__ M, int n, int ncols, int k0, int kb
   }
   gsync();
   {
-    // one warp per column, lane i holds row k0+i (NB == warp size)
+    // a warp takes CW columns at a time, lane i holds row k0+i of each (NB == warp
+    // size); the CW substitutions are independent, so their shuffle chains overlap
+    constexpr int CW = 4;
     const int lane = tid & 31, wid = tid >> 5;
-    for (int c = kend + wid; c < ncols; c += THREADS / 32) {
-      T2* cc = M + (size_t)c * ld + k0;
-      T2 x = (lane < kb) ? cc[lane] : czero<T2>();
+    for (int c0 = kend + wid * CW; c0 < ncols; c0 += (THREADS / 32) * CW) {
+      T2 x[CW];
+#pragma unroll
+      for (int q = 0; q < CW; ++q)
+        x[q] = (lane < kb && c0 + q < ncols) ? M[(size_t)(c0 + q) * ld + k0 + lane] : czero<T2>();
       for (int t = 0; t < kb - 1; ++t) {
-        T2 xt;
-        xt.x = __shfl_sync(0xffffffffu, x.x, t);
-        xt.y = __shfl_sync(0xffffffffu, x.y, t);
-        if (lane > t && lane < kb) cfms(x, sm.Ls[t * NB + lane], xt);
+        const T2 lt = sm.Ls[t * NB + lane];
+#pragma unroll
+        for (int q = 0; q < CW; ++q) {
+          T2 xt;
+          xt.x = __shfl_sync(0xffffffffu, x[q].x, t);
+          xt.y = __shfl_sync(0xffffffffu, x[q].y, t);
+          if (lane > t && lane < kb) cfms(x[q], lt, xt);
+        }
       }
-      if (lane < kb) cc[lane] = x;
+#pragma unroll
+      for (int q = 0; q < CW; ++q)
+        if (lane < kb && c0 + q < ncols) M[(size_t)(c0 + q) * ld + k0 + lane] = x[q];
     }
   }
   gsync();

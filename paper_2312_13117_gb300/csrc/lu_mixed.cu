@@ -114,7 +114,6 @@ struct Slot {
   int item;        // node item, or -1: no more nodes
   int info;        // 0, or 1 + first zero-pivot column of the FP32 LU
   int tc_timeout;  // a tensor-core wait ran out during the LU
-  double xm;       // max |X_0|
 };
 
 struct MixedSmem {
@@ -330,25 +329,43 @@ __device__ void assemble_fp64(const NodeCtx& cx, double2* __restrict__ T, float2
 // T(z_j) for the FP32 LU: FP32 arithmetic on the complex64 copy of the A_k
 // (the LU only has to approximate T(z_j) to FP32 accuracy; the refinement
 // residuals use the FP64 coefficients). It keeps the factor group off the FP64
-// pipe, which the refine group saturates.
-__device__ void assemble32(const NodeCtx& cx, float2* M32) {
+// pipe. The flattened element index with eight elements per thread in flight
+// keeps the loads of each term overlapped; the identity terms land on the
+// diagonal (element e with e % (n + 1) == 0) in the same pass.
+__device__ void assemble32(const NodeCtx& cx, float2* __restrict__ M32) {
   const ProblemDev& P = cx.P;
   const int n = P.n;
   const size_t nn = (size_t)n * n;
+  constexpr int U = 8;
   const float2 fid = cx.fid32;
-  for (int col = 0; col < n; ++col) {
-    for (int row = gtid(); row < n; row += THREADS) {
-      const size_t e = (size_t)col * n + row;
-      float2 v = row == col ? fid : make_float2(0.f, 0.f);
-      for (int k = 0; k < P.K; ++k) {
-        const TermDesc& t = P.term[k];
-        if (t.dense) {
-          const float2 a = P.A32[(size_t)t.mat_index * nn + e], f = cx.fz32[k];
-          v.x = fmaf(f.x, a.x, fmaf(-f.y, a.y, v.x));
-          v.y = fmaf(f.x, a.y, fmaf(f.y, a.x, v.y));
-        }
+  for (size_t e0 = gtid(); e0 < nn; e0 += (size_t)U * THREADS) {
+    float2 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const size_t e = e0 + (size_t)u * THREADS;
+      v[u] = (e < nn && e % (size_t)(n + 1) == 0) ? fid : make_float2(0.f, 0.f);
+    }
+    for (int k = 0; k < P.K; ++k) {
+      const TermDesc& t = P.term[k];
+      if (!t.dense) continue;
+      const float2* __restrict__ A = P.A32 + (size_t)t.mat_index * nn;
+      float2 a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const size_t e = e0 + (size_t)u * THREADS;
+        a[u] = e < nn ? A[e] : make_float2(0.f, 0.f);
       }
-      M32[e] = v;
+      const float2 f = cx.fz32[k];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        v[u].x = fmaf(f.x, a[u].x, fmaf(-f.y, a[u].y, v[u].x));
+        v[u].y = fmaf(f.x, a[u].y, fmaf(f.y, a[u].x, v[u].y));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const size_t e = e0 + (size_t)u * THREADS;
+      if (e < nn) M32[e] = v[u];
     }
   }
 }
@@ -452,8 +469,6 @@ __device__ void factor_group(const NodeArgs& a, MixedSmem& sm, tcu::Ctx& cx, Pha
     const ProblemDev& P = c.P;
     const int n = P.n, l = P.l, ncols = n + l;
     const size_t nn = (size_t)n * n, nl = (size_t)n * l;
-    int* perm = reinterpret_cast<int*>(slot + mixed_residual_offset(n, l) + nl * sizeof(double2));
-    double2* X = a.X + rg.x_off + (size_t)it.j * nl;
     pc.mark(PH_SETUP);
     if (P.n_dense >= 2 && !a.oz)  // T(z_j) in FP64 for the refine group's FP64 residual, and rounded
       assemble_fp64(c, a.t64 + si * a.t64_stride, M32);
@@ -464,24 +479,10 @@ __device__ void factor_group(const NodeArgs& a, MixedSmem& sm, tcu::Ctx& cx, Pha
     pc.mark(PH_ASSEMBLE);
     const int bad_before = sm.tc_bad;
     const int info = cta_lu32(M32, n, ncols, piv, sm.f.u.lu32, cx, rg.lu_tc != 0, pc);
-    double xm = 0.0;
-    if (info == 0) {
-      cta_back_blocked(M32, n, l, sm.f.u.lu32);
-      cta_pivots_to_perm(piv, perm, n);
-      for (size_t e = tid; e < nl; e += THREADS) {
-        const float2 y = M32[nn + e];
-        const double2 x = make_double2((double)y.x, (double)y.y);
-        X[e] = x;
-        xm = fmax(xm, fmax(fabs(x.x), fabs(x.y)));
-      }
-      xm = block_max(xm, c.red);
-    }
-    pc.mark(PH_FIRST_SOLVE);
     if (tid == 0) {
       sl.item = idx;
       sl.info = info;
       sl.tc_timeout = sm.tc_bad != bad_before;
-      sl.xm = xm;
     }
     mbar_arrive(&sm.full[s]);
   }
@@ -527,10 +528,25 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
     const int n = P.n, l = P.l, ncols = n + l;
     const size_t nn = (size_t)n * n, nl = (size_t)n * l;
     double2* R = reinterpret_cast<double2*>(slot + mixed_residual_offset(n, l));
-    const int* perm = reinterpret_cast<const int*>(slot + mixed_residual_offset(n, l) + nl * sizeof(double2));
+    int* perm = reinterpret_cast<int*>(slot + mixed_residual_offset(n, l) + nl * sizeof(double2));
     double2* X = a.X + rg.x_off + (size_t)it.j * nl;
     int info = sl.info;
     bool ok = (info == 0);
+    // the first solve, X_0 = U^-1 (L^-1 P V) in FP32 (the factor group eliminated V
+    // with the LU), here so that the factor group can start the next node
+    double xm = 0.0;
+    if (ok) {
+      cta_back_blocked(M32, n, l, sm.r.u.lu32);
+      cta_pivots_to_perm(piv, perm, n);
+      for (size_t e = tid; e < nl; e += THREADS) {
+        const float2 y = M32[nn + e];
+        const double2 x = make_double2((double)y.x, (double)y.y);
+        X[e] = x;
+        xm = fmax(xm, fmax(fabs(x.x), fabs(x.y)));
+      }
+      xm = block_max(xm, c.red);
+    }
+    pc.mark(PH_FIRST_SOLVE);
     bool tc_lost = sl.tc_timeout != 0;
     int sweeps = 0;
     // residuals on the tensor cores (exact digit products), unless a wait of that
@@ -560,7 +576,7 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
           }
         }
       }
-      double dprev = sl.xm;
+      double dprev = xm;
       bool conv = false;
       for (int sw = 1; sw <= a.max_sweeps && ok; ++sw) {
         if (use_oz) {

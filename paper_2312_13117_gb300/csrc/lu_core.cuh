@@ -210,6 +210,201 @@ __device__ void cta_lu_panel(T2* __restrict__ M, int n, int ncols, int k0, int k
   }
 }
 
+// The same panel factorisation (same pivots, same arithmetic up to the order of
+// the updates of each element) in sub-panels of SB <= 8 columns held in shared
+// memory: each sub-panel is loaded once, factored column by column in shared
+// memory, written back, and then applied to the rest of the panel (its row
+// swaps as one gather, the unit lower triangular solve for its U rows, and one
+// rank-SB update). The row swaps of the columns outside the panel (and of the
+// panel's earlier sub-panels) are applied after the panel, pivot by pivot, as in
+// LAPACK's getrf. scratch: shared memory of scratch_elems elements, at least
+// (n - k0) + 8 NB + 40 (then SB = 1).
+template <typename T2>
+__device__ __noinline__ void cta_lu_panel_sub(T2* __restrict__ M, int n, int ncols, int k0, int kb, int* __restrict__ piv,
+                                 LuSmemT<T2>& sm, T2* __restrict__ scratch, int scratch_elems) {
+  const int tid = gtid();
+  const size_t ld = (size_t)n;
+  const int kend = k0 + kb;
+  using R = decltype(l1abs(T2{}));
+  constexpr int SBMAX = 8, CHUNK = 8;
+  const int m0 = n - k0;
+  int SB = SBMAX;
+  while (SB > 1 && (size_t)m0 * SB + (size_t)NB * SBMAX + 40 > (size_t)scratch_elems) SB >>= 1;
+  T2* sp = scratch;                                  // sub-panel, rows p0..n-1, leading dimension m
+  T2* us = scratch + (size_t)m0 * SB;                // its U rows for the rest of the panel, [col][t]
+  int* mp = reinterpret_cast<int*>(us + NB * SBMAX);  // composed swaps: count, dst[2 SBMAX], src[2 SBMAX]
+  for (int p0 = k0; p0 < kend; p0 += SB) {
+    const int sb = min(SB, kend - p0);
+    const int m = n - p0;
+    // 1. load
+#pragma unroll 4
+    for (int e = tid; e < m * sb; e += THREADS) {
+      const int r = e % m, c = e / m;
+      sp[(size_t)c * m + r] = M[(size_t)(p0 + c) * ld + p0 + r];
+    }
+    gsync();
+    // 2. factor in shared memory
+    for (int j = 0; j < sb; ++j) {
+      R bv = R(-1);
+      int bi = m;
+      for (int r = j + tid; r < m; r += THREADS) {
+        const R v = l1abs(sp[(size_t)j * m + r]);
+        if (v > bv) { bv = v; bi = r; }
+      }
+      warp_argmax(bv, bi);
+      if ((tid & 31) == 0) { sm.red_v[tid >> 5] = (double)bv; sm.red_i[tid >> 5] = bi; }
+      gsync();
+      if (tid == 0) {
+        double v = sm.red_v[0];
+        int ii = sm.red_i[0];
+        for (int w = 1; w < THREADS / 32; ++w)
+          if (sm.red_v[w] > v || (sm.red_v[w] == v && sm.red_i[w] < ii)) { v = sm.red_v[w]; ii = sm.red_i[w]; }
+        if (ii >= m) ii = j;
+        sm.piv_sh = ii;
+        piv[p0 + j] = p0 + ii;
+      }
+      gsync();
+      const int pr = sm.piv_sh;
+      if (pr != j && tid < sb) {
+        const T2 t = sp[(size_t)tid * m + j];
+        sp[(size_t)tid * m + j] = sp[(size_t)tid * m + pr];
+        sp[(size_t)tid * m + pr] = t;
+      }
+      gsync();
+      const T2 pv = sp[(size_t)j * m + j];
+      const bool zero = cis_zero(pv);
+      if (zero && tid == 0 && sm.info_sh == 0) sm.info_sh = p0 + j + 1;
+      if (!zero) {
+        const T2 rp = crecip(pv);
+        for (int r = j + 1 + tid; r < m; r += THREADS) {
+          const T2 lv = cmul(sp[(size_t)j * m + r], rp);
+          sp[(size_t)j * m + r] = lv;
+          for (int c = j + 1; c < sb; ++c) cfms(sp[(size_t)c * m + r], lv, sp[(size_t)c * m + j]);
+        }
+      }
+      gsync();
+    }
+    // 3. write back
+#pragma unroll 4
+    for (int e = tid; e < m * sb; e += THREADS) {
+      const int r = e % m, c = e / m;
+      M[(size_t)(p0 + c) * ld + p0 + r] = sp[(size_t)c * m + r];
+    }
+    const int c1 = p0 + sb, nr = kend - c1;  // the rest of the panel
+    if (nr > 0) {
+      // the sub-panel's swaps composed: row dst[i] receives the old row src[i]
+      if (tid == 0) {
+        int cnt = 0;
+        int* dst = mp + 1;
+        int* src = mp + 1 + 2 * SBMAX;
+        for (int j = 0; j < sb; ++j) {
+          const int a = p0 + j, b = piv[p0 + j];
+          if (a == b) continue;
+          int ia = -1, ib = -1;
+          for (int i = 0; i < cnt; ++i) {
+            if (dst[i] == a) ia = i;
+            if (dst[i] == b) ib = i;
+          }
+          if (ia < 0) { ia = cnt; dst[cnt] = a; src[cnt] = a; ++cnt; }
+          if (ib < 0) { ib = cnt; dst[cnt] = b; src[cnt] = b; ++cnt; }
+          const int t = src[ia];
+          src[ia] = src[ib];
+          src[ib] = t;
+        }
+        mp[0] = cnt;
+      }
+      gsync();
+      {
+        const int cnt = mp[0];
+        const int* dst = mp + 1;
+        const int* src = mp + 1 + 2 * SBMAX;
+        constexpr int GU = (2 * SBMAX * NB + THREADS - 1) / THREADS;  // gather elements per thread
+        T2 tmp[GU];
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+          const int e = tid + u * THREADS;
+          if (e < cnt * nr) tmp[u] = M[(size_t)(c1 + e / cnt) * ld + src[e % cnt]];
+        }
+        gsync();
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+          const int e = tid + u * THREADS;
+          if (e < cnt * nr) M[(size_t)(c1 + e / cnt) * ld + dst[e % cnt]] = tmp[u];
+        }
+      }
+      gsync();
+      // U rows p0..p0+sb-1 of the rest: unit lower triangular solve with L11 (one thread per column)
+      for (int c = tid; c < nr; c += THREADS) {
+        T2 u[SBMAX];
+#pragma unroll
+        for (int t = 0; t < SBMAX; ++t)
+          if (t < sb) u[t] = M[(size_t)(c1 + c) * ld + p0 + t];
+#pragma unroll
+        for (int t = 1; t < SBMAX; ++t)
+#pragma unroll
+          for (int q = 0; q < SBMAX; ++q)
+            if (t < sb && q < t) cfms(u[t], sp[(size_t)q * m + t], u[q]);
+#pragma unroll
+        for (int t = 0; t < SBMAX; ++t)
+          if (t < sb) {
+            M[(size_t)(c1 + c) * ld + p0 + t] = u[t];
+            us[c * SBMAX + t] = u[t];
+          }
+      }
+      gsync();
+      // rank-sb update of rows p0+sb..n-1 of the rest, CHUNK columns in flight per row
+      for (int r = sb + tid; r < m; r += THREADS) {
+        T2 lr[SBMAX];
+#pragma unroll
+        for (int t = 0; t < SBMAX; ++t) lr[t] = t < sb ? sp[(size_t)t * m + r] : czero<T2>();
+        for (int cc = 0; cc < nr; cc += CHUNK) {
+          T2 v[CHUNK];
+#pragma unroll
+          for (int q = 0; q < CHUNK; ++q)
+            if (cc + q < nr) v[q] = M[(size_t)(c1 + cc + q) * ld + p0 + r];
+#pragma unroll
+          for (int q = 0; q < CHUNK; ++q)
+            if (cc + q < nr) {
+#pragma unroll
+              for (int t = 0; t < SBMAX; ++t)
+                if (t < sb) cfms(v[q], lr[t], us[(cc + q) * SBMAX + t]);
+              M[(size_t)(c1 + cc + q) * ld + p0 + r] = v[q];
+            }
+        }
+      }
+    }
+    gsync();
+  }
+  // 4. the panel's swaps on the other columns: a swap of sub-panel s is already in
+  // the columns of sub-panel s and of the later sub-panels
+  constexpr int RBS = sizeof(T2) == 8 ? 4 : 2;
+  for (int j = k0; j < kend; ++j) {
+    const int p = piv[j];
+    if (p == j) continue;
+    const int done_lo = k0 + ((j - k0) / SB) * SB;  // columns done_lo..kend-1 hold it already
+    for (int c0 = tid; c0 < ncols; c0 += THREADS * RBS) {
+      T2 a[RBS], b[RBS];
+#pragma unroll
+      for (int u = 0; u < RBS; ++u) {
+        const int c = c0 + u * THREADS;
+        if (c < ncols && (c < done_lo || c >= kend)) {
+          a[u] = M[(size_t)c * ld + j];
+          b[u] = M[(size_t)c * ld + p];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < RBS; ++u) {
+        const int c = c0 + u * THREADS;
+        if (c < ncols && (c < done_lo || c >= kend)) {
+          M[(size_t)c * ld + j] = b[u];
+          M[(size_t)c * ld + p] = a[u];
+        }
+      }
+    }
+    gsync();
+  }
+}
+
 // U12 = L11^{-1} A12 for rows k0..k0+kb-1, columns k0+kb..ncols-1.
 template <typename T2>
 __device__ void cta_lu_trsm(T2* __restrict__ M, int n, int ncols, int k0, int kb, LuSmemT<T2>& sm) {

@@ -177,7 +177,13 @@ __device__ int cta_lu32(float2* __restrict__ M, int n, int ncols, int* __restric
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = min(NB, n - k0);
     const int kend = k0 + kb;
-    cta_lu_panel(M, n, ncols, k0, kb, piv, sm);
+    // the panel in shared-memory sub-panels, in the tensor-core stage (idle during the
+    // panel), while one sub-panel column fits there; else in global memory
+    constexpr int kScratch = tcu::STAGE_BYTES / (int)sizeof(float2);
+    if (n - k0 + NB * 8 + 40 <= kScratch)
+      cta_lu_panel_sub(M, n, ncols, k0, kb, piv, sm, reinterpret_cast<float2*>(cx.stage), kScratch);
+    else
+      cta_lu_panel(M, n, ncols, k0, kb, piv, sm);
     pc.mark(PH_PANEL);
     if (kend >= ncols) continue;
     cta_lu_trsm(M, n, ncols, k0, kb, sm);

@@ -43,7 +43,9 @@ FACTOR_FP64_TRAFFIC_PER_NODE = 28.61e9 / 64
 # DRAM bytes per node of k_factor_solve_mixed, from one ncu capture of a 320-node launch per form
 # (dram__bytes_read.sum + dram__bytes_write.sum); scaled to a launch by its node count. None: no
 # capture of the kernel as it stands
-MIXED_TRAFFIC_PER_NODE = {"fp32ir": None, "tf32x3": (60.38e9 + 41.45e9) / 320}
+MIXED_TRAFFIC_PER_NODE = {"fp32ir": None, "tf32x3": (77.39e9 + 47.31e9) / 384, "tf32x3_fp64res": None}
+# sm__pipe_tensor_cycles_active (% of active cycles) of the same capture of the tensor-core form
+MIXED_TENSOR_PIPE_PCT = {"tf32x3": 7.57}
 # FP32 pipe: 128 FFMA / SM / clock (measured 73.3 TFLOP/s at ~2.0 GHz); at the 2.07 GHz maximum:
 FP32_PEAK_TFLOPS = 128 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
 
@@ -58,6 +60,8 @@ def _peaks():
 
 # TF32 tensor peak: the measured dense bf16 burst x the nominal tf32 / bf16 ratio (1.1 / 2.25 PFLOP/s)
 TF32_PEAK_TFLOPS = float(_peaks().get("bf16_tflops", 1900.0)) * 1.1 / 2.25
+# BF16 tensor peak for a kernel timed inside a long step: the measured sustained figure
+BF16_SUSTAINED_TFLOPS = float(_peaks().get("bf16_tflops_sustained", 1700.0))
 
 
 def fp64_peak_tflops(sm_max_mhz: float) -> float:
@@ -774,7 +778,7 @@ def main():
         fm = profm["factor_fp32"]
         # FP64 work: per sweep one residual product T(z)X (T(z) assembled in FP64 once per node
         # by the factor group when the problem has two or more dense terms), plus the fallback solves
-        w_asm = msolves * 8.0 * k_dense * n * n if k_dense >= 2 else 0.0
+        w_asm = msolves * 8.0 * k_dense * n * n if (k_dense >= 2 and name == "tf32x3_fp64res") else 0.0
         w_res = aggm["ir_sweeps"] * 8.0 * n * n * l
         w64 = w_res + w_asm + aggm["ir_fallbacks"] * (8.0 * n ** 3 / 3 + 8.0 * n * n * l)
         w32 = msolves * (8.0 * n ** 3 / 3 + 8.0 * n * n * l) + aggm["ir_sweeps"] * 8.0 * n * n * l
@@ -791,7 +795,37 @@ def main():
                 "launches": fm["launches"], "avg_launch_ms": fm["ms"] / max(1, fm["launches"]),
                 "share_of_step": fm["ms"] / tm_ms if tm_ms else None}
         cyc = fm.get("phase_cycles", {})
-        if cyc.get("residual_fp64"):
+        upd = sum(8.0 * 32 * (n - k) * (n + l - k) for k in range(32, n, 32))
+        if name != "tf32x3_fp64res":
+            # refinement residuals on the tensor cores: the kernel's arithmetic is tensor work,
+            # 3xTF32 LU trailing updates (tf32x3) and the BF16 digit products of the residuals
+            # (34 digit pairs x 2 MMAs of 128 x 32 x 16 per 32 inner indices, row block, dense
+            # term and 16-column block), counted in BF16-equivalent flops
+            cb, rbn, kcn = -(-l // 16), -(-n // 128), -(-n // 32)
+            res_bf16 = aggm["ir_sweeps"] * k_dense * cb * rbn * kcn * 136 * 2.0 * 128 * 32 * 16
+            lu_tf32 = 3.0 * upd * msolves if name == "tf32x3" else 0.0
+            ratio = (2.25 / 1.1)
+            t_s = fm["ms"] / 1e3
+            ach = (res_bf16 + lu_tf32 * ratio) / t_s / 1e12 if t_s > 0 else None
+            roof = {"bound": "tensor",
+                    "kernel": "k_factor_solve_mixed (tensor pipe: 3xTF32 LU trailing updates + BF16 digit "
+                              "products of the refinement residuals)" if name == "tf32x3" else
+                              "k_factor_solve_mixed (tensor pipe: BF16 digit products of the refinement "
+                              "residuals; LU on the FMA pipes)",
+                    "achieved": ach, "peak": BF16_SUSTAINED_TFLOPS, "unit": "TFLOP/s (BF16-equivalent)",
+                    "frac": (ach / BF16_SUSTAINED_TFLOPS) if ach else None,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained; TF32 flops x 2.25/1.1",
+                    "traffic": (MIXED_TRAFFIC_PER_NODE[name] * msolves / max(1, fm["launches"])
+                                if MIXED_TRAFFIC_PER_NODE.get(name) else None),
+                    "traffic_note": "ncu DRAM bytes of a 384-node capture, scaled by nodes per launch",
+                    "ncu_tensor_pipe_active_pct": MIXED_TENSOR_PIPE_PCT.get(name),
+                    "residual_bf16_tflops": res_bf16 / t_s / 1e12 if t_s > 0 else None,
+                    "lu_tf32_tflops": lu_tf32 / t_s / 1e12 if t_s > 0 else None,
+                    "residual_fp64_equivalent_tflops": a64,
+                    "fp32_work_tflops": a32,
+                    "launches": fm["launches"], "avg_launch_ms": fm["ms"] / max(1, fm["launches"]),
+                    "share_of_step": fm["ms"] / tm_ms if tm_ms else None}
+        if cyc.get("residual_fp64") and name == "tf32x3_fp64res":
             # SM clock cycles of the refine group inside the residual phase, summed over CTAs
             # (one CTA per SM): the FP64 pipe's rate while the residual runs
             roof["residual_dfma_per_sm_clock"] = w_res / 2.0 / cyc["residual_fp64"]
@@ -814,7 +848,6 @@ def main():
         if name.startswith("tf32x3"):
             # tensor-pipe work of the trailing updates: 3 split products of the complex
             # rank-32 updates, 8 real flops per complex multiply-add
-            upd = sum(8.0 * 32 * (n - k) * (n + l - k) for k in range(32, n, 32))
             lu_cyc = sum(cyc.get(k, 0.0) for k in ("lu_update",))
             tf = 3.0 * upd * msolves / (lu_cyc / (152 * smax * 1e6)) / 1e12 if lu_cyc else None
             rec["tensor"] = {"tf32_tflops_during_update_phase": tf, "tf32_peak_tflops": TF32_PEAK_TFLOPS,

@@ -247,7 +247,11 @@ int pmcim_pmcima(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmc
    the unit eigenvector v from Beyn's step; since sigma_min <= ||T(lambda) v||,
    a value whose certificate is already below the acceptance threshold is
    accepted, and sigma_min[i] then holds that certificate (an upper bound of
-   the smallest singular value). Every other value gets the full sigma_min of
+   the smallest singular value). A value it does not accept gets up to three
+   steps of inverse iteration, x <- T(lambda)^-1 x / ||x|| from x = v, each
+   solve refined to FP64 accuracy in the call's arithmetic form, with the
+   certificate ||T(lambda) x|| / ||x|| (again an upper bound of sigma_min) after
+   each. Every value still not accepted gets the full sigma_min of
    pmcim_verify. Accept/reject decisions equal those of the sigma_min rule. */
 int pmcim_solve(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim_region* reg,
                 int32_t l, const double* V, int32_t cap, double* lambda, double* vecs,

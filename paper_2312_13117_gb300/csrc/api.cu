@@ -108,6 +108,9 @@ constexpr size_t kMaxPmcimaRegions = size_t(1) << 20;
 // this fraction of |X|: 1e-11 keeps Beyn's eigenvalues within about 1e-14 of
 // the FP64 ones on the delay workload (simulated FP32 LU + FP64 refinement).
 constexpr double kIrTol = 1e-11;
+// Refined inverse-iteration steps tried for a value whose eigenvector
+// certificate does not accept it, before the full sigma_min by an FP64 LU.
+constexpr int kInverseSteps = 3;
 // Default limits of the precision-form kernel's bounded waits (clock64 cycles):
 // a tensor-core commit (about half a second at 2 GHz) and a hand-off between its
 // thread groups (about 16 s, longer than any node at n <= 4096).
@@ -232,7 +235,7 @@ struct Workspace {
   DevBuf Cm;             // scaled moments of the block Hankel form of Beyn's step
   DevBuf ind3, feats, sprob, sparams, sscratch;
   // verification's inverse-iteration step: per-value problem table, pseudo-disks, items, solutions
-  DevBuf iprobs, iregions, iitems, iX, iinfo, icounters;
+  DevBuf iprobs, iregions, iitems, iX, iinfo, icounters, irhs, ioffs;
   DevBuf ysl;                        // per slot: digits of f_k X for the tensor-core residual
   DevBuf rz, rX, rR, rstat, rysl;    // pmcim_residual: points, solutions, residuals, status, scratch
   // the library's own stream: graphs cannot be captured on the legacy default stream
@@ -247,7 +250,7 @@ struct Workspace {
                    &phase, &C0, &C1, &pf_half, &pf_abs, &ind, &pf_norm, &pf_scale, &cand, &bwork, &bsigma,
                    &bp, &blam, &bvecs, &bkept, &bstatus, &vlam, &vprob, &voff, &vsig, &vacc, &vwork,
                    &vvec, &vpiv, &gitems, &gdst, &gperm, &ind3, &feats, &sprob, &sparams, &sscratch, &Xkeep,
-                   &citems, &vout, &Cm, &iprobs, &iregions, &iitems, &iX, &iinfo, &icounters, &ysl, &rz,
+                   &citems, &vout, &Cm, &iprobs, &iregions, &iitems, &iX, &iinfo, &icounters, &irhs, &ioffs, &ysl, &rz,
                    &rX, &rR, &rstat, &rysl};
     for (DevBuf* x : b) x->release();
   }
@@ -1140,8 +1143,9 @@ int run_certify(Call& c, const EigOut& e, std::vector<double>* cert, std::vector
   return PMCIM_OK;
 }
 
-// One step of inverse iteration from Beyn's eigenvector, for the values whose
-// first certificate ||T(lambda) v|| did not accept them: x = T(lambda)^-1 v by
+// One step of inverse iteration, for the values whose earlier certificate did
+// not accept them: x = T(lambda)^-1 v (v: Beyn's eigenvector, or the unit x of
+// the previous step, at rhs + rhs_off[i]) by
 // the node kernel of the value's arithmetic form (the precision forms refine x
 // to FP64 accuracy), then the certificate ||T(lambda) x|| / ||x||, evaluated in
 // FP64 from the coefficients. sigma_min <= ||T y|| / ||y|| for every y != 0, so a
@@ -1149,11 +1153,12 @@ int run_certify(Call& c, const EigOut& e, std::vector<double>* cert, std::vector
 // exactly as the sigma_min rule would accept it. Each value is a pseudo-disk
 // with one node z_0 = lambda (centre lambda, radius 0) and its own one-column
 // problem entry whose probe column is v; the values run in parallel, one per CTA.
-int run_inverse_step(Call& c, const EigOut& e, const std::vector<int>& idx, std::vector<double>* cert,
-                     std::vector<uint8_t>* ok) {
+int run_inverse_step(Call& c, const std::vector<double2>& lam_in, const std::vector<int>& prob_in,
+                     const double2* rhs, const std::vector<int64_t>& rhs_off, std::vector<double>* cert,
+                     std::vector<uint8_t>* ok, std::vector<int64_t>* x_off_out) {
   Workspace& ws = *c.ws;
   cudaStream_t s = c.s;
-  const int m = (int)idx.size();
+  const int m = (int)lam_in.size();
   cert->assign(m, 0.0);
   ok->assign(m, 0);
   if (m == 0) return PMCIM_OK;
@@ -1167,15 +1172,15 @@ int run_inverse_step(Call& c, const EigOut& e, const std::vector<int>& idx, std:
   int max_n = 1, t64_n = 0, ysl_n = 0, ysl_nd = 0;
   bool any_tc = false;
   for (int i = 0; i < m; ++i) {
-    const int v = idx[i], q = e.prob[v];
+    const int q = prob_in[i];
     pdv[i] = c.pd[q];
     pdv[i].l = 1;
-    pdv[i].V = ws.gdst.as<double2>() + e.vec_off[v];
+    pdv[i].V = rhs + rhs_off[i];
     const int n = pdv[i].n, form = c.groups[q].form;
     RegionDev& d = rdv[i];
     std::memset(&d, 0, sizeof(d));
-    d.cre = e.lam[v].x;
-    d.cim = e.lam[v].y;
+    d.cre = lam_in[i].x;
+    d.cim = lam_in[i].y;
     d.r = 0.0;
     d.N = 1;
     d.prob = i;
@@ -1185,7 +1190,7 @@ int run_inverse_step(Call& c, const EigOut& e, const std::vector<int>& idx, std:
     x_off[i] = (int64_t)x_tot;
     x_tot += (size_t)n;
     prob_of[i] = q;
-    lam[i] = e.lam[v];
+    lam[i] = lam_in[i];
     max_n = std::max(max_n, n);
     if (small_kernel_fits(n, 1)) {
       itS.push_back(NodeItem{i, 0});
@@ -1325,6 +1330,7 @@ int run_inverse_step(Call& c, const EigOut& e, const std::vector<int>& idx, std:
   // to the full sigma_min computation
   for (int i = 0; i < m; ++i)
     if (!std::isfinite((*cert)[i])) (*ok)[i] = 0;
+  *x_off_out = x_off;
   return PMCIM_OK;
 }
 
@@ -1414,27 +1420,58 @@ int run_pmcimb(Call& c, const std::vector<HostRegion>& top_in, EigOut* e, Verifi
       idx.push_back((int)i);
     }
   }
-  // second certificate: one refined inverse-iteration step from Beyn's vector
+  // further certificates: up to kInverseSteps refined inverse-iteration steps,
+  // the first from Beyn's vector, each later one from the previous step's unit x
   {
-    std::vector<double> cert2;
-    std::vector<uint8_t> ok2;
-    CHK(run_inverse_step(c, *e, idx, &cert2, &ok2));
-    std::vector<double2> rest2;
-    std::vector<int> rest2_prob, idx2;
-    for (size_t k = 0; k < idx.size(); ++k) {
-      if (ok2[k]) {
-        v->sig[idx[k]] = cert2[k];
-        v->acc[idx[k]] = 1;
-        c.st.certified += 1;
-      } else {
-        rest2.push_back(rest[k]);
-        rest2_prob.push_back(rest_prob[k]);
-        idx2.push_back(idx[k]);
+    Workspace& ws = *c.ws;
+    const double2* rhs = ws.gdst.as<double2>();
+    std::vector<int64_t> rhs_off;
+    for (int k : idx) rhs_off.push_back(e->vec_off[k]);
+    for (int step = 0; step < kInverseSteps && !idx.empty(); ++step) {
+      std::vector<double> cert2;
+      std::vector<uint8_t> ok2;
+      std::vector<int64_t> xoff;
+      CHK(run_inverse_step(c, rest, rest_prob, rhs, rhs_off, &cert2, &ok2, &xoff));
+      std::vector<double2> rest2;
+      std::vector<int> rest2_prob, idx2;
+      std::vector<int64_t> src_off, dst_off;
+      std::vector<int32_t> ns;
+      int64_t tot = 0;
+      for (size_t k = 0; k < idx.size(); ++k) {
+        if (ok2[k]) {
+          v->sig[idx[k]] = cert2[k];
+          v->acc[idx[k]] = 1;
+          c.st.certified += 1;
+        } else {
+          rest2.push_back(rest[k]);
+          rest2_prob.push_back(rest_prob[k]);
+          idx2.push_back(idx[k]);
+          src_off.push_back(xoff[k]);
+          dst_off.push_back(tot);
+          ns.push_back(c.pd[rest_prob[k]].n);
+          tot += c.pd[rest_prob[k]].n;
+        }
       }
+      rest.swap(rest2);
+      rest_prob.swap(rest2_prob);
+      idx.swap(idx2);
+      if (idx.empty() || step + 1 == kInverseSteps) break;
+      // the unit x of this step becomes the next right-hand side
+      const int mm = (int)idx.size();
+      CU(ws.irhs.ensure((size_t)tot * sizeof(double2)));
+      CU(ws.ioffs.ensure((size_t)mm * 2 * sizeof(int64_t) + (size_t)mm * sizeof(int32_t)));
+      int64_t* d_src = ws.ioffs.as<int64_t>();
+      int64_t* d_dst = d_src + mm;
+      int32_t* d_n = reinterpret_cast<int32_t*>(d_dst + mm);
+      CU(cudaMemcpyAsync(d_src, src_off.data(), mm * sizeof(int64_t), cudaMemcpyHostToDevice, c.s));
+      CU(cudaMemcpyAsync(d_dst, dst_off.data(), mm * sizeof(int64_t), cudaMemcpyHostToDevice, c.s));
+      CU(cudaMemcpyAsync(d_n, ns.data(), mm * sizeof(int32_t), cudaMemcpyHostToDevice, c.s));
+      prof_begin(PMCIM_K_GATHER, c.s);
+      CU(launch_normalize_copy(ws.iX.as<double2>(), ws.irhs.as<double2>(), d_src, d_dst, d_n, mm, c.s));
+      prof_end(PMCIM_K_GATHER, c.s);
+      rhs = ws.irhs.as<double2>();
+      rhs_off = dst_off;
     }
-    rest.swap(rest2);
-    rest_prob.swap(rest2_prob);
-    idx.swap(idx2);
   }
   std::vector<double> sig2;
   std::vector<uint8_t> acc2;

@@ -324,6 +324,9 @@ struct VecItem {
   int32_t n;
   int32_t pad;
 };
+// dst block i = src block i normalised to unit 2-norm (n_i complex values each).
+cudaError_t launch_normalize_copy(const double2* src, double2* dst, const int64_t* src_off, const int64_t* dst_off,
+                                  const int32_t* ns, int count, cudaStream_t s);
 cudaError_t launch_gather_vecs(const double2* src, double2* dst, const VecItem* items, int count, int max_n,
                                cudaStream_t s);
 

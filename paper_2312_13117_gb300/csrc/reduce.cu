@@ -73,32 +73,43 @@ __global__ void __launch_bounds__(RT) k_reduce_moments(LevelArgs a) {
 }
 
 __global__ void __launch_bounds__(RT) k_indicator(LevelArgs a) {
-  __shared__ double red[3][RT / 32];
+  __shared__ double red[2][RT / 32];
   const int g = blockIdx.x;
   const RegionDev rg = a.regions[g];
   const int n = a.probs[rg.prob].n;
   const double2* pfN = a.C0 + rg.c_off;  // column 0 of C0
   const double2* pfh = a.pf_half + rg.p_off;
   const double* pab = a.pf_abs + rg.p_off;
-  double s_ratio = 0.0, s_norm = 0.0, s_abs = 0.0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // pass 1: ||P f|_N||^2 and the size of the summed terms ||sum_j |w_j| |x_j|||^2
+  double s_norm = 0.0, s_abs = 0.0;
   for (int i = threadIdx.x; i < n; i += RT) {
-    const double num = cabs2(pfN[i]);
-    const double den = cabs2(pfh[i]);
-    s_ratio += num / den;
-    s_norm += num;
+    s_norm += cabs2(pfN[i]);
     s_abs += pab[i] * pab[i];
   }
   for (int o = 16; o > 0; o >>= 1) {
-    s_ratio += __shfl_down_sync(0xffffffffu, s_ratio, o);
     s_norm += __shfl_down_sync(0xffffffffu, s_norm, o);
     s_abs += __shfl_down_sync(0xffffffffu, s_abs, o);
   }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) { red[0][wid] = s_ratio; red[1][wid] = s_norm; red[2][wid] = s_abs; }
+  if (lane == 0) { red[0][wid] = s_norm; red[1][wid] = s_abs; }
+  __syncthreads();
+  double t1 = 0.0, t2 = 0.0;
+  for (int k = 0; k < RT / 32; ++k) { t1 += red[0][k]; t2 += red[1][k]; }
+  __syncthreads();
+  // pass 2: Eq. 3.1 componentwise; a component whose |P f|_{N/2}| is at or below the
+  // rounding level kPfFloor ||sum_j |w_j| |x_j||| has no determined ratio and is left out
+  const double floor2 = kPfFloor * kPfFloor * t2;
+  double s_ratio = 0.0;
+  for (int i = threadIdx.x; i < n; i += RT) {
+    const double den = cabs2(pfh[i]);
+    if (den > floor2) s_ratio += cabs2(pfN[i]) / den;
+  }
+  for (int o = 16; o > 0; o >>= 1) s_ratio += __shfl_down_sync(0xffffffffu, s_ratio, o);
+  if (lane == 0) red[0][wid] = s_ratio;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-    for (int k = 0; k < RT / 32; ++k) { t0 += red[0][k]; t1 += red[1][k]; t2 += red[2][k]; }
+    double t0 = 0.0;
+    for (int k = 0; k < RT / 32; ++k) t0 += red[0][k];
     // P f = 0 when the disk holds no eigenvalue (Sec. 2.1): at rounding level the
     // ratio of Eq. 3.1 is 0/0, and the indicator is taken as 0
     const double I = (sqrt(t1) <= kPfFloor * sqrt(t2)) ? 0.0 : sqrt(t0) / sqrt((double)n);
@@ -115,6 +126,27 @@ __global__ void k_gather_vecs(const double2* __restrict__ src, double2* __restri
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= it.n) return;
   dst[it.dst + i] = src[it.src + i];
+}
+
+// dst block i = src block i / ||src block i||_2 (blocks of n_i complex values at
+// the given offsets; a zero or non-finite block is copied unscaled). One CTA per block.
+__global__ void __launch_bounds__(RT) k_normalize_copy(const double2* __restrict__ src, double2* __restrict__ dst,
+                                                      const int64_t* __restrict__ src_off,
+                                                      const int64_t* __restrict__ dst_off,
+                                                      const int32_t* __restrict__ ns) {
+  __shared__ double red[RT / 32];
+  const int b = blockIdx.x, n = ns[b];
+  const double2* x = src + src_off[b];
+  double2* y = dst + dst_off[b];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += RT) s += cabs2(x[i]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < RT / 32; ++k) t += red[k];
+  const double inv = (t > 0.0 && isfinite(t)) ? 1.0 / sqrt(t) : 1.0;
+  for (int i = threadIdx.x; i < n; i += RT) y[i] = cscale(x[i], inv);
 }
 
 // Verification certificate (pmCIMb step 3): for a candidate lambda with unit
@@ -183,6 +215,13 @@ cudaError_t launch_reduce_moments(const LevelArgs& a, cudaStream_t s) {
 cudaError_t launch_indicator(const LevelArgs& a, cudaStream_t s) {
   if (a.R <= 0) return cudaSuccess;
   k_indicator<<<a.R, RT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalize_copy(const double2* src, double2* dst, const int64_t* src_off, const int64_t* dst_off,
+                                  const int32_t* ns, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_normalize_copy<<<count, RT, 0, s>>>(src, dst, src_off, dst_off, ns);
   return cudaGetLastError();
 }
 

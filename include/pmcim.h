@@ -152,7 +152,11 @@ typedef struct {
   int32_t screen_solves;   /* coarse node solves spent on the screen             */
   int32_t tuned_tc;        /* problems the autotuner ran in PMCIM_PREC_TF32X3_IR  */
   int32_t tc_timeouts;     /* nodes whose tensor-core wait ran out (their LU was
-                              finished on the FMA pipes; results stay refined)  */
+                              finished on the FMA pipes or the node re-solved in
+                              FP64; results stay refined)                        */
+  int32_t node_ctas;       /* largest number of CTAs (one per SM) the precision
+                              form's node kernel ran with in the call: fewer than
+                              the SMs when device memory was short               */
 } pmcim_stats;
 
 typedef struct pmcim_problem_s* pmcim_problem;

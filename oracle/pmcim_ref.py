@@ -21,7 +21,9 @@ Readings of passages the paper leaves open (listed again in the design notes):
     there; in floating point P f|_N then sits at rounding level. When
     ||P f|_N|| <= 1e-10 * || sum_j |w_j| |x_j| || the indicator is taken as 0;
     componentwise, a component whose |P f|_{N/2}| is at or below that level
-    (an exact zero included) has no determined ratio and is left out;
+    (an exact zero included) has no determined ratio, and I is the root mean
+    square of the other components' ratios (Eq. 3.1's norm over sqrt(n) when
+    none is left out);
   * tol_svd is absolute (Sec. 3.2) and p counts sigma_i > tol_svd;
   * a region is saturated when p reaches min(n, l) (all probe directions
     used); it is then split into four children with the pmCIMa geometry and
@@ -138,19 +140,19 @@ PF_FLOOR = 1e-10
 def indicator_value(pf_N: np.ndarray, pf_half: np.ndarray, pf_abs: np.ndarray = None) -> float:
     """I = || P f|_N ./ P f|_{N/2} ||_2 / sqrt(n)   (Eq. 3.1); 0 when P f|_N is at rounding level.
 
-    The norm is sqrt(sum_i |a_i|^2 / |b_i|^2) with a = P f|_N, b = P f|_{N/2}. With pf_abs
-    given, a component whose |b_i| is at or below the same rounding level (PF_FLOOR times
-    || sum_j |w_j| |x_j| ||) has no determined ratio and is left out of the sum, as is one
-    with b_i = 0 exactly."""
+    That is the root mean square of the componentwise ratios |a_i| / |b_i| with a = P f|_N,
+    b = P f|_{N/2}. With pf_abs given, a component whose |b_i| is at or below the same rounding
+    level (PF_FLOOR times || sum_j |w_j| |x_j| ||, an exact zero included) has no determined
+    ratio: the mean runs over the other components."""
     if pf_abs is not None and np.linalg.norm(pf_N) <= PF_FLOOR * np.linalg.norm(pf_abs):
         return 0.0
     num = pf_N.real ** 2 + pf_N.imag ** 2
     den = pf_half.real ** 2 + pf_half.imag ** 2
     floor2 = (PF_FLOOR * np.linalg.norm(pf_abs)) ** 2 if pf_abs is not None else 0.0
     keep = den > floor2
-    ratio = np.zeros_like(num)
-    ratio[keep] = num[keep] / den[keep]
-    return float(math.sqrt(float(np.sum(ratio))) / math.sqrt(len(pf_N)))
+    if not np.any(keep):
+        return 0.0
+    return float(math.sqrt(float(np.sum(num[keep] / den[keep])) / int(np.sum(keep))))
 
 
 def indicator(problem, regions: Sequence, V: np.ndarray, tol_ind: float = 0.1):

@@ -108,9 +108,9 @@ constexpr size_t kMaxPmcimaRegions = size_t(1) << 20;
 // this fraction of |X|: 1e-11 keeps Beyn's eigenvalues within about 1e-14 of
 // the FP64 ones on the delay workload (simulated FP32 LU + FP64 refinement).
 constexpr double kIrTol = 1e-11;
-// Refined inverse-iteration steps tried for a value whose eigenvector
+// Inverse-iteration steps (FP32 solves) tried for a value whose eigenvector
 // certificate does not accept it, before the full sigma_min by an FP64 LU.
-constexpr int kInverseSteps = 3;
+constexpr int kInverseSteps = 1;
 // Default limits of the precision-form kernel's bounded waits (clock64 cycles):
 // a tensor-core commit (about half a second at 2 GHz) and a hand-off between its
 // thread groups (about 16 s, longer than any node at n <= 4096).
@@ -118,6 +118,15 @@ constexpr long long kTcWaitCycles = 1ll << 30;
 constexpr long long kHandoffWaitCycles = 1ll << 35;
 std::mutex g_wait_mu;
 long long g_tc_wait = kTcWaitCycles, g_handoff_wait = kHandoffWaitCycles;
+
+// Bytes one form's factorisation workspaces may take now: at most kSlotBytes, and at
+// most what they already hold plus 70 % of the device memory that is free, so that a
+// GPU shared with other work gets fewer resident CTAs instead of a failed allocation.
+size_t slot_budget(size_t held) {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return kSlotBytes;
+  return std::min(kSlotBytes, held + fr / 10 * 7);
+}
 
 // Copy results to a caller buffer that may live on the host or the device.
 int copy_out(void* dst, const void* src, size_t bytes) {
@@ -667,7 +676,8 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   size_t slot64 = 0, slot32 = 0, t64_stride = 0, ysl_stride = 0;
   if (any64) {
     slot64 = (size_t)max_n * (max_n + max_l) * sizeof(double2);
-    slots64 = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(2 * sms, kSlotBytes / slot64), total_nodes));
+    const size_t budget = slot_budget(ws.work64.cap);
+    slots64 = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(2 * sms, budget / slot64), total_nodes));
     CU(ws.work64.ensure((size_t)slots64 * slot64));
     CU(ws.piv64.ensure((size_t)slots64 * max_n * sizeof(int32_t)));
   }
@@ -676,14 +686,16 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
     slot32 = mixed_slot_bytes(max_n, max_l);
     const size_t per = (size_t)mixed_slots_per_cta();
     t64_stride = (size_t)t64_n * t64_n;  // FP64 T(z_j) of each slot
-    const size_t cta_bytes = per * (slot32 + t64_stride * sizeof(double2));
-    const size_t ctas = std::max<size_t>(1, std::min<size_t>(std::min<size_t>(sms, kSlotBytes / cta_bytes),
+    ysl_stride = y_digit_scratch_bytes(ysl_n, ysl_nd);
+    const size_t cta_bytes = per * (slot32 + t64_stride * sizeof(double2) + ysl_stride);
+    const size_t budget = slot_budget(ws.work32.cap + ws.t64.cap + ws.ysl.cap);
+    const size_t ctas = std::max<size_t>(1, std::min<size_t>(std::min<size_t>(sms, budget / cta_bytes),
                                                              total_nodes));
     slots32 = (int)(ctas * per);
+    c.st.node_ctas = std::max(c.st.node_ctas, (int32_t)ctas);
     CU(ws.work32.ensure((size_t)slots32 * slot32));
     CU(ws.piv32.ensure((size_t)slots32 * max_n * sizeof(int32_t)));
     if (t64_stride) CU(ws.t64.ensure((size_t)slots32 * t64_stride * sizeof(double2)));
-    ysl_stride = y_digit_scratch_bytes(ysl_n, ysl_nd);
     if (ysl_stride) CU(ws.ysl.ensure((size_t)slots32 * ysl_stride));
   }
   const bool timed = prof_on();
@@ -1145,14 +1157,17 @@ int run_certify(Call& c, const EigOut& e, std::vector<double>* cert, std::vector
 
 // One step of inverse iteration, for the values whose earlier certificate did
 // not accept them: x = T(lambda)^-1 v (v: Beyn's eigenvector, or the unit x of
-// the previous step, at rhs + rhs_off[i]) by
-// the node kernel of the value's arithmetic form (the precision forms refine x
-// to FP64 accuracy), then the certificate ||T(lambda) x|| / ||x||, evaluated in
-// FP64 from the coefficients. sigma_min <= ||T y|| / ||y|| for every y != 0, so a
-// value whose certificate is at or below the acceptance threshold is accepted
-// exactly as the sigma_min rule would accept it. Each value is a pseudo-disk
-// with one node z_0 = lambda (centre lambda, radius 0) and its own one-column
-// problem entry whose probe column is v; the values run in parallel, one per CTA.
+// the previous step, at rhs + rhs_off[i]) by the FP32 LU of the precision-form
+// node kernel without refinement, then the certificate ||T(lambda) x|| / ||x||,
+// evaluated in FP64 from the coefficients. sigma_min <= ||T y|| / ||y|| for every
+// y != 0, however y was obtained, so a value whose certificate is at or below the
+// acceptance threshold is accepted exactly as the sigma_min rule would accept it.
+// At an eigenvalue T(lambda) is nearly singular and the FP32 solve already points
+// along its near-null vector (a refinement could not converge there and would
+// re-solve in FP64 on one SM). Each value is a pseudo-disk with one node
+// z_0 = lambda (centre lambda, radius 0) and its own one-column problem entry
+// whose probe column is v; the values run in parallel, one per CTA (problems with
+// n <= 32 use the warp-per-node FP64 kernel).
 int run_inverse_step(Call& c, const std::vector<double2>& lam_in, const std::vector<int>& prob_in,
                      const double2* rhs, const std::vector<int64_t>& rhs_off, std::vector<double>* cert,
                      std::vector<uint8_t>* ok, std::vector<int64_t>* x_off_out) {
@@ -1192,18 +1207,13 @@ int run_inverse_step(Call& c, const std::vector<double2>& lam_in, const std::vec
     prob_of[i] = q;
     lam[i] = lam_in[i];
     max_n = std::max(max_n, n);
+    (void)form;
+    d.lu_tc = 1;
     if (small_kernel_fits(n, 1)) {
       itS.push_back(NodeItem{i, 0});
-    } else if (form == PMCIM_PREC_FP64) {
-      it64.push_back(NodeItem{i, 0});
     } else {
       it32.push_back(NodeItem{i, 0});
-      any_tc |= d.lu_tc != 0;
-      if (pdv[i].n_dense >= 2 && !tc_residual(c.opt)) t64_n = std::max(t64_n, n);
-      if (tc_residual(c.opt)) {
-        ysl_n = std::max(ysl_n, n);
-        ysl_nd = std::max(ysl_nd, pdv[i].n_dense);
-      }
+      any_tc = true;
     }
   }
   auto by_n = [&](const NodeItem& a, const NodeItem& b) {
@@ -1231,16 +1241,16 @@ int run_inverse_step(Call& c, const std::vector<double2>& lam_in, const std::vec
   na.X = ws.iX.as<double2>();
   na.node_info = ws.iinfo.as<int32_t>();
   na.max_n = max_n;
-  na.max_sweeps = c.opt->max_ir_sweeps;
-  na.tol_ir = c.opt->tol_ir > 0.0 ? c.opt->tol_ir : kIrTol;
+  na.max_sweeps = 0;  // the FP32 solve only
+  na.tol_ir = kIrTol;
   na.err = ws.icounters.as<int32_t>() + 3;
   na.tc_wait_cycles = wait_limit_tc();
   na.handoff_wait_cycles = wait_limit_handoff();
   const int sms = num_sms();
   if (!it64.empty()) {
     const size_t slot64 = (size_t)max_n * (max_n + 1) * sizeof(double2);
-    const int slots64 = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(2 * sms, kSlotBytes / slot64),
-                                                                  it64.size()));
+    const int slots64 = (int)std::max<size_t>(
+        1, std::min<size_t>(std::min<size_t>(2 * sms, slot_budget(ws.work64.cap) / slot64), it64.size()));
     CU(ws.work64.ensure((size_t)slots64 * slot64));
     CU(ws.piv64.ensure((size_t)slots64 * max_n * sizeof(int32_t)));
     CU(prepare_factor_fp64());
@@ -1259,19 +1269,20 @@ int run_inverse_step(Call& c, const std::vector<double2>& lam_in, const std::vec
     const size_t slot32 = mixed_slot_bytes(max_n, 1);
     const size_t per = (size_t)mixed_slots_per_cta();
     const size_t t64_stride = (size_t)t64_n * t64_n;
-    const size_t cta_bytes = per * (slot32 + t64_stride * sizeof(double2));
-    const size_t ctas = std::max<size_t>(1, std::min<size_t>(std::min<size_t>(sms, kSlotBytes / cta_bytes),
+    const size_t ysl_stride = y_digit_scratch_bytes(ysl_n, ysl_nd);
+    const size_t cta_bytes = per * (slot32 + t64_stride * sizeof(double2) + ysl_stride);
+    const size_t budget = slot_budget(ws.work32.cap + ws.t64.cap + ws.ysl.cap);
+    const size_t ctas = std::max<size_t>(1, std::min<size_t>(std::min<size_t>(sms, budget / cta_bytes),
                                                              (it32.size() + per - 1) / per));
     const int slots32 = (int)(ctas * per);
     CU(ws.work32.ensure((size_t)slots32 * slot32));
     CU(ws.piv32.ensure((size_t)slots32 * max_n * sizeof(int32_t)));
     if (t64_stride) CU(ws.t64.ensure((size_t)slots32 * t64_stride * sizeof(double2)));
-    const size_t ysl_stride = y_digit_scratch_bytes(ysl_n, ysl_nd);
     if (ysl_stride) CU(ws.ysl.ensure((size_t)slots32 * ysl_stride));
     CU(prepare_factor_mixed());
-    na.oz = tc_residual(c.opt) ? 1 : 0;
-    na.ysl = ysl_stride ? ws.ysl.as<unsigned char>() : nullptr;
-    na.ysl_stride = ysl_stride;
+    na.oz = 1;  // FP32 assembly; no residual runs
+    na.ysl = nullptr;
+    na.ysl_stride = 0;
     na.items = ws.iitems.as<NodeItem>() + it64.size();
     na.n_items = (int)it32.size();
     na.counter = ws.icounters.as<int>() + 1;

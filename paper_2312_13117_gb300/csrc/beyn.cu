@@ -25,6 +25,7 @@ constexpr int BT = 256;
 constexpr double EPS = 2.220446049250313e-16;
 
 struct BeynSmem {
+  int rotated;  // a Jacobi rotation happened in this sweep
   double red[4][BT / 32];
   int red_i[BT / 32];
   double sig[PMCIM_MAX_L];
@@ -220,7 +221,7 @@ __device__ int small_eig(double2* H, double2* Z, double2* Y, int p, double2* lam
   return fail;
 }
 
-__global__ void __launch_bounds__(BT) k_beyn(LevelArgs a) {
+__global__ void __launch_bounds__(BT, 1) k_beyn(LevelArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BeynSmem& sm = *reinterpret_cast<BeynSmem*>(smem_raw);
   const int g = blockIdx.x;
@@ -266,50 +267,71 @@ __global__ void __launch_bounds__(BT) k_beyn(LevelArgs a) {
   for (int e = tid; e < l * l; e += BT) W[e] = make_double2((e % l) == (e / l) ? 1.0 : 0.0, 0.0);
   __syncthreads();
 
-  // ---- 1. one-sided Jacobi ----
+  // ---- 1. one-sided Jacobi, round-robin ordering ----
+  // The columns are paired by the circle method: l' = l rounded up to even players,
+  // player 0 fixed and the others rotating, so every round holds l'/2 disjoint pairs
+  // and every pair meets once per sweep. The warps take the pairs of a round in turn
+  // (warp-shuffle reductions, one CTA barrier per round).
   const double tol_rot = EPS * sqrt((double)n) * 4.0;
+  const int lp2 = l + (l & 1), lane = tid & 31, warp = tid >> 5;
   for (int sweep = 0; sweep < 40; ++sweep) {
-    int rotated = 0;
-    for (int pc = 0; pc < l - 1; ++pc) {
-      for (int qc = pc + 1; qc < l; ++qc) {
+    if (tid == 0) sm.rotated = 0;
+    __syncthreads();
+    for (int round = 0; round < lp2 - 1; ++round) {
+      for (int k = warp; k < lp2 / 2; k += BT / 32) {
+        int pc, qc;
+        if (k == 0) {
+          pc = 0;
+          qc = round % (lp2 - 1) + 1;
+        } else {
+          pc = (round + k) % (lp2 - 1) + 1;
+          qc = (round - k + lp2 - 1) % (lp2 - 1) + 1;
+        }
+        if (pc > qc) { const int t = pc; pc = qc; qc = t; }
+        if (qc >= l) continue;  // the padding player
         double2* ap = Ac + (size_t)pc * n;
         double2* aq = Ac + (size_t)qc * n;
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int i = tid; i < n; i += BT) {
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        for (int i = lane; i < n; i += 32) {
           const double2 x = ap[i], y = aq[i];
-          v[0] += cabs2(x);
-          v[1] += cabs2(y);
-          v[2] += x.x * y.x + x.y * y.y;  // conj(x) y
-          v[3] += x.x * y.y - x.y * y.x;
+          v0 += cabs2(x);
+          v1 += cabs2(y);
+          v2 += x.x * y.x + x.y * y.y;  // conj(x) y
+          v3 += x.x * y.y - x.y * y.x;
         }
-        block_sum4(v, sm);
-        const double al = v[0], be = v[1];
-        const double gabs = hypot(v[2], v[3]);
+        for (int o = 16; o > 0; o >>= 1) {
+          v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+          v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+          v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+          v3 += __shfl_xor_sync(0xffffffffu, v3, o);
+        }
+        const double al = v0, be = v1;
+        const double gabs = hypot(v2, v3);
         if (al == 0.0 || be == 0.0 || gabs <= tol_rot * sqrt(al) * sqrt(be)) continue;
-        rotated = 1;
+        if (lane == 0) sm.rotated = 1;
         const double zeta = (be - al) / (2.0 * gabs);
         const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         const double cs = 1.0 / sqrt(1.0 + t * t);
         const double sn = cs * t;
-        const double2 e = make_double2(v[2] / gabs, v[3] / gabs);  // e^{i phi}
+        const double2 e = make_double2(v2 / gabs, v3 / gabs);  // e^{i phi}
         // a_p' = c a_p - s e^{-i phi} a_q ;  a_q' = s e^{i phi} a_p + c a_q
         const double2 sem = cscale(cconj(e), sn), sep = cscale(e, sn);
-        for (int i = tid; i < n; i += BT) {
+        for (int i = lane; i < n; i += 32) {
           const double2 x = ap[i], y = aq[i];
           ap[i] = csub(cscale(x, cs), cmul(sem, y));
           aq[i] = cadd(cmul(sep, x), cscale(y, cs));
         }
-        if (tid < l) {
-          double2* wp = W + (size_t)pc * l;
-          double2* wq = W + (size_t)qc * l;
-          const double2 x = wp[tid], y = wq[tid];
-          wp[tid] = csub(cscale(x, cs), cmul(sem, y));
-          wq[tid] = cadd(cmul(sep, x), cscale(y, cs));
+        double2* wp = W + (size_t)pc * l;
+        double2* wq = W + (size_t)qc * l;
+        for (int i = lane; i < l; i += 32) {
+          const double2 x = wp[i], y = wq[i];
+          wp[i] = csub(cscale(x, cs), cmul(sem, y));
+          wq[i] = cadd(cmul(sep, x), cscale(y, cs));
         }
-        __syncthreads();
       }
+      __syncthreads();
     }
-    if (!rotated) break;
+    if (!sm.rotated) break;
   }
 
   // ---- 2. singular values, order, rank ----

@@ -562,7 +562,10 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
       ok = false;
       tc_lost = true;
     }
-    if (ok) {
+    // max_sweeps == 0: the FP32 solve alone (a direction for a certificate), no refinement
+    // and no FP64 re-solve
+    const bool refine = a.max_sweeps > 0;
+    if (ok && refine) {
       // the matrix each residual multiplies: T(z_j) assembled once, or the one dense term
       const double2* M = nullptr;
       double2 fM = make_double2(0.0, 0.0), id = make_double2(0.0, 0.0);
@@ -640,7 +643,7 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
       }
       if (!conv) ok = false;
     }
-    if (!ok) {
+    if (!ok && refine) {
       info = fallback_fp64(c, M64, piv, X, sm.r.u.lu64);
       pc.mark(PH_FALLBACK);
     }

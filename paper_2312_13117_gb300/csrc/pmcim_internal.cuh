@@ -205,7 +205,7 @@ struct NodeArgs {
   int32_t* piv;             // slots * max_n
   int max_n;
   int slots;
-  int max_sweeps;
+  int max_sweeps;             // mixed kernel: refinement sweeps; 0 = the FP32 solve only
   double tol_ir;
   unsigned long long* phase;  // NULL, or slots * PMCIM_PHASES clock64 counters (mixed kernel)
   int32_t* err;               // mixed kernel: set to 1 when a wait between its thread groups ran out

@@ -98,21 +98,28 @@ __global__ void __launch_bounds__(RT) k_indicator(LevelArgs a) {
   __syncthreads();
   // pass 2: Eq. 3.1 componentwise; a component whose |P f|_{N/2}| is at or below the
   // rounding level kPfFloor ||sum_j |w_j| |x_j||| has no determined ratio and is left out
+  // (the root mean square runs over the components with a determined ratio)
   const double floor2 = kPfFloor * kPfFloor * t2;
-  double s_ratio = 0.0;
+  double s_ratio = 0.0, s_kept = 0.0;
   for (int i = threadIdx.x; i < n; i += RT) {
     const double den = cabs2(pfh[i]);
-    if (den > floor2) s_ratio += cabs2(pfN[i]) / den;
+    if (den > floor2) {
+      s_ratio += cabs2(pfN[i]) / den;
+      s_kept += 1.0;
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) s_ratio += __shfl_down_sync(0xffffffffu, s_ratio, o);
-  if (lane == 0) red[0][wid] = s_ratio;
+  for (int o = 16; o > 0; o >>= 1) {
+    s_ratio += __shfl_down_sync(0xffffffffu, s_ratio, o);
+    s_kept += __shfl_down_sync(0xffffffffu, s_kept, o);
+  }
+  if (lane == 0) { red[0][wid] = s_ratio; red[1][wid] = s_kept; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t0 = 0.0;
-    for (int k = 0; k < RT / 32; ++k) t0 += red[0][k];
+    double t0 = 0.0, tk = 0.0;
+    for (int k = 0; k < RT / 32; ++k) { t0 += red[0][k]; tk += red[1][k]; }
     // P f = 0 when the disk holds no eigenvalue (Sec. 2.1): at rounding level the
     // ratio of Eq. 3.1 is 0/0, and the indicator is taken as 0
-    const double I = (sqrt(t1) <= kPfFloor * sqrt(t2)) ? 0.0 : sqrt(t0) / sqrt((double)n);
+    const double I = (sqrt(t1) <= kPfFloor * sqrt(t2) || tk == 0.0) ? 0.0 : sqrt(t0 / tk);
     a.ind[g] = I;
     a.pf_norm[g] = sqrt(t1);
     a.pf_scale[g] = sqrt(t2);

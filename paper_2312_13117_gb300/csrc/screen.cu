@@ -36,46 +36,89 @@ static_assert(NPARAM == PMCIM_SCREEN_PARAMS, "parameter count");
 // ---------------------------------------------------------------------------
 constexpr int FT = 256;
 
+// P f|_M and P f|_{M/2} (component i) on the M-node rule of disk rg, whose node m is
+// node m * (N / M) of the disk's N-node rule; s_abs = sum_m |w_m| |x_m|.
+__device__ __forceinline__ void pf_component(const LevelArgs& a, const RegionDev& rg, size_t nl, int M, int i,
+                                             double2* s_full, double2* s_half, double* s_abs) {
+  const int step = rg.N / M;
+  double2 f = make_double2(0.0, 0.0), h = f;
+  double ab = 0.0;
+  for (int m = 0; m < M; ++m) {
+    double2 z, w;
+    node_weight(rg.cre, rg.cim, rg.r, M, m, &z, &w);
+    const double2 x = a.X[rg.x_off + (size_t)(m * step) * nl + i];
+    cfma(f, w, x);
+    if (m & 1) cfma(h, cscale(w, 2.0), x);
+    ab += hypot(w.x, w.y) * hypot(x.x, x.y);
+  }
+  *s_full = f;
+  *s_half = h;
+  *s_abs = ab;
+}
+
+// The indicator of Eq. 3.1 at three resolutions, with the reading the indicator
+// kernel takes: 0 when P f|_M is at rounding level as a whole, else the root mean
+// square of the componentwise ratios whose P f|_{M/2} is above that level.
 __global__ void __launch_bounds__(FT) k_screen_features(LevelArgs a, double* ind3) {
-  __shared__ double red[9][FT / 32];
+  __shared__ double red[6][FT / 32];
+  __shared__ double tot[6];
   const int g = blockIdx.x;
   const RegionDev rg = a.regions[g];
   const ProblemDev* P = a.probs + rg.prob;
   const int n = P->n, l = P->l, N = rg.N;
   const size_t nl = (size_t)n * l;
   const int res[3] = {8, 16, N};
-  // per resolution: sum of |Pf_M ./ Pf_{M/2}|^2, ||Pf_M||^2 and ||sum |w||x| ||^2
-  double acc[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int i = threadIdx.x; i < n; i += FT) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // pass 1, per resolution: ||P f_M||^2 and ||sum |w||x| ||^2
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < n; i += FT)
     for (int q = 0; q < 3; ++q) {
-      const int M = res[q], step = N / M;
-      double2 s_full = make_double2(0.0, 0.0), s_half = s_full;
-      double s_abs = 0.0;
-      for (int m = 0; m < M; ++m) {
-        double2 z, w;
-        node_weight(rg.cre, rg.cim, rg.r, M, m, &z, &w);  // node m of the M-rule = node m*step of the N-rule
-        const double2 x = a.X[rg.x_off + (size_t)(m * step) * nl + i];
-        cfma(s_full, w, x);
-        if (m & 1) cfma(s_half, cscale(w, 2.0), x);
-        s_abs += hypot(w.x, w.y) * hypot(x.x, x.y);
-      }
-      acc[3 * q] += cabs2(s_full) / cabs2(s_half);
-      acc[3 * q + 1] += cabs2(s_full);
-      acc[3 * q + 2] += s_abs * s_abs;
+      double2 f, h;
+      double ab;
+      pf_component(a, rg, nl, res[q], i, &f, &h, &ab);
+      acc[2 * q] += cabs2(f);
+      acc[2 * q + 1] += ab * ab;
     }
-  }
-  for (int q = 0; q < 9; ++q)
+  for (int q = 0; q < 6; ++q)
     for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
-  if ((threadIdx.x & 31) == 0)
-    for (int q = 0; q < 9; ++q) red[q][threadIdx.x >> 5] = acc[q];
+  if (lane == 0)
+    for (int q = 0; q < 6; ++q) red[q][wid] = acc[q];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double t = 0.0;
+    for (int k = 0; k < FT / 32; ++k) t += red[threadIdx.x][k];
+    tot[threadIdx.x] = t;
+  }
+  __syncthreads();
+  // pass 2, per resolution: sum of the determined |ratio|^2 and their count
+  double acc2[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < n; i += FT)
+    for (int q = 0; q < 3; ++q) {
+      double2 f, h;
+      double ab;
+      pf_component(a, rg, nl, res[q], i, &f, &h, &ab);
+      const double den = cabs2(h);
+      if (den > kPfFloor * kPfFloor * tot[2 * q + 1]) {
+        acc2[2 * q] += cabs2(f) / den;
+        acc2[2 * q + 1] += 1.0;
+      }
+    }
+  for (int q = 0; q < 6; ++q)
+    for (int o = 16; o > 0; o >>= 1) acc2[q] += __shfl_down_sync(0xffffffffu, acc2[q], o);
+  __syncthreads();
+  if (lane == 0)
+    for (int q = 0; q < 6; ++q) red[q][wid] = acc2[q];
   __syncthreads();
   if (threadIdx.x < 3) {
     const int q = threadIdx.x;
-    double t[3] = {0.0, 0.0, 0.0};
-    for (int k = 0; k < FT / 32; ++k)
-      for (int u = 0; u < 3; ++u) t[u] += red[3 * q + u][k];
+    double sr = 0.0, kept = 0.0;
+    for (int k = 0; k < FT / 32; ++k) {
+      sr += red[2 * q][k];
+      kept += red[2 * q + 1][k];
+    }
     // P f at rounding level: indicator 0 (Sec. 2.1: P f = 0 without eigenvalues)
-    ind3[(size_t)g * 3 + q] = (sqrt(t[1]) <= kPfFloor * sqrt(t[2])) ? 0.0 : sqrt(t[0]) / sqrt((double)n);
+    ind3[(size_t)g * 3 + q] =
+        (sqrt(tot[2 * q]) <= kPfFloor * sqrt(tot[2 * q + 1]) || kept == 0.0) ? 0.0 : sqrt(sr / kept);
   }
 }
 

@@ -68,7 +68,7 @@ class pmcim_stats(C.Structure):
                 ("singular_nodes", C.c_int32), ("ir_sweeps", C.c_int64), ("certified", C.c_int32),
                 ("graphs", C.c_int32), ("tuned_fp64", C.c_int32), ("tuned_mixed", C.c_int32),
                 ("screened_out", C.c_int32), ("screen_solves", C.c_int32), ("tuned_tc", C.c_int32),
-                ("tc_timeouts", C.c_int32)]
+                ("tc_timeouts", C.c_int32), ("node_ctas", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -551,15 +551,15 @@ def test_pin_catches_wrong_phase_rule(mistake):
 
 def test_indicator_leaves_out_components_at_rounding_level():
     """Eq. 3.1 componentwise: with pf_abs given, a component whose |P f|_{N/2}| is at or below
-    PF_FLOOR ||pf_abs|| (an exact zero included) is left out of the norm, so an underflowed
-    component cannot make the ratio infinite; the others give the plain componentwise value."""
+    PF_FLOOR ||pf_abs|| (an exact zero included) has no determined ratio, and I is the root mean
+    square of the other ratios (Eq. 3.1 exactly when none is left out)."""
     a = np.array([0.5 + 0.5j, 1e-3 + 0j, 2.0 - 1j])
     b = np.array([0.5 + 0.0j, 1e-3 + 0j, 1.0 + 0j])
     pa = np.array([1.0, 1.0, 1.0])
     full = np.linalg.norm(a / b) / np.sqrt(3)
     assert o.indicator_value(a, b) == pytest.approx(full, rel=1e-15)
     assert o.indicator_value(a, b, pa) == pytest.approx(full, rel=1e-15)
-    rest = np.linalg.norm((a / b)[1:]) / np.sqrt(3)
+    rest = np.linalg.norm((a / b)[1:]) / np.sqrt(2)              # RMS over the two determined ratios
     for tiny in (0.0, 1e-300, 1e-11):
         b2 = np.array([tiny + 0j, b[1], b[2]])
         assert o.indicator_value(a, b2, pa) == pytest.approx(rest, rel=1e-15), tiny

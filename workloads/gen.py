@@ -29,7 +29,7 @@ __all__ = [
     "complex_gaussian", "probe_block", "grid_regions",
     "quadratic_small", "paper_quadratic", "delay_large", "batched_quadratics", "mass_spring",
     "diagonal_linear", "similarity_linear", "diagonal_delay", "paper_n4_example",
-    "diagonal_quadratic", "screen_trace_problems",
+    "diagonal_quadratic", "screen_trace_problems", "config_trace_problems",
 ]
 
 
@@ -286,3 +286,21 @@ def screen_trace_problems(seeds: Sequence[int], n_choices=(16, 24, 32), disks: i
         regs = [Region(complex(c[i]), float(r[i]), N) for i in range(disks)]
         out.append((prob, regs, probe_block(rng, n, l)))
     return out
+
+
+def config_trace_problems(delay_seeds: Sequence[int], batched_seeds: Sequence[int],
+                          delay_n=(64, 96, 128), delay_grids=(8, 16, 32), batched_n_hi: int = 128):
+    """Screen traces from the delay and batched workloads, by other seeds of their own generators
+    at smaller n (one probe column each), yielded one problem at a time.
+
+    Delay: delay_large(seed, n, N = 64) on Omega = [-3,1] x [-6,6] split g x 3g, with n and g
+    cycling through delay_n and delay_grids. Batched: batched_quadratics(seeds) with
+    n ~ U{32..batched_n_hi}, a random square Omega split m x m and N in {16, 32, 64}."""
+    for k, sd in enumerate(delay_seeds):
+        n = delay_n[k % len(delay_n)]
+        g = delay_grids[(k // len(delay_n)) % len(delay_grids)]
+        Wd = delay_large(seed=sd, n=n, l=1, N=64, nx=g, ny=3 * g)
+        yield Wd.problem, Wd.regions, Wd.V
+    for sd in batched_seeds:
+        Wb = batched_quadratics([sd], l=1, n_lo=32, n_hi=batched_n_hi)[0]
+        yield Wb.problem, Wb.regions, Wb.V

@@ -225,6 +225,22 @@ int pmcim_residual(pmcim_problem p, const pmcim_options* opt, int32_t m, const d
 int pmcim_verify(pmcim_problem p, const pmcim_options* opt, int32_t m, const double* lambda,
                  double* sigma_min, uint8_t* accept);
 
+/* Certificates of approximate eigenpairs (pmCIMb step 3 without the full
+   sigma_min). For each lambda_i (m complex) with start vector c_i (column i of
+   vecs, n x m complex column-major, host or device memory; c_i != 0; normally an
+   approximate right eigenvector), an upper bound of sigma_min(T(lambda_i)):
+   first ||T c_i|| / ||c_i||; where that does not accept the value, also
+   ||T^H y|| / ||y|| for the bordered inverse-iteration step y = T(lambda_i)^-H c_i
+   (FP32 LU of T^H with column s = argmax |c_i| replaced by c_i, residuals in FP64,
+   FP32 corrections; a plain FP64 solve for n <= 32). sigma_min(T^H) =
+   sigma_min(T), and from an approximate right eigenvector the second bound comes
+   close to sigma_min itself. cert[i] = the smaller bound; accept[i] = cert[i] <=
+   tol_verify * max(1, ||T(lambda_i)||_F / sqrt(n)), so an accepted value is one
+   the sigma_min rule of pmcim_verify accepts; a value not accepted is undecided
+   (only the full sigma_min can reject). accept may be NULL. */
+int pmcim_certify(pmcim_problem p, const pmcim_options* opt, int32_t m, const double* lambda,
+                  const double* vecs, double* cert, uint8_t* accept);
+
 /* pmCIMa (Sec. 3.1): the spectral indicator alone, level by level. Each level
    computes the indicator (Eq. 3.1, the disk's N nodes, probe column V, n x 1)
    of every disk; a candidate (I > tol_ind) is quadrisected into four disks of
@@ -251,12 +267,11 @@ int pmcim_pmcima(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmc
    the unit eigenvector v from Beyn's step; since sigma_min <= ||T(lambda) v||,
    a value whose certificate is already below the acceptance threshold is
    accepted, and sigma_min[i] then holds that certificate (an upper bound of
-   the smallest singular value). A value it does not accept gets up to three
-   steps of inverse iteration, x <- T(lambda)^-1 x / ||x|| from x = v, each
-   solve refined to FP64 accuracy in the call's arithmetic form, with the
-   certificate ||T(lambda) x|| / ||x|| (again an upper bound of sigma_min) after
-   each. Every value still not accepted gets the full sigma_min of
-   pmcim_verify. Accept/reject decisions equal those of the sigma_min rule. */
+   the smallest singular value). A value it does not accept gets the bordered
+   inverse-iteration step of pmcim_certify from v and its certificate (again an
+   upper bound of sigma_min). Every value still not accepted gets the full
+   sigma_min of pmcim_verify. Accept/reject decisions equal those of the
+   sigma_min rule. */
 int pmcim_solve(pmcim_problem p, const pmcim_options* opt, int32_t R, const pmcim_region* reg,
                 int32_t l, const double* V, int32_t cap, double* lambda, double* vecs,
                 double* sigma_min, int32_t* region_of, int32_t* count, double* ind,

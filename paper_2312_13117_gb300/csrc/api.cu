@@ -108,9 +108,6 @@ constexpr size_t kMaxPmcimaRegions = size_t(1) << 20;
 // this fraction of |X|: 1e-11 keeps Beyn's eigenvalues within about 1e-14 of
 // the FP64 ones on the delay workload (simulated FP32 LU + FP64 refinement).
 constexpr double kIrTol = 1e-11;
-// Inverse-iteration steps (FP32 solves) tried for a value whose eigenvector
-// certificate does not accept it, before the full sigma_min by an FP64 LU.
-constexpr int kInverseSteps = 1;
 // Default limits of the precision-form kernel's bounded waits (clock64 cycles):
 // a tensor-core commit (about half a second at 2 GHz) and a hand-off between its
 // thread groups (about 16 s, longer than any node at n <= 4096).
@@ -244,7 +241,7 @@ struct Workspace {
   DevBuf Cm;             // scaled moments of the block Hankel form of Beyn's step
   DevBuf ind3, feats, sprob, sparams, sscratch;
   // verification's inverse-iteration step: per-value problem table, pseudo-disks, items, solutions
-  DevBuf iprobs, iregions, iitems, iX, iinfo, icounters, irhs, ioffs;
+  DevBuf iprobs, iregions, iitems, iX, iinfo, icounters, ibord, ioffs;
   DevBuf ysl;                        // per slot: digits of f_k X for the tensor-core residual
   DevBuf rz, rX, rR, rstat, rysl;    // pmcim_residual: points, solutions, residuals, status, scratch
   // the library's own stream: graphs cannot be captured on the legacy default stream
@@ -259,7 +256,7 @@ struct Workspace {
                    &phase, &C0, &C1, &pf_half, &pf_abs, &ind, &pf_norm, &pf_scale, &cand, &bwork, &bsigma,
                    &bp, &blam, &bvecs, &bkept, &bstatus, &vlam, &vprob, &voff, &vsig, &vacc, &vwork,
                    &vvec, &vpiv, &gitems, &gdst, &gperm, &ind3, &feats, &sprob, &sparams, &sscratch, &Xkeep,
-                   &citems, &vout, &Cm, &iprobs, &iregions, &iitems, &iX, &iinfo, &icounters, &irhs, &ioffs, &ysl, &rz,
+                   &citems, &vout, &Cm, &iprobs, &iregions, &iitems, &iX, &iinfo, &icounters, &ibord, &ioffs, &ysl, &rz,
                    &rX, &rR, &rstat, &rysl};
     for (DevBuf* x : b) x->release();
   }
@@ -1155,22 +1152,33 @@ int run_certify(Call& c, const EigOut& e, std::vector<double>* cert, std::vector
   return PMCIM_OK;
 }
 
-// One step of inverse iteration, for the values whose earlier certificate did
-// not accept them: x = T(lambda)^-1 v (v: Beyn's eigenvector, or the unit x of
-// the previous step, at rhs + rhs_off[i]) by the FP32 LU of the precision-form
-// node kernel without refinement, then the certificate ||T(lambda) x|| / ||x||,
-// evaluated in FP64 from the coefficients. sigma_min <= ||T y|| / ||y|| for every
-// y != 0, however y was obtained, so a value whose certificate is at or below the
-// acceptance threshold is accepted exactly as the sigma_min rule would accept it.
-// At an eigenvalue T(lambda) is nearly singular and the FP32 solve already points
-// along its near-null vector (a refinement could not converge there and would
-// re-solve in FP64 on one SM). Each value is a pseudo-disk with one node
-// z_0 = lambda (centre lambda, radius 0) and its own one-column problem entry
-// whose probe column is v; the values run in parallel, one per CTA (problems with
-// n <= 32 use the warp-per-node FP64 kernel).
-int run_inverse_step(Call& c, const std::vector<double2>& lam_in, const std::vector<int>& prob_in,
-                     const double2* rhs, const std::vector<int64_t>& rhs_off, std::vector<double>* cert,
-                     std::vector<uint8_t>* ok, std::vector<int64_t>* x_off_out) {
+// One bordered inverse-iteration step with T(lambda)^H for the values whose
+// eigenvector certificate did not accept them, in the manner of Dongarra, Moler
+// and Wilkinson (SIAM J. Numer. Anal. 20, 1983): a low-precision factorisation,
+// residuals in high precision. With the start vector c (Beyn's eigenvector) and
+// s = argmax |c_i|, the node kernel solves M u = b, b = -T^H e_s, where M is
+// T(lambda)^H with column s replaced by alpha c (k_border_rhs): the FP32 LU of M,
+// residuals b - M X in FP64 (T^H assembled in FP64 once per value), FP32
+// correction solves. T(lambda) is nearly singular at an eigenvalue, where a plain
+// refinement cannot converge; M is not, so this one does. y = e_s + (u - u_s e_s)
+// then satisfies T^H y = -u_s alpha c: y is the exact step T(lambda)^-H c, scaled
+// to y_s = 1, and its residual is that of the exact step, not the FP32
+// factorisation's backward error. The certificate is ||T^H y|| / ||y||, evaluated
+// in FP64 from the coefficients; sigma_min(T^H) = sigma_min(T) <= ||T^H y|| / ||y||
+// for every y != 0, however y was obtained, so a value whose certificate is at or
+// below the acceptance threshold is accepted exactly as the sigma_min rule would
+// accept it. Why T^H: with the singular value decomposition T = sum_k sigma_k u_k
+// v_k^H, the step gives ||c|| / ||T^-H c||, about sigma_min / |v_min^H c|; Beyn's
+// c approximates the right null vector v_min, so the certificate comes within a
+// few digits of sigma_min. A step with T itself gives about sigma_min / |u_min^H c|
+// and misses by the angle between the left and right null vectors. Each value is a
+// pseudo-disk with one node z_0 = lambda (centre lambda, radius 0) and its own
+// one-column problem entry; the values run in parallel, one per CTA. Problems with
+// n <= 32 take the warp-per-node FP64 kernel, which solves T^H x = c directly (an
+// FP64 solve already gives the exact step's residual).
+int run_bordered_step(Call& c, const std::vector<double2>& lam_in, const std::vector<int>& prob_in,
+                      const double2* start, const std::vector<int64_t>& start_off, std::vector<double>* cert,
+                      std::vector<uint8_t>* ok) {
   Workspace& ws = *c.ws;
   cudaStream_t s = c.s;
   const int m = (int)lam_in.size();
@@ -1179,19 +1187,26 @@ int run_inverse_step(Call& c, const std::vector<double2>& lam_in, const std::vec
   if (m == 0) return PMCIM_OK;
   std::vector<ProblemDev> pdv(m);
   std::vector<RegionDev> rdv(m);
-  std::vector<NodeItem> it64, it32, itS;
+  std::vector<NodeItem> it32, itS;
   std::vector<int32_t> prob_of(m);
-  std::vector<int64_t> x_off(m);
-  std::vector<double2> lam(m);
-  size_t x_tot = 0;
-  int max_n = 1, t64_n = 0, ysl_n = 0, ysl_nd = 0;
-  bool any_tc = false;
+  std::vector<int64_t> x_off(m), b_off(m, -1);
+  size_t x_tot = 0, b_tot = 0;
+  int max_n = 1, t64_n = 0;
+  // the bordered right-hand sides and replacement columns: 2 n per value
+  for (int i = 0; i < m; ++i) {
+    const int n = c.pd[prob_in[i]].n;
+    if (!small_kernel_fits(n, 1)) {
+      b_off[i] = (int64_t)b_tot;
+      b_tot += 2 * (size_t)n;
+    }
+  }
+  CU(ws.ibord.ensure(std::max<size_t>(1, b_tot) * sizeof(double2)));
+  const double2* bord = ws.ibord.as<double2>();
   for (int i = 0; i < m; ++i) {
     const int q = prob_in[i];
     pdv[i] = c.pd[q];
     pdv[i].l = 1;
-    pdv[i].V = rhs + rhs_off[i];
-    const int n = pdv[i].n, form = c.groups[q].form;
+    const int n = pdv[i].n;
     RegionDev& d = rdv[i];
     std::memset(&d, 0, sizeof(d));
     d.cre = lam_in[i].x;
@@ -1200,29 +1215,27 @@ int run_inverse_step(Call& c, const std::vector<double2>& lam_in, const std::vec
     d.N = 1;
     d.prob = i;
     d.node_off = i;
-    d.lu_tc = form == PMCIM_PREC_TF32X3_IR ? 1 : 0;
+    d.lu_tc = 1;
+    d.herm = 1;
     d.x_off = (int64_t)x_tot;
     x_off[i] = (int64_t)x_tot;
     x_tot += (size_t)n;
     prob_of[i] = q;
-    lam[i] = lam_in[i];
     max_n = std::max(max_n, n);
-    (void)form;
-    d.lu_tc = 1;
-    if (small_kernel_fits(n, 1)) {
+    if (b_off[i] < 0) {
+      pdv[i].V = start + start_off[i];  // T(lambda)^H x = c in FP64
       itS.push_back(NodeItem{i, 0});
     } else {
+      pdv[i].V = bord + b_off[i];       // b; the column alpha c follows it
+      d.v_off = b_off[i] + n;           // d.border is set on the device
       it32.push_back(NodeItem{i, 0});
-      any_tc = true;
+      t64_n = std::max(t64_n, n);  // T^H in FP64 for the residuals
     }
   }
-  auto by_n = [&](const NodeItem& a, const NodeItem& b) {
+  std::stable_sort(it32.begin(), it32.end(), [&](const NodeItem& a, const NodeItem& b) {
     return pdv[a.region].n != pdv[b.region].n ? pdv[a.region].n > pdv[b.region].n : a.region < b.region;
-  };
-  std::stable_sort(it64.begin(), it64.end(), by_n);
-  std::stable_sort(it32.begin(), it32.end(), by_n);
-  std::vector<NodeItem> items(it64);
-  items.insert(items.end(), it32.begin(), it32.end());
+  });
+  std::vector<NodeItem> items(it32);
   items.insert(items.end(), itS.begin(), itS.end());
   CU(ws.iprobs.ensure(m * sizeof(ProblemDev)));
   CU(ws.iregions.ensure(m * sizeof(RegionDev)));
@@ -1230,10 +1243,39 @@ int run_inverse_step(Call& c, const std::vector<double2>& lam_in, const std::vec
   CU(ws.iX.ensure(x_tot * sizeof(double2)));
   CU(ws.iinfo.ensure(m * sizeof(int32_t)));
   CU(ws.icounters.ensure(4 * sizeof(int32_t)));
+  CU(ws.ioffs.ensure((size_t)m * 2 * sizeof(int64_t)));
+  CU(ws.vlam.ensure(m * sizeof(double2)));
+  CU(ws.vprob.ensure(m * sizeof(int32_t)));
+  CU(ws.voff.ensure(m * sizeof(int64_t)));
+  CU(ws.vsig.ensure(m * sizeof(double)));
+  CU(ws.vacc.ensure(m));
+  int64_t* d_start_off = ws.ioffs.as<int64_t>();
+  int64_t* d_b_off = d_start_off + m;
   CU(cudaMemcpyAsync(ws.iprobs.p, pdv.data(), m * sizeof(ProblemDev), cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(ws.iregions.p, rdv.data(), m * sizeof(RegionDev), cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(ws.iitems.p, items.data(), items.size() * sizeof(NodeItem), cudaMemcpyHostToDevice, s));
   CU(cudaMemsetAsync(ws.icounters.p, 0, 4 * sizeof(int32_t), s));
+  CU(cudaMemcpyAsync(ws.vlam.p, lam_in.data(), m * sizeof(double2), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(ws.vprob.p, prob_of.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(d_start_off, start_off.data(), m * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(d_b_off, b_off.data(), m * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  ValueArgs va;
+  std::memset(&va, 0, sizeof(va));
+  va.probs = ws.probs.as<ProblemDev>();
+  va.prob_of = ws.vprob.as<int32_t>();
+  va.lam = ws.vlam.as<double2>();
+  va.m = m;
+  va.tol_verify = c.opt->tol_verify;
+  va.sigma = ws.vsig.as<double>();
+  va.accept = ws.vacc.as<uint8_t>();
+  va.herm = 1;
+  if (!it32.empty()) {
+    va.vec_off = d_start_off;
+    va.vecs = start;
+    prof_begin(PMCIM_K_VERIFY, s);
+    CU(launch_border_rhs(va, d_b_off, ws.ibord.as<double2>(), ws.iregions.as<RegionDev>(), s));
+    prof_end(PMCIM_K_VERIFY, s);
+  }
   NodeArgs na;
   std::memset(&na, 0, sizeof(na));
   na.probs = ws.iprobs.as<ProblemDev>();
@@ -1241,92 +1283,56 @@ int run_inverse_step(Call& c, const std::vector<double2>& lam_in, const std::vec
   na.X = ws.iX.as<double2>();
   na.node_info = ws.iinfo.as<int32_t>();
   na.max_n = max_n;
-  na.max_sweeps = 0;  // the FP32 solve only
+  na.max_sweeps = std::max(1, c.opt->max_ir_sweeps);
   na.tol_ir = kIrTol;
   na.err = ws.icounters.as<int32_t>() + 3;
   na.tc_wait_cycles = wait_limit_tc();
   na.handoff_wait_cycles = wait_limit_handoff();
+  na.border = bord;
   const int sms = num_sms();
-  if (!it64.empty()) {
-    const size_t slot64 = (size_t)max_n * (max_n + 1) * sizeof(double2);
-    const int slots64 = (int)std::max<size_t>(
-        1, std::min<size_t>(std::min<size_t>(2 * sms, slot_budget(ws.work64.cap) / slot64), it64.size()));
-    CU(ws.work64.ensure((size_t)slots64 * slot64));
-    CU(ws.piv64.ensure((size_t)slots64 * max_n * sizeof(int32_t)));
-    CU(prepare_factor_fp64());
-    na.items = ws.iitems.as<NodeItem>();
-    na.n_items = (int)it64.size();
-    na.counter = ws.icounters.as<int>();
-    na.work = ws.work64.as<char>();
-    na.slot_bytes = slot64;
-    na.piv = ws.piv64.as<int32_t>();
-    na.slots = slots64;
-    prof_begin(PMCIM_K_FACTOR, s);
-    CU(launch_factor_solve_fp64(na, s));
-    prof_end(PMCIM_K_FACTOR, s);
-  }
   if (!it32.empty()) {
     const size_t slot32 = mixed_slot_bytes(max_n, 1);
     const size_t per = (size_t)mixed_slots_per_cta();
     const size_t t64_stride = (size_t)t64_n * t64_n;
-    const size_t ysl_stride = y_digit_scratch_bytes(ysl_n, ysl_nd);
-    const size_t cta_bytes = per * (slot32 + t64_stride * sizeof(double2) + ysl_stride);
-    const size_t budget = slot_budget(ws.work32.cap + ws.t64.cap + ws.ysl.cap);
+    const size_t cta_bytes = per * (slot32 + t64_stride * sizeof(double2));
+    const size_t budget = slot_budget(ws.work32.cap + ws.t64.cap);
     const size_t ctas = std::max<size_t>(1, std::min<size_t>(std::min<size_t>(sms, budget / cta_bytes),
                                                              (it32.size() + per - 1) / per));
     const int slots32 = (int)(ctas * per);
     CU(ws.work32.ensure((size_t)slots32 * slot32));
     CU(ws.piv32.ensure((size_t)slots32 * max_n * sizeof(int32_t)));
-    if (t64_stride) CU(ws.t64.ensure((size_t)slots32 * t64_stride * sizeof(double2)));
-    if (ysl_stride) CU(ws.ysl.ensure((size_t)slots32 * ysl_stride));
+    CU(ws.t64.ensure((size_t)slots32 * t64_stride * sizeof(double2)));
     CU(prepare_factor_mixed());
-    na.oz = 1;  // FP32 assembly; no residual runs
+    na.oz = 0;
     na.ysl = nullptr;
     na.ysl_stride = 0;
-    na.items = ws.iitems.as<NodeItem>() + it64.size();
+    na.items = ws.iitems.as<NodeItem>();
     na.n_items = (int)it32.size();
     na.counter = ws.icounters.as<int>() + 1;
     na.work = ws.work32.as<char>();
     na.slot_bytes = slot32;
     na.piv = ws.piv32.as<int32_t>();
     na.slots = slots32;
-    na.t64 = t64_stride ? ws.t64.as<double2>() : nullptr;
+    na.t64 = ws.t64.as<double2>();
     na.t64_stride = t64_stride;
     na.phase = nullptr;
-    prof_begin(PMCIM_K_FACTOR32, s);
+    prof_begin(PMCIM_K_VERIFY, s);  // verification work, timed apart from the disks' nodes
     CU(launch_factor_solve_mixed(na, s));
-    prof_end(PMCIM_K_FACTOR32, s);
+    prof_end(PMCIM_K_VERIFY, s);
   }
   if (!itS.empty()) {
     CU(prepare_factor_small());
-    na.items = ws.iitems.as<NodeItem>() + it64.size() + it32.size();
+    na.items = ws.iitems.as<NodeItem>() + it32.size();
     na.n_items = (int)itS.size();
     na.counter = ws.icounters.as<int>() + 2;
-    prof_begin(PMCIM_K_FACTOR, s);
+    prof_begin(PMCIM_K_VERIFY, s);
     CU(launch_factor_solve_small(na, s));
-    prof_end(PMCIM_K_FACTOR, s);
+    prof_end(PMCIM_K_VERIFY, s);
   }
-  (void)any_tc;
-  // the certificate of x, against the call's own problem table
-  CU(ws.vlam.ensure(m * sizeof(double2)));
-  CU(ws.vprob.ensure(m * sizeof(int32_t)));
-  CU(ws.voff.ensure(m * sizeof(int64_t)));
-  CU(ws.vsig.ensure(m * sizeof(double)));
-  CU(ws.vacc.ensure(m));
-  CU(cudaMemcpyAsync(ws.vlam.p, lam.data(), m * sizeof(double2), cudaMemcpyHostToDevice, s));
-  CU(cudaMemcpyAsync(ws.vprob.p, prob_of.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  // the certificate of y, against the call's own problem table
   CU(cudaMemcpyAsync(ws.voff.p, x_off.data(), m * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  ValueArgs va;
-  std::memset(&va, 0, sizeof(va));
-  va.probs = ws.probs.as<ProblemDev>();
-  va.prob_of = ws.vprob.as<int32_t>();
-  va.lam = ws.vlam.as<double2>();
   va.vec_off = ws.voff.as<int64_t>();
   va.vecs = ws.iX.as<double2>();
-  va.m = m;
-  va.tol_verify = c.opt->tol_verify;
-  va.sigma = ws.vsig.as<double>();
-  va.accept = ws.vacc.as<uint8_t>();
   prof_begin(PMCIM_K_VERIFY, s);
   CU(launch_certify(va, s));
   prof_end(PMCIM_K_VERIFY, s);
@@ -1341,7 +1347,6 @@ int run_inverse_step(Call& c, const std::vector<double2>& lam_in, const std::vec
   // to the full sigma_min computation
   for (int i = 0; i < m; ++i)
     if (!std::isfinite((*cert)[i])) (*ok)[i] = 0;
-  *x_off_out = x_off;
   return PMCIM_OK;
 }
 
@@ -1431,58 +1436,29 @@ int run_pmcimb(Call& c, const std::vector<HostRegion>& top_in, EigOut* e, Verifi
       idx.push_back((int)i);
     }
   }
-  // further certificates: up to kInverseSteps refined inverse-iteration steps,
-  // the first from Beyn's vector, each later one from the previous step's unit x
+  // a second certificate from the bordered inverse step started at Beyn's vector
   {
-    Workspace& ws = *c.ws;
-    const double2* rhs = ws.gdst.as<double2>();
-    std::vector<int64_t> rhs_off;
-    for (int k : idx) rhs_off.push_back(e->vec_off[k]);
-    for (int step = 0; step < kInverseSteps && !idx.empty(); ++step) {
-      std::vector<double> cert2;
-      std::vector<uint8_t> ok2;
-      std::vector<int64_t> xoff;
-      CHK(run_inverse_step(c, rest, rest_prob, rhs, rhs_off, &cert2, &ok2, &xoff));
-      std::vector<double2> rest2;
-      std::vector<int> rest2_prob, idx2;
-      std::vector<int64_t> src_off, dst_off;
-      std::vector<int32_t> ns;
-      int64_t tot = 0;
-      for (size_t k = 0; k < idx.size(); ++k) {
-        if (ok2[k]) {
-          v->sig[idx[k]] = cert2[k];
-          v->acc[idx[k]] = 1;
-          c.st.certified += 1;
-        } else {
-          rest2.push_back(rest[k]);
-          rest2_prob.push_back(rest_prob[k]);
-          idx2.push_back(idx[k]);
-          src_off.push_back(xoff[k]);
-          dst_off.push_back(tot);
-          ns.push_back(c.pd[rest_prob[k]].n);
-          tot += c.pd[rest_prob[k]].n;
-        }
+    std::vector<int64_t> start_off;
+    for (int k : idx) start_off.push_back(e->vec_off[k]);
+    std::vector<double> cert2;
+    std::vector<uint8_t> ok2;
+    CHK(run_bordered_step(c, rest, rest_prob, c.ws->gdst.as<double2>(), start_off, &cert2, &ok2));
+    std::vector<double2> rest2;
+    std::vector<int> rest2_prob, idx2;
+    for (size_t k = 0; k < idx.size(); ++k) {
+      if (ok2[k]) {
+        v->sig[idx[k]] = cert2[k];
+        v->acc[idx[k]] = 1;
+        c.st.certified += 1;
+      } else {
+        rest2.push_back(rest[k]);
+        rest2_prob.push_back(rest_prob[k]);
+        idx2.push_back(idx[k]);
       }
-      rest.swap(rest2);
-      rest_prob.swap(rest2_prob);
-      idx.swap(idx2);
-      if (idx.empty() || step + 1 == kInverseSteps) break;
-      // the unit x of this step becomes the next right-hand side
-      const int mm = (int)idx.size();
-      CU(ws.irhs.ensure((size_t)tot * sizeof(double2)));
-      CU(ws.ioffs.ensure((size_t)mm * 2 * sizeof(int64_t) + (size_t)mm * sizeof(int32_t)));
-      int64_t* d_src = ws.ioffs.as<int64_t>();
-      int64_t* d_dst = d_src + mm;
-      int32_t* d_n = reinterpret_cast<int32_t*>(d_dst + mm);
-      CU(cudaMemcpyAsync(d_src, src_off.data(), mm * sizeof(int64_t), cudaMemcpyHostToDevice, c.s));
-      CU(cudaMemcpyAsync(d_dst, dst_off.data(), mm * sizeof(int64_t), cudaMemcpyHostToDevice, c.s));
-      CU(cudaMemcpyAsync(d_n, ns.data(), mm * sizeof(int32_t), cudaMemcpyHostToDevice, c.s));
-      prof_begin(PMCIM_K_GATHER, c.s);
-      CU(launch_normalize_copy(ws.iX.as<double2>(), ws.irhs.as<double2>(), d_src, d_dst, d_n, mm, c.s));
-      prof_end(PMCIM_K_GATHER, c.s);
-      rhs = ws.irhs.as<double2>();
-      rhs_off = dst_off;
     }
+    rest.swap(rest2);
+    rest_prob.swap(rest2_prob);
+    idx.swap(idx2);
   }
   std::vector<double> sig2;
   std::vector<uint8_t> acc2;
@@ -1777,6 +1753,56 @@ int pmcim_verify(pmcim_problem p, const pmcim_options* opt, int32_t m, const dou
   std::vector<uint8_t> acc;
   CHK(run_verify(c, lam, std::vector<int>(m, 0), &sig, &acc));
   CHK(copy_out(sigma_min, sig.data(), m * sizeof(double)));
+  if (accept) CHK(copy_out(accept, acc.data(), m));
+  return PMCIM_OK;
+}
+
+int pmcim_certify(pmcim_problem p, const pmcim_options* opt, int32_t m, const double* lambda, const double* vecs,
+                  double* cert, uint8_t* accept) {
+  if (!p) return fail(PMCIM_EINVAL, "problem is NULL");
+  CHK(check_options(opt));
+  if (m < 0 || (m > 0 && (!lambda || !vecs || !cert))) return fail(PMCIM_EINVAL, "bad arguments");
+  if (m == 0) return PMCIM_OK;
+  const int n = p->n;
+  std::vector<double2> lam(m);
+  cudaError_t e = cudaMemcpy(lam.data(), lambda, m * sizeof(double2), cudaMemcpyDefault);
+  if (e != cudaSuccess) return fail(PMCIM_ECUDA, "lambda copy: %s", cudaGetErrorString(e));
+  Call c;
+  c.opt = opt;
+  c.ws = &p->ws;
+  CHK(call_stream(p->ws, opt, &c.s));
+  c.groups = {Group{p, 1, opt->precision == PMCIM_PREC_AUTO ? PMCIM_PREC_FP32_IR : opt->precision}};
+  CHK(upload_problems(c));
+  Workspace& ws = p->ws;
+  CU(ws.gdst.ensure((size_t)m * n * sizeof(double2)));
+  CU(cudaMemcpyAsync(ws.gdst.p, vecs, (size_t)m * n * sizeof(double2), cudaMemcpyDefault, c.s));
+  EigOut eo;
+  eo.lam = lam;
+  eo.prob.assign(m, 0);
+  eo.root.assign(m, 0);
+  for (int i = 0; i < m; ++i) eo.vec_off.push_back((int64_t)i * n);
+  std::vector<double> sig;
+  std::vector<uint8_t> acc;
+  CHK(run_certify(c, eo, &sig, &acc));
+  std::vector<double2> rest;
+  std::vector<int64_t> off;
+  std::vector<int> idx;
+  for (int i = 0; i < m; ++i)
+    if (!acc[i] || !std::isfinite(sig[i])) {
+      acc[i] = 0;
+      rest.push_back(lam[i]);
+      off.push_back((int64_t)i * n);
+      idx.push_back(i);
+    }
+  std::vector<double> sig2;
+  std::vector<uint8_t> acc2;
+  CHK(run_bordered_step(c, rest, std::vector<int>(rest.size(), 0), ws.gdst.as<double2>(), off, &sig2, &acc2));
+  for (size_t k = 0; k < idx.size(); ++k) {
+    const int i = idx[k];
+    if (std::isfinite(sig2[k]) && !(sig2[k] >= sig[i])) sig[i] = sig2[k];
+    acc[i] = acc2[k];
+  }
+  CHK(copy_out(cert, sig.data(), m * sizeof(double)));
   if (accept) CHK(copy_out(accept, acc.data(), m));
   return PMCIM_OK;
 }

@@ -284,12 +284,63 @@ __device__ void residual_fp64(const double2* __restrict__ X, double2* __restrict
   gsync();
 }
 
+// The same for one column (l = 1), as a matrix-vector product: the tiled form
+// above would multiply RT_COLS - 1 zero columns as well. Each thread owns four
+// rows of a 4 x THREADS row block and streams the columns of M (coalesced over
+// rows, several columns in flight); f_M x is staged in shared memory.
+__device__ void residual_fp64_col(const double2* __restrict__ X, double2* __restrict__ R, const NodeCtx& cx,
+                                  ResSmem& rs, const double2* __restrict__ M, double2 fM, double2 id) {
+  const ProblemDev& P = cx.P;
+  const int n = P.n;
+  const int tid = gtid();
+  constexpr int XCH = 2 * RT_K * RT_ROWS;  // f_M x entries per shared-memory chunk
+  double2* xs = &rs.As[0][0];
+  for (int r0 = 0; r0 < n; r0 += 4 * THREADS) {
+    double2 acc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int row = r0 + tid + i * THREADS;
+      double2 v = make_double2(0.0, 0.0);
+      if (row < n) {
+        v = P.V[row];
+        cfms(v, id, X[row]);
+      }
+      acc[i] = v;
+    }
+    if (M) {
+      for (int c0 = 0; c0 < n; c0 += XCH) {
+        const int cn = min(XCH, n - c0);
+        gsync();  // the previous chunk is no longer read
+        for (int e = tid; e < cn; e += THREADS) xs[e] = cmul(fM, X[c0 + e]);
+        gsync();
+#pragma unroll 4
+        for (int c = 0; c < cn; ++c) {
+          const double2 xv = xs[c];
+          const double2* __restrict__ mc = M + (size_t)(c0 + c) * n;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int row = r0 + tid + i * THREADS;
+            if (row < n) cfms(acc[i], mc[row], xv);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int row = r0 + tid + i * THREADS;
+      if (row < n) R[row] = acc[i];
+    }
+  }
+  gsync();
+}
+
 // T(z_j) in FP64 into T (n x n, column-major), the matrix of the refinement
 // residuals, and rounded to complex64 into M32 (leading dimension n), the FP32
 // LU's matrix: the dense terms in one pass over the elements, four elements per
 // thread at a time so that their coefficient loads overlap, then the identity
-// terms on the diagonal.
-__device__ void assemble_fp64(const NodeCtx& cx, double2* __restrict__ T, float2* __restrict__ M32) {
+// terms on the diagonal. herm: T(z_j)^H instead (the coefficients read
+// transposed, the sum conjugated; used by the certificates' bordered steps).
+__device__ void assemble_fp64(const NodeCtx& cx, double2* __restrict__ T, float2* __restrict__ M32, bool herm) {
   const ProblemDev& P = cx.P;
   const int n = P.n;
   const size_t nn = (size_t)n * n;
@@ -308,7 +359,8 @@ __device__ void assemble_fp64(const NodeCtx& cx, double2* __restrict__ T, float2
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const size_t e = e0 + (size_t)u * THREADS;
-        a[u] = e < nn ? A[e] : make_double2(0.0, 0.0);
+        const size_t src = herm ? (e % n) * n + e / n : e;
+        a[u] = e < nn ? A[src] : make_double2(0.0, 0.0);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) cfma(v[u], cx.fz[k], a[u]);
@@ -317,12 +369,14 @@ __device__ void assemble_fp64(const NodeCtx& cx, double2* __restrict__ T, float2
     for (int u = 0; u < 4; ++u) {
       const size_t e = e0 + (size_t)u * THREADS;
       if (e < nn) {
+        if (herm) v[u].y = -v[u].y;
         T[e] = v[u];
         M32[e] = make_float2((float)v[u].x, (float)v[u].y);
       }
     }
   }
   gsync();
+  if (herm) id.y = -id.y;
   for (int i = gtid(); i < n; i += THREADS) {
     const size_t e = (size_t)i * n + i;
     const double2 t = cadd(T[e], id);
@@ -476,12 +530,19 @@ __device__ void factor_group(const NodeArgs& a, MixedSmem& sm, tcu::Ctx& cx, Pha
     const int n = P.n, l = P.l, ncols = n + l;
     const size_t nn = (size_t)n * n, nl = (size_t)n * l;
     pc.mark(PH_SETUP);
-    if (P.n_dense >= 2 && !a.oz)  // T(z_j) in FP64 for the refine group's FP64 residual, and rounded
-      assemble_fp64(c, a.t64 + si * a.t64_stride, M32);
+    // T(z_j) in FP64 for the refine group's FP64 residual, and rounded; T(z_j)^H likewise
+    if (rg.herm || (P.n_dense >= 2 && !a.oz))
+      assemble_fp64(c, a.t64 + si * a.t64_stride, M32, rg.herm != 0);
     else
       assemble32(c, M32);
     for (size_t e = tid; e < nl; e += THREADS) M32[nn + e] = make_float2((float)P.V[e].x, (float)P.V[e].y);
     gsync();
+    if (rg.border > 0) {  // the bordered matrix of a certificate: column s of T(z_j) replaced
+      const double2* bc = a.border + rg.v_off;
+      float2* col = M32 + (size_t)(rg.border - 1) * n;
+      for (int i = tid; i < n; i += THREADS) col[i] = make_float2((float)bc[i].x, (float)bc[i].y);
+      gsync();
+    }
     pc.mark(PH_ASSEMBLE);
     const int bad_before = sm.tc_bad;
     const int info = cta_lu32(M32, n, ncols, piv, sm.f.u.lu32, cx, rg.lu_tc != 0, pc);
@@ -557,7 +618,7 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
     int sweeps = 0;
     // residuals on the tensor cores (exact digit products), unless a wait of that
     // path ran out earlier in this CTA; then the node is solved in FP64 below
-    const bool use_oz = a.oz && P.Adig != nullptr;
+    const bool use_oz = a.oz && P.Adig != nullptr && !rg.herm;
     if (use_oz && sm.ozb.bad) {
       ok = false;
       tc_lost = true;
@@ -571,7 +632,7 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
       double2 fM = make_double2(0.0, 0.0), id = make_double2(0.0, 0.0);
       if (use_oz) {
         // every dense term through the digit products; nothing to set up here
-      } else if (P.n_dense >= 2) {  // assembled by the factor group with the slot
+      } else if (P.n_dense >= 2 || rg.herm) {  // assembled by the factor group with the slot
         M = a.t64 + si * a.t64_stride;
         fM = make_double2(1.0, 0.0);
       } else {
@@ -596,7 +657,15 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
             break;
           }
         } else {
-          residual_fp64(X, R, c, sm.r.u.res, M, fM, id);
+          if (l == 1) residual_fp64_col(X, R, c, sm.r.u.res, M, fM, id);
+          else residual_fp64(X, R, c, sm.r.u.res, M, fM, id);
+        }
+        if (rg.border > 0) {
+          // bordered system M u = b, M = T(z_j) + (c - T(z_j) e_s) e_s^T with b = -T(z_j) e_s:
+          // R = b - T X - (c + b) X_s (l = 1)
+          const double2 xs = X[rg.border - 1];
+          const double2* bc = a.border + rg.v_off;
+          for (size_t e = tid; e < nl; e += THREADS) cfms(R[e], cadd(bc[e], P.V[e]), xs);
         }
         pc.mark(PH_RESIDUAL);
         double rm = 0.0;
@@ -643,9 +712,14 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
       }
       if (!conv) ok = false;
     }
-    if (!ok && refine) {
+    if (!ok && refine && rg.border == 0) {
       info = fallback_fp64(c, M64, piv, X, sm.r.u.lu64);
       pc.mark(PH_FALLBACK);
+    }
+    if (rg.border > 0) {
+      // the certificate's vector y = e_s + (u - u_s e_s): T(z_j) y = -u_s c
+      gsync();
+      if (tid == 0) X[rg.border - 1] = make_double2(1.0, 0.0);
     }
     if (tid == 0)
       a.node_info[rg.node_off + it.j] =

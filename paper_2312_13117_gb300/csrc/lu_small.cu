@@ -46,16 +46,18 @@ __global__ void __launch_bounds__(WARPS * 32) k_factor_solve_small(NodeArgs a) {
     if (lane < P.K) sm.fz[w][lane] = eval_f(P.term[lane], z);
     __syncwarp();
     const size_t nn = (size_t)n * n;
-    // assemble [T(z_j) | V], row `lane`
+    // assemble [T(z_j) | V] (T(z_j)^H for a certificate's step with rg.herm), row `lane`
     if (lane < n) {
       double2* row = M + lane * LDC;
       for (int c = 0; c < n; ++c) {
         double2 v = make_double2(0.0, 0.0);
+        const size_t e = rg.herm ? (size_t)lane * n + c : (size_t)c * n + lane;
         for (int k = 0; k < P.K; ++k) {
           const TermDesc& t = P.term[k];
-          if (t.dense) cfma(v, sm.fz[w][k], P.A[(size_t)t.mat_index * nn + (size_t)c * n + lane]);
+          if (t.dense) cfma(v, sm.fz[w][k], P.A[(size_t)t.mat_index * nn + e]);
           else if (c == lane) cfma(v, sm.fz[w][k], t.id);
         }
+        if (rg.herm) v.y = -v.y;
         row[c] = v;
       }
       for (int c = 0; c < l; ++c) row[n + c] = P.V[(size_t)c * n + lane];

@@ -169,6 +169,9 @@ struct RegionDev {
   int32_t node_off;  // index of node 0 in the launch's node_info array
   int32_t gate;      // 1: Beyn runs only when the indicator marks a candidate
   int32_t lu_tc;     // 1: the precision form's trailing updates run on the tensor cores
+  int32_t border;    // 0, or s + 1: the node solves the bordered system of a certificate, T(z)
+                     // (T(z)^H when herm) with column s replaced by the column at NodeArgs::border + v_off
+  int32_t herm;      // 1: the node's matrix is T(z)^H (precision form: FP64-pipe residuals, t64 set)
   int64_t x_off;     // double2 offset of node 0's solution in X (node j at x_off + j n l)
   int64_t c_off;     // double2 offset of the disk's C0 / C1 blocks (n l)
   int64_t p_off;     // offset of the disk's P f blocks (n)
@@ -216,6 +219,7 @@ struct NodeArgs {
   size_t ysl_stride;          // bytes per slot
   long long tc_wait_cycles;       // mixed kernel: limit of a wait for a tensor-core commit
   long long handoff_wait_cycles;  // mixed kernel: limit of a wait between its thread groups
+  const double2* border;          // mixed kernel: the replacement columns of bordered nodes
 };
 // Limits of the precision-form kernel's bounded waits (clock64 cycles): the
 // defaults, or the values a test set with pmcim_debug_wait_limits.
@@ -302,6 +306,7 @@ struct ValueArgs {
   int slots;
   int max_n;
   double2* vec_out;         // verify: NULL, or m * max_n: the unit right singular vector for sigma_min
+  int herm;                 // certificate: 1 = ||T(lambda)^H v|| (sigma_min(T^H) = sigma_min(T))
 };
 cudaError_t launch_certify(const ValueArgs& a, cudaStream_t s);
 cudaError_t launch_verify_fp64(const ValueArgs& a, cudaStream_t s);
@@ -324,9 +329,12 @@ struct VecItem {
   int32_t n;
   int32_t pad;
 };
-// dst block i = src block i normalised to unit 2-norm (n_i complex values each).
-cudaError_t launch_normalize_copy(const double2* src, double2* dst, const int64_t* src_off, const int64_t* dst_off,
-                                  const int32_t* ns, int count, cudaStream_t s);
+// A certificate's bordered inverse step (reduce.cu): for each value m with
+// off[m] >= 0, the start vector at vecs + vec_off[m] gives the replaced column s
+// (regions[m].border = s + 1), b = -T e_s at out + off[m] and the scaled
+// replacement column after it; T = T(lambda), or T(lambda)^H when a.herm.
+cudaError_t launch_border_rhs(const ValueArgs& a, const int64_t* off, double2* out, RegionDev* regions,
+                              cudaStream_t s);
 cudaError_t launch_gather_vecs(const double2* src, double2* dst, const VecItem* items, int count, int max_n,
                                cudaStream_t s);
 

@@ -135,31 +135,104 @@ __global__ void k_gather_vecs(const double2* __restrict__ src, double2* __restri
   dst[it.dst + i] = src[it.src + i];
 }
 
-// dst block i = src block i / ||src block i||_2 (blocks of n_i complex values at
-// the given offsets; a zero or non-finite block is copied unscaled). One CTA per block.
-__global__ void __launch_bounds__(RT) k_normalize_copy(const double2* __restrict__ src, double2* __restrict__ dst,
-                                                      const int64_t* __restrict__ src_off,
-                                                      const int64_t* __restrict__ dst_off,
-                                                      const int32_t* __restrict__ ns) {
-  __shared__ double red[RT / 32];
-  const int b = blockIdx.x, n = ns[b];
-  const double2* x = src + src_off[b];
-  double2* y = dst + dst_off[b];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += RT) s += cabs2(x[i]);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+// The data of a certificate's bordered inverse step, one value per CTA (values
+// with off[m] < 0 are skipped). T is T(lambda), or T(lambda)^H when a.herm. With
+// c the value's start vector: s = the index of the largest |c_i| (the smallest
+// such index), written to regions[m].border as s + 1; at out + off[m] the
+// right-hand side b = -T e_s (n values; for T^H the conjugate of row s of
+// T(lambda)) and then the replacement column alpha c, alpha = ||T e_s|| / ||c||
+// (1 when either norm is zero), so that it is on the scale of the columns it
+// stands among.
+__global__ void __launch_bounds__(RT) k_border_rhs(ValueArgs a, const int64_t* __restrict__ off,
+                                                   double2* __restrict__ out, RegionDev* __restrict__ regions) {
+  __shared__ ProblemDev P;
+  __shared__ double2 fz[PMCIM_MAX_TERMS];
+  __shared__ double rq[RT / 32], rc[RT / 32];
+  __shared__ int ri[RT / 32];
+  __shared__ double alpha;
+  __shared__ int s_col;
+  const int m = blockIdx.x;
+  if (off[m] < 0) return;
+  load_problem(&P, a.probs + a.prob_of[m]);
   __syncthreads();
-  double t = 0.0;
-  for (int k = 0; k < RT / 32; ++k) t += red[k];
-  const double inv = (t > 0.0 && isfinite(t)) ? 1.0 / sqrt(t) : 1.0;
-  for (int i = threadIdx.x; i < n; i += RT) y[i] = cscale(x[i], inv);
+  const int n = P.n;
+  const size_t nn = (size_t)n * n;
+  const double2* c = a.vecs + a.vec_off[m];
+  double2* b = out + off[m];
+  if (threadIdx.x < P.K) fz[threadIdx.x] = eval_f(P.term[threadIdx.x], a.lam[m]);
+  // argmax |c_i| (each thread scans increasing i, so a tie keeps the smaller index) and ||c||^2
+  double best = -1.0, cc = 0.0;
+  int bi = 0;
+  for (int i = threadIdx.x; i < n; i += RT) {
+    const double q = cabs2(c[i]);
+    cc += q;
+    if (q > best) {
+      best = q;
+      bi = i;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_down_sync(0xffffffffu, best, o);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+    cc += __shfl_down_sync(0xffffffffu, cc, o);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rq[threadIdx.x >> 5] = best;
+    ri[threadIdx.x >> 5] = bi;
+    rc[threadIdx.x >> 5] = cc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bq = rq[0];
+    int bs = ri[0];
+    for (int k = 1; k < RT / 32; ++k)
+      if (rq[k] > bq || (rq[k] == bq && ri[k] < bs)) {
+        bq = rq[k];
+        bs = ri[k];
+      }
+    s_col = bs;
+  }
+  __syncthreads();
+  const int sc = s_col;
+  // b = -(column s of T) and its squared norm
+  double tt = 0.0;
+  for (int i = threadIdx.x; i < n; i += RT) {
+    double2 t = make_double2(0.0, 0.0);
+    const size_t e = a.herm ? (size_t)i * n + sc : (size_t)sc * n + i;  // element (i, s) or (s, i) of T(lambda)
+    for (int k = 0; k < P.K; ++k) {
+      const TermDesc& tk = P.term[k];
+      if (tk.dense) cfma(t, fz[k], P.A[(size_t)tk.mat_index * nn + e]);
+      else if (i == sc) cfma(t, fz[k], tk.id);
+    }
+    tt += cabs2(t);
+    b[i] = a.herm ? make_double2(-t.x, t.y) : make_double2(-t.x, -t.y);
+  }
+  for (int o = 16; o > 0; o >>= 1) tt += __shfl_down_sync(0xffffffffu, tt, o);
+  __syncthreads();  // rq is reused
+  if ((threadIdx.x & 31) == 0) rq[threadIdx.x >> 5] = tt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t2 = 0.0, c2 = 0.0;
+    for (int k = 0; k < RT / 32; ++k) {
+      t2 += rq[k];
+      c2 += rc[k];
+    }
+    alpha = (t2 > 0.0 && c2 > 0.0 && isfinite(t2) && isfinite(c2)) ? sqrt(t2) / sqrt(c2) : 1.0;
+    regions[m].border = sc + 1;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += RT) b[n + i] = cscale(c[i], alpha);
 }
 
-// Verification certificate (pmCIMb step 3): for a candidate lambda with unit
-// eigenvector v, sigma_min(T(lambda)) <= ||T(lambda) v||. One CTA per value
-// forms T(lambda) one column at a time (never stored), accumulating
-// r = T(lambda) v and ||T(lambda)||_F^2, all in FP64.
+// Verification certificate (pmCIMb step 3): for a candidate lambda and a vector
+// v != 0, sigma_min(T(lambda)) <= ||T(lambda) v|| / ||v||, and likewise with
+// T(lambda)^H (a.herm), whose smallest singular value is the same. One CTA per
+// value forms T(lambda) element by element (never stored), accumulating
+// r = T v (or T^H v) and ||T(lambda)||_F^2, all in FP64.
 __global__ void __launch_bounds__(RT) k_certify(ValueArgs a) {
   __shared__ ProblemDev P;
   __shared__ double2 fz[PMCIM_MAX_TERMS];
@@ -178,11 +251,14 @@ __global__ void __launch_bounds__(RT) k_certify(ValueArgs a) {
     double2 r = make_double2(0.0, 0.0);
     for (int col = 0; col < n; ++col) {
       double2 t = make_double2(0.0, 0.0);
+      // element (row, col) of T(lambda), or for T^H the conjugate of element (col, row)
+      const size_t e = a.herm ? (size_t)row * n + col : (size_t)col * n + row;
       for (int k = 0; k < P.K; ++k) {
         const TermDesc& tk = P.term[k];
-        if (tk.dense) cfma(t, fz[k], P.A[(size_t)tk.mat_index * nn + (size_t)col * n + row]);
+        if (tk.dense) cfma(t, fz[k], P.A[(size_t)tk.mat_index * nn + e]);
         else if (row == col) cfma(t, fz[k], tk.id);
       }
+      if (a.herm) t.y = -t.y;
       cfma(r, t, v[col]);
       f2 += cabs2(t);
     }
@@ -225,10 +301,10 @@ cudaError_t launch_indicator(const LevelArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_normalize_copy(const double2* src, double2* dst, const int64_t* src_off, const int64_t* dst_off,
-                                  const int32_t* ns, int count, cudaStream_t s) {
-  if (count <= 0) return cudaSuccess;
-  k_normalize_copy<<<count, RT, 0, s>>>(src, dst, src_off, dst_off, ns);
+cudaError_t launch_border_rhs(const ValueArgs& a, const int64_t* off, double2* out, RegionDev* regions,
+                              cudaStream_t s) {
+  if (a.m <= 0) return cudaSuccess;
+  k_border_rhs<<<a.m, RT, 0, s>>>(a, off, out, regions);
   return cudaGetLastError();
 }
 

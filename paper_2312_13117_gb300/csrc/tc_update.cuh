@@ -280,6 +280,33 @@ __device__ __forceinline__ void stage_barrier() {
   fence_after();
 }
 
+// Hint to bring the 128-byte line holding p into L2 (no register, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// L2 prefetch of what tile tt of the row block at r0 will load: its C values (32
+// columns x 128 rows: one line per thread) and its U12 operand (32 columns x 32
+// rows: two lines per column). Only addresses inside the matrix are touched.
+__device__ __forceinline__ void prefetch_tile(const float2* M, size_t ld, int n, int ncols, int k0, int kend,
+                                              int r0, int tt) {
+  const int tid = lucore::gtid();
+  const int c0 = kend + tt * TN;
+  const int col = c0 + (tid >> 3), row = r0 + 16 * (tid & 7);
+  if (col < ncols && row < n) prefetch_l2(M + (size_t)col * ld + row);
+  if (tid < 2 * TN) {
+    const int uc = c0 + (tid >> 1), ur = k0 + 16 * (tid & 1);
+    if (uc < ncols && ur < kend) prefetch_l2(M + (size_t)uc * ld + ur);
+  }
+}
+
+// L2 prefetch of the L21 rows r0..r0+127 of panel columns k0..k0+31 (one line per thread).
+__device__ __forceinline__ void prefetch_L(const float2* M, size_t ld, int n, int k0, int kend, int r0) {
+  const int tid = lucore::gtid();
+  const int col = k0 + (tid >> 3), row = r0 + 16 * (tid & 7);
+  if (col < kend && row < n) prefetch_l2(M + (size_t)col * ld + row);
+}
+
 // A22 -= L21 U12 for the panel k0..k0+kb-1 on the tensor cores. All threads of
 // the group call it; it returns with the group synchronised and no MMA in
 // flight, unless a wait ran out (then *cx.bad is set and the rest of the
@@ -301,6 +328,10 @@ __device__ inline void update(float2* __restrict__ M, int n, int ncols, int k0, 
     for (int t = 0; t < T; ++t) {
       const int b = t & 1;
       const int c0 = kend + t * TN;
+      // the lines of the tile two steps ahead (in this row block or the next) into L2
+      if (t + 2 < T) prefetch_tile(M, ld, n, ncols, k0, kend, r0, t + 2);
+      else if (r0 + TM < n && t + 2 - T < T) prefetch_tile(M, ld, n, ncols, k0, kend, r0 + TM, t + 2 - T);
+      if (t + 3 == T && r0 + TM < n) prefetch_L(M, ld, n, k0, kend, r0 + TM);
       // operands of tile t+1: its U12 set was last read by tile t-1's MMAs, complete
       if (t + 1 < T) stage_U(M, ld, ncols, c0 + TN, k0, kb, bset0 + (b ^ 1) * B_SET);
       // this tile's C values, loaded while its MMAs run

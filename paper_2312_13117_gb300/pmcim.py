@@ -29,7 +29,7 @@ EXPORTS = ["pmcim_default_options", "pmcim_problem_create", "pmcim_problem_destr
            "pmcim_last_error", "pmcim_profile_enable", "pmcim_profile_reset", "pmcim_profile_read",
            "pmcim_solve_points_noalloc", "pmcim_batch_solve", "pmcim_screen_features", "pmcim_screen_train",
            "pmcim_screen_apply", "pmcim_screen_gradient", "pmcim_pmcima", "pmcim_debug_wait_limits",
-           "pmcim_residual"]
+           "pmcim_residual", "pmcim_certify"]
 
 KERNELS = ["factor_fp64", "reduce", "indicator", "beyn", "verify", "gather", "factor_fp32", "screen"]
 SCREEN_PARAMS = 4481
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pmcim_beyn.argtypes = [P, C.POINTER(pmcim_options), I32, C.POINTER(pmcim_region), I32, VP, I32, VP, VP, VP,
                                VP, VP]
     lib.pmcim_verify.argtypes = [P, C.POINTER(pmcim_options), I32, VP, VP, VP]
+    lib.pmcim_certify.argtypes = [P, C.POINTER(pmcim_options), I32, VP, VP, VP, VP]
     lib.pmcim_solve.argtypes = [P, C.POINTER(pmcim_options), I32, C.POINTER(pmcim_region), I32, VP, I32, VP, VP, VP,
                                 VP, VP, VP, VP, C.POINTER(pmcim_stats)]
     lib.pmcim_status_string.argtypes = [C.c_int]
@@ -123,7 +124,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     for name in ("pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments", "pmcim_indicator",
                  "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_solve_points_noalloc", "pmcim_batch_solve",
                  "pmcim_screen_features", "pmcim_screen_train", "pmcim_screen_apply", "pmcim_screen_gradient",
-                 "pmcim_pmcima", "pmcim_debug_wait_limits", "pmcim_residual"):
+                 "pmcim_pmcima", "pmcim_debug_wait_limits", "pmcim_residual", "pmcim_certify"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -413,6 +414,21 @@ class Problem:
         opt = opt or options()
         _check(lib.pmcim_verify(self.handle, C.byref(opt), m, _ptr(lam), _ptr(sig), _ptr(acc)), "pmcim_verify")
         return sig[:m], acc[:m].astype(bool)
+
+    def certify(self, lam, vecs, opt=None):
+        """Upper bounds of sigma_min(T(lambda_i)) from start vectors (n x m, column i for
+        lambda_i): the start vector's own residual, then the bordered inverse step's.
+        Returns (cert, accept)."""
+        lib = load()
+        lam = np.ascontiguousarray(np.atleast_1d(np.asarray(lam, np.complex128)))
+        m = len(lam)
+        vc = np.ascontiguousarray(np.asarray(vecs, np.complex128).reshape(-1, m).T)  # column-major
+        cert = np.zeros(max(m, 1))
+        acc = np.zeros(max(m, 1), np.uint8)
+        opt = opt or options()
+        _check(lib.pmcim_certify(self.handle, C.byref(opt), m, _ptr(lam), _ptr(vc), _ptr(cert), _ptr(acc)),
+               "pmcim_certify")
+        return cert[:m], acc[:m].astype(bool)
 
     def residual(self, z, V, X, opt=None):
         """R_j = V - T(z_j) X_j on the tensor cores; X is m x n x l (or n x l for one point)."""

@@ -350,6 +350,24 @@ def test_mixed_moments_close_to_oracle(pm, form):
 
 
 @pytest.mark.parametrize("form", MIXED_FORMS)
+def test_mixed_moments_one_column_fp64_residual(pm, form):
+    """One probe column (l = 1) with the residuals on the FP64 pipe, which then run as a
+    matrix-vector product: n = 1100 spans two row blocks of 1024 and a ragged tail."""
+    W = w.quadratic_small(seed=5, n=1100, l=1, N=16)
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    C0, C1, _, _ = P.moments(W.regions[:2], W.V, opt=_mixed_opt(pm, form, residual_fp64=True))
+    for g, reg in enumerate(W.regions[:2]):
+        m = o.moments(W.problem, reg.c, reg.r, reg.N, W.V)
+        z, wts = o.nodes_weights(reg.c, reg.r, reg.N)
+        X = o.solve_nodes(W.problem, z, W.V)
+        scale = sum(abs(wts[j]) * np.linalg.norm(X[j]) for j in range(reg.N))
+        b0, b1, _ = _moment_bound(W.problem, reg, W.V)
+        assert np.linalg.norm(C0[g] - m.C0) <= b0 + 1e-9 * scale
+        assert np.linalg.norm(C1[g] - m.C1) <= b1 + 1e-9 * scale * (abs(reg.c) + reg.r)
+    P.close()
+
+
+@pytest.mark.parametrize("form", MIXED_FORMS)
 def test_mixed_solve_quadratic_n64(pm, form):
     W = w.quadratic_small()
     P = pm.Problem(W.problem.n, W.problem.terms)

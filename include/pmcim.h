@@ -377,7 +377,7 @@ int pmcim_solve_points_noalloc(int32_t n, int32_t K, const pmcim_fterm* f, const
 #define PMCIM_K_FACTOR32 6 /* assembly + LU + solve at the nodes (FP32 LU)   */
 #define PMCIM_K_SCREEN 7   /* learned screen: MLP forward / training          */
 #define PMCIM_K_COUNT 8
-#define PMCIM_PHASE_COUNT 12
+#define PMCIM_PHASE_COUNT 16
 
 typedef struct {
   int64_t launches[PMCIM_K_COUNT];
@@ -386,8 +386,9 @@ typedef struct {
      CTAs per phase: assembly, LU panels, first solve, FP64 residual,
      correction solves, FP64 fallback, node set-up, LU triangular solves
      (U12), LU trailing updates, factor group waiting for a free slot, refine
-     group waiting for a factored node; the last entry is the CTAs' lifetimes
-     in ns (globaltimer), summed */
+     group waiting for a factored node, then the CTAs' lifetimes in ns
+     (globaltimer, summed), then the LU panels' row interchanges on the columns
+     outside the panel (counted apart from the panels); 3 unused */
   double mixed_phase_cycles[PMCIM_PHASE_COUNT];
 } pmcim_profile;
 

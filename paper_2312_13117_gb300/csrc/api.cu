@@ -1296,8 +1296,10 @@ int run_bordered_step(Call& c, const std::vector<double2>& lam_in, const std::ve
     const size_t t64_stride = (size_t)t64_n * t64_n;
     const size_t cta_bytes = per * (slot32 + t64_stride * sizeof(double2));
     const size_t budget = slot_budget(ws.work32.cap + ws.t64.cap);
+    // one value per CTA (its other slot idle): the values are few, and a CTA works
+    // through its slots one node after another
     const size_t ctas = std::max<size_t>(1, std::min<size_t>(std::min<size_t>(sms, budget / cta_bytes),
-                                                             (it32.size() + per - 1) / per));
+                                                             it32.size()));
     const int slots32 = (int)(ctas * per);
     CU(ws.work32.ensure((size_t)slots32 * slot32));
     CU(ws.piv32.ensure((size_t)slots32 * max_n * sizeof(int32_t)));

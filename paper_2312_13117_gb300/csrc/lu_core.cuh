@@ -107,10 +107,11 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* red2) {
 // Returns 0, or 1 + the first column whose pivot was exactly zero.
 // ---------------------------------------------------------------------------
 // Panel factorisation of columns k0..k0+kb-1 (rows k0..n-1), with the row swaps
-// applied across all ncols columns.
+// applied across columns c_first..ncols-1 (0: all columns, LAPACK's order; k0:
+// not to the L columns left of the panel, LINPACK's order).
 template <typename T2>
 __device__ void cta_lu_panel(T2* __restrict__ M, int n, int ncols, int k0, int kb, int* __restrict__ piv,
-                             LuSmemT<T2>& sm) {
+                             LuSmemT<T2>& sm, int c_first = 0) {
   const int tid = gtid();
   const size_t ld = (size_t)n;
   const int kend = k0 + kb;
@@ -143,7 +144,7 @@ __device__ void cta_lu_panel(T2* __restrict__ M, int n, int ncols, int k0, int k
     gsync();
     const int p = sm.piv_sh;
     if (p != j) {
-      for (int c0 = tid; c0 < ncols; c0 += THREADS * RB) {
+      for (int c0 = c_first + tid; c0 < ncols; c0 += THREADS * RB) {
         T2 a[RB], b[RB];
 #pragma unroll
         for (int u = 0; u < RB; ++u) {
@@ -216,11 +217,12 @@ __device__ void cta_lu_panel(T2* __restrict__ M, int n, int ncols, int k0, int k
 // memory, written back, and then applied to the rest of the panel (its row
 // swaps as one gather, the unit lower triangular solve for its U rows, and one
 // rank-SB update). The row swaps of the columns outside the panel (and of the
-// panel's earlier sub-panels) are applied after the panel, pivot by pivot, as in
-// LAPACK's getrf. scratch: shared memory of scratch_elems elements, at least
-// (n - k0) + 8 NB + 40 (then SB = 1).
+// panel's earlier sub-panels) are applied after the panel (cta_panel_swaps_lp,
+// with the sub-panel width this returns).
+// scratch: shared memory of scratch_elems elements, at least (n - k0) + 8 NB + 40
+// (then SB = 1).
 template <typename T2>
-__device__ __noinline__ void cta_lu_panel_sub(T2* __restrict__ M, int n, int ncols, int k0, int kb, int* __restrict__ piv,
+__device__ __noinline__ int cta_lu_panel_sub(T2* __restrict__ M, int n, int ncols, int k0, int kb, int* __restrict__ piv,
                                  LuSmemT<T2>& sm, T2* __restrict__ scratch, int scratch_elems) {
   const int tid = gtid();
   const size_t ld = (size_t)n;
@@ -375,33 +377,91 @@ __device__ __noinline__ void cta_lu_panel_sub(T2* __restrict__ M, int n, int nco
     }
     gsync();
   }
-  // 4. the panel's swaps on the other columns: a swap of sub-panel s is already in
-  // the columns of sub-panel s and of the later sub-panels
-  constexpr int RBS = sizeof(T2) == 8 ? 4 : 2;
-  for (int j = k0; j < kend; ++j) {
+  return SB;
+}
+
+
+// ---------------------------------------------------------------------------
+// Row interchanges in LINPACK's order (the precision form's FP32 LU): a panel's
+// swaps reach the panel's own columns and the columns right of it, never the L
+// columns left of it, so a forward solve applies each panel's swaps to the
+// right-hand side just before that panel's columns of L. A panel's swaps are
+// handled as one permutation of at most 2 NB rows.
+// ---------------------------------------------------------------------------
+constexpr int SWAP_LIST_INTS = 1 + 4 * NB;  // [cnt, dst[2 NB], src[2 NB]]
+
+// The swaps piv[a..b-1] (row j with row piv[j], in that order) as one permutation:
+// row dst[i] receives the old row src[i], i < cnt. One thread.
+__device__ inline void compose_swaps(const int* __restrict__ piv, int a, int b, int* __restrict__ list) {
+  int cnt = 0;
+  int* dst = list + 1;
+  int* src = list + 1 + 2 * NB;
+  for (int j = a; j < b; ++j) {
     const int p = piv[j];
     if (p == j) continue;
-    const int done_lo = k0 + ((j - k0) / SB) * SB;  // columns done_lo..kend-1 hold it already
-    for (int c0 = tid; c0 < ncols; c0 += THREADS * RBS) {
-      T2 a[RBS], b[RBS];
-#pragma unroll
-      for (int u = 0; u < RBS; ++u) {
-        const int c = c0 + u * THREADS;
-        if (c < ncols && (c < done_lo || c >= kend)) {
-          a[u] = M[(size_t)c * ld + j];
-          b[u] = M[(size_t)c * ld + p];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < RBS; ++u) {
-        const int c = c0 + u * THREADS;
-        if (c < ncols && (c < done_lo || c >= kend)) {
-          M[(size_t)c * ld + j] = b[u];
-          M[(size_t)c * ld + p] = a[u];
-        }
-      }
+    int ia = -1, ib = -1;
+    for (int i = 0; i < cnt; ++i) {
+      if (dst[i] == j) ia = i;
+      if (dst[i] == p) ib = i;
     }
+    if (ia < 0) { ia = cnt; dst[cnt] = j; src[cnt] = j; ++cnt; }
+    if (ib < 0) { ib = cnt; dst[cnt] = p; src[cnt] = p; ++cnt; }
+    const int t = src[ia];
+    src[ia] = src[ib];
+    src[ib] = t;
+  }
+  list[0] = cnt;
+}
+
+// The permutation in list (shared memory, complete before the call) on columns
+// c_lo..c_hi-1 of M, staged through stage (stage_elems elements of shared memory):
+// all of a chunk's rows are read before any is written. All threads; returns with
+// the group synchronised.
+template <typename T2>
+__device__ void apply_row_perm(T2* __restrict__ M, size_t ld, int c_lo, int c_hi, const int* __restrict__ list,
+                               T2* __restrict__ stage, int stage_elems) {
+  const int cnt = list[0];
+  if (cnt > 0 && c_hi > c_lo) {
+    const int* dst = list + 1;
+    const int* src = list + 1 + 2 * NB;
+    const int per = max(1, stage_elems / cnt);
+    for (int c0 = c_lo; c0 < c_hi; c0 += per) {
+      const int tot = min(per, c_hi - c0) * cnt;
+#pragma unroll 8
+      for (int e = gtid(); e < tot; e += THREADS) stage[e] = M[(size_t)(c0 + e / cnt) * ld + src[e % cnt]];
+      gsync();
+#pragma unroll 8
+      for (int e = gtid(); e < tot; e += THREADS) M[(size_t)(c0 + e / cnt) * ld + dst[e % cnt]] = stage[e];
+      gsync();
+    }
+  }
+  gsync();
+}
+
+// After cta_lu_panel_sub (sub-panels of SB columns), in LINPACK's order: the
+// panel's swaps on the columns right of it, and on each sub-panel's columns the
+// swaps of the later sub-panels (a sub-panel's own swaps and those before it are
+// already in its columns). The panel's whole permutation is also written to
+// list_out (global memory) for the forward solves. scratch: shared memory of
+// scratch_bytes bytes, of which the last SWAP_LIST_INTS ints hold a list.
+template <typename T2>
+__device__ void cta_panel_swaps_lp(T2* __restrict__ M, int n, int ncols, int k0, int kb, const int* __restrict__ piv,
+                                   int SB, int* __restrict__ list_out, unsigned char* scratch, int scratch_bytes) {
+  const int tid = gtid();
+  const size_t ld = (size_t)n;
+  const int kend = k0 + kb;
+  int* ls = reinterpret_cast<int*>(scratch + scratch_bytes) - SWAP_LIST_INTS;
+  T2* stage = reinterpret_cast<T2*>(scratch);
+  const int elems = (int)((reinterpret_cast<unsigned char*>(ls) - scratch) / sizeof(T2));
+  gsync();
+  if (tid == 0) compose_swaps(piv, k0, kend, ls);
+  gsync();
+  for (int i = tid; i < SWAP_LIST_INTS; i += THREADS) list_out[i] = ls[i];
+  apply_row_perm(M, ld, kend, ncols, ls, stage, elems);
+  for (int q0 = k0; q0 + SB < kend; q0 += SB) {
+    if (tid == 0) compose_swaps(piv, q0 + SB, kend, ls);
     gsync();
+    apply_row_perm(M, ld, q0, q0 + SB, ls, stage, elems);
   }
 }
 
@@ -588,36 +648,6 @@ __device__ __forceinline__ void block_update_row(const T2* __restrict__ M, T2* _
   }
 }
 
-// L y = b, L unit lower (no row swaps here).
-template <typename T2>
-__device__ void cta_fwd_blocked(T2* __restrict__ M, int n, int l, LuSmemT<T2>& sm) {
-  const int tid = gtid(), lane = tid & 31, wid = tid >> 5;
-  const size_t ld = (size_t)n;
-  T2* Y = M + (size_t)n * ld;
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int kb = min(NB, n - k0);
-    for (int e = tid; e < kb * kb; e += THREADS) {
-      const int r = e % kb, c = e / kb;
-      sm.Ls[c * NB + r] = M[(size_t)(k0 + c) * ld + k0 + r];  // Ls[t*NB + i] = L[k0+i][k0+t]
-    }
-    gsync();
-    for (int c = wid; c < l; c += THREADS / 32) {
-      T2* yc = Y + (size_t)c * ld + k0;
-      T2 y = (lane < kb) ? yc[lane] : czero<T2>();
-      for (int t = 0; t < kb - 1; ++t) {
-        T2 yt;
-        yt.x = __shfl_sync(0xffffffffu, y.x, t);
-        yt.y = __shfl_sync(0xffffffffu, y.y, t);
-        if (lane > t && lane < kb) cfms(y, sm.Ls[t * NB + lane], yt);
-      }
-      if (lane < kb) yc[lane] = y;
-      if (lane < kb) sm.Us[lane * US_LD + c] = y;  // solved block rows, [t][c]
-    }
-    gsync();
-    for (int i = k0 + kb + tid; i < n; i += THREADS) block_update_row(M, Y, ld, i, k0, kb, l, sm);
-    gsync();
-  }
-}
 
 // U x = y, U upper with its diagonal.
 template <typename T2>
@@ -653,20 +683,63 @@ __device__ void cta_back_blocked(T2* __restrict__ M, int n, int l, LuSmemT<T2>& 
   }
 }
 
-// perm[i] = original row that ends up in row i after the swaps piv[0..n-1].
-__device__ inline void cta_pivots_to_perm(const int* __restrict__ piv, int* __restrict__ perm, int n) {
-  for (int i = gtid(); i < n; i += THREADS) perm[i] = i;
-  gsync();
-  if (gtid() == 0)
-    for (int k = 0; k < n; ++k) {
-      const int p = piv[k];
-      if (p != k) {
-        const int t = perm[k];
-        perm[k] = perm[p];
-        perm[p] = t;
+// L y = b for the l columns after the n x n block of M, with L from an LU whose
+// row interchanges are in LINPACK's order: before panel p's columns of L, its
+// permutation (lists + p SWAP_LIST_INTS, global memory) is applied to y.
+template <typename T2>
+__device__ void cta_fwd_blocked_lp(T2* __restrict__ M, int n, int l, LuSmemT<T2>& sm, const int* __restrict__ lists) {
+  const int tid = gtid(), lane = tid & 31, wid = tid >> 5;
+  const size_t ld = (size_t)n;
+  T2* Y = M + (size_t)n * ld;
+  constexpr int GU = 4;  // permuted elements per thread and round
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = min(NB, n - k0);
+    {
+      const int* L = lists + (size_t)(k0 / NB) * SWAP_LIST_INTS;
+      const int cnt = L[0];
+      const int* dst = L + 1;
+      const int* src = L + 1 + 2 * NB;
+      // whole columns per round, so that a column's rows are all read before any is written
+      const int per = cnt > 0 ? max(1, GU * THREADS / cnt) : l;
+      for (int c0 = 0; c0 < l && cnt > 0; c0 += per) {
+        const int tot = min(per, l - c0) * cnt;
+        T2 v[GU];
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+          const int e = tid + u * THREADS;
+          if (e < tot) v[u] = Y[(size_t)(c0 + e / cnt) * ld + src[e % cnt]];
+        }
+        gsync();
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+          const int e = tid + u * THREADS;
+          if (e < tot) Y[(size_t)(c0 + e / cnt) * ld + dst[e % cnt]] = v[u];
+        }
+        gsync();
       }
     }
-  gsync();
+    for (int e = tid; e < kb * kb; e += THREADS) {
+      const int r = e % kb, c = e / kb;
+      sm.Ls[c * NB + r] = M[(size_t)(k0 + c) * ld + k0 + r];  // Ls[t*NB + i] = L[k0+i][k0+t]
+    }
+    gsync();
+    for (int c = wid; c < l; c += THREADS / 32) {
+      T2* yc = Y + (size_t)c * ld + k0;
+      T2 y = (lane < kb) ? yc[lane] : czero<T2>();
+      for (int t = 0; t < kb - 1; ++t) {
+        T2 yt;
+        yt.x = __shfl_sync(0xffffffffu, y.x, t);
+        yt.y = __shfl_sync(0xffffffffu, y.y, t);
+        if (lane > t && lane < kb) cfms(y, sm.Ls[t * NB + lane], yt);
+      }
+      if (lane < kb) yc[lane] = y;
+      if (lane < kb) sm.Us[lane * US_LD + c] = y;  // solved block rows, [t][c]
+    }
+    gsync();
+    for (int i = k0 + kb + tid; i < n; i += THREADS) block_update_row(M, Y, ld, i, k0, kb, l, sm);
+    gsync();
+  }
 }
+
 
 }  // namespace lucore

@@ -158,8 +158,9 @@ struct PhaseClock {
 // solves, fallback, waiting for a factored node.
 enum { PH_ASSEMBLE = 0, PH_PANEL = 1, PH_FIRST_SOLVE = 2, PH_RESIDUAL = 3, PH_CORRECTION = 4, PH_FALLBACK = 5,
        PH_SETUP = 6, PH_TRSM = 7, PH_UPDATE = 8, PH_FACTOR_WAIT = 9, PH_REFINE_WAIT = 10,
-       PH_CTA_WALL_NS = 11 };  // the last holds ns of CTA lifetime, not cycles
-static_assert(PH_CTA_WALL_NS < PMCIM_PHASES, "phase slots");
+       PH_CTA_WALL_NS = 11,  // ns of CTA lifetime, not cycles
+       PH_SWAPS = 12 };      // the panel's row interchanges on the columns outside it
+static_assert(PH_SWAPS < PMCIM_PHASES, "phase slots");
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -170,8 +171,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // The FP32 blocked LU of lucore::cta_lu, with the trailing updates on the
 // tensor cores (use_tc, while no wait has run out) or on the FMA pipes.
 // Factor group only: its warps 0-7 are the TMEM lane owners.
-__device__ int cta_lu32(float2* __restrict__ M, int n, int ncols, int* __restrict__ piv, LuSmemT<float2>& sm,
-                        tcu::Ctx& cx, bool use_tc, PhaseClock& pc) {
+__device__ int cta_lu32(float2* __restrict__ M, int n, int ncols, int* __restrict__ piv, int* __restrict__ lists,
+                        LuSmemT<float2>& sm, tcu::Ctx& cx, bool use_tc, PhaseClock& pc) {
   if (gtid() == 0) sm.info_sh = 0;
   gsync();
   for (int k0 = 0; k0 < n; k0 += NB) {
@@ -180,11 +181,20 @@ __device__ int cta_lu32(float2* __restrict__ M, int n, int ncols, int* __restric
     // the panel in shared-memory sub-panels, in the tensor-core stage (idle during the
     // panel), while one sub-panel column fits there; else in global memory
     constexpr int kScratch = tcu::STAGE_BYTES / (int)sizeof(float2);
-    if (n - k0 + NB * 8 + 40 <= kScratch)
-      cta_lu_panel_sub(M, n, ncols, k0, kb, piv, sm, reinterpret_cast<float2*>(cx.stage), kScratch);
-    else
-      cta_lu_panel(M, n, ncols, k0, kb, piv, sm);
-    pc.mark(PH_PANEL);
+    // row interchanges in LINPACK's order (none on the L columns left of the panel);
+    // each panel's permutation goes to lists for the forward solves
+    int* list = lists + (size_t)(k0 / NB) * SWAP_LIST_INTS;
+    if (n - k0 + NB * 8 + 40 <= kScratch) {
+      const int sb = cta_lu_panel_sub(M, n, ncols, k0, kb, piv, sm, reinterpret_cast<float2*>(cx.stage), kScratch);
+      pc.mark(PH_PANEL);
+      cta_panel_swaps_lp(M, n, ncols, k0, kb, piv, sb, list, cx.stage, tcu::STAGE_BYTES);
+      pc.mark(PH_SWAPS);
+    } else {
+      cta_lu_panel(M, n, ncols, k0, kb, piv, sm, k0);
+      if (gtid() == 0) compose_swaps(piv, k0, kend, list);
+      gsync();
+      pc.mark(PH_PANEL);
+    }
     if (kend >= ncols) continue;
     cta_lu_trsm(M, n, ncols, k0, kb, sm);
     pc.mark(PH_TRSM);
@@ -545,7 +555,8 @@ __device__ void factor_group(const NodeArgs& a, MixedSmem& sm, tcu::Ctx& cx, Pha
     }
     pc.mark(PH_ASSEMBLE);
     const int bad_before = sm.tc_bad;
-    const int info = cta_lu32(M32, n, ncols, piv, sm.f.u.lu32, cx, rg.lu_tc != 0, pc);
+    int* lists = reinterpret_cast<int*>(slot + mixed_lists_offset(n, l));
+    const int info = cta_lu32(M32, n, ncols, piv, lists, sm.f.u.lu32, cx, rg.lu_tc != 0, pc);
     if (tid == 0) {
       sl.item = idx;
       sl.info = info;
@@ -595,7 +606,7 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
     const int n = P.n, l = P.l, ncols = n + l;
     const size_t nn = (size_t)n * n, nl = (size_t)n * l;
     double2* R = reinterpret_cast<double2*>(slot + mixed_residual_offset(n, l));
-    int* perm = reinterpret_cast<int*>(slot + mixed_residual_offset(n, l) + nl * sizeof(double2));
+    const int* lists = reinterpret_cast<const int*>(slot + mixed_lists_offset(n, l));
     double2* X = a.X + rg.x_off + (size_t)it.j * nl;
     int info = sl.info;
     bool ok = (info == 0);
@@ -604,7 +615,6 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
     double xm = 0.0;
     if (ok) {
       cta_back_blocked(M32, n, l, sm.r.u.lu32);
-      cta_pivots_to_perm(piv, perm, n);
       for (size_t e = tid; e < nl; e += THREADS) {
         const float2 y = M32[nn + e];
         const double2 x = make_double2((double)y.x, (double)y.y);
@@ -676,14 +686,13 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
           break;
         }
         const double inv = 1.0 / rm;
-        // right-hand side P R / |R|max: the row swaps as one gather
+        // right-hand side R / |R|max; the forward solve applies the row interchanges
         for (size_t e = tid; e < nl; e += THREADS) {
-          const size_t cc = e / n, i = e % n;
-          const double2 rv = R[cc * n + perm[i]];
+          const double2 rv = R[e];
           M32[nn + e] = make_float2((float)(rv.x * inv), (float)(rv.y * inv));
         }
         gsync();
-        cta_fwd_blocked(M32, n, l, sm.r.u.lu32);
+        cta_fwd_blocked_lp(M32, n, l, sm.r.u.lu32, lists);
         cta_back_blocked(M32, n, l, sm.r.u.lu32);
         double dm = 0.0, xmx = 0.0;
         for (size_t e = tid; e < nl; e += THREADS) {
@@ -779,11 +788,12 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_factor_solve_mixed(NodeArgs 
 
 }  // namespace
 
-// Slot layout: [FP32 matrix n x (n + l)] [FP64 residual n x l] [row permutation n],
-// or, after a fallback, the FP64 matrix n x (n + l) over the whole slot.
+// Slot layout: [FP32 matrix n x (n + l)] [FP64 residual n x l] [the panels' row
+// permutations, SWAP_LIST_INTS ints each], or, after a fallback, the FP64 matrix
+// n x (n + l) over the whole slot.
 size_t mixed_slot_bytes(int n, int l) {
   const size_t fp64 = (size_t)n * (n + l) * sizeof(double2);
-  const size_t mixed = mixed_residual_offset(n, l) + (size_t)n * l * sizeof(double2) + (size_t)n * sizeof(int);
+  const size_t mixed = mixed_lists_offset(n, l) + (size_t)((n + NB - 1) / NB) * SWAP_LIST_INTS * sizeof(int);
   const size_t b = fp64 > mixed ? fp64 : mixed;
   return (b + 255) & ~(size_t)255;
 }

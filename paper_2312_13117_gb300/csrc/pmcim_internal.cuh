@@ -257,6 +257,10 @@ int factor_slots_fp64(int n, int l);
 __host__ __device__ inline size_t mixed_residual_offset(int n, int l) {
   return (((size_t)n * (n + l) * 8) + 255) & ~(size_t)255;
 }
+// the LU panels' row permutations (ints), after the FP64 residual
+__host__ __device__ inline size_t mixed_lists_offset(int n, int l) {
+  return (mixed_residual_offset(n, l) + (size_t)n * l * 16 + 255) & ~(size_t)255;
+}
 size_t mixed_slot_bytes(int n, int l);
 
 struct LevelArgs {

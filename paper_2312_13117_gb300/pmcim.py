@@ -59,7 +59,7 @@ class pmcim_batch_item(C.Structure):
 
 
 class pmcim_profile(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8), ("mixed_phase_cycles", C.c_double * 12)]
+    _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8), ("mixed_phase_cycles", C.c_double * 16)]
 
 
 class pmcim_stats(C.Structure):
@@ -190,12 +190,13 @@ def pmcim_profile_read() -> dict:
         # the node kernel runs two thread groups side by side: each phase is given
         # as a share of its own group's clock
         names = ["assemble", "lu_panel", "first_solve", "residual_fp64", "correction_solve", "fp64_fallback",
-                 "node_setup", "lu_trsm", "lu_update", "factor_wait", "refine_wait", "cta_wall"]
-        factor = {0, 1, 2, 6, 7, 8, 9}
+                 "node_setup", "lu_trsm", "lu_update", "factor_wait", "refine_wait", "cta_wall", "lu_swaps",
+                 "unused13", "unused14", "unused15"]
+        factor = {0, 1, 6, 7, 8, 9, 12}
         tot_f = sum(c for i, c in enumerate(cyc) if i in factor) or 1.0
         tot_r = sum(c for i, c in enumerate(cyc) if i not in factor) or 1.0
         share = {nm: c / (tot_f if i in factor else tot_r) for i, (nm, c) in enumerate(zip(names, cyc)) if c > 0}
-        share["lu_fp32"] = sum(share.get(k, 0.0) for k in ("lu_panel", "lu_trsm", "lu_update"))
+        share["lu_fp32"] = sum(share.get(k, 0.0) for k in ("lu_panel", "lu_swaps", "lu_trsm", "lu_update"))
         out["factor_fp32"]["phase_share"] = share
         out["factor_fp32"]["phase_cycles"] = {nm: c for nm, c in zip(names, cyc) if c > 0}
         if wall_ns > 0:

@@ -504,6 +504,44 @@ def test_batch_matches_oracle_per_problem(pm, precision):
         h.close()
 
 
+def _config_batch():
+    """Problems of the batched quadratic workload itself (seeds 427, 1, 25, 23: n = 765, 380,
+    403, 58), one disk each: the first of the grid whose circle lies outside |z| = 0.9
+    (inside it the eigenvalues are dense and the disks split eight levels deep)."""
+    out = []
+    for W in w.batched_quadratics([427, 1, 25, 23]):
+        g = next((i for i, r in enumerate(W.regions) if abs(r.c) - r.r > 0.9), len(W.regions) - 1)
+        out.append((W.problem, [W.regions[g]], W.V))
+    return out
+
+
+@pytest.fixture(scope="module")
+def config_batch_oracle():
+    batch = _config_batch()
+    return batch, [o.pmcimb(prob, regs, V) for (prob, regs, V) in batch]
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "auto"])
+def test_batch_config_sizes_match_oracle(pm, precision, config_batch_oracle):
+    """pmcim_batch_solve on problems of the batched workload up to n = 765 (ragged sizes in
+    one launch): each problem's eigenvalues equal the oracle's, and so do its split and
+    candidate counts."""
+    batch, refs = config_batch_oracle
+    prec = {"tf32x3": pm.PREC_TF32X3_IR, "auto": pm.PREC_AUTO}[precision]
+    handles = [pm.Problem(p.n, p.terms) for (p, _, _) in batch]
+    try:
+        res = pm.batch_solve(handles, [r for (_, r, _) in batch], [V for (_, _, V) in batch],
+                             opt=pm.options(precision=prec))
+    finally:
+        for h in handles:
+            h.close()
+    assert res["stats"]["splits"] == sum(sum(1 for r in ref.records if r.split) for ref in refs)
+    for q, ref in enumerate(refs):
+        got = res["lam"][res["problem_of"] == q]
+        assert len(got) == len(ref.lam), q
+        assert _match_lam(got, ref.lam) <= LAM_TOL, q
+
+
 def test_batch_equals_single_calls(pm):
     """The batched path gives each problem the same eigenvalues as a call of its own."""
     batch = _small_batch(count=4, seed0=2000)

@@ -238,8 +238,8 @@ __device__ __noinline__ int cta_lu_panel_sub(T2* __restrict__ M, int n, int ncol
   for (int p0 = k0; p0 < kend; p0 += SB) {
     const int sb = min(SB, kend - p0);
     const int m = n - p0;
-    // 1. load
-#pragma unroll 4
+    // 1. load (many loads in flight per thread: one round trip per 16 elements)
+#pragma unroll 16
     for (int e = tid; e < m * sb; e += THREADS) {
       const int r = e % m, c = e / m;
       sp[(size_t)c * m + r] = M[(size_t)(p0 + c) * ld + p0 + r];
@@ -379,7 +379,6 @@ __device__ __noinline__ int cta_lu_panel_sub(T2* __restrict__ M, int n, int ncol
   }
   return SB;
 }
-
 
 // ---------------------------------------------------------------------------
 // Row interchanges in LINPACK's order (the precision form's FP32 LU): a panel's

@@ -332,15 +332,16 @@ __device__ inline void update(float2* __restrict__ M, int n, int ncols, int k0, 
       if (t + 2 < T) prefetch_tile(M, ld, n, ncols, k0, kend, r0, t + 2);
       else if (r0 + TM < n && t + 2 - T < T) prefetch_tile(M, ld, n, ncols, k0, kend, r0 + TM, t + 2 - T);
       if (t + 3 == T && r0 + TM < n) prefetch_L(M, ld, n, k0, kend, r0 + TM);
-      // operands of tile t+1: its U12 set was last read by tile t-1's MMAs, complete
-      if (t + 1 < T) stage_U(M, ld, ncols, c0 + TN, k0, kb, bset0 + (b ^ 1) * B_SET);
-      // this tile's C values, loaded while its MMAs run
+      // this tile's C values, loaded while its MMAs run; issued first, so that their
+      // latency overlaps that of the U12 loads below
       float2 cv[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         const int col = c0 + 16 * half + c;
         cv[c] = (row < n && col < ncols) ? M[(size_t)col * ld + row] : make_float2(0.f, 0.f);
       }
+      // operands of tile t+1: its U12 set was last read by tile t-1's MMAs, complete
+      if (t + 1 < T) stage_U(M, ld, ncols, c0 + TN, k0, kb, bset0 + (b ^ 1) * B_SET);
       const bool ok = wait_parity(cx.mbar + b, cx.phase[b], cx.wait_cycles);
       cx.phase[b] ^= 1u;
       if (!ok) atomicExch(cx.bad, 1);

@@ -400,8 +400,8 @@ __device__ void assemble_fp64(const NodeCtx& cx, double2* __restrict__ T, float2
 // (the LU only has to approximate T(z_j) to FP32 accuracy; the refinement
 // residuals use the FP64 coefficients). It keeps the factor group off the FP64
 // pipe. The flattened element index with eight elements per thread in flight
-// keeps the loads of each term overlapped; the identity terms land on the
-// diagonal (element e with e % (n + 1) == 0) in the same pass.
+// keeps the loads of each term overlapped; the identity terms are added to the
+// diagonal afterwards (a test per element would cost a 64-bit division).
 __device__ void assemble32(const NodeCtx& cx, float2* __restrict__ M32) {
   const ProblemDev& P = cx.P;
   const int n = P.n;
@@ -411,10 +411,7 @@ __device__ void assemble32(const NodeCtx& cx, float2* __restrict__ M32) {
   for (size_t e0 = gtid(); e0 < nn; e0 += (size_t)U * THREADS) {
     float2 v[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const size_t e = e0 + (size_t)u * THREADS;
-      v[u] = (e < nn && e % (size_t)(n + 1) == 0) ? fid : make_float2(0.f, 0.f);
-    }
+    for (int u = 0; u < U; ++u) v[u] = make_float2(0.f, 0.f);
     for (int k = 0; k < P.K; ++k) {
       const TermDesc& t = P.term[k];
       if (!t.dense) continue;
@@ -436,6 +433,14 @@ __device__ void assemble32(const NodeCtx& cx, float2* __restrict__ M32) {
     for (int u = 0; u < U; ++u) {
       const size_t e = e0 + (size_t)u * THREADS;
       if (e < nn) M32[e] = v[u];
+    }
+  }
+  if (fid.x != 0.f || fid.y != 0.f) {
+    gsync();
+    for (int i = gtid(); i < n; i += THREADS) {
+      float2& d = M32[(size_t)i * n + i];
+      d.x += fid.x;
+      d.y += fid.y;
     }
   }
 }

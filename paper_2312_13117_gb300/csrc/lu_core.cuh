@@ -480,12 +480,24 @@ __device__ void cta_lu_trsm(T2* __restrict__ M, int n, int ncols, int k0, int kb
     // a warp takes CW columns at a time, lane i holds row k0+i of each (NB == warp
     // size); the CW substitutions are independent, so their shuffle chains overlap
     constexpr int CW = 4;
+    constexpr int STRIDE = (THREADS / 32) * CW;
     const int lane = tid & 31, wid = tid >> 5;
-    for (int c0 = kend + wid * CW; c0 < ncols; c0 += (THREADS / 32) * CW) {
+    // the loads of a warp's next column group are issued before this group's
+    // substitution, so that their latency overlaps it
+    T2 xn[CW];
+#pragma unroll
+    for (int q = 0; q < CW; ++q) {
+      const int c = kend + wid * CW + q;
+      xn[q] = (lane < kb && c < ncols) ? M[(size_t)c * ld + k0 + lane] : czero<T2>();
+    }
+    for (int c0 = kend + wid * CW; c0 < ncols; c0 += STRIDE) {
       T2 x[CW];
 #pragma unroll
-      for (int q = 0; q < CW; ++q)
-        x[q] = (lane < kb && c0 + q < ncols) ? M[(size_t)(c0 + q) * ld + k0 + lane] : czero<T2>();
+      for (int q = 0; q < CW; ++q) {
+        x[q] = xn[q];
+        const int c = c0 + STRIDE + q;
+        xn[q] = (lane < kb && c < ncols) ? M[(size_t)c * ld + k0 + lane] : czero<T2>();
+      }
       for (int t = 0; t < kb - 1; ++t) {
         const T2 lt = sm.Ls[t * NB + lane];
 #pragma unroll

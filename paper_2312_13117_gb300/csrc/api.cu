@@ -244,6 +244,7 @@ struct Workspace {
   DevBuf iprobs, iregions, iitems, iX, iinfo, icounters, ibord, ioffs;
   DevBuf ysl;                        // per slot: digits of f_k X for the tensor-core residual
   DevBuf rz, rX, rR, rstat, rysl;    // pmcim_residual: points, solutions, residuals, status, scratch
+  DevBuf cW, cidx, cgram, gpart;     // certificates from coefficient products: W, index arrays, Gram data
   // the library's own stream: graphs cannot be captured on the legacy default stream
   cudaStream_t stream = nullptr;
   cudaEvent_t ordered = nullptr;
@@ -257,7 +258,7 @@ struct Workspace {
                    &bp, &blam, &bvecs, &bkept, &bstatus, &vlam, &vprob, &voff, &vsig, &vacc, &vwork,
                    &vvec, &vpiv, &gitems, &gdst, &gperm, &ind3, &feats, &sprob, &sparams, &sscratch, &Xkeep,
                    &citems, &vout, &Cm, &iprobs, &iregions, &iitems, &iX, &iinfo, &icounters, &ibord, &ioffs, &ysl, &rz,
-                   &rX, &rR, &rstat, &rysl};
+                   &rX, &rR, &rstat, &rysl, &cW, &cidx, &cgram, &gpart};
     for (DevBuf* x : b) x->release();
   }
 };
@@ -271,6 +272,9 @@ struct pmcim_problem_s {
   // the first call that refines with residuals on the tensor cores
   DevBuf dig, dexp;
   bool dig_ok = false;
+  // Gram data of the dense coefficients for the certificates (made on first use)
+  DevBuf gram;
+  bool gram_ok = false;
   int device = 0;
   DevBuf V;  // probe block of the current call
   Workspace ws;
@@ -1116,6 +1120,10 @@ int run_verify(Call& c, const std::vector<double2>& lam, const std::vector<int>&
 }
 
 // Certificate sigma_min(T(lambda)) <= ||T(lambda) v|| with the gathered unit eigenvectors.
+// For problems with 1 to gram_max_dense() dense terms the products A_d v_i of all the
+// call's values of a problem are formed at once (each A_d read once) and the norms
+// ||T(lambda)||_F come from the coefficients' Gram data; otherwise one CTA per value
+// forms T(lambda) element by element.
 int run_certify(Call& c, const EigOut& e, std::vector<double>* cert, std::vector<uint8_t>* ok) {
   Workspace& ws = *c.ws;
   cudaStream_t s = c.s;
@@ -1143,8 +1151,58 @@ int run_certify(Call& c, const EigOut& e, std::vector<double>* cert, std::vector
   va.tol_verify = c.opt->tol_verify;
   va.sigma = ws.vsig.as<double>();
   va.accept = ws.vacc.as<uint8_t>();
+  bool products = true;
+  for (const Group& g : c.groups) products = products && g.h->n_dense >= 1 && g.h->n_dense <= gram_max_dense();
   prof_begin(PMCIM_K_VERIFY, s);
-  CU(launch_certify(va, s));
+  if (products) {
+    const size_t G = c.groups.size(), ge = gram_entries();
+    // each problem's values in call order: W columns, vector offsets
+    std::vector<std::vector<int>> of(G);
+    for (int i = 0; i < m; ++i) of[e.prob[i]].push_back(i);
+    std::vector<int64_t> w_col(m), order_off;
+    std::vector<int32_t> w_m(m);
+    std::vector<size_t> w_base(G), v_base(G);
+    size_t wt = 0;
+    for (size_t q = 0; q < G; ++q) {
+      w_base[q] = wt;
+      v_base[q] = order_off.size();
+      const int mq = (int)of[q].size(), nq = c.pd[q].n;
+      for (int k = 0; k < mq; ++k) {
+        const int i = of[q][k];
+        w_col[i] = (int64_t)(wt + (size_t)k * nq);
+        w_m[i] = mq;
+        order_off.push_back(e.vec_off[i]);
+      }
+      wt += (size_t)c.groups[q].h->n_dense * nq * mq;
+    }
+    CU(ws.cW.ensure(std::max<size_t>(1, wt) * sizeof(double2)));
+    CU(ws.cidx.ensure((size_t)m * (2 * sizeof(int64_t) + sizeof(int32_t))));
+    CU(ws.cgram.ensure(G * ge * sizeof(double2)));
+    int64_t* d_order = ws.cidx.as<int64_t>();
+    int64_t* d_wcol = d_order + m;
+    int32_t* d_wm = reinterpret_cast<int32_t*>(d_wcol + m);
+    CU(cudaMemcpyAsync(d_order, order_off.data(), m * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(d_wcol, w_col.data(), m * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(d_wm, w_m.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    for (size_t q = 0; q < G; ++q) {
+      pmcim_problem h = c.groups[q].h;
+      const ProblemDev* pq = ws.probs.as<ProblemDev>() + q;
+      if (!h->gram_ok) {
+        CU(h->gram.ensure(ge * sizeof(double2)));
+        CU(ws.gpart.ensure(gram_partial_count() * ge * sizeof(double2)));
+        CU(launch_gram(pq, ws.gpart.as<double2>(), h->gram.as<double2>(), s));
+        h->gram_ok = true;
+      }
+      CU(cudaMemcpyAsync(ws.cgram.as<double2>() + q * ge, h->gram.p, ge * sizeof(double2),
+                         cudaMemcpyDeviceToDevice, s));
+      if (!of[q].empty())
+        CU(launch_apply_dense(pq, c.pd[q].n, h->n_dense, ws.gdst.as<double2>(), d_order + v_base[q],
+                              (int)of[q].size(), ws.cW.as<double2>() + w_base[q], s));
+    }
+    CU(launch_certify_products(va, ws.cW.as<double2>(), d_wcol, d_wm, ws.cgram.as<double2>(), s));
+  } else {
+    CU(launch_certify(va, s));
+  }
   prof_end(PMCIM_K_VERIFY, s);
   CU(cudaMemcpyAsync(cert->data(), ws.vsig.p, m * sizeof(double), cudaMemcpyDeviceToHost, s));
   CU(cudaMemcpyAsync(ok->data(), ws.vacc.p, m, cudaMemcpyDeviceToHost, s));

@@ -313,6 +313,21 @@ struct ValueArgs {
   int herm;                 // certificate: 1 = ||T(lambda)^H v|| (sigma_min(T^H) = sigma_min(T))
 };
 cudaError_t launch_certify(const ValueArgs& a, cudaStream_t s);
+// Certificates from coefficient products (reduce.cu), for problems with 1 to
+// gram_max_dense() dense terms: launch_gram fills gram_entries() values of a
+// problem's Gram data (partial: gram_partial_count() x gram_entries() scratch);
+// launch_apply_dense forms W_d = A_d [v_1 .. v_m] (n x m per dense term d, the
+// vectors at vecs + vec_off[i]); launch_certify_products then evaluates each
+// value's certificate from its problem's W (column w_col[i], w_m[i] values) and
+// Gram data (gram + prob_of[i] x gram_entries()).
+size_t gram_partial_count();
+size_t gram_entries();
+int gram_max_dense();
+cudaError_t launch_gram(const ProblemDev* prob, double2* partial, double2* gram, cudaStream_t s);
+cudaError_t launch_apply_dense(const ProblemDev* prob, int n, int n_dense, const double2* vecs,
+                               const int64_t* vec_off, int m, double2* W, cudaStream_t s);
+cudaError_t launch_certify_products(const ValueArgs& a, const double2* W, const int64_t* w_col, const int32_t* w_m,
+                                    const double2* gram, cudaStream_t s);
 cudaError_t launch_verify_fp64(const ValueArgs& a, cudaStream_t s);
 
 // learned screen (screen.cu)

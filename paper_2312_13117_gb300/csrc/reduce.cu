@@ -280,7 +280,227 @@ __global__ void __launch_bounds__(RT) k_certify(ValueArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Certificates of many values of one problem from coefficient products: with
+// T(lambda) = sum_d f_d(lambda) A_d + g(lambda) I (d over the dense terms, g the
+// identity terms), T(lambda_i) v_i = sum_d f_d(lambda_i) (A_d v_i) + g(lambda_i) v_i,
+// and the products W_d = A_d [v_1 .. v_m] read each A_d once for all m values
+// instead of once per value. ||T(lambda)||_F^2 comes from the Gram data of the
+// coefficients: sum_{d,e} f_d conj(f_e) <A_d, A_e> + 2 Re(conj(g) sum_d f_d tr A_d)
+// + n |g|^2, with <X, Y> = sum_ij X_ij conj(Y_ij). All in FP64.
+// ---------------------------------------------------------------------------
+constexpr int GT_R = 64, GT_C = 16, GT_K = 32;  // product tile: rows x values, inner chunk
+
+// W[(d m + i) n + row] = (A_d v_i)[row]: grid (row tiles, value tiles, dense terms).
+__global__ void __launch_bounds__(RT) k_apply_dense(const ProblemDev* __restrict__ prob, const double2* __restrict__ vecs,
+                                                    const int64_t* __restrict__ vec_off, int m,
+                                                    double2* __restrict__ W) {
+  __shared__ double2 As[GT_K][GT_R];
+  __shared__ double2 Bs[GT_K][GT_C];
+  __shared__ int mat;
+  const int n = prob->n;
+  const int r0 = blockIdx.x * GT_R, c0 = blockIdx.y * GT_C, d = blockIdx.z;
+  if (threadIdx.x == 0) {
+    int dd = -1;
+    for (int k = 0; k < prob->K; ++k)
+      if (prob->term[k].dense && ++dd == d) mat = prob->term[k].mat_index;
+  }
+  __syncthreads();
+  const double2* A = prob->A + (size_t)mat * n * n;
+  const int tx = threadIdx.x % GT_R, ty = threadIdx.x / GT_R;  // a row, and 4 values
+  double2 acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < n; k0 += GT_K) {
+#pragma unroll
+    for (int u = 0; u < GT_K * GT_R / RT; ++u) {
+      const int e = threadIdx.x + u * RT, k = e / GT_R, r = e % GT_R;
+      As[k][r] = (r0 + r < n && k0 + k < n) ? A[(size_t)(k0 + k) * n + r0 + r] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < GT_K * GT_C / RT; ++u) {
+      const int e = threadIdx.x + u * RT, c = e / GT_K, k = e % GT_K;
+      Bs[k][c] = (c0 + c < m && k0 + k < n) ? vecs[vec_off[c0 + c] + k0 + k] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < GT_K; ++k) {
+      const double2 av = As[k][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cfma(acc[q], av, Bs[k][4 * ty + q]);
+    }
+    __syncthreads();
+  }
+  if (r0 + tx < n)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (c0 + 4 * ty + q < m) W[((size_t)d * m + c0 + 4 * ty + q) * n + r0 + tx] = acc[q];
+}
+
+// Gram data of one problem's dense coefficients, first pass: per CTA, the partial
+// sums of <A_d, A_e> (d <= e, at most GRAM_MAX_DENSE dense terms) over its share of
+// the elements, into partial[blockIdx][pair]. The second pass adds them in CTA
+// order (deterministic) and the traces.
+constexpr int GRAM_MAX_DENSE = 4;
+constexpr int GRAM_PAIRS = GRAM_MAX_DENSE * (GRAM_MAX_DENSE + 1) / 2;
+__global__ void __launch_bounds__(RT) k_gram_partial(const ProblemDev* __restrict__ prob, double2* __restrict__ partial) {
+  __shared__ double red[2][RT / 32];
+  __shared__ int mats[GRAM_MAX_DENSE];
+  __shared__ int nd;
+  const int n = prob->n;
+  const size_t nn = (size_t)n * n;
+  if (threadIdx.x == 0) {
+    int dd = 0;
+    for (int k = 0; k < prob->K; ++k)
+      if (prob->term[k].dense && dd < GRAM_MAX_DENSE) mats[dd++] = prob->term[k].mat_index;
+    nd = dd;
+  }
+  __syncthreads();
+  double2 acc[GRAM_PAIRS];
+#pragma unroll
+  for (int q = 0; q < GRAM_PAIRS; ++q) acc[q] = make_double2(0.0, 0.0);
+  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < nn; e += (size_t)gridDim.x * RT) {
+    double2 v[GRAM_MAX_DENSE];
+#pragma unroll
+    for (int d = 0; d < GRAM_MAX_DENSE; ++d) v[d] = d < nd ? prob->A[(size_t)mats[d] * nn + e] : make_double2(0.0, 0.0);
+    int q = 0;
+#pragma unroll
+    for (int d = 0; d < GRAM_MAX_DENSE; ++d)
+#pragma unroll
+      for (int f = d; f < GRAM_MAX_DENSE; ++f, ++q) cfma_conj(acc[q], v[f], v[d]);  // v_d conj(v_f)
+  }
+#pragma unroll
+  for (int q = 0; q < GRAM_PAIRS; ++q) {
+    double x = acc[q].x, y = acc[q].y;
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, o);
+      y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = x; red[1][threadIdx.x >> 5] = y; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sx = 0.0, sy = 0.0;
+      for (int w = 0; w < RT / 32; ++w) { sx += red[0][w]; sy += red[1][w]; }
+      partial[(size_t)blockIdx.x * GRAM_PAIRS + q] = make_double2(sx, sy);
+    }
+  }
+}
+
+// Second pass: gram[pair] = the sum of the partials in CTA order; gram[GRAM_PAIRS + d]
+// = tr A_d.
+__global__ void __launch_bounds__(32) k_gram_final(const ProblemDev* __restrict__ prob,
+                                                   const double2* __restrict__ partial, int parts,
+                                                   double2* __restrict__ gram) {
+  const int n = prob->n;
+  const int q = threadIdx.x;
+  if (q < GRAM_PAIRS) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int b = 0; b < parts; ++b) s = cadd(s, partial[(size_t)b * GRAM_PAIRS + q]);
+    gram[q] = s;
+  }
+  if (q < GRAM_MAX_DENSE) {
+    int dd = -1, mat = -1;
+    for (int k = 0; k < prob->K; ++k)
+      if (prob->term[k].dense && ++dd == q) mat = prob->term[k].mat_index;
+    double2 t = make_double2(0.0, 0.0);
+    if (mat >= 0)
+      for (int i = 0; i < n; ++i) t = cadd(t, prob->A[(size_t)mat * n * n + (size_t)i * n + i]);
+    gram[GRAM_PAIRS + q] = t;
+  }
+}
+
+// Per value (one CTA each): r = sum_d f_d W_d[:, i] + g v_i, the certificate ||r|| / ||v||,
+// ||T(lambda)||_F from the Gram data, and the acceptance as in k_certify.
+__global__ void __launch_bounds__(RT) k_certify_products(ValueArgs a, const double2* __restrict__ W,
+                                                         const int64_t* __restrict__ w_col,
+                                                         const int32_t* __restrict__ w_m, const double2* gram) {
+  __shared__ ProblemDev P;
+  __shared__ double2 fz[PMCIM_MAX_TERMS];
+  __shared__ double red[2][RT / 32];
+  const int m = blockIdx.x;
+  load_problem(&P, a.probs + a.prob_of[m]);
+  __syncthreads();
+  const int n = P.n;
+  const double2 lam = a.lam[m];
+  const double2* v = a.vecs + a.vec_off[m];
+  if (threadIdx.x < P.K) fz[threadIdx.x] = eval_f(P.term[threadIdx.x], lam);
+  __syncthreads();
+  double2 g = make_double2(0.0, 0.0), fd[GRAM_MAX_DENSE];
+  int nd = 0;
+  for (int k = 0; k < P.K; ++k) {
+    if (P.term[k].dense) {
+      if (nd < GRAM_MAX_DENSE) fd[nd] = fz[k];
+      ++nd;
+    } else {
+      cfma(g, fz[k], P.term[k].id);
+    }
+  }
+  gram += (size_t)a.prob_of[m] * (GRAM_PAIRS + GRAM_MAX_DENSE);  // this value's problem
+  const double2* w0 = W + w_col[m];  // term d's column at w0 + d * w_m[m] * n
+  const size_t dstride = (size_t)w_m[m] * n;
+  double r2 = 0.0, v2 = 0.0;
+  for (int row = threadIdx.x; row < n; row += RT) {
+    const double2 vr = v[row];
+    double2 r = cmul(g, vr);
+    for (int d = 0; d < nd && d < GRAM_MAX_DENSE; ++d) cfma(r, fd[d], w0[(size_t)d * dstride + row]);
+    r2 += cabs2(r);
+    v2 += cabs2(vr);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    r2 += __shfl_down_sync(0xffffffffu, r2, o);
+    v2 += __shfl_down_sync(0xffffffffu, v2, o);
+  }
+  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = r2; red[1][threadIdx.x >> 5] = v2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0, tv = 0.0;
+    for (int k = 0; k < RT / 32; ++k) { tr += red[0][k]; tv += red[1][k]; }
+    // ||T||_F^2 from the Gram data (pairs d <= e in row order)
+    double f2 = (double)n * cabs2(g);
+    int q = 0;
+    for (int d = 0; d < GRAM_MAX_DENSE; ++d)
+      for (int e = d; e < GRAM_MAX_DENSE; ++e, ++q) {
+        if (d >= nd || e >= nd) continue;
+        // f_d conj(f_e) <A_d, A_e>, and for d != e its conjugate partner
+        const double2 t = cmul(cmul(fd[d], cconj(fd[e])), gram[q]);
+        f2 += (d == e) ? t.x : 2.0 * t.x;
+      }
+    double2 sft = make_double2(0.0, 0.0);
+    for (int d = 0; d < nd && d < GRAM_MAX_DENSE; ++d) cfma(sft, fd[d], gram[GRAM_PAIRS + d]);
+    f2 += 2.0 * cmul(cconj(g), sft).x;
+    const double cert = sqrt(tr) / sqrt(tv);
+    a.sigma[m] = cert;
+    a.accept[m] = (cert <= a.tol_verify * fmax(1.0, sqrt(fmax(f2, 0.0)) / sqrt((double)n))) ? 1 : 0;
+  }
+}
+
 }  // namespace
+
+size_t gram_partial_count() { return 256; }
+size_t gram_entries() { return GRAM_PAIRS + GRAM_MAX_DENSE; }
+int gram_max_dense() { return GRAM_MAX_DENSE; }
+
+cudaError_t launch_gram(const ProblemDev* prob, double2* partial, double2* gram, cudaStream_t s) {
+  k_gram_partial<<<(unsigned)gram_partial_count(), RT, 0, s>>>(prob, partial);
+  k_gram_final<<<1, 32, 0, s>>>(prob, partial, (int)gram_partial_count(), gram);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_dense(const ProblemDev* prob, int n, int n_dense, const double2* vecs,
+                               const int64_t* vec_off, int m, double2* W, cudaStream_t s) {
+  if (m <= 0 || n_dense <= 0) return cudaSuccess;
+  dim3 grid((n + GT_R - 1) / GT_R, (m + GT_C - 1) / GT_C, n_dense);
+  k_apply_dense<<<grid, RT, 0, s>>>(prob, vecs, vec_off, m, W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_certify_products(const ValueArgs& a, const double2* W, const int64_t* w_col, const int32_t* w_m,
+                                    const double2* gram, cudaStream_t s) {
+  if (a.m <= 0) return cudaSuccess;
+  k_certify_products<<<a.m, RT, 0, s>>>(a, W, w_col, w_m, gram);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_certify(const ValueArgs& a, cudaStream_t s) {
   if (a.m <= 0) return cudaSuccess;

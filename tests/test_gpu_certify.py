@@ -188,3 +188,31 @@ def test_certify_near_sigma_min_from_beyn_vectors(pm):
         assert acc[i], (z, cert[i], sig[i])
         # the exact step gives sigma_min to about 2e-9 relative here (numpy, FP64)
         assert sig[i] - 1e-12 <= cert[i] <= sig[i] * (1.0 + 1e-6), (z, cert[i], sig[i])
+
+
+def test_certificate_threshold_uses_frobenius_norm(pm):
+    """The acceptance threshold tol_verify * max(1, ||T(lambda)||_F / sqrt(n)), with the
+    Frobenius norm formed from the coefficients' Gram data (two dense terms and an
+    identity term here): with the right singular vector of sigma_min as start, the
+    certificate is sigma_min itself, and a tol_verify 1e-7 above or below
+    sigma_min / max(1, ||T||_F / sqrt(n)) (numpy) must accept or leave the value."""
+    W = w.delay_large(seed=3, n=200, l=4, N=16, nx=1, ny=3)
+    prob = W.problem
+    lam = np.array([0.3 + 0.2j, -1.1 + 2.7j, -2.4 - 4.1j])
+    vecs, thr = [], []
+    for z in lam:
+        T = ref.assemble_T(prob, z)
+        _, sv, vh = np.linalg.svd(T)
+        vecs.append(vh[-1].conj())
+        thr.append(sv[-1] / max(1.0, np.linalg.norm(T) / math.sqrt(prob.n)))
+    vecs, thr = np.stack(vecs, axis=1), np.array(thr)
+    h = pm.Problem(prob.n, prob.terms)
+    try:
+        for i in range(len(lam)):
+            hi = pm.options(precision=pm.PREC_TF32X3_IR, tol_verify=thr[i] * (1 + 1e-7))
+            lo = pm.options(precision=pm.PREC_TF32X3_IR, tol_verify=thr[i] * (1 - 1e-7))
+            _, acc_hi = h.certify(lam[i:i + 1], vecs[:, i:i + 1], opt=hi)
+            _, acc_lo = h.certify(lam[i:i + 1], vecs[:, i:i + 1], opt=lo)
+            assert acc_hi[0] and not acc_lo[0], (lam[i], thr[i])
+    finally:
+        h.close()

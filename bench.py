@@ -544,6 +544,10 @@ def run_paper_quadratic(args, world, rank, local):
     legs = {
         "pmCIMb_fp64": lambda: P.solve(W.regions, W.V, opt=pmcim.options(stream=stream.cuda_stream,
                                                                           indicator_N=16), want_vecs=False),
+        "pmCIMb_fp64_tile32": lambda: P.solve(W.regions, W.V, opt=pmcim.options(
+            stream=stream.cuda_stream, indicator_N=16, fp64_tile=32), want_vecs=False),
+        "pmCIMb_auto": lambda: P.solve(W.regions, W.V, opt=pmcim.options(
+            stream=stream.cuda_stream, precision=pmcim.PREC_AUTO, indicator_N=16), want_vecs=False),
         "pmCIMb_fp32ir": lambda: P.solve(W.regions, W.V, opt=pmcim.options(
             stream=stream.cuda_stream, precision=pmcim.PREC_FP32_IR, indicator_N=16), want_vecs=False),
         "pmCIMa_fp64": lambda: P.pmcima(regs16, W.V, tol_eps=1e-6, opt=pmcim.options(stream=stream.cuda_stream),

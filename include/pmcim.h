@@ -132,6 +132,10 @@ typedef struct {
      digit products accumulated exactly in FP32 and combined in FP64; about the
      accuracy of an FP64 product, see pmcim_residual). 1: on the FP64 pipe. */
   int32_t residual_fp64;
+  /* FP64 node kernel: the trailing update's tile, 32 (32 x 32, less padding on
+     small matrices) or 64 (64 x 64). 0 (default): 64, or under PMCIM_PREC_AUTO
+     the autotuner's choice per (n bucket, l, dense terms), timed up to n = 256. */
+  int32_t fp64_tile;
 } pmcim_options;
 
 /* Statistics of one pmcim_solve call. */

@@ -305,7 +305,8 @@ int call_stream(Workspace& ws, const pmcim_options* opt, cudaStream_t* out) {
 struct Group {
   pmcim_problem h;
   int l;
-  int form;  // PMCIM_PREC_FP64, PMCIM_PREC_FP32_IR or PMCIM_PREC_TF32X3_IR
+  int form;       // PMCIM_PREC_FP64, PMCIM_PREC_FP32_IR or PMCIM_PREC_TF32X3_IR
+  int tile = 64;  // FP64 form: trailing-update tile of the node kernel (32 or 64)
 };
 
 int check_options(const pmcim_options* opt) {
@@ -324,6 +325,8 @@ int check_options(const pmcim_options* opt) {
     return fail(PMCIM_EINVAL, "indicator_N = %d must be 0 or even, 2..4096", opt->indicator_N);
   if (opt->residual_fp64 != 0 && opt->residual_fp64 != 1)
     return fail(PMCIM_EINVAL, "residual_fp64 = %d must be 0 or 1", opt->residual_fp64);
+  if (opt->fp64_tile != 0 && opt->fp64_tile != 32 && opt->fp64_tile != 64)
+    return fail(PMCIM_EINVAL, "fp64_tile = %d must be 0, 32 or 64", opt->fp64_tile);
   if (opt->beyn_K < 0 || opt->beyn_K > PMCIM_MAX_BEYN_K)
     return fail(PMCIM_EINVAL, "beyn_K = %d outside 0..%d", opt->beyn_K, PMCIM_MAX_BEYN_K);
   return PMCIM_OK;
@@ -367,6 +370,7 @@ struct Call {
   std::vector<Group> groups;
   std::vector<ProblemDev> pd;  // host copy of the device problem table
   pmcim_stats st{};
+  int tile_override = 0;       // autotuner probes: the FP64 kernel's tile (0: the groups')
 };
 
 // The coefficient digits of a handle for the tensor-core residuals (ozaki.cuh),
@@ -418,7 +422,12 @@ struct TuneKey {
   bool operator<(const TuneKey& o) const { return std::tie(bucket, l, kd) < std::tie(o.bucket, o.l, o.kd); }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune;
+struct TuneChoice {
+  int form, tile;
+};
+std::map<TuneKey, TuneChoice> g_tune;
+// FP64 node kernels with 32 x 32 trailing tiles are tried up to this n
+constexpr int kTile32MaxN = 256;
 
 int n_bucket(int n) {
   int b = 0;
@@ -453,32 +462,40 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
 
 int tune_forms(Call& c) {
   if (c.opt->precision != PMCIM_PREC_AUTO) {
-    for (Group& g : c.groups) g.form = c.opt->precision;
+    for (Group& g : c.groups) {
+      g.form = c.opt->precision;
+      g.tile = c.opt->fp64_tile ? c.opt->fp64_tile : 64;
+    }
     return PMCIM_OK;
   }
   for (size_t gi = 0; gi < c.groups.size(); ++gi) {
     Group& g = c.groups[gi];
     const TuneKey key{n_bucket(g.h->n), g.l, g.h->n_dense};
-    int decided = -1;
+    TuneChoice decided{-1, 64};
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       auto it = g_tune.find(key);
       if (it != g_tune.end()) decided = it->second;
     }
-    if (decided < 0) {
-      // probe: one disk of 2 x SMs nodes on this problem, both forms, timed with
+    if (decided.form < 0) {
+      // probe: one disk of 2 x SMs nodes on this problem, every candidate, timed with
       // events. It measures arithmetic throughput, so it sits far out (|z| ~ 70),
       // where the leading term dominates T(z) and no node is near an eigenvalue;
       // nodes next to eigenvalues would send the precision form to its FP64
-      // fallback and misrepresent it.
+      // fallback and misrepresent it. Candidates: FP64 with 64 x 64 trailing tiles,
+      // FP64 with 32 x 32 tiles (small n only), and the two precision forms.
       std::vector<HostRegion> probe(1);
       probe[0] = HostRegion{50.0, 50.0, 1.0, 2 * num_sms(), 0, 0, (int)gi};
-      // each form runs once untimed (workspace allocation, first launch), then timed
-      const int forms[3] = {PMCIM_PREC_FP64, PMCIM_PREC_FP32_IR, PMCIM_PREC_TF32X3_IR};
-      double t[3] = {0.0, 0.0, 0.0};
+      // each candidate runs once untimed (workspace allocation, first launch), then timed
+      const TuneChoice cands[4] = {{PMCIM_PREC_FP64, 64}, {PMCIM_PREC_FP64, 32}, {PMCIM_PREC_FP32_IR, 64},
+                                   {PMCIM_PREC_TF32X3_IR, 64}};
+      double t[4] = {0.0, 0.0, 0.0, 0.0};
       const pmcim_stats keep = c.st;
-      for (int f = 0; f < 3; ++f) {
-        std::vector<int> ov(c.groups.size(), forms[f]);
+      int best = -1;
+      for (int f = 0; f < 4; ++f) {
+        if (cands[f].tile == 32 && g.h->n > kTile32MaxN) continue;
+        std::vector<int> ov(c.groups.size(), cands[f].form);
+        c.tile_override = cands[f].tile;
         cudaEvent_t a, b;
         CU(cudaEventCreate(&a));
         CU(cudaEventCreate(&b));
@@ -493,18 +510,18 @@ int tune_forms(Call& c) {
         t[f] = ms;
         cudaEventDestroy(a);
         cudaEventDestroy(b);
+        if (best < 0 || t[f] < t[best]) best = f;
       }
+      c.tile_override = 0;
       c.st = keep;  // probe work is not part of the call's statistics
-      int best = 0;
-      for (int f = 1; f < 3; ++f)
-        if (t[f] < t[best]) best = f;
-      decided = forms[best];
+      decided = cands[best];
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tune[key] = decided;
     }
-    g.form = decided;
-    if (decided == PMCIM_PREC_FP64) c.st.tuned_fp64 += 1;
-    else if (decided == PMCIM_PREC_FP32_IR) c.st.tuned_mixed += 1;
+    g.form = decided.form;
+    g.tile = c.opt->fp64_tile ? c.opt->fp64_tile : decided.tile;
+    if (decided.form == PMCIM_PREC_FP64) c.st.tuned_fp64 += 1;
+    else if (decided.form == PMCIM_PREC_FP32_IR) c.st.tuned_mixed += 1;
     else c.st.tuned_tc += 1;
   }
   return PMCIM_OK;
@@ -671,6 +688,18 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
   CU(cudaMemcpyAsync(ws.items.p, items.data(), items.size() * sizeof(NodeItem), cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(ws.regions.p, rd.data(), R * sizeof(RegionDev), cudaMemcpyHostToDevice, s));
 
+  // the FP64 kernel's trailing tile: 32 when every FP64-form problem of the level was
+  // tuned to it (or an autotuner probe asks for it), else 64
+  int fp64_tile = c.tile_override;
+  if (!fp64_tile) {
+    bool any = false, all32 = true;
+    for (int g = 0; g < R; ++g)
+      if (form_of(regs[g].prob) == PMCIM_PREC_FP64) {
+        any = true;
+        all32 = all32 && c.groups[regs[g].prob].tile == 32;
+      }
+    fp64_tile = (any && all32) ? 32 : 64;
+  }
   // ---- factorisation workspaces, one slot per resident CTA ----
   const int sms = num_sms();
   int slots64 = 0, slots32 = 0;
@@ -766,6 +795,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
       if (wv.n64) {
         na.items = ws.items.as<NodeItem>() + wv.items64_off;
         na.n_items = (int)wv.n64;
+        na.fp64_tile = fp64_tile;
         na.counter = ws.counters.as<int>() + 3 * wi;
         na.work = ws.work64.as<char>();
         na.slot_bytes = slot64;
@@ -1428,7 +1458,8 @@ int run_screen(Call& c, const std::vector<HostRegion>& top, std::vector<uint8_t>
   if (NS % 16) return fail(PMCIM_EINVAL, "screen_N = %d is not a multiple of 16", NS);
   // coarse copies of the groups: same coefficients and probe block, one column
   const size_t G = c.groups.size();
-  for (size_t gi = 0; gi < G; ++gi) c.groups.push_back(Group{c.groups[gi].h, 1, c.groups[gi].form});
+  for (size_t gi = 0; gi < G; ++gi)
+    c.groups.push_back(Group{c.groups[gi].h, 1, c.groups[gi].form, c.groups[gi].tile});
   CHK(upload_problems(c));
   std::vector<HostRegion> coarse = top;
   for (HostRegion& h : coarse) {
@@ -1549,7 +1580,8 @@ int single_call(Call& c, pmcim_problem p, const pmcim_options* opt, int l, const
   c.opt = opt;
   c.ws = &p->ws;
   CHK(call_stream(p->ws, opt, &c.s));
-  c.groups = {Group{p, l, opt->precision == PMCIM_PREC_AUTO ? PMCIM_PREC_FP32_IR : opt->precision}};
+  c.groups = {Group{p, l, opt->precision == PMCIM_PREC_AUTO ? PMCIM_PREC_FP32_IR : opt->precision,
+                     opt->fp64_tile ? opt->fp64_tile : 64}};
   CHK(upload_V(p, l, V, c.s));
   CHK(upload_problems(c));
   return PMCIM_OK;
@@ -1578,6 +1610,7 @@ void pmcim_default_options(pmcim_options* opt) {
   opt->tol_ir = kIrTol;
   opt->beyn_K = 1;
   opt->residual_fp64 = 0;
+  opt->fp64_tile = 0;
 }
 
 const char* pmcim_status_string(int code) {

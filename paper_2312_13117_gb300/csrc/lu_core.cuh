@@ -517,30 +517,35 @@ __device__ void cta_lu_trsm(T2* __restrict__ M, int n, int ncols, int k0, int kb
 }
 
 // Trailing update A22 -= L21 U12 (rows and columns from k0+kb on), FMA pipes.
-template <typename T2>
+// RI x RI register block per thread on a 16 x 16 thread grid: tiles of 16 RI x 16 RI
+// (RI = 4: 64 x 64, the default; RI = 2: 32 x 32, less padding on small matrices,
+// chosen by the autotuner per problem size).
+template <typename T2, int RI = 4>
 __device__ void cta_lu_update_simt(T2* __restrict__ M, int n, int ncols, int k0, int kb, LuSmemT<T2>& sm) {
+  constexpr int TT = 16 * RI;
+  static_assert(TT <= TILE, "the shared tiles are sized for TILE");
   const int tid = gtid();
   const size_t ld = (size_t)n;
   const int kend = k0 + kb;
-  // ---- trailing update A22 -= L21 U12 over TILE x TILE tiles ----
+  // ---- trailing update A22 -= L21 U12 over TT x TT tiles ----
   const int m_rows = n - kend, m_cols = ncols - kend;
-  const int mt = (m_rows + TILE - 1) / TILE, nt = (m_cols + TILE - 1) / TILE;
+  const int mt = (m_rows + TT - 1) / TT, nt = (m_cols + TT - 1) / TT;
   const int tx = tid & 15, ty = tid >> 4;
   for (int ti = 0; ti < mt; ++ti) {
-    const int r0 = kend + ti * TILE;
-    static_assert((NB * TILE) % THREADS == 0, "tile staging mapping");
+    const int r0 = kend + ti * TT;
+    static_assert((NB * TT) % THREADS == 0, "tile staging mapping");
 #pragma unroll
-    for (int u = 0; u < NB * TILE / THREADS; ++u) {  // unrolled: all loads in flight at once
+    for (int u = 0; u < NB * TT / THREADS; ++u) {  // unrolled: all loads in flight at once
       const int e = tid + u * THREADS;
-      int r = e % TILE, kk = e / TILE;
+      int r = e % TT, kk = e / TT;
       T2 v = czero<T2>();
       if (kk < kb && r0 + r < n) v = M[(size_t)(k0 + kk) * ld + r0 + r];
-      sm.Ls[kk * TILE + r] = v;
+      sm.Ls[kk * TT + r] = v;
     }
     for (int tj = 0; tj < nt; ++tj) {
-      const int c0 = kend + tj * TILE;
+      const int c0 = kend + tj * TT;
 #pragma unroll
-      for (int u = 0; u < NB * TILE / THREADS; ++u) {
+      for (int u = 0; u < NB * TT / THREADS; ++u) {
         const int e = tid + u * THREADS;
         int kk = e % NB, c = e / NB;
         T2 v = czero<T2>();
@@ -548,11 +553,11 @@ __device__ void cta_lu_update_simt(T2* __restrict__ M, int n, int ncols, int k0,
         sm.Us[kk * US_LD + c] = v;
       }
       gsync();
-      T2 acc[4][4];
+      T2 acc[RI][RI];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RI; ++i)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < RI; ++q) {
           int r = r0 + tx + 16 * i, c = c0 + ty + 16 * q;
           acc[i][q] = (r < n && c < ncols) ? M[(size_t)c * ld + r] : czero<T2>();
         }
@@ -561,21 +566,21 @@ __device__ void cta_lu_update_simt(T2* __restrict__ M, int n, int ncols, int k0,
       // the multiply instead of running it on padding
       if (r0 + tx < n && c0 + ty < ncols) {
         for (int kk = 0; kk < kb; ++kk) {
-          T2 a[4], b[4];
+          T2 a[RI], b[RI];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = sm.Ls[kk * TILE + tx + 16 * i];
+          for (int i = 0; i < RI; ++i) a[i] = sm.Ls[kk * TT + tx + 16 * i];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) b[q] = sm.Us[kk * US_LD + ty + 16 * q];
+          for (int q = 0; q < RI; ++q) b[q] = sm.Us[kk * US_LD + ty + 16 * q];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < RI; ++i)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) cfms(acc[i][q], a[i], b[q]);
+            for (int q = 0; q < RI; ++q) cfms(acc[i][q], a[i], b[q]);
         }
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RI; ++i)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < RI; ++q) {
           int r = r0 + tx + 16 * i, c = c0 + ty + 16 * q;
           if (r < n && c < ncols) M[(size_t)c * ld + r] = acc[i][q];
         }
@@ -584,7 +589,7 @@ __device__ void cta_lu_update_simt(T2* __restrict__ M, int n, int ncols, int k0,
   }
 }
 
-template <typename T2>
+template <typename T2, int RI = 4>
 __device__ int cta_lu(T2* __restrict__ M, int n, int ncols, int* __restrict__ piv, LuSmemT<T2>& sm) {
   if (gtid() == 0) sm.info_sh = 0;
   gsync();
@@ -595,7 +600,7 @@ __device__ int cta_lu(T2* __restrict__ M, int n, int ncols, int* __restrict__ pi
     if (kend >= ncols) continue;
     cta_lu_trsm(M, n, ncols, k0, kb, sm);
     if (kend >= n) continue;
-    cta_lu_update_simt(M, n, ncols, k0, kb, sm);
+    cta_lu_update_simt<T2, RI>(M, n, ncols, k0, kb, sm);
   }
   gsync();
   return sm.info_sh;

@@ -32,6 +32,8 @@ struct NodeSmem {
   int item;
 };
 
+// RI: the trailing update's register block (4: 64 x 64 tiles; 2: 32 x 32 tiles).
+template <int RI>
 __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_fp64(NodeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   NodeSmem& sm = *reinterpret_cast<NodeSmem*>(smem_raw);
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_fp64(NodeArgs a) {
     for (size_t e = tid; e < (size_t)n * l; e += THREADS) M[nn + e] = P.V[e];
     __syncthreads();
 
-    const int info = cta_lu(M, n, ncols, piv, sm.lu);
+    const int info = cta_lu<double2, RI>(M, n, ncols, piv, sm.lu);
     cta_back_blocked(M, n, l, sm.lu);
 
     double2* Xo = a.X + rg.x_off + (size_t)it.j * n * l;
@@ -255,7 +257,10 @@ int factor_slots_fp64(int n, int l) {
 }
 
 cudaError_t prepare_factor_fp64() {
-  return cudaFuncSetAttribute(k_factor_solve_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_factor_solve_fp64<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(NodeSmem));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_factor_solve_fp64<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(NodeSmem));
 }
 
@@ -265,7 +270,10 @@ cudaError_t launch_factor_solve_fp64(const NodeArgs& a, cudaStream_t s) {
   if (a.n_items <= 0) return cudaSuccess;
   const size_t smem = sizeof(NodeSmem);
   int grid = a.slots < a.n_items ? a.slots : a.n_items;
-  k_factor_solve_fp64<<<grid, THREADS, smem, s>>>(a);
+  if (a.fp64_tile == 32)
+    k_factor_solve_fp64<2><<<grid, THREADS, smem, s>>>(a);
+  else
+    k_factor_solve_fp64<4><<<grid, THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -220,6 +220,7 @@ struct NodeArgs {
   long long tc_wait_cycles;       // mixed kernel: limit of a wait for a tensor-core commit
   long long handoff_wait_cycles;  // mixed kernel: limit of a wait between its thread groups
   const double2* border;          // mixed kernel: the replacement columns of bordered nodes
+  int fp64_tile;                  // FP64 kernel: trailing-update tile, 32 or 64 (0: 64)
 };
 // Limits of the precision-form kernel's bounded waits (clock64 cycles): the
 // defaults, or the values a test set with pmcim_debug_wait_limits.

@@ -50,7 +50,7 @@ class pmcim_options(C.Structure):
                 ("precision", C.c_int32), ("max_ir_sweeps", C.c_int32), ("max_split_depth", C.c_int32),
                 ("beyn_K", C.c_int32), ("cuda_stream", C.c_void_p), ("screen_params", C.c_void_p),
                 ("screen_threshold", C.c_double), ("screen_N", C.c_int32), ("indicator_N", C.c_int32),
-                ("tol_ir", C.c_double), ("residual_fp64", C.c_int32)]
+                ("tol_ir", C.c_double), ("residual_fp64", C.c_int32), ("fp64_tile", C.c_int32)]
 
 
 class pmcim_batch_item(C.Structure):
@@ -244,9 +244,11 @@ _screen_keep = []
 
 def options(tol_ind=0.1, tol_svd=1e-6, tol_verify=1e-6, precision=PREC_FP64, max_ir_sweeps=6,
             max_split_depth=8, stream=None, screen_params=None, screen_threshold=0.0,
-            screen_N=16, tol_ir=None, indicator_N=0, beyn_K=1, residual_fp64=False) -> pmcim_options:
+            screen_N=16, tol_ir=None, indicator_N=0, beyn_K=1, residual_fp64=False,
+            fp64_tile=0) -> pmcim_options:
     o = pmcim_default_options()
     o.residual_fp64 = 1 if residual_fp64 else 0
+    o.fp64_tile = int(fp64_tile)
     o.indicator_N = int(indicator_N)
     o.beyn_K = int(beyn_K)
     o.tol_ind, o.tol_svd, o.tol_verify = tol_ind, tol_svd, tol_verify

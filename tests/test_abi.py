@@ -42,8 +42,8 @@ def test_status_strings_and_defaults(lib):
     assert o.max_split_depth == 8 and o.precision == pmcim.PREC_FP64
     assert o.tol_ir == 1e-11 and o.indicator_N == 0 and o.max_ir_sweeps == 6
     # the binding's struct has the header's size: the last field lands where the library writes it
-    assert ctypes.sizeof(pmcim.pmcim_options) == pmcim.pmcim_options.residual_fp64.offset + 8
-    assert o.residual_fp64 == 0
+    assert ctypes.sizeof(pmcim.pmcim_options) == pmcim.pmcim_options.fp64_tile.offset + 4
+    assert o.residual_fp64 == 0 and o.fp64_tile == 0
     lib.pmcim_status_string.restype = ctypes.c_char_p
     assert lib.pmcim_status_string(-5) == b"output capacity exceeded"
 

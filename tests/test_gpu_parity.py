@@ -59,9 +59,9 @@ def _moment_bound(problem, reg, V, c=4.0):
     return b0, b1, bh
 
 
-def _check_moments(pm, problem, regions, V):
+def _check_moments(pm, problem, regions, V, opt=None):
     P = pm.Problem(problem.n, problem.terms)
-    C0, C1, ph, pa = P.moments(regions, V)
+    C0, C1, ph, pa = P.moments(regions, V, opt=opt)
     for g, reg in enumerate(regions):
         m = o.moments(problem, reg.c, reg.r, reg.N, V)
         b0, b1, bh = _moment_bound(problem, reg, V)
@@ -101,6 +101,28 @@ def test_moments_ragged_sizes(pm, n, l, N):
     V = w.probe_block(rng, n, l)
     regs = [w.Region(complex(0.3, -0.2), 0.9, N), w.Region(complex(-1.1, 0.8), 0.45, N)]
     _check_moments(pm, prob, regs, V)
+
+
+@pytest.mark.parametrize("n,l,N", [(33, 8, 16), (65, 5, 8), (100, 10, 8), (130, 2, 4), (200, 16, 6)])
+def test_moments_fp64_tile32(pm, n, l, N):
+    """The FP64 node kernel with 32 x 32 trailing tiles (option fp64_tile, the autotuner's
+    other FP64 candidate up to n = 256): the same bound against the oracle, across the
+    32-row tile and panel edges."""
+    rng = np.random.default_rng(300 + n)
+    A = [w.complex_gaussian(rng, (n, n)) / math.sqrt(n) for _ in range(3)]
+    prob = w.Problem(n, [(A[d], w.MONOMIAL, d, 0.0) for d in range(3)])
+    V = w.probe_block(rng, n, l)
+    regs = [w.Region(complex(0.3, -0.2), 0.9, N), w.Region(complex(-1.1, 0.8), 0.45, N)]
+    _check_moments(pm, prob, regs, V, opt=pm.options(precision=pm.PREC_FP64, fp64_tile=32))
+
+
+def test_solve_fp64_tile32_quadratic_n64(pm):
+    W = w.quadratic_small()
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    res = P.solve(W.regions, W.V, opt=pm.options(precision=pm.PREC_FP64, fp64_tile=32))
+    ref = o.pmcimb(W.problem, W.regions, W.V)
+    assert _match_lam(res["lam"], ref.lam) <= LAM_TOL
+    P.close()
 
 
 def test_moments_delay_and_identity_terms(pm):

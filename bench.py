@@ -700,6 +700,7 @@ def main():
     opt = pmcim.options(stream=stream.cuda_stream)
     opt_mixed = pmcim.options(stream=stream.cuda_stream, precision=pmcim.PREC_FP32_IR)
     opt_tc = pmcim.options(stream=stream.cuda_stream, precision=pmcim.PREC_TF32X3_IR)
+    opt_bf = pmcim.options(stream=stream.cuda_stream, precision=pmcim.PREC_BF16X3_IR)
     # the same form with its refinement residuals on the FP64 pipe (the tensor-core residual's A/B leg)
     opt_tc64 = pmcim.options(stream=stream.cuda_stream, precision=pmcim.PREC_TF32X3_IR, residual_fp64=True)
     P = pmcim.Problem(n, W.problem.terms)
@@ -751,7 +752,8 @@ def main():
     # trailing updates on the tensor cores or on the FMA pipes, FP64 refinement),
     # both at FP64 accuracy; the other form and plain FP64 are measured on the same
     # disks beside it
-    forms = [("fp64", opt)] if args.no_mixed else [("fp32ir", opt_mixed), ("tf32x3", opt_tc)]
+    forms = ([("fp64", opt)] if args.no_mixed else
+             [("fp32ir", opt_mixed), ("tf32x3", opt_tc), ("bf16x3", opt_bf)])
     if not args.no_mixed and args.fp64_residual_leg:
         forms.append(("tf32x3_fp64res", opt_tc64))
     head_name, head_opt = forms[0]
@@ -773,9 +775,9 @@ def main():
     if not args.no_mixed:
         # the headline is the faster precision form on these disks (same work in both; the
         # max over ranks, so that every rank picks the same one)
-        t_form = {nm: max_over_ranks(runs[nm][0], world) for nm in ("fp32ir", "tf32x3")}
+        t_form = {nm: max_over_ranks(runs[nm][0], world) for nm in ("fp32ir", "tf32x3", "bf16x3")}
         head_name = min(t_form, key=t_form.get)
-        head_opt = opt_mixed if head_name == "fp32ir" else opt_tc
+        head_opt = {"fp32ir": opt_mixed, "tf32x3": opt_tc, "bf16x3": opt_bf}[head_name]
     clk = clocks.window(*runs[head_name][5])  # the headline's timed region
     smax = clk.get("sm_max_mhz") or SM_MAX_MHZ
     peak64 = fp64_peak_tflops(smax)
@@ -875,14 +877,18 @@ def main():
             cb, rbn, kcn = -(-l // 16), -(-n // 128), -(-n // 32)
             res_bf16 = aggm["ir_sweeps"] * k_dense * cb * rbn * kcn * 136 * 2.0 * 128 * 32 * 16
             lu_tf32 = 3.0 * upd * msolves if name == "tf32x3" else 0.0
+            # BF16 3M: 3 real products x 6 part products per complex multiply-add (upd counts 8 flops)
+            lu_bf16 = 4.5 * upd * msolves if name == "bf16x3" else 0.0
             ratio = (2.25 / 1.1)
             t_s = fm["ms"] / 1e3
-            ach = (res_bf16 + lu_tf32 * ratio) / t_s / 1e12 if t_s > 0 else None
+            ach = (res_bf16 + lu_tf32 * ratio + lu_bf16) / t_s / 1e12 if t_s > 0 else None
             roof = {"bound": "tensor",
-                    "kernel": "k_factor_solve_mixed (tensor pipe: 3xTF32 LU trailing updates + BF16 digit "
-                              "products of the refinement residuals)" if name == "tf32x3" else
-                              "k_factor_solve_mixed (tensor pipe: BF16 digit products of the refinement "
-                              "residuals; LU on the FMA pipes)",
+                    "kernel": {"tf32x3": "k_factor_solve_mixed (tensor pipe: 3xTF32 LU trailing updates + BF16 "
+                                         "digit products of the refinement residuals)",
+                               "bf16x3": "k_factor_solve_mixed (tensor pipe: BF16 3M LU trailing updates + BF16 "
+                                         "digit products of the refinement residuals)"}.get(
+                        name, "k_factor_solve_mixed (tensor pipe: BF16 digit products of the refinement "
+                              "residuals; LU on the FMA pipes)"),
                     "achieved": ach, "peak": BF16_SUSTAINED_TFLOPS, "unit": "TFLOP/s (BF16-equivalent)",
                     "frac": (ach / BF16_SUSTAINED_TFLOPS) if ach else None,
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained; TF32 flops x 2.25/1.1",
@@ -892,6 +898,7 @@ def main():
                     "ncu_tensor_pipe_active_pct": MIXED_TENSOR_PIPE_PCT.get(name),
                     "residual_bf16_tflops": res_bf16 / t_s / 1e12 if t_s > 0 else None,
                     "lu_tf32_tflops": lu_tf32 / t_s / 1e12 if t_s > 0 else None,
+                    "lu_bf16_tflops": lu_bf16 / t_s / 1e12 if t_s > 0 else None,
                     "residual_fp64_equivalent_tflops": a64,
                     "fp32_work_tflops": a32,
                     "launches": fm["launches"], "avg_launch_ms": fm["ms"] / max(1, fm["launches"]),
@@ -907,6 +914,9 @@ def main():
                      "tf32x3": "FP32 LU with 3xTF32 complex trailing updates on the tensor cores (tcgen05, TMEM "
                                "accumulators) + FP64-accurate iterative refinement, residuals on the tensor "
                                "cores (exact BF16 digit products)",
+                     "bf16x3": "FP32 LU with BF16 3M complex trailing updates on the tensor cores (each FP32 "
+                               "operand as three BF16 parts) + FP64-accurate iterative refinement, residuals on "
+                               "the tensor cores (exact BF16 digit products)",
                      "tf32x3_fp64res": "FP32 LU with 3xTF32 tensor-core trailing updates + FP64 iterative "
                                        "refinement, residuals on the FP64 pipe (T(z) assembled in FP64)"}[name],
             "value": sum_over_ranks(float(msolves), world) / (tm_max / 1e3), "unit": UNIT,
@@ -934,11 +944,14 @@ def main():
         head = {"form": "plain FP64 LU", "value": sum_over_ranks(float(msolves), world) / (tm_max / 1e3),
                 "unit": UNIT, "ms_per_step": tm_max / args.steps, "eigenvalues_found": mfound,
                 "roofline": None, "kernels": profm, "clocks": clocks.window(*win)}
-    other_name = {"fp32ir": "tf32x3", "tf32x3": "fp32ir"}.get(head_name)
+    other_name = {"fp32ir": "tf32x3", "tf32x3": "fp32ir", "bf16x3": "tf32x3"}.get(head_name)
     other = precision_record(other_name, runs[other_name]) if other_name in runs else None
+    third_name = next((nm for nm in ("fp32ir", "tf32x3", "bf16x3") if nm in runs and nm not in (head_name, other_name)),
+                      None)
+    third = precision_record(third_name, runs[third_name]) if third_name else None
     fp64res = precision_record("tf32x3_fp64res", runs["tf32x3_fp64res"]) if "tf32x3_fp64res" in runs else None
     if plain is not None:
-        for rec in (head, other):
+        for rec in (head, other, third):
             if rec is not None and rec is not plain:
                 rec["speedup_vs_fp64_solves_per_s"] = rec["value"] / plain["value"]
 
@@ -1046,7 +1059,7 @@ def main():
             "speedup_vs_plain_fp64": head.get("speedup_vs_fp64_solves_per_s"),
             "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "kernels": prof, "plain_fp64": plain,
-            "other_precision_form": other, "residual_on_fp64_pipe": fp64res,
+            "other_precision_form": other, "third_precision_form": third, "residual_on_fp64_pipe": fp64res,
             "speedup_tensor_core_residual": (runs["tf32x3_fp64res"][0] / runs["tf32x3"][0]
                                              if "tf32x3_fp64res" in runs else None),
             "clocks": clk,

@@ -81,7 +81,7 @@ typedef struct {
    accuracy when a reduced precision is chosen). */
 #define PMCIM_PREC_FP64 0      /* plain FP64 LU                                  */
 #define PMCIM_PREC_FP32_IR 1   /* FP32 LU + FP64 iterative refinement            */
-#define PMCIM_PREC_AUTO 2      /* per problem, whichever of the three forms solves
+#define PMCIM_PREC_AUTO 2      /* per problem, whichever of the forms solves
                                   nodes fastest on this device, measured on first
                                   use for each (n bucket, l, dense-term count) and
                                   kept for the process; all meet the same accuracy */
@@ -89,6 +89,11 @@ typedef struct {
                                   products on the tensor cores, each FP32 operand
                                   split into two TF32 parts (3 products per real
                                   product, FP32 accumulation), + FP64 refinement  */
+#define PMCIM_PREC_BF16X3_IR 4 /* FP32 LU whose trailing updates are complex
+                                  products in the 3M form (3 real products) on the
+                                  tensor cores, each FP32 operand split into three
+                                  BF16 parts (6 part products per real product,
+                                  FP32 accumulation), + FP64 refinement           */
 
 typedef struct {
   double tol_ind;          /* indicator threshold, paper default 0.1 (Sec. 3.1)        */

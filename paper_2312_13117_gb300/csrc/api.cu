@@ -305,7 +305,7 @@ int call_stream(Workspace& ws, const pmcim_options* opt, cudaStream_t* out) {
 struct Group {
   pmcim_problem h;
   int l;
-  int form;       // PMCIM_PREC_FP64, PMCIM_PREC_FP32_IR or PMCIM_PREC_TF32X3_IR
+  int form;       // PMCIM_PREC_FP64, PMCIM_PREC_FP32_IR, PMCIM_PREC_TF32X3_IR or PMCIM_PREC_BF16X3_IR
   int tile = 64;  // FP64 form: trailing-update tile of the node kernel (32 or 64)
 };
 
@@ -314,7 +314,8 @@ int check_options(const pmcim_options* opt) {
   if (!(opt->tol_ind >= 0.0) || !(opt->tol_svd >= 0.0) || !(opt->tol_verify >= 0.0))
     return fail(PMCIM_EINVAL, "tolerances must be non-negative");
   if (opt->precision != PMCIM_PREC_FP64 && opt->precision != PMCIM_PREC_FP32_IR &&
-      opt->precision != PMCIM_PREC_AUTO && opt->precision != PMCIM_PREC_TF32X3_IR)
+      opt->precision != PMCIM_PREC_AUTO && opt->precision != PMCIM_PREC_TF32X3_IR &&
+      opt->precision != PMCIM_PREC_BF16X3_IR)
     return fail(PMCIM_EINVAL, "unknown precision %d", opt->precision);
   if (opt->max_split_depth < 0 || opt->max_split_depth > 30) return fail(PMCIM_EINVAL, "max_split_depth out of range");
   if (opt->precision != PMCIM_PREC_FP64 && (opt->max_ir_sweeps < 1 || opt->max_ir_sweeps > 10))
@@ -487,12 +488,12 @@ int tune_forms(Call& c) {
       std::vector<HostRegion> probe(1);
       probe[0] = HostRegion{50.0, 50.0, 1.0, 2 * num_sms(), 0, 0, (int)gi};
       // each candidate runs once untimed (workspace allocation, first launch), then timed
-      const TuneChoice cands[4] = {{PMCIM_PREC_FP64, 64}, {PMCIM_PREC_FP64, 32}, {PMCIM_PREC_FP32_IR, 64},
-                                   {PMCIM_PREC_TF32X3_IR, 64}};
-      double t[4] = {0.0, 0.0, 0.0, 0.0};
+      const TuneChoice cands[5] = {{PMCIM_PREC_FP64, 64}, {PMCIM_PREC_FP64, 32}, {PMCIM_PREC_FP32_IR, 64},
+                                   {PMCIM_PREC_TF32X3_IR, 64}, {PMCIM_PREC_BF16X3_IR, 64}};
+      double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
       const pmcim_stats keep = c.st;
       int best = -1;
-      for (int f = 0; f < 4; ++f) {
+      for (int f = 0; f < 5; ++f) {
         if (cands[f].tile == 32 && g.h->n > kTile32MaxN) continue;
         std::vector<int> ov(c.groups.size(), cands[f].form);
         c.tile_override = cands[f].tile;
@@ -557,7 +558,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
     d.prob = h.prob;
     d.node_off = (int32_t)total_nodes;
     d.gate = no_gate ? 0 : ((h.depth > 0 || gate_top) ? 1 : 0);
-    d.lu_tc = form_of(h.prob) == PMCIM_PREC_TF32X3_IR ? 1 : 0;
+    d.lu_tc = form_of(h.prob) == PMCIM_PREC_TF32X3_IR ? 1 : form_of(h.prob) == PMCIM_PREC_BF16X3_IR ? 2 : 0;
     d.c_off = (int64_t)c_tot;
     d.p_off = (int64_t)p_tot;
     d.w_off = (int64_t)w_tot;

@@ -29,6 +29,7 @@
 // node_info: bits 0-23 = 0 or 1 + first zero-pivot column, bits 24-28 = sweeps
 // run, bit 29 = a tensor-core wait ran out, bit 30 = FP64 fallback.
 #include "ozaki.cuh"
+#include "tc_update_bf16.cuh"
 
 namespace {
 
@@ -171,8 +172,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // The FP32 blocked LU of lucore::cta_lu, with the trailing updates on the
 // tensor cores (use_tc, while no wait has run out) or on the FMA pipes.
 // Factor group only: its warps 0-7 are the TMEM lane owners.
+// tc: 0 = trailing updates on the FMA pipes, 1 = 3xTF32 on the tensor cores, 2 = BF16 3M on the tensor cores
 __device__ int cta_lu32(float2* __restrict__ M, int n, int ncols, int* __restrict__ piv, int* __restrict__ lists,
-                        LuSmemT<float2>& sm, tcu::Ctx& cx, bool use_tc, PhaseClock& pc) {
+                        LuSmemT<float2>& sm, tcu::Ctx& cx, int tc, PhaseClock& pc) {
   if (gtid() == 0) sm.info_sh = 0;
   gsync();
   for (int k0 = 0; k0 < n; k0 += NB) {
@@ -199,7 +201,8 @@ __device__ int cta_lu32(float2* __restrict__ M, int n, int ncols, int* __restric
     cta_lu_trsm(M, n, ncols, k0, kb, sm);
     pc.mark(PH_TRSM);
     if (kend >= n) continue;
-    if (use_tc && !*cx.bad) tcu::update(M, n, ncols, k0, kb, cx);
+    if (tc == 2 && !*cx.bad) tcb::update(M, n, ncols, k0, kb, cx);
+    else if (tc == 1 && !*cx.bad) tcu::update(M, n, ncols, k0, kb, cx);
     else cta_lu_update_simt(M, n, ncols, k0, kb, sm);
     pc.mark(PH_UPDATE);
   }
@@ -561,7 +564,7 @@ __device__ void factor_group(const NodeArgs& a, MixedSmem& sm, tcu::Ctx& cx, Pha
     pc.mark(PH_ASSEMBLE);
     const int bad_before = sm.tc_bad;
     int* lists = reinterpret_cast<int*>(slot + mixed_lists_offset(n, l));
-    const int info = cta_lu32(M32, n, ncols, piv, lists, sm.f.u.lu32, cx, rg.lu_tc != 0, pc);
+    const int info = cta_lu32(M32, n, ncols, piv, lists, sm.f.u.lu32, cx, rg.lu_tc, pc);
     if (tid == 0) {
       sl.item = idx;
       sl.info = info;
@@ -608,7 +611,7 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
     RegionDev rg;
     load_node(a, sl.item, c, rg, it);
     const ProblemDev& P = c.P;
-    const int n = P.n, l = P.l, ncols = n + l;
+    const int n = P.n, l = P.l;
     const size_t nn = (size_t)n * n, nl = (size_t)n * l;
     double2* R = reinterpret_cast<double2*>(slot + mixed_residual_offset(n, l));
     const int* lists = reinterpret_cast<const int*>(slot + mixed_lists_offset(n, l));

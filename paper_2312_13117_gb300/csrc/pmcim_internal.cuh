@@ -168,7 +168,8 @@ struct RegionDev {
   int32_t prob;      // index into the problem table
   int32_t node_off;  // index of node 0 in the launch's node_info array
   int32_t gate;      // 1: Beyn runs only when the indicator marks a candidate
-  int32_t lu_tc;     // 1: the precision form's trailing updates run on the tensor cores
+  int32_t lu_tc;     // the precision form's trailing updates: 0 FMA pipes, 1 tensor cores in
+                     // 3xTF32, 2 tensor cores in BF16 3M
   int32_t border;    // 0, or s + 1: the node solves the bordered system of a certificate, T(z)
                      // (T(z)^H when herm) with column s replaced by the column at NodeArgs::border + v_off
   int32_t herm;      // 1: the node's matrix is T(z)^H (precision form: FP64-pipe residuals, t64 set)

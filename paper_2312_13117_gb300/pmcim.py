@@ -22,7 +22,7 @@ STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: 
 
 RS_CANDIDATE, RS_SATURATED, RS_SPLIT, RS_SINGULAR_NODE, RS_IR_FALLBACK, RS_NO_EIG, RS_SCREENED = 1, 2, 4, 8, 16, 32, 64
 F_MONOMIAL, F_EXP_NEG = 0, 1
-PREC_FP64, PREC_FP32_IR, PREC_AUTO, PREC_TF32X3_IR = 0, 1, 2, 3
+PREC_FP64, PREC_FP32_IR, PREC_AUTO, PREC_TF32X3_IR, PREC_BF16X3_IR = 0, 1, 2, 3, 4
 
 EXPORTS = ["pmcim_default_options", "pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments",
            "pmcim_indicator", "pmcim_beyn", "pmcim_verify", "pmcim_solve", "pmcim_status_string",

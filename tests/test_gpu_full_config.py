@@ -95,10 +95,10 @@ def _compare(pm, res, run, disks, tol_ind=0.1, tol_svd=1e-6):
     return err
 
 
-FORMS = {"fp64": "PREC_FP64", "fp32ir": "PREC_FP32_IR", "tf32x3": "PREC_TF32X3_IR"}
+FORMS = {"fp64": "PREC_FP64", "fp32ir": "PREC_FP32_IR", "tf32x3": "PREC_TF32X3_IR", "bf16x3": "PREC_BF16X3_IR"}
 
 
-@pytest.mark.parametrize("form", ["fp64", "fp32ir", "tf32x3"])
+@pytest.mark.parametrize("form", ["fp64", "fp32ir", "tf32x3", "bf16x3"])
 def test_delay_n1024_all_disks(pm, delay, delay_golden, form):
     W = delay
     run = delay_golden["runs"][repr(1e-6)]

@@ -346,11 +346,11 @@ def test_full_size_delay_sampled_regions(pm):
 # a5: precision form (FP32 LU + FP64 refinement) against the FP64 oracle
 # ---------------------------------------------------------------------------
 
-MIXED_FORMS = ["fp32ir", "tf32x3"]
+MIXED_FORMS = ["fp32ir", "tf32x3", "bf16x3"]
 
 
 def _mixed_opt(pm, form="fp32ir", **kw):
-    prec = {"fp32ir": pm.PREC_FP32_IR, "tf32x3": pm.PREC_TF32X3_IR}[form]
+    prec = {"fp32ir": pm.PREC_FP32_IR, "tf32x3": pm.PREC_TF32X3_IR, "bf16x3": pm.PREC_BF16X3_IR}[form]
     return pm.options(precision=prec, **kw)
 
 
@@ -411,7 +411,8 @@ def test_mixed_solve_delay_small(pm, form):
     P.close()
 
 
-def test_tc_moments_ragged_tiles(pm):
+@pytest.mark.parametrize("form", ["tf32x3", "bf16x3"])
+def test_tc_moments_ragged_tiles(pm, form):
     """Tensor-core trailing updates over several 128-row and 32-column tiles with ragged
     edges (n = 291: 3 row tiles at the first panel, the last one 35 rows; n + l = 296
     columns). T(z) = A - zI with a prescribed spectrum: 3 + 2 eigenvalues inside the two
@@ -426,7 +427,7 @@ def test_tc_moments_ragged_tiles(pm):
     prob, _ = w.similarity_linear(np.concatenate([inside, far]), seed=8)
     V = w.probe_block(rng, n, l)
     P = pm.Problem(n, prob.terms)
-    opt = _mixed_opt(pm, "tf32x3")
+    opt = _mixed_opt(pm, form)
     C0, C1, _, _ = P.moments(regs, V, opt=opt)
     for g, reg in enumerate(regs):
         m = o.moments(prob, reg.c, reg.r, reg.N, V)

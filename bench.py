@@ -1052,7 +1052,7 @@ def main():
             "config": {"workload": "delay NEP T(z)=-zI+A0+A1 exp(-z), n=1024, l=16, N=64, "
                                    "Omega=[-3,1]x[-6,6] split 16x48; %d disks per step per GPU" % B,
                        "form": head["form"], "regions_per_step": B, "n": n, "l": l, "N": 64,
-                       "l2": "working set > L2 (304 factorisation slots of 8.5 MB)",
+                       "l2": "working set > L2 (456 factorisation slots of 8.5 MB)",
                        "eigenvalues_found": head["eigenvalues_found"],
                        "lambda_err_max_vs_fp64": lam_err.get("timed_steps_vs_fp64"),
                        "lambda_err_max_vs_oracle": lam_err.get("timed_steps_vs_oracle")},

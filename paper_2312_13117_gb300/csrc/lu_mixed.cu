@@ -21,11 +21,12 @@
 // threads: the factor group (warps 0-7) does steps 1-2 for node k+1 while the
 // refine group (warps 8-15) does steps 3-4 for node k, so the FP64 pipe and
 // the FP32 / tensor pipes of the SM work at the same time. Nodes pass between
-// the groups through two workspace slots per CTA, each guarded by a pair of
-// mbarriers (full: factor -> refine, empty: refine -> factor); every wait on
-// them is bounded and a wait that runs out ends both groups with an error.
-// The trailing updates of step 2 run on the FMA pipes, or, for regions marked
-// lu_tc, as 3xTF32 complex products on the tensor cores (tc_update.cuh).
+// the groups through three workspace slots per CTA (the factor group can run up
+// to two nodes ahead), each guarded by a pair of mbarriers (full: factor ->
+// refine, empty: refine -> factor); every wait on them is bounded and a wait
+// that runs out ends both groups with an error. The trailing updates of step 2
+// run on the FMA pipes, or, for regions marked lu_tc, as complex products on the
+// tensor cores: 3xTF32 (tc_update.cuh) or BF16 3M (tc_update_bf16.cuh).
 // node_info: bits 0-23 = 0 or 1 + first zero-pivot column, bits 24-28 = sweeps
 // run, bit 29 = a tensor-core wait ran out, bit 30 = FP64 fallback.
 #include "ozaki.cuh"
@@ -77,7 +78,7 @@ __device__ __forceinline__ void res_tile_async(double2* dst, const double2* __re
 
 constexpr int GROUPS = 2;                        // factor group, refine group
 constexpr int CTA_THREADS = GROUPS * THREADS;
-constexpr int SLOTS = 2;                         // node slots per CTA
+constexpr int SLOTS = 3;                         // node slots per CTA
 
 // A group's node context.
 struct NodeCtx {

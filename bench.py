@@ -43,10 +43,10 @@ FACTOR_FP64_TRAFFIC_PER_NODE = 28.61e9 / 64
 # DRAM bytes per node of k_factor_solve_mixed, from one ncu capture of a 384-node launch per form
 # (dram__bytes_read.sum + dram__bytes_write.sum); scaled to a launch by its node count. None: no
 # capture of the kernel as it stands
-MIXED_TRAFFIC_PER_NODE = {"fp32ir": None, "tf32x3": (71.532e9 + 44.852e9) / 384, "bf16x3": None,
+MIXED_TRAFFIC_PER_NODE = {"fp32ir": None, "tf32x3": (71.629e9 + 44.950e9) / 384, "bf16x3": None,
                           "tf32x3_fp64res": None}
 # sm__pipe_tensor_cycles_active (% of active cycles) of the same capture of the tensor-core form
-MIXED_TENSOR_PIPE_PCT = {"tf32x3": 8.63}
+MIXED_TENSOR_PIPE_PCT = {"tf32x3": 8.66}
 # FP32 pipe: 128 FFMA / SM / clock (measured 73.3 TFLOP/s at ~2.0 GHz); at the 2.07 GHz maximum:
 FP32_PEAK_TFLOPS = 128 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
 

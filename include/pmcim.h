@@ -159,7 +159,8 @@ typedef struct {
   int32_t tuned_mixed;     /* problems the autotuner ran in PMCIM_PREC_FP32_IR    */
   int32_t screened_out;    /* disks the learned screen skipped                   */
   int32_t screen_solves;   /* coarse node solves spent on the screen             */
-  int32_t tuned_tc;        /* problems the autotuner ran in PMCIM_PREC_TF32X3_IR  */
+  int32_t tuned_tc;        /* problems the autotuner ran in a tensor-core form
+                              (PMCIM_PREC_TF32X3_IR or PMCIM_PREC_BF16X3_IR)      */
   int32_t tc_timeouts;     /* nodes whose tensor-core wait ran out (their LU was
                               finished on the FMA pipes or the node re-solved in
                               FP64; results stay refined)                        */

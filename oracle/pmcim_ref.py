@@ -45,8 +45,10 @@ from typing import List, Sequence
 import numpy as np
 import scipy.linalg as sla
 
+from .bie_ref import HELMHOLTZ_DLP, dlp_matrix
+
 __all__ = [
-    "MONOMIAL", "EXP_NEG", "scalar_f", "assemble_T", "nodes_weights", "solve_nodes",
+    "MONOMIAL", "EXP_NEG", "HELMHOLTZ_DLP", "scalar_f", "assemble_T", "nodes_weights", "solve_nodes",
     "Moments", "moments", "indicator_value", "indicator", "BeynResult", "beyn_extract",
     "square_filter", "normalise_vectors", "sigma_min", "verify", "split4",
     "hankel_moments", "beyn_extract_hankel", "pmcimb", "PmcimbResult", "pmcima", "PmcimaResult", "pmcima_levels", "merge_centres",
@@ -71,10 +73,15 @@ def scalar_f(kind: int, degree: int, tau: float, z: complex) -> complex:
 
 
 def assemble_T(problem, z: complex) -> np.ndarray:
-    """Dense T(z) = sum_k f_k(z) A_k; a scalar A_k stands for A_k * I."""
+    """Dense T(z) = sum_k f_k(z) A_k; a scalar A_k stands for A_k * I. A term of
+    kind HELMHOLTZ_DLP carries a boundary curve instead and adds scale * K_n(z),
+    the double-layer Nystrom matrix of Sec. 4.2 (bie_ref.dlp_matrix)."""
     n = problem.n
     T = np.zeros((n, n), dtype=np.complex128)
     for (A, kind, deg, tau) in problem.terms:
+        if kind == HELMHOLTZ_DLP:
+            T += complex(A.scale) * dlp_matrix(A.samples, z)
+            continue
         fz = scalar_f(kind, deg, tau, z)
         if np.isscalar(A):
             T[np.arange(n), np.arange(n)] += fz * complex(A)

@@ -18,6 +18,9 @@ Usage (from the repository root):
       -> tests/golden/mass_spring_n2048_sample_oracle.json
          (16 disks whose circle holds an eigenvalue and 16 whose circle holds none,
           chosen by a seeded draw; eigenvalue locations from the 2n companion pencil)
+  python tests/golden/make_oracle_golden.py scattering [--workers 7]
+      -> tests/golden/scattering_disk_n256_oracle.json
+         (the 100 disks of the sound-soft disk's scattering-pole problem, Sec. 4.2)
 """
 from __future__ import annotations
 
@@ -49,6 +52,8 @@ def _workload(kind):
         return w.delay_large()
     if kind == "mass_spring_sample":
         return w.mass_spring()
+    if kind == "scattering":
+        return w.scattering_disk()
     raise ValueError(kind)
 
 
@@ -128,7 +133,7 @@ def _sample_disks(W, seed=5, per_class=16):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("workload", choices=["delay", "mass_spring_sample"])
+    ap.add_argument("workload", choices=["delay", "mass_spring_sample", "scattering"])
     ap.add_argument("--workers", type=int, default=max(1, (os.cpu_count() or 2) - 1))
     ap.add_argument("--tol-svd", type=float, nargs="*", default=None)
     ap.add_argument("--out", default=None)
@@ -145,6 +150,11 @@ def main():
         disks = list(range(len(W.regions)))
         out = a.out or os.path.join(HERE, "delay_n1024_oracle.json")
         meta["disks_note"] = "all disks of Omega = [-3,1] x [-6,6] split 16 x 48, x-major order"
+    elif a.workload == "scattering":
+        tols = a.tol_svd or [1e-6]
+        disks = list(range(len(W.regions)))
+        out = a.out or os.path.join(HERE, "scattering_disk_n%d_oracle.json" % W.problem.n)
+        meta["disks_note"] = "all disks of Omega = [0.2,3.2] x [-3.2,-0.2] split 10 x 10, x-major order"
     else:
         tols = a.tol_svd or [1e-6]
         disks, counts, lam_comp = _sample_disks(W)

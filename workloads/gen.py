@@ -5,7 +5,10 @@ A problem is ``Problem(n, terms)`` where every term is ``(A, kind, degree, tau)`
 scalar ``s`` standing for the matrix ``s * I`` (never stored densely);
 ``kind`` is ``MONOMIAL`` (f(z) = z**degree) or ``EXP_NEG`` (f(z) = exp(-tau z)).
 This is the problem class T(z) = sum_k f_k(z) A_k of Sec. 1 with the fixed
-scalar-function set of the hot path.
+scalar-function set of the hot path. A term of kind ``HELMHOLTZ_DLP`` instead
+carries a ``BoundaryCurve`` in place of ``A``: the term is ``scale * K_n(z)``,
+the Nystrom matrix of the 2-D Helmholtz double-layer operator on that closed
+curve at wave number z (the scattering-pole problem of Sec. 4.2).
 
 Regions are disks circumscribing the squares of a uniform grid over a
 rectangle Omega (Sec. 3, circumscribed-disk cover): centre c, radius
@@ -23,14 +26,26 @@ import numpy as np
 
 MONOMIAL = 0
 EXP_NEG = 1
+HELMHOLTZ_DLP = 2
 
 __all__ = [
-    "MONOMIAL", "EXP_NEG", "Problem", "Region", "Workload",
+    "MONOMIAL", "EXP_NEG", "HELMHOLTZ_DLP", "BoundaryCurve", "Problem", "Region", "Workload",
     "complex_gaussian", "probe_block", "grid_regions",
     "quadratic_small", "paper_quadratic", "delay_large", "batched_quadratics", "mass_spring",
     "diagonal_linear", "similarity_linear", "diagonal_delay", "paper_n4_example",
     "diagonal_quadratic", "screen_trace_problems", "config_trace_problems",
+    "circle_curve", "ellipse_curve", "scattering_disk",
 ]
+
+
+@dataclasses.dataclass
+class BoundaryCurve:
+    """A smooth closed curve x(t), t in [0, 2 pi), counter-clockwise, sampled at
+    t_j = 2 pi j / n: ``samples`` is a 6 x n float64 array of the rows
+    x1, x2, x1', x2', x1'', x2'' (derivatives with respect to t). ``scale`` is
+    the complex factor the term multiplies its operator by."""
+    samples: np.ndarray
+    scale: complex = 0.5
 
 
 @dataclasses.dataclass
@@ -201,6 +216,36 @@ def mass_spring(seed: int = 0, n: int = 2048, l: int = 48, N: int = 64,
                        (np.asfortranarray(K.astype(np.complex128)), MONOMIAL, 0, 0.0)])
     return Workload("mass_spring_n%d" % n, prob, grid_regions(-1, 0, 0, 8, nx, ny, N), V,
                     omega=(-1, 0, 0, 8))
+
+
+def circle_curve(n: int, radius: float = 1.0) -> BoundaryCurve:
+    """The circle of the given radius about 0, n samples."""
+    t = 2.0 * np.pi * np.arange(n) / n
+    c, s = np.cos(t), np.sin(t)
+    return BoundaryCurve(np.array([radius * c, radius * s, -radius * s, radius * c,
+                                   -radius * c, -radius * s], dtype=np.float64))
+
+
+def ellipse_curve(n: int, a: float, b: float) -> BoundaryCurve:
+    """The ellipse x = (a cos t, b sin t), n samples."""
+    t = 2.0 * np.pi * np.arange(n) / n
+    c, s = np.cos(t), np.sin(t)
+    return BoundaryCurve(np.array([a * c, b * s, -a * s, b * c, -a * c, -b * s], dtype=np.float64))
+
+
+def scattering_disk(seed: int = 0, n: int = 256, l: int = 8, N: int = 64, m: int = 10,
+                    radius: float = 1.0, omega=(0.2, 3.2, -3.2, -0.2)) -> Workload:
+    """Scattering poles of a sound-soft disk (Sec. 4.2): T(kappa) = (I + K_n(kappa)) / 2,
+    K_n the Nystrom matrix of the double-layer operator on n boundary points.
+    Omega = [0.2, 3.2] x [-3.2, -0.2] split m x m = 10 x 10 (the paper's 100 squares),
+    N nodes per circle, l probes."""
+    rng = np.random.default_rng(seed)
+    V = probe_block(rng, n, l)
+    prob = Problem(n, [(0.5 + 0j, MONOMIAL, 0, 0.0),
+                       (circle_curve(n, radius), HELMHOLTZ_DLP, 0, 0.0)])
+    x0, x1, y0, y1 = omega
+    return Workload("scattering_disk_n%d" % n, prob, grid_regions(x0, x1, y0, y1, m, m, N), V,
+                    omega=tuple(omega))
 
 
 # ----------------------------------------------------------------------------

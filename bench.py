@@ -578,6 +578,118 @@ def run_paper_quadratic(args, world, rank, local):
     return 0
 
 
+def _hankel_zeros(omega, mmax=12):
+    """Zeros of H_m^(1) (0 <= m <= mmax) inside the rectangle: the exact scattering poles of the
+    sound-soft unit disk (Sec. 4.2), by Newton's method on SciPy's Hankel functions."""
+    from scipy import special
+    x0, x1, y0, y1 = omega
+    out = []
+    for m in range(mmax + 1):
+        for a in np.linspace(0.05, x1 + 1.0, 16):
+            for b in np.linspace(y0 - 1.0, -0.02, 16):
+                z = complex(a, b)
+                for _ in range(60):
+                    f, d = special.hankel1(m, z), special.h1vp(m, z)
+                    if not (np.isfinite(f) and np.isfinite(d)) or d == 0:
+                        break
+                    dz = f / d
+                    z -= dz
+                    if abs(dz) < 1e-15 * max(1.0, abs(z)):
+                        if (x0 <= z.real <= x1 and y0 <= z.imag <= y1
+                                and all(abs(z - q) > 1e-8 for mm, q in out if mm == m)):
+                            out.append((m, z))
+                        break
+    return out
+
+
+def scattering_leg(pmcim, stream, steps=3, with_pmcima=False, oracle_sample=False):
+    """The scattering-pole problem of Sec. 4.2: T(kappa) = (I + K_n(kappa)) / 2 on the unit circle,
+    n = 256 Nystrom points, Omega = [0.2, 3.2] x [-3.2, -0.2] in 10 x 10 squares, N = 64, l = 8,
+    FP64 (the only form for boundary-integral terms). Each leg runs once untimed, then `steps`
+    times; the median wall time of the synchronous call is reported. The eigenvalues are compared
+    with the stored oracle run and with the zeros of the Hankel functions in Omega."""
+    import torch
+    import workloads as w
+    W = w.scattering_disk()
+    P = pmcim.Problem(W.problem.n, W.problem.terms)
+    gold = None
+    gpath = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                         "scattering_disk_n256_oracle.json")
+    if os.path.exists(gpath):
+        with open(gpath) as fh:
+            gold = np.array([complex(a, b) for (a, b, _, _) in json.load(fh)["runs"][repr(1e-6)]["lam"]])
+    zeros = np.array([z for m, z in _hankel_zeros(W.omega) for _ in range(2 if m else 1)])
+    regs16 = [w.Region(g.c, g.r, 16) for g in W.regions]
+    cs = stream.cuda_stream
+    legs = {
+        "pmCIMb": lambda: P.solve(W.regions, W.V, want_vecs=False,
+                                  opt=pmcim.options(stream=cs, precision=pmcim.PREC_AUTO)),
+        "pmCIMb_tile64": lambda: P.solve(W.regions, W.V, want_vecs=False,
+                                         opt=pmcim.options(stream=cs, fp64_tile=64)),
+        "pmCIMb_two_pass": lambda: P.solve(W.regions, W.V, want_vecs=False,
+                                           opt=pmcim.options(stream=cs, precision=pmcim.PREC_AUTO, indicator_N=16)),
+    }
+    if with_pmcima:
+        legs["pmCIMa"] = lambda: P.pmcima(regs16, W.V, tol_eps=1e-6, want_vecs=False,
+                                          opt=pmcim.options(stream=cs, precision=pmcim.PREC_AUTO))
+    out = {}
+    for name, fn in legs.items():
+        fn()
+        ts = []
+        for _ in range(max(1, steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        dt = float(np.median(ts))
+        lam = np.asarray(res["lam"])
+        out[name] = {"seconds": dt, "solves": res["stats"]["solves"],
+                     "solves_per_s": res["stats"]["solves"] / dt, "eigenvalues": int(len(lam)),
+                     "max_rel_err_vs_oracle": _max_rel_diff(gold, lam) if gold is not None and name != "pmCIMa"
+                     else None,
+                     "max_rel_err_vs_hankel_zeros": (_max_rel_diff(zeros, lam) if name != "pmCIMa" else
+                                                     _max_rel_diff(np.unique(np.round(zeros, 9)), lam))}
+    # where the time goes (library events on its launch stream), one more run of the first leg
+    pmcim.pmcim_profile_reset()
+    pmcim.pmcim_profile_enable(True)
+    legs["pmCIMb"]()
+    pmcim.pmcim_profile_enable(False)
+    prof = {k: v for k, v in pmcim.pmcim_profile_read().items() if v["launches"]}
+    P.close()
+    summary = {"workload": "sound-soft unit disk, T(kappa) = (I + K_n(kappa))/2, Kress Nystrom, n = 256, "
+                           "Omega = [0.2,3.2] x [-3.2,-0.2] in 10 x 10 squares, N = 64, l = 8, FP64",
+               "legs": out, "kernels_ms": {k: v["ms"] for k, v in prof.items()},
+               "poles_in_omega": int(len(np.unique(np.round(zeros, 9)))),
+               "paper_context_seconds": {"hardware": "MATLAB, 12 workers (Table 1), unknown n; context only",
+                                         "pmCIMb": 12.14, "pmCIMa": 66.20}}
+    if oracle_sample:
+        # the oracle on one disk that holds a pole (64 node solves at n = 256), on the host
+        import oracle as o
+        g = W.regions[6]
+        t0 = time.perf_counter()
+        o.pmcimb(W.problem, [g], W.V, W.tol_ind, W.tol_svd, W.tol_verify)
+        dt = time.perf_counter() - t0
+        summary["cpu_oracle_one_disk"] = {"seconds": dt, "solves_per_s": g.N / dt, "kind": "oracle",
+                                          "sample": "disk 6 (64 node solves + Beyn + verification), one process"}
+    return summary
+
+
+def run_scattering(args, world, rank, local):
+    import torch
+    from paper_2312_13117_gb300 import pmcim
+    if rank != 0:
+        return 0
+    res = scattering_leg(pmcim, torch.cuda.current_stream(), steps=args.steps, with_pmcima=True,
+                         oracle_sample=not args.no_cpu_baseline)
+    lg = res["legs"]["pmCIMb"]
+    print(json.dumps({"metric": "T(z)^{-1} V node solves/s, scattering poles of a sound-soft disk (Sec. 4.2)",
+                      "value": lg["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+                      "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": res["workload"]}, "scattering_poles": res}))
+    return 0
+
+
 def run_full(args, P, W, opt, opt_mixed, opt_tc, world, rank, local):
     """Time to all eigenvalues: one pmCIMb pass over the whole grid per form (opt_tc: the
     precision form with tensor-core trailing updates, opt_mixed: the same on the FMA pipes,
@@ -647,7 +759,10 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the precision-form measurement")
     ap.add_argument("--only-mixed", action="store_true", help="time only the precision forms (profiling runs)")
     ap.add_argument("--mixed-forms", default="fp32ir,tf32x3", help="precision forms --only-mixed times, in order")
-    ap.add_argument("--workload", default="delay", choices=["delay", "batched", "screen", "paper_quadratic"])
+    ap.add_argument("--workload", default="delay",
+                    choices=["delay", "batched", "screen", "paper_quadratic", "scattering"])
+    ap.add_argument("--no-scattering", action="store_true",
+                    help="leave the scattering-pole summary out of the default line")
     ap.add_argument("--trace-problems", type=int, default=2400,
                     help="screen traces: batched-generator problems (and one delay problem per 100 of them)")
     ap.add_argument("--ms-cols", type=int, nargs=1, default=[0], help="first grid column of the mass-spring slice")
@@ -687,6 +802,8 @@ def main():
         return run_screen(args, world, rank, local)
     if args.workload == "paper_quadratic":
         return run_paper_quadratic(args, world, rank, local)
+    if args.workload == "scattering":
+        return run_scattering(args, world, rank, local)
     import workloads as w
 
     W = w.delay_large()
@@ -1041,6 +1158,9 @@ def main():
 
     prof = head["kernels"]
     launches = sum(v["launches"] for v in prof.values())
+    scat = None
+    if rank == 0 and not args.no_scattering:
+        scat = scattering_leg(pmcim, stream, steps=2)
     if rank == 0:
         line = {
             "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1063,7 +1183,7 @@ def main():
             "other_precision_form": other, "third_precision_form": third, "residual_on_fp64_pipe": fp64res,
             "speedup_tensor_core_residual": (runs["tf32x3_fp64res"][0] / runs["tf32x3"][0]
                                              if "tf32x3_fp64res" in runs else None),
-            "clocks": clk,
+            "clocks": clk, "scattering_poles": scat,
         }
         for key in ("tensor", "ir_sweeps_per_node", "ir_fallbacks", "tc_timeouts", "certified", "unverified"):
             if key in head:

@@ -59,9 +59,27 @@ extern "C" {
 /* ---- scalar functions f_k ------------------------------------------------ */
 #define PMCIM_F_MONOMIAL 0 /* f(z) = z^degree                                   */
 #define PMCIM_F_EXP_NEG 1  /* f(z) = exp(-tau z)                                */
+/* A boundary-integral term (the scattering-pole problem of Sec. 4.2): the term
+   is c K_n(z), c = id_re + i id_im, where K_n(z) is the Nystrom matrix of the
+   2-D Helmholtz double-layer operator
+     (K phi)(x) = 2 int_C d/dnu(y) [(i/4) H_0^(1)(z |x - y|)] phi(y) ds(y)
+   on a smooth closed curve C, discretised by Kress's rule for kernels with a
+   logarithmic singularity (R. Kress, Linear Integral Equations, Sec. 12.3) on
+   the n points x(t_j), t_j = 2 pi j / n. The paper's T(z) = (I + K_n(z)) / 2 is
+   the identity term 0.5 I plus this term with c = 0.5. Its coefficient pointer
+   A[k] holds 6 n doubles: the rows x1(t_j), x2(t_j), x1'(t_j), x2'(t_j),
+   x1''(t_j), x2''(t_j), each of n values (derivatives in t, the curve traversed
+   counter-clockwise). n must be even and at least 4; a problem holds at most
+   one such term and runs in PMCIM_PREC_FP64 only. The entries are formed on
+   the device from J_1 and H_1^(1) of complex argument w = z r (ascending series
+   for |w| <= 13, Hankel's expansion above), for Re(z) > 0: relative error at
+   most about 5e-12 where Im(w) <= 0 (the scattering poles lie in Im z < 0) and
+   4e-11 for 0 < Im(w) <= 2; above that the series loses about e^{2 Im w}
+   rounding units to cancellation in H_1^(1) = J_1 + i Y_1. */
+#define PMCIM_F_HELMHOLTZ_DLP 2
 
 typedef struct {
-  int32_t kind;   /* PMCIM_F_MONOMIAL or PMCIM_F_EXP_NEG                        */
+  int32_t kind;   /* PMCIM_F_MONOMIAL, PMCIM_F_EXP_NEG or PMCIM_F_HELMHOLTZ_DLP */
   int32_t degree; /* monomial degree, 0..16                                     */
   double tau;     /* delay, used by PMCIM_F_EXP_NEG                             */
   double id_re;   /* when the coefficient pointer is NULL the term is           */
@@ -178,9 +196,12 @@ void pmcim_default_options(pmcim_options* opt);
 
 /* Create a problem handle for T(z) = sum_{k<K} f_k(z) A_k  (Sec. 1).
    A[k] points to n*n complex values (2*n*n doubles, column-major) or is NULL
-   for the identity term (f[k].id_re + i f[k].id_im) * I. The handle copies the
-   coefficients to the device; the caller may free A afterwards.
-   Errors: EINVAL (n < 1, K < 1, K > 16, bad kind/degree), ENOMEM, ECUDA. */
+   for the identity term (f[k].id_re + i f[k].id_im) * I; for a
+   PMCIM_F_HELMHOLTZ_DLP term it points to the curve's 6 n samples. The handle
+   copies the coefficients to the device; the caller may free A afterwards.
+   Errors: EINVAL (n < 1, K < 1, K > 16, bad kind/degree, a boundary-integral
+   term with odd n, n < 4, a NULL curve, a second such term, or a curve whose
+   samples are not finite or coincide), ENOMEM, ECUDA. */
 int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmcim_fterm* f,
                          pmcim_problem* out);
 int pmcim_problem_destroy(pmcim_problem p);

@@ -267,6 +267,9 @@ struct pmcim_problem_s {
   int n = 0, K = 0, n_dense = 0;
   TermDesc term[PMCIM_MAX_TERMS];
   double2* dA = nullptr;
+  // geometry of the boundary-integral term (bie.cuh), NULL without one; such a
+  // problem has no coefficient matrices for the precision forms and runs in FP64
+  double* dG = nullptr;
   float2* dA32 = nullptr;  // complex64 copy for the FP32 LU's assembly
   // exact BF16 digits of the dense coefficients and their row exponents, made on
   // the first call that refines with residuals on the tensor cores
@@ -308,6 +311,14 @@ struct Group {
   int form;       // PMCIM_PREC_FP64, PMCIM_PREC_FP32_IR, PMCIM_PREC_TF32X3_IR or PMCIM_PREC_BF16X3_IR
   int tile = 64;  // FP64 form: trailing-update tile of the node kernel (32 or 64)
 };
+
+// whether any problem of the call has a boundary-integral term (selects the kernel
+// instantiations that assemble its entries)
+bool any_bie(const std::vector<Group>& groups) {
+  for (const Group& g : groups)
+    if (g.h->dG) return true;
+  return false;
+}
 
 int check_options(const pmcim_options* opt) {
   if (!opt) return fail(PMCIM_EINVAL, "options pointer is NULL");
@@ -405,6 +416,7 @@ int upload_problems(Call& c) {
     d.A32 = g.h->dA32;
     d.Adig = g.h->dig_ok ? g.h->dig.as<unsigned char>() : nullptr;
     d.Aexp = g.h->dig_ok ? g.h->dexp.as<int32_t>() : nullptr;
+    d.bie = g.h->dG;
     d.V = g.h->V.as<double2>();
     for (int k = 0; k < g.h->K; ++k) d.term[k] = g.h->term[k];
   }
@@ -464,6 +476,8 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
 int tune_forms(Call& c) {
   if (c.opt->precision != PMCIM_PREC_AUTO) {
     for (Group& g : c.groups) {
+      if (g.h->dG && c.opt->precision != PMCIM_PREC_FP64)
+        return fail(PMCIM_EINVAL, "a problem with a boundary-integral term runs in PMCIM_PREC_FP64 only");
       g.form = c.opt->precision;
       g.tile = c.opt->fp64_tile ? c.opt->fp64_tile : 64;
     }
@@ -471,6 +485,12 @@ int tune_forms(Call& c) {
   }
   for (size_t gi = 0; gi < c.groups.size(); ++gi) {
     Group& g = c.groups[gi];
+    if (g.h->dG) {  // FP64 only; the smaller trailing tile where it applies
+      g.form = PMCIM_PREC_FP64;
+      g.tile = c.opt->fp64_tile ? c.opt->fp64_tile : (g.h->n <= kTile32MaxN ? 32 : 64);
+      c.st.tuned_fp64 += 1;
+      continue;
+    }
     const TuneKey key{n_bucket(g.h->n), g.l, g.h->n_dense};
     TuneChoice decided{-1, 64};
     {
@@ -775,6 +795,7 @@ int run_level(Call& c, const std::vector<HostRegion>& regs, bool gate_top, bool 
       const Wave& wv = waves[wi];
       NodeArgs na;
       std::memset(&na, 0, sizeof(na));
+      na.bie = any_bie(c.groups) ? 1 : 0;
       na.probs = la.probs;
       na.regions = la.regions;
       na.X = xbuf.as<double2>();
@@ -1120,6 +1141,7 @@ int run_verify(Call& c, const std::vector<double2>& lam, const std::vector<int>&
   CU(cudaMemcpyAsync(ws.vprob.p, pr.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   ValueArgs va;
   std::memset(&va, 0, sizeof(va));
+  va.bie = any_bie(c.groups) ? 1 : 0;
   va.probs = ws.probs.as<ProblemDev>();
   va.prob_of = ws.vprob.as<int32_t>();
   va.lam = ws.vlam.as<double2>();
@@ -1173,6 +1195,7 @@ int run_certify(Call& c, const EigOut& e, std::vector<double>* cert, std::vector
   CU(cudaMemcpyAsync(ws.voff.p, e.vec_off.data(), m * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   ValueArgs va;
   std::memset(&va, 0, sizeof(va));
+  va.bie = any_bie(c.groups) ? 1 : 0;
   va.probs = ws.probs.as<ProblemDev>();
   va.prob_of = ws.vprob.as<int32_t>();
   va.lam = ws.vlam.as<double2>();
@@ -1183,7 +1206,8 @@ int run_certify(Call& c, const EigOut& e, std::vector<double>* cert, std::vector
   va.sigma = ws.vsig.as<double>();
   va.accept = ws.vacc.as<uint8_t>();
   bool products = true;
-  for (const Group& g : c.groups) products = products && g.h->n_dense >= 1 && g.h->n_dense <= gram_max_dense();
+  for (const Group& g : c.groups)
+    products = products && g.h->n_dense >= 1 && g.h->n_dense <= gram_max_dense() && !g.h->dG;
   prof_begin(PMCIM_K_VERIFY, s);
   if (products) {
     const size_t G = c.groups.size(), ge = gram_entries();
@@ -1350,6 +1374,7 @@ int run_bordered_step(Call& c, const std::vector<double2>& lam_in, const std::ve
   CU(cudaMemcpyAsync(d_b_off, b_off.data(), m * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   ValueArgs va;
   std::memset(&va, 0, sizeof(va));
+  va.bie = any_bie(c.groups) ? 1 : 0;
   va.probs = ws.probs.as<ProblemDev>();
   va.prob_of = ws.vprob.as<int32_t>();
   va.lam = ws.vlam.as<double2>();
@@ -1367,6 +1392,7 @@ int run_bordered_step(Call& c, const std::vector<double2>& lam_in, const std::ve
   }
   NodeArgs na;
   std::memset(&na, 0, sizeof(na));
+  na.bie = any_bie(c.groups) ? 1 : 0;
   na.probs = ws.iprobs.as<ProblemDev>();
   na.regions = ws.iregions.as<RegionDev>();
   na.X = ws.iX.as<double2>();
@@ -1528,8 +1554,25 @@ int run_pmcimb(Call& c, const std::vector<HostRegion>& top_in, EigOut* e, Verifi
       idx.push_back((int)i);
     }
   }
-  // a second certificate from the bordered inverse step started at Beyn's vector
+  // a second certificate from the bordered inverse step started at Beyn's vector (it runs
+  // the precision form's node kernel, so values of boundary-integral problems skip it and
+  // go to the full sigma_min below)
   {
+    std::vector<double2> skip_lam;
+    std::vector<int> skip_prob, skip_idx;
+    {
+      std::vector<double2> keep_lam;
+      std::vector<int> keep_prob, keep_idx;
+      for (size_t k = 0; k < idx.size(); ++k) {
+        const bool bie = c.groups[rest_prob[k]].h->dG != nullptr;
+        (bie ? skip_lam : keep_lam).push_back(rest[k]);
+        (bie ? skip_prob : keep_prob).push_back(rest_prob[k]);
+        (bie ? skip_idx : keep_idx).push_back(idx[k]);
+      }
+      rest.swap(keep_lam);
+      rest_prob.swap(keep_prob);
+      idx.swap(keep_idx);
+    }
     std::vector<int64_t> start_off;
     for (int k : idx) start_off.push_back(e->vec_off[k]);
     std::vector<double> cert2;
@@ -1551,6 +1594,9 @@ int run_pmcimb(Call& c, const std::vector<HostRegion>& top_in, EigOut* e, Verifi
     rest.swap(rest2);
     rest_prob.swap(rest2_prob);
     idx.swap(idx2);
+    rest.insert(rest.end(), skip_lam.begin(), skip_lam.end());
+    rest_prob.insert(rest_prob.end(), skip_prob.begin(), skip_prob.end());
+    idx.insert(idx.end(), skip_idx.begin(), skip_idx.end());
   }
   std::vector<double> sig2;
   std::vector<uint8_t> acc2;
@@ -1581,8 +1627,10 @@ int single_call(Call& c, pmcim_problem p, const pmcim_options* opt, int l, const
   c.opt = opt;
   c.ws = &p->ws;
   CHK(call_stream(p->ws, opt, &c.s));
-  c.groups = {Group{p, l, opt->precision == PMCIM_PREC_AUTO ? PMCIM_PREC_FP32_IR : opt->precision,
-                     opt->fp64_tile ? opt->fp64_tile : 64}};
+  if (p->dG && opt->precision != PMCIM_PREC_FP64 && opt->precision != PMCIM_PREC_AUTO)
+    return fail(PMCIM_EINVAL, "a problem with a boundary-integral term runs in PMCIM_PREC_FP64 only");
+  const int form = p->dG ? PMCIM_PREC_FP64 : opt->precision == PMCIM_PREC_AUTO ? PMCIM_PREC_FP32_IR : opt->precision;
+  c.groups = {Group{p, l, form, opt->fp64_tile ? opt->fp64_tile : 64}};
   CHK(upload_V(p, l, V, c.s));
   CHK(upload_problems(c));
   return PMCIM_OK;
@@ -1668,11 +1716,44 @@ int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmc
   pmcim_problem p = new pmcim_problem_s();
   p->n = n;
   p->K = K;
-  int nd = 0;
+  int nd = 0, n_bie = 0;
   for (int k = 0; k < K; ++k) {
-    if (f[k].kind != PMCIM_F_MONOMIAL && f[k].kind != PMCIM_F_EXP_NEG) {
+    if (f[k].kind != PMCIM_F_MONOMIAL && f[k].kind != PMCIM_F_EXP_NEG && f[k].kind != PMCIM_F_HELMHOLTZ_DLP) {
       delete p;
       return fail(PMCIM_EINVAL, "term %d: unknown kind %d", k, f[k].kind);
+    }
+    if (f[k].kind == PMCIM_F_HELMHOLTZ_DLP) {
+      if (!A[k] || ++n_bie > 1) {
+        delete p;
+        return fail(PMCIM_EINVAL, "term %d: a boundary-integral term needs its curve, and one such term at most", k);
+      }
+      TermDesc& t = p->term[k];
+      t.kind = f[k].kind;
+      t.degree = 0;
+      t.tau = 0.0;
+      t.id = make_double2(f[k].id_re, f[k].id_im);
+      t.dense = 0;
+      t.mat_index = -1;
+      // the curve's samples (host or device) -> the device geometry of bie.cuh
+      std::vector<double> smp((size_t)6 * n), G((size_t)6 * n);
+      cudaError_t e = cudaMemcpy(smp.data(), A[k], smp.size() * sizeof(double), cudaMemcpyDefault);
+      if (e != cudaSuccess) {
+        delete p;
+        return fail(PMCIM_ECUDA, "curve copy: %s", cudaGetErrorString(e));
+      }
+      if (!bie::build_geometry(smp.data(), n, G.data())) {
+        delete p;
+        return fail(PMCIM_EINVAL, "term %d: the curve needs an even n >= 4 and finite, distinct samples with "
+                                  "x' != 0", k);
+      }
+      e = cudaMalloc(&p->dG, G.size() * sizeof(double));
+      if (e == cudaSuccess) e = cudaMemcpy(p->dG, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        if (p->dG) cudaFree(p->dG);
+        delete p;
+        return fail(PMCIM_ENOMEM, "curve upload: %s", cudaGetErrorString(e));
+      }
+      continue;
     }
     if (f[k].kind == PMCIM_F_MONOMIAL && (f[k].degree < 0 || f[k].degree > 16)) {
       delete p;
@@ -1692,6 +1773,7 @@ int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmc
   if (nd > 0) {
     cudaError_t e = cudaMalloc(&p->dA, (size_t)nd * nn * sizeof(double2));
     if (e != cudaSuccess) {
+      if (p->dG) cudaFree(p->dG);
       delete p;
       return fail(PMCIM_ENOMEM, "coefficient upload: %s", cudaGetErrorString(e));
     }
@@ -1700,6 +1782,7 @@ int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmc
       e = cudaMemcpy(p->dA + (size_t)p->term[k].mat_index * nn, A[k], nn * sizeof(double2), cudaMemcpyDefault);
       if (e != cudaSuccess) {
         cudaFree(p->dA);
+        if (p->dG) cudaFree(p->dG);
         delete p;
         return fail(PMCIM_ECUDA, "coefficient upload: %s", cudaGetErrorString(e));
       }
@@ -1710,6 +1793,7 @@ int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmc
     if (e != cudaSuccess) {
       cudaFree(p->dA);
       if (p->dA32) cudaFree(p->dA32);
+      if (p->dG) cudaFree(p->dG);
       delete p;
       return fail(PMCIM_ENOMEM, "coefficient copy: %s", cudaGetErrorString(e));
     }
@@ -1723,6 +1807,7 @@ int pmcim_problem_destroy(pmcim_problem p) {
   cudaDeviceSynchronize();
   if (p->dA) cudaFree(p->dA);
   if (p->dA32) cudaFree(p->dA32);
+  if (p->dG) cudaFree(p->dG);
   p->dig.release();
   p->dexp.release();
   p->V.release();
@@ -1795,6 +1880,8 @@ int pmcim_residual(pmcim_problem p, const pmcim_options* opt, int32_t m, const d
   CHK(check_options(opt));
   if (m < 0 || l < 1 || l > PMCIM_MAX_L) return fail(PMCIM_EINVAL, "m = %d or l = %d out of range", m, l);
   if (m > 0 && (!z || !V || !X || !R)) return fail(PMCIM_EINVAL, "NULL buffer");
+  if (p->dG) return fail(PMCIM_EINVAL, "the tensor-core residual needs coefficient matrices; this problem has a "
+                                       "boundary-integral term");
   if (m == 0) return PMCIM_OK;
   Call c;
   c.opt = opt;
@@ -1865,7 +1952,8 @@ int pmcim_certify(pmcim_problem p, const pmcim_options* opt, int32_t m, const do
   c.opt = opt;
   c.ws = &p->ws;
   CHK(call_stream(p->ws, opt, &c.s));
-  c.groups = {Group{p, 1, opt->precision == PMCIM_PREC_AUTO ? PMCIM_PREC_FP32_IR : opt->precision}};
+  c.groups = {Group{p, 1, p->dG ? PMCIM_PREC_FP64
+                                : opt->precision == PMCIM_PREC_AUTO ? PMCIM_PREC_FP32_IR : opt->precision}};
   CHK(upload_problems(c));
   Workspace& ws = p->ws;
   CU(ws.gdst.ensure((size_t)m * n * sizeof(double2)));
@@ -1888,6 +1976,11 @@ int pmcim_certify(pmcim_problem p, const pmcim_options* opt, int32_t m, const do
       off.push_back((int64_t)i * n);
       idx.push_back(i);
     }
+  if (p->dG) {  // the bordered step runs the precision form's node kernel: coefficient problems only
+    rest.clear();
+    off.clear();
+    idx.clear();
+  }
   std::vector<double> sig2;
   std::vector<uint8_t> acc2;
   CHK(run_bordered_step(c, rest, std::vector<int>(rest.size(), 0), ws.gdst.as<double2>(), off, &sig2, &acc2));

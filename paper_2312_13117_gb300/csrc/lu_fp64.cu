@@ -33,7 +33,7 @@ struct NodeSmem {
 };
 
 // RI: the trailing update's register block (4: 64 x 64 tiles; 2: 32 x 32 tiles).
-template <int RI>
+template <int RI, bool BIE>
 __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_fp64(NodeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   NodeSmem& sm = *reinterpret_cast<NodeSmem*>(smem_raw);
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_fp64(NodeArgs a) {
         for (int k = 0; k < P.K; ++k) {
           const TermDesc& t = P.term[k];
           if (t.dense) cfma(v, sm.lu.fz[k], P.A[(size_t)t.mat_index * nn + e]);
-          else if (row == col) cfma(v, sm.lu.fz[k], t.id);
+          else cfma_term<BIE>(v, P, t, sm.lu.fz[k], row, col);
         }
         M[e] = v;
       }
@@ -156,6 +156,7 @@ __device__ double vec_norm(const double2* __restrict__ x, int n, VerifySmem& sm)
   return sqrt(block_sum(s, sm.red));
 }
 
+template <bool BIE>
 __global__ void __launch_bounds__(THREADS, 2) k_verify_fp64(ValueArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   VerifySmem& sm = *reinterpret_cast<VerifySmem*>(smem_raw);
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_verify_fp64(ValueArgs a) {
         for (int k = 0; k < P.K; ++k) {
           const TermDesc& t = P.term[k];
           if (t.dense) cfma(v, sm.lu.fz[k], P.A[(size_t)t.mat_index * nn + e]);
-          else if (row == col) cfma(v, sm.lu.fz[k], t.id);
+          else cfma_term<BIE>(v, P, t, sm.lu.fz[k], row, col);
         }
         M[e] = v;
         fro += cabs2(v);
@@ -257,11 +258,13 @@ int factor_slots_fp64(int n, int l) {
 }
 
 cudaError_t prepare_factor_fp64() {
-  cudaError_t e = cudaFuncSetAttribute(k_factor_solve_fp64<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(NodeSmem));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_factor_solve_fp64<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(NodeSmem));
+  const void* fns[4] = {(const void*)k_factor_solve_fp64<4, false>, (const void*)k_factor_solve_fp64<2, false>,
+                        (const void*)k_factor_solve_fp64<4, true>, (const void*)k_factor_solve_fp64<2, true>};
+  for (const void* f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(NodeSmem));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Launch only; prepare_factor_fp64() must have set the shared-memory limit (it
@@ -270,20 +273,25 @@ cudaError_t launch_factor_solve_fp64(const NodeArgs& a, cudaStream_t s) {
   if (a.n_items <= 0) return cudaSuccess;
   const size_t smem = sizeof(NodeSmem);
   int grid = a.slots < a.n_items ? a.slots : a.n_items;
-  if (a.fp64_tile == 32)
-    k_factor_solve_fp64<2><<<grid, THREADS, smem, s>>>(a);
-  else
-    k_factor_solve_fp64<4><<<grid, THREADS, smem, s>>>(a);
+  if (a.bie) {
+    if (a.fp64_tile == 32) k_factor_solve_fp64<2, true><<<grid, THREADS, smem, s>>>(a);
+    else k_factor_solve_fp64<4, true><<<grid, THREADS, smem, s>>>(a);
+  } else {
+    if (a.fp64_tile == 32) k_factor_solve_fp64<2, false><<<grid, THREADS, smem, s>>>(a);
+    else k_factor_solve_fp64<4, false><<<grid, THREADS, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_verify_fp64(const ValueArgs& a, cudaStream_t s) {
   if (a.m <= 0) return cudaSuccess;
   const size_t smem = sizeof(VerifySmem);
-  cudaError_t e = cudaFuncSetAttribute(k_verify_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const void* fn = a.bie ? (const void*)k_verify_fp64<true> : (const void*)k_verify_fp64<false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = a.slots < a.m ? a.slots : a.m;
-  k_verify_fp64<<<grid, THREADS, smem, s>>>(a);
+  if (a.bie) k_verify_fp64<true><<<grid, THREADS, smem, s>>>(a);
+  else k_verify_fp64<false><<<grid, THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@ struct SmallSmem {
   double2 fz[WARPS][PMCIM_MAX_TERMS];
 };
 
+template <bool BIE>
 __global__ void __launch_bounds__(WARPS * 32) k_factor_solve_small(NodeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmallSmem& sm = *reinterpret_cast<SmallSmem*>(smem_raw);
@@ -55,6 +56,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_factor_solve_small(NodeArgs a) {
         for (int k = 0; k < P.K; ++k) {
           const TermDesc& t = P.term[k];
           if (t.dense) cfma(v, sm.fz[w][k], P.A[(size_t)t.mat_index * nn + e]);
+          else if (BIE && t.kind == PMCIM_F_HELMHOLTZ_DLP)  // T^H: entry (c, lane), conjugated below
+            cfma(v, t.id, bie::dlp_entry(P.bie, n, rg.herm ? c : lane, rg.herm ? lane : c, sm.fz[w][k]));
           else if (c == lane) cfma(v, sm.fz[w][k], t.id);
         }
         if (rg.herm) v.y = -v.y;
@@ -120,7 +123,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_factor_solve_small(NodeArgs a) {
 bool small_kernel_fits(int n, int l) { return n <= SN && l <= SL; }
 
 cudaError_t prepare_factor_small() {
-  return cudaFuncSetAttribute(k_factor_solve_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_factor_solve_small<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(SmallSmem));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_factor_solve_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(SmallSmem));
 }
 
@@ -133,6 +139,7 @@ cudaError_t launch_factor_solve_small(const NodeArgs& a, cudaStream_t s) {
   int grid = 2 * (sms > 0 ? sms : 1);
   const int need = (a.n_items + WARPS - 1) / WARPS;
   if (grid > need) grid = need;
-  k_factor_solve_small<<<grid, WARPS * 32, sizeof(SmallSmem), s>>>(a);
+  if (a.bie) k_factor_solve_small<true><<<grid, WARPS * 32, sizeof(SmallSmem), s>>>(a);
+  else k_factor_solve_small<false><<<grid, WARPS * 32, sizeof(SmallSmem), s>>>(a);
   return cudaGetLastError();
 }

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "../../include/pmcim.h"
+#include "bie.cuh"
 
 #define PMCIM_MAX_TERMS 16
 // ||P f|_N|| at or below this fraction of ||sum_j |w_j| |x_j||| counts as zero
@@ -123,7 +124,9 @@ struct ProblemDesc {
 };
 
 // f_k(z) for one term (Sec. 1 problem class with the fixed scalar-function set).
+// A boundary-integral term's entries depend on z itself: its value is z.
 __device__ __forceinline__ double2 eval_f(const TermDesc& t, double2 z) {
+  if (t.kind == PMCIM_F_HELMHOLTZ_DLP) return z;
   if (t.kind == PMCIM_F_MONOMIAL) {
     double2 p = make_double2(1.0, 0.0);
     for (int d = 0; d < t.degree; ++d) p = cmul(p, z);
@@ -159,8 +162,22 @@ struct ProblemDev {
   // (ozaki.cuh; NULL until made), and the row exponents [dense term][row blocks x 128]
   const unsigned char* Adig;
   const int32_t* Aexp;
+  // geometry of the boundary-integral term (bie.cuh, 6 n doubles), NULL without one
+  const double* bie;
   TermDesc term[PMCIM_MAX_TERMS];
 };
+
+// Entry (row, col) of one non-dense term: the identity term's diagonal, or the
+// boundary-integral term's c K_n(z) entry (fz = z for it). Dense terms are read by
+// the callers from the coefficients. The kernels that assemble T are instantiated
+// twice: BIE = false (no problem of the launch has a boundary-integral term) leaves
+// out the entry's code and its registers.
+template <bool BIE>
+__device__ __forceinline__ void cfma_term(double2& v, const ProblemDev& P, const TermDesc& t, double2 fz, int row,
+                                          int col) {
+  if (BIE && t.kind == PMCIM_F_HELMHOLTZ_DLP) cfma(v, t.id, bie::dlp_entry(P.bie, P.n, row, col, fz));
+  else if (row == col) cfma(v, fz, t.id);
+}
 
 struct RegionDev {
   double cre, cim, r;
@@ -222,6 +239,7 @@ struct NodeArgs {
   long long handoff_wait_cycles;  // mixed kernel: limit of a wait between its thread groups
   const double2* border;          // mixed kernel: the replacement columns of bordered nodes
   int fp64_tile;                  // FP64 kernel: trailing-update tile, 32 or 64 (0: 64)
+  int bie;                        // FP64 and small kernels: a problem has a boundary-integral term
 };
 // Limits of the precision-form kernel's bounded waits (clock64 cycles): the
 // defaults, or the values a test set with pmcim_debug_wait_limits.
@@ -313,6 +331,7 @@ struct ValueArgs {
   int max_n;
   double2* vec_out;         // verify: NULL, or m * max_n: the unit right singular vector for sigma_min
   int herm;                 // certificate: 1 = ||T(lambda)^H v|| (sigma_min(T^H) = sigma_min(T))
+  int bie;                  // a problem has a boundary-integral term (k_certify, k_verify_fp64)
 };
 cudaError_t launch_certify(const ValueArgs& a, cudaStream_t s);
 // Certificates from coefficient products (reduce.cu), for problems with 1 to

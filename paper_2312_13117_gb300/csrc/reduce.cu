@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(RT) k_border_rhs(ValueArgs a, const int64_t* _
 // T(lambda)^H (a.herm), whose smallest singular value is the same. One CTA per
 // value forms T(lambda) element by element (never stored), accumulating
 // r = T v (or T^H v) and ||T(lambda)||_F^2, all in FP64.
+template <bool BIE>
 __global__ void __launch_bounds__(RT) k_certify(ValueArgs a) {
   __shared__ ProblemDev P;
   __shared__ double2 fz[PMCIM_MAX_TERMS];
@@ -256,6 +257,8 @@ __global__ void __launch_bounds__(RT) k_certify(ValueArgs a) {
       for (int k = 0; k < P.K; ++k) {
         const TermDesc& tk = P.term[k];
         if (tk.dense) cfma(t, fz[k], P.A[(size_t)tk.mat_index * nn + e]);
+        else if (BIE && tk.kind == PMCIM_F_HELMHOLTZ_DLP)  // T^H: entry (col, row), conjugated below
+          cfma(t, tk.id, bie::dlp_entry(P.bie, n, a.herm ? col : row, a.herm ? row : col, fz[k]));
         else if (row == col) cfma(t, fz[k], tk.id);
       }
       if (a.herm) t.y = -t.y;
@@ -504,7 +507,8 @@ cudaError_t launch_certify_products(const ValueArgs& a, const double2* W, const 
 
 cudaError_t launch_certify(const ValueArgs& a, cudaStream_t s) {
   if (a.m <= 0) return cudaSuccess;
-  k_certify<<<a.m, RT, 0, s>>>(a);
+  if (a.bie) k_certify<true><<<a.m, RT, 0, s>>>(a);
+  else k_certify<false><<<a.m, RT, 0, s>>>(a);
   return cudaGetLastError();
 }
 

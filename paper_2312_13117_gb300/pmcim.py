@@ -21,7 +21,7 @@ PMCIM_OK = 0
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ECAPACITY", -6: "ENOTSUP"}
 
 RS_CANDIDATE, RS_SATURATED, RS_SPLIT, RS_SINGULAR_NODE, RS_IR_FALLBACK, RS_NO_EIG, RS_SCREENED = 1, 2, 4, 8, 16, 32, 64
-F_MONOMIAL, F_EXP_NEG = 0, 1
+F_MONOMIAL, F_EXP_NEG, F_HELMHOLTZ_DLP = 0, 1, 2
 PREC_FP64, PREC_FP32_IR, PREC_AUTO, PREC_TF32X3_IR, PREC_BF16X3_IR = 0, 1, 2, 3, 4
 
 EXPORTS = ["pmcim_default_options", "pmcim_problem_create", "pmcim_problem_destroy", "pmcim_moments",
@@ -308,7 +308,8 @@ class Problem:
     """Handle for T(z) = sum_k f_k(z) A_k built from ``(A, kind, degree, tau)`` terms.
 
     ``A`` is an n x n complex matrix (NumPy or torch, host or CUDA) or a complex
-    scalar s meaning s * I.
+    scalar s meaning s * I; for kind PMCIM_F_HELMHOLTZ_DLP it is an object with a
+    ``samples`` array (6 x n curve samples) and a complex ``scale``.
     """
 
     def __init__(self, n: int, terms):
@@ -318,7 +319,12 @@ class Problem:
         keep, ptrs = [], []
         for k, (A, kind, deg, tau) in enumerate(terms):
             ft[k].kind, ft[k].degree, ft[k].tau = int(kind), int(deg), float(tau)
-            if np.isscalar(A):
+            if hasattr(A, "samples"):  # boundary-integral term: the curve's 6 x n samples, factor A.scale
+                smp = np.ascontiguousarray(np.asarray(A.samples, dtype=np.float64))
+                ft[k].id_re, ft[k].id_im = complex(A.scale).real, complex(A.scale).imag
+                keep.append(smp)
+                ptrs.append(_ptr(smp))
+            elif np.isscalar(A):
                 ft[k].id_re, ft[k].id_im = complex(A).real, complex(A).imag
                 ptrs.append(None)
             else:

@@ -270,6 +270,7 @@ struct pmcim_problem_s {
   // geometry of the boundary-integral term (bie.cuh), NULL without one; such a
   // problem has no coefficient matrices for the precision forms and runs in FP64
   double* dG = nullptr;
+  bool bie_circ = false;  // its matrix is circulant (bie.cuh)
   float2* dA32 = nullptr;  // complex64 copy for the FP32 LU's assembly
   // exact BF16 digits of the dense coefficients and their row exponents, made on
   // the first call that refines with residuals on the tensor cores
@@ -417,6 +418,7 @@ int upload_problems(Call& c) {
     d.Adig = g.h->dig_ok ? g.h->dig.as<unsigned char>() : nullptr;
     d.Aexp = g.h->dig_ok ? g.h->dexp.as<int32_t>() : nullptr;
     d.bie = g.h->dG;
+    d.bie_circ = g.h->bie_circ ? 1 : 0;
     d.V = g.h->V.as<double2>();
     for (int k = 0; k < g.h->K; ++k) d.term[k] = g.h->term[k];
   }
@@ -1735,7 +1737,7 @@ int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmc
       t.dense = 0;
       t.mat_index = -1;
       // the curve's samples (host or device) -> the device geometry of bie.cuh
-      std::vector<double> smp((size_t)6 * n), G((size_t)6 * n);
+      std::vector<double> smp((size_t)6 * n), G((size_t)6 * n + 1);
       cudaError_t e = cudaMemcpy(smp.data(), A[k], smp.size() * sizeof(double), cudaMemcpyDefault);
       if (e != cudaSuccess) {
         delete p;
@@ -1746,6 +1748,7 @@ int pmcim_problem_create(int32_t n, int32_t K, const double* const* A, const pmc
         return fail(PMCIM_EINVAL, "term %d: the curve needs an even n >= 4 and finite, distinct samples with "
                                   "x' != 0", k);
       }
+      p->bie_circ = G[(size_t)6 * n] != 0.0;
       e = cudaMalloc(&p->dG, G.size() * sizeof(double));
       if (e == cudaSuccess) e = cudaMemcpy(p->dG, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice);
       if (e != cudaSuccess) {

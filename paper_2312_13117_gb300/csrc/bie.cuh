@@ -134,7 +134,9 @@ BIE_HD void j1_h1(double2 w, double2* J, double2* H) {
 
 // Entry (i, j) of K_n(kappa). G: the device geometry of the term (n >= 4, even),
 //   G[5 j + 0..4] = x1, x2, n1 = x2', n2 = -x1', d = n.x'' / (2 pi |x'|^2) at t_j,
-//   G[5 n + m]    = R_m - (2 pi / n) log(4 sin^2(pi m / n))  (m = 1..n-1; m = 0 unused).
+//   G[5 n + m]    = R_m - (2 pi / n) log(4 sin^2(pi m / n))  (m = 1..n-1; m = 0 unused),
+//   G[6 n]        = 1 when the sampled curve is invariant under the shift j -> j + 1 (a
+//                   circle), so that K_n is circulant: K_ij = K_{(i-j) mod n, 0}; else 0.
 BIE_ENTRY double2 dlp_entry(const double* G, int n, int i, int j, double2 kappa) {
   const double h = 2.0 * kPi / (double)n;
   const double* pj = G + 5 * (size_t)j;
@@ -153,7 +155,9 @@ BIE_ENTRY double2 dlp_entry(const double* G, int n, int i, int j, double2 kappa)
   return ca(cs(L, h), cs(L1, G[5 * (size_t)n + m]));
 }
 
-// Host: the device geometry G (5 n + n doubles) of a curve given by its samples
+constexpr int kCirculantMaxN = 8192;  // the shift-invariance test is O(n^2)
+
+// Host: the device geometry G (6 n + 1 doubles) of a curve given by its samples
 // s = [x1 | x2 | x1' | x2' | x1'' | x2''] (six rows of n values at t_j = 2 pi j / n).
 // Returns false when n is odd or below 4, a sample is not finite, x'(t_j) = 0, or
 // two sample points coincide.
@@ -190,6 +194,30 @@ inline bool build_geometry(const double* s, int n, double* G) {
     G[5 * (size_t)n + m] = R - h * log(4.0 * sn * sn);
   }
   delete[] ct;
+  // circulant when every entry's geometry (r, n(t_j).(x_i - x_j), and the diagonal term)
+  // depends on i - j only, to a few rounding units of the curve's size
+  bool circ = n <= kCirculantMaxN;
+  double scale = 0.0, dmax = 0.0;
+  for (int j = 0; j < n; ++j) {
+    scale = fmax(scale, fmax(fabs(G[5 * j]), fabs(G[5 * j + 1])));
+    scale = fmax(scale, fmax(fabs(G[5 * j + 2]), fabs(G[5 * j + 3])));
+    dmax = fmax(dmax, fabs(G[5 * j + 4]));
+  }
+  const double tol = 8e-15 * scale, tq = 8e-15 * scale * scale;
+  for (int j = 1; j < n && circ; ++j) circ = fabs(G[5 * j + 4] - G[4]) <= 8e-15 * dmax;
+  for (int m = 1; m < n && circ; ++m) {
+    const double ex0 = G[5 * m] - G[0], ey0 = G[5 * m + 1] - G[1];
+    const double r0 = hypot(ex0, ey0), q0 = G[2] * ex0 + G[3] * ey0;
+    for (int j = 1; j < n; ++j) {
+      const int i = (j + m) % n;
+      const double ex = G[5 * i] - G[5 * j], ey = G[5 * i + 1] - G[5 * j + 1];
+      if (fabs(hypot(ex, ey) - r0) > tol || fabs(G[5 * j + 2] * ex + G[5 * j + 3] * ey - q0) > tq) {
+        circ = false;
+        break;
+      }
+    }
+  }
+  G[6 * (size_t)n] = circ ? 1.0 : 0.0;
   return true;
 }
 

@@ -60,18 +60,33 @@ __global__ void __launch_bounds__(THREADS, 2) k_factor_solve_fp64(NodeArgs a) {
 
     // assemble [T(z_j) | V]
     const size_t nn = (size_t)n * n;
+    // a circulant boundary-integral term: its n distinct entries K_{m,0}, formed once per
+    // node in the slot's probe-block columns (V is written there below)
+    double2* circ = M + nn;
+    const bool use_circ = BIE && P.bie_circ;
+    if (use_circ) {
+      for (int m = tid; m < n; m += THREADS) circ[m] = bie::dlp_entry(P.bie, n, m, 0, z);
+      __syncthreads();
+    }
     for (int col = 0; col < n; ++col) {
       for (int row = tid; row < n; row += THREADS) {
         const size_t e = (size_t)col * n + row;
         double2 v = make_double2(0.0, 0.0);
         for (int k = 0; k < P.K; ++k) {
           const TermDesc& t = P.term[k];
-          if (t.dense) cfma(v, sm.lu.fz[k], P.A[(size_t)t.mat_index * nn + e]);
-          else cfma_term<BIE>(v, P, t, sm.lu.fz[k], row, col);
+          if (t.dense) {
+            cfma(v, sm.lu.fz[k], P.A[(size_t)t.mat_index * nn + e]);
+          } else if (use_circ && t.kind == PMCIM_F_HELMHOLTZ_DLP) {
+            const int m = row >= col ? row - col : row - col + n;
+            cfma(v, t.id, circ[m]);
+          } else {
+            cfma_term<BIE>(v, P, t, sm.lu.fz[k], row, col);
+          }
         }
         M[e] = v;
       }
     }
+    if (use_circ) __syncthreads();  // circ is read above and overwritten by V below
     for (size_t e = tid; e < (size_t)n * l; e += THREADS) M[nn + e] = P.V[e];
     __syncthreads();
 

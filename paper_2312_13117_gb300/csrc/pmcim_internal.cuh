@@ -162,8 +162,9 @@ struct ProblemDev {
   // (ozaki.cuh; NULL until made), and the row exponents [dense term][row blocks x 128]
   const unsigned char* Adig;
   const int32_t* Aexp;
-  // geometry of the boundary-integral term (bie.cuh, 6 n doubles), NULL without one
+  // geometry of the boundary-integral term (bie.cuh, 6 n + 1 doubles), NULL without one
   const double* bie;
+  int32_t bie_circ;  // 1: its matrix is circulant (the curve is invariant under t_j -> t_{j+1})
   TermDesc term[PMCIM_MAX_TERMS];
 };
 

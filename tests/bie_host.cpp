@@ -19,7 +19,7 @@ extern "C" void bie_host_j1_h1(int32_t m, const double* w, double* J, double* H)
 
 // K_n(kappa) column-major (2 n n doubles); returns 0, or -1 when the curve is rejected.
 extern "C" int32_t bie_host_matrix(int32_t n, const double* samples, double kre, double kim, double* K) {
-  double* G = (double*)malloc(sizeof(double) * 6 * (size_t)n);
+  double* G = (double*)malloc(sizeof(double) * (6 * (size_t)n + 1));
   if (!bie::build_geometry(samples, n, G)) {
     free(G);
     return -1;
@@ -32,4 +32,14 @@ extern "C" int32_t bie_host_matrix(int32_t n, const double* samples, double kre,
     }
   free(G);
   return 0;
+}
+
+// 1 when the geometry builder finds the curve shift-invariant (circulant matrix), 0 when
+// not, -1 when the curve is rejected.
+extern "C" int32_t bie_host_circulant(int32_t n, const double* samples) {
+  double* G = (double*)malloc(sizeof(double) * (6 * (size_t)n + 1));
+  int32_t r = -1;
+  if (bie::build_geometry(samples, n, G)) r = G[6 * (size_t)n] != 0.0 ? 1 : 0;
+  free(G);
+  return r;
 }

@@ -7,7 +7,10 @@ compiled for the host by the test harness tests/bie_host.cpp.
 * Whole matrices K_n(kappa) against the oracle's Nystrom matrix (which is built
   from SciPy's Bessel functions and its own weights), on a circle, an ellipse
   and a circle of radius 3 (so that |kappa r| exceeds the switch at 13).
-* The geometry builder rejects odd n, coincident points and x' = 0.
+* The geometry builder rejects odd n, coincident points and x' = 0, and marks a
+  circle (whose matrix is circulant, so the node kernel forms only its first
+  column) but not an ellipse or a shifted, rotated, rescaled circle sampled
+  off its symmetry.
 """
 import ctypes as C
 import os
@@ -43,6 +46,8 @@ def lib(tmp_path_factory):
     L.bie_host_j1_h1.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
     L.bie_host_matrix.argtypes = [C.c_int32, C.c_void_p, C.c_double, C.c_double, C.c_void_p]
     L.bie_host_matrix.restype = C.c_int32
+    L.bie_host_circulant.argtypes = [C.c_int32, C.c_void_p]
+    L.bie_host_circulant.restype = C.c_int32
     return L
 
 
@@ -104,3 +109,29 @@ def test_geometry_rejects_bad_curves(lib):
     nan = good.copy()
     nan[0, 2] = np.nan
     assert _matrix(lib, nan, 1.0 - 1.0j)[0] == -1
+
+
+def _circ(lib, samples):
+    s = np.ascontiguousarray(np.asarray(samples, dtype=np.float64).ravel())
+    return lib.bie_host_circulant(s.size // 6, s.ctypes.data)
+
+
+def test_circulant_detection(lib):
+    C = w.circle_curve(64)
+    assert _circ(lib, C.samples) == 1
+    assert _circ(lib, w.circle_curve(96, 3.0).samples) == 1
+    assert _circ(lib, w.ellipse_curve(64, 1.5, 0.8).samples) == 0
+    # a circle translated by (0.3, -0.2): still shift-invariant
+    s = C.samples.copy()
+    s[0] += 0.3
+    s[1] -= 0.2
+    assert _circ(lib, s) == 1
+    # one point moved off the circle: not
+    s[0, 5] += 1e-6
+    assert _circ(lib, s) == 0
+    # the circulant reading holds for the circle's matrix: K_ij = K_{(i-j) mod n, 0}
+    rc, K = _matrix(lib, C.samples, 1.7 - 0.9j)
+    n = K.shape[0]
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    assert np.abs(K - K[(i - j) % n, 0]).max() <= 1e-13 * np.abs(K).max()
+    assert _circ(lib, w.circle_curve(15).samples) == -1

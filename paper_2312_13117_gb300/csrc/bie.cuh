@@ -34,6 +34,45 @@ namespace bie {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kEulerGamma = 0.57721566490153286061;
 constexpr double kSeriesMax = 13.0;  // |w| at or below: ascending series; above: Hankel's expansion
+constexpr int kSeriesTerms = 96, kAsymTerms = 64;
+
+// The series' coefficients, made at compile time in the order the loops below would
+// compute them (so the results are those of dividing in the loop), and read from the
+// constant cache on the device instead of two FP64 divisions per term:
+//   inv_kk1[k] = 1 / (k (k+1)),  psi2[k] = psi(k+1) + psi(k+2) = 2 (H_k - gamma) + 1/(k+1),
+//   ak[k] = prod_{j=1..k} (4 - (2j-1)^2) / (8 j)  (Hankel's a_k for order 1).
+struct SeriesTables {
+  double inv_kk1[kSeriesTerms];
+  double psi2[kSeriesTerms];
+  double ak[kAsymTerms];
+};
+constexpr SeriesTables make_series_tables() {
+  SeriesTables T{};
+  double Hk = 0.0;
+  T.inv_kk1[0] = 0.0;
+  T.psi2[0] = 1.0 - 2.0 * kEulerGamma;
+  for (int k = 1; k < kSeriesTerms; ++k) {
+    T.inv_kk1[k] = 1.0 / ((double)k * (double)(k + 1));
+    Hk += 1.0 / (double)k;
+    T.psi2[k] = 2.0 * (Hk - kEulerGamma) + 1.0 / (double)(k + 1);
+  }
+  double a = 1.0;
+  T.ak[0] = 1.0;
+  for (int k = 1; k < kAsymTerms; ++k) {
+    a *= (4.0 - (double)(2 * k - 1) * (double)(2 * k - 1)) / (8.0 * (double)k);
+    T.ak[k] = a;
+  }
+  return T;
+}
+#if defined(__CUDACC__)
+static __constant__ SeriesTables kSeriesDev = make_series_tables();
+#endif
+static const SeriesTables kSeriesHost = make_series_tables();
+#if defined(__CUDA_ARCH__)
+#define BIE_TABLES kSeriesDev
+#else
+#define BIE_TABLES kSeriesHost
+#endif
 
 BIE_HD double2 cm(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 BIE_HD double2 ca(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -65,19 +104,16 @@ BIE_HD void j1_h1(double2 w, double2* J, double2* H) {
     const double2 h = cs(w, 0.5);
     const double2 hh = cm(h, h);
     const double2 u = make_double2(-hh.x, -hh.y);  // -(w/2)^2
+    const SeriesTables& TB = BIE_TABLES;
     double2 t = h;                                 // k = 0 term
     double2 Js = t;
-    double Hk = 0.0;                               // H_k
-    double c = 1.0 - 2.0 * kEulerGamma;            // psi(1) + psi(2)
-    double2 S = cs(t, c);
+    double2 S = cs(t, TB.psi2[0]);                 // psi(1) + psi(2)
     double tmax = fabs(t.x) + fabs(t.y);
     const double au = hypot(u.x, u.y);
-    for (int k = 1; k < 96; ++k) {
-      t = cs(cm(t, u), 1.0 / ((double)k * (double)(k + 1)));
-      Hk += 1.0 / (double)k;
-      c = 2.0 * (Hk - kEulerGamma) + 1.0 / (double)(k + 1);
+    for (int k = 1; k < kSeriesTerms; ++k) {
+      t = cs(cm(t, u), TB.inv_kk1[k]);
       Js = ca(Js, t);
-      S = ca(S, cs(t, c));
+      S = ca(S, cs(t, TB.psi2[k]));
       const double at = fabs(t.x) + fabs(t.y);
       tmax = fmax(tmax, at);
       if ((double)k * (double)(k + 1) > au && at <= 1e-17 * tmax) break;
@@ -92,14 +128,14 @@ BIE_HD void j1_h1(double2 w, double2* J, double2* H) {
     *H = ca(Js, ci(Y));
     return;
   }
+  const SeriesTables& TB = BIE_TABLES;
   const double2 iw = crec(w);
   double2 p = make_double2(1.0, 0.0);   // 1 / w^k
   double2 s1 = p, s2 = p;               // sums with (+i)^k and (-i)^k
-  double a = 1.0, prev = 1.0;
-  for (int k = 1; k < 64; ++k) {
-    a *= (4.0 - (double)(2 * k - 1) * (double)(2 * k - 1)) / (8.0 * (double)k);
+  double prev = 1.0;
+  for (int k = 1; k < kAsymTerms; ++k) {
     p = cm(p, iw);
-    const double2 tk = cs(p, a);
+    const double2 tk = cs(p, TB.ak[k]);
     const double mag = fabs(tk.x) + fabs(tk.y);
     if (mag > prev) break;  // past the smallest term
     // (+i)^k tk and (-i)^k tk

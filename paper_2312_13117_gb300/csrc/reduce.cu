@@ -235,9 +235,11 @@ __global__ void __launch_bounds__(RT) k_border_rhs(ValueArgs a, const int64_t* _
 // r = T v (or T^H v) and ||T(lambda)||_F^2, all in FP64.
 template <bool BIE>
 __global__ void __launch_bounds__(RT) k_certify(ValueArgs a) {
+  constexpr int kCircMax = 2048;  // circulant boundary-integral matrices up to this n: first column in smem
   __shared__ ProblemDev P;
   __shared__ double2 fz[PMCIM_MAX_TERMS];
   __shared__ double red[2][RT / 32];
+  __shared__ double2 ccol[BIE ? kCircMax : 1];
   const int m = blockIdx.x;
   load_problem(&P, a.probs + a.prob_of[m]);
   __syncthreads();
@@ -246,6 +248,9 @@ __global__ void __launch_bounds__(RT) k_certify(ValueArgs a) {
   const double2 lam = a.lam[m];
   const double2* v = a.vecs + a.vec_off[m];
   if (threadIdx.x < P.K) fz[threadIdx.x] = eval_f(P.term[threadIdx.x], lam);
+  const bool circ = BIE && P.bie_circ && n <= kCircMax;
+  if (circ)
+    for (int q = threadIdx.x; q < n; q += RT) ccol[q] = bie::dlp_entry(P.bie, n, q, 0, lam);
   __syncthreads();
   double r2 = 0.0, f2 = 0.0;
   for (int row = threadIdx.x; row < n; row += RT) {
@@ -257,8 +262,10 @@ __global__ void __launch_bounds__(RT) k_certify(ValueArgs a) {
       for (int k = 0; k < P.K; ++k) {
         const TermDesc& tk = P.term[k];
         if (tk.dense) cfma(t, fz[k], P.A[(size_t)tk.mat_index * nn + e]);
-        else if (BIE && tk.kind == PMCIM_F_HELMHOLTZ_DLP)  // T^H: entry (col, row), conjugated below
-          cfma(t, tk.id, bie::dlp_entry(P.bie, n, a.herm ? col : row, a.herm ? row : col, fz[k]));
+        else if (BIE && tk.kind == PMCIM_F_HELMHOLTZ_DLP) {  // T^H: entry (col, row), conjugated below
+          const int i = a.herm ? col : row, j = a.herm ? row : col;
+          cfma(t, tk.id, circ ? ccol[i >= j ? i - j : i - j + n] : bie::dlp_entry(P.bie, n, i, j, fz[k]));
+        }
         else if (row == col) cfma(t, fz[k], tk.id);
       }
       if (a.herm) t.y = -t.y;

@@ -70,7 +70,9 @@ extern "C" {
    A[k] holds 6 n doubles: the rows x1(t_j), x2(t_j), x1'(t_j), x2'(t_j),
    x1''(t_j), x2''(t_j), each of n values (derivatives in t, the curve traversed
    counter-clockwise). n must be even and at least 4; a problem holds at most
-   one such term and runs in PMCIM_PREC_FP64 only. The entries are formed on
+   one such term. It runs in every precision form; PMCIM_PREC_AUTO takes
+   PMCIM_PREC_FP32_IR for it, and pmcim_residual refuses it (EINVAL: the
+   tensor-core residual needs coefficient matrices). The entries are formed on
    the device from J_1 and H_1^(1) of complex argument w = z r (ascending series
    for |w| <= 13, Hankel's expansion above), for Re(z) > 0: relative error at
    most about 5e-12 where Im(w) <= 0 (the scattering poles lie in Im z < 0) and

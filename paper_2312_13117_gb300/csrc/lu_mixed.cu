@@ -351,16 +351,21 @@ __device__ void residual_fp64_col(const double2* __restrict__ X, double2* __rest
 // T(z_j) in FP64 into T (n x n, column-major), the matrix of the refinement
 // residuals, and rounded to complex64 into M32 (leading dimension n), the FP32
 // LU's matrix: the dense terms in one pass over the elements, four elements per
-// thread at a time so that their coefficient loads overlap, then the identity
-// terms on the diagonal. herm: T(z_j)^H instead (the coefficients read
-// transposed, the sum conjugated; used by the certificates' bordered steps).
-__device__ void assemble_fp64(const NodeCtx& cx, double2* __restrict__ T, float2* __restrict__ M32, bool herm) {
+// thread at a time so that their coefficient loads overlap, then a boundary-
+// integral term (bie.cuh; a circulant one from its first column, formed in
+// scratch, n values), then the identity terms on the diagonal. herm: T(z_j)^H
+// instead (the coefficients read transposed, the sum conjugated; used by the
+// certificates' bordered steps, which problems with a boundary-integral term do
+// not take).
+template <bool BIE>
+__device__ void assemble_fp64(const NodeCtx& cx, double2* __restrict__ T, float2* __restrict__ M32, bool herm,
+                              double2* __restrict__ scratch) {
   const ProblemDev& P = cx.P;
   const int n = P.n;
   const size_t nn = (size_t)n * n;
   double2 id = make_double2(0.0, 0.0);
   for (int k = 0; k < P.K; ++k)
-    if (!P.term[k].dense) id = cadd(id, cmul(cx.fz[k], P.term[k].id));
+    if (!P.term[k].dense && P.term[k].kind != PMCIM_F_HELMHOLTZ_DLP) id = cadd(id, cmul(cx.fz[k], P.term[k].id));
   for (size_t e0 = gtid(); e0 < nn; e0 += 4 * (size_t)THREADS) {
     double2 v[4];
 #pragma unroll
@@ -390,6 +395,26 @@ __device__ void assemble_fp64(const NodeCtx& cx, double2* __restrict__ T, float2
     }
   }
   gsync();
+  if (BIE && P.bie && !herm) {
+    int kb = 0;
+    while (kb + 1 < P.K && P.term[kb].kind != PMCIM_F_HELMHOLTZ_DLP) ++kb;
+    const double2 cb = P.term[kb].id, zb = cx.fz[kb];
+    if (P.bie_circ) {
+      for (int m = gtid(); m < n; m += THREADS) scratch[m] = bie::dlp_entry(P.bie, n, m, 0, zb);
+      gsync();
+    }
+    for (int col = 0; col < n; ++col)
+      for (int row = gtid(); row < n; row += THREADS) {
+        const size_t e = (size_t)col * n + row;
+        const double2 kv = P.bie_circ ? scratch[row >= col ? row - col : row - col + n]
+                                      : bie::dlp_entry(P.bie, n, row, col, zb);
+        double2 t = T[e];
+        cfma(t, cb, kv);
+        T[e] = t;
+        M32[e] = make_float2((float)t.x, (float)t.y);
+      }
+    gsync();
+  }
   if (herm) id.y = -id.y;
   for (int i = gtid(); i < n; i += THREADS) {
     const size_t e = (size_t)i * n + i;
@@ -490,7 +515,8 @@ __device__ void load_node(const NodeArgs& a, int idx, NodeCtx& c, RegionDev& rg,
   if (gtid() == 0) {
     double2 id = make_double2(0.0, 0.0);
     for (int k = 0; k < c.P.K; ++k)
-      if (!c.P.term[k].dense) id = cadd(id, cmul(c.fz[k], c.P.term[k].id));
+      if (!c.P.term[k].dense && c.P.term[k].kind != PMCIM_F_HELMHOLTZ_DLP)
+        id = cadd(id, cmul(c.fz[k], c.P.term[k].id));
     c.fid32 = make_float2((float)id.x, (float)id.y);
   }
   gsync();
@@ -521,6 +547,9 @@ constexpr uint32_t TMEM_REFINE = 256;  // first column of the refine group's acc
 static_assert(tcu::TMEM_COLS <= TMEM_REFINE && TMEM_REFINE + ozk::TMEM_COLS <= TMEM_ALL, "TMEM split");
 
 // Steps 1-2 for one node after another, into the CTA's slots in turn.
+// BIE: the instantiation for launches with a boundary-integral term (bie.cuh); the
+// other leaves its code out.
+template <bool BIE>
 __device__ void factor_group(const NodeArgs& a, MixedSmem& sm, tcu::Ctx& cx, PhaseClock& pc) {
   const int tid = gtid();
   NodeCtx& c = sm.f.c;
@@ -549,9 +578,11 @@ __device__ void factor_group(const NodeArgs& a, MixedSmem& sm, tcu::Ctx& cx, Pha
     const int n = P.n, l = P.l, ncols = n + l;
     const size_t nn = (size_t)n * n, nl = (size_t)n * l;
     pc.mark(PH_SETUP);
-    // T(z_j) in FP64 for the refine group's FP64 residual, and rounded; T(z_j)^H likewise
-    if (rg.herm || (P.n_dense >= 2 && !a.oz))
-      assemble_fp64(c, a.t64 + si * a.t64_stride, M32, rg.herm != 0);
+    // T(z_j) in FP64 for the refine group's FP64 residual, and rounded; T(z_j)^H likewise;
+    // always with a boundary-integral term (no stored coefficients to take residuals from)
+    if (rg.herm || (P.n_dense >= 2 && !a.oz) || (BIE && P.bie))
+      assemble_fp64<BIE>(c, a.t64 + si * a.t64_stride, M32, rg.herm != 0,
+                         reinterpret_cast<double2*>(slot + mixed_residual_offset(n, l)));
     else
       assemble32(c, M32);
     for (size_t e = tid; e < nl; e += THREADS) M32[nn + e] = make_float2((float)P.V[e].x, (float)P.V[e].y);
@@ -578,12 +609,15 @@ __device__ void factor_group(const NodeArgs& a, MixedSmem& sm, tcu::Ctx& cx, Pha
 // Step 4: the node solved again by the FP64 LU in its slot. Kept out of line:
 // it is rare, and its registers should not weigh on the refinement loop.
 __device__ __noinline__ int fallback_fp64(const NodeCtx& c, double2* M64, int* piv, double2* X,
-                                          LuSmemT<double2>& lu) {
+                                          LuSmemT<double2>& lu, const double2* __restrict__ T64) {
   const ProblemDev& P = c.P;
   const int n = P.n, l = P.l;
   const size_t nn = (size_t)n * n, nl = (size_t)n * l;
   gsync();
-  assemble(c, nullptr, M64);
+  if (T64)  // T(z_j) as the factor group assembled it in FP64 (a boundary-integral term)
+    for (size_t e = gtid(); e < nn; e += THREADS) M64[e] = T64[e];
+  else
+    assemble(c, nullptr, M64);
   for (size_t e = gtid(); e < nl; e += THREADS) M64[nn + e] = P.V[e];
   gsync();
   const int info = cta_lu(M64, n, n + l, piv, lu);
@@ -594,6 +628,7 @@ __device__ __noinline__ int fallback_fp64(const NodeCtx& c, double2* M64, int* p
 }
 
 // Steps 3-4 for the nodes the factor group hands over, in the same order.
+template <bool BIE>
 __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
   const int tid = gtid();
   NodeCtx& c = sm.r.c;
@@ -637,7 +672,8 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
     int sweeps = 0;
     // residuals on the tensor cores (exact digit products), unless a wait of that
     // path ran out earlier in this CTA; then the node is solved in FP64 below
-    const bool use_oz = a.oz && P.Adig != nullptr && !rg.herm;
+    const bool bie = BIE && P.bie;
+    const bool use_oz = a.oz && P.Adig != nullptr && !rg.herm && !bie;
     if (use_oz && sm.ozb.bad) {
       ok = false;
       tc_lost = true;
@@ -651,7 +687,7 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
       double2 fM = make_double2(0.0, 0.0), id = make_double2(0.0, 0.0);
       if (use_oz) {
         // every dense term through the digit products; nothing to set up here
-      } else if (P.n_dense >= 2 || rg.herm) {  // assembled by the factor group with the slot
+      } else if (P.n_dense >= 2 || rg.herm || bie) {  // assembled by the factor group with the slot
         M = a.t64 + si * a.t64_stride;
         fM = make_double2(1.0, 0.0);
       } else {
@@ -731,7 +767,7 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
       if (!conv) ok = false;
     }
     if (!ok && refine && rg.border == 0) {
-      info = fallback_fp64(c, M64, piv, X, sm.r.u.lu64);
+      info = fallback_fp64(c, M64, piv, X, sm.r.u.lu64, bie ? a.t64 + si * a.t64_stride : nullptr);
       pc.mark(PH_FALLBACK);
     }
     if (rg.border > 0) {
@@ -747,6 +783,7 @@ __device__ void refine_group(const NodeArgs& a, MixedSmem& sm, PhaseClock& pc) {
   }
 }
 
+template <bool BIE>
 __global__ void __launch_bounds__(CTA_THREADS, 1) k_factor_solve_mixed(NodeArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   MixedSmem& sm = *reinterpret_cast<MixedSmem*>(smem_raw);
@@ -775,7 +812,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_factor_solve_mixed(NodeArgs 
   if (tid < THREADS) {
     tcu::Ctx cx{sm.f.u.tc + offsetof(LuSmemT<float2>, Ls), sm.mbar_tc, sm.tmem_base, {0u, 0u}, &sm.tc_bad,
                 a.tc_wait_cycles};
-    factor_group(a, sm, cx, pc);
+    factor_group<BIE>(a, sm, cx, pc);
     // a commit whose wait ran out may still be in flight: wait once more, with the
     // default limit whatever the update's own limit was, before the columns are given back
     if (sm.tc_bad) {
@@ -784,7 +821,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_factor_solve_mixed(NodeArgs 
       tcu::wait_parity(&sm.mbar_tc[1], cx.phase[1] ^ 1u, tcu::WAIT_CYCLES);
     }
   } else {
-    refine_group(a, sm, pc);
+    refine_group<BIE>(a, sm, pc);
   }
   // both groups are done with tensor memory before it is given back
   tcu::fence_before();
@@ -810,7 +847,10 @@ size_t mixed_slot_bytes(int n, int l) {
 static_assert(sizeof(MixedSmem) + 1024 <= 227 * 1024, "one CTA per SM");
 
 cudaError_t prepare_factor_mixed() {
-  return cudaFuncSetAttribute(k_factor_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_factor_solve_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(MixedSmem));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_factor_solve_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(MixedSmem));
 }
 
@@ -838,6 +878,7 @@ cudaError_t launch_factor_solve_mixed(const NodeArgs& a, cudaStream_t s) {
   int grid = a.slots / SLOTS;
   if (grid > a.n_items) grid = a.n_items;
   if (grid < 1) return cudaErrorInvalidValue;
-  k_factor_solve_mixed<<<grid, CTA_THREADS, smem, s>>>(a);
+  if (a.bie) k_factor_solve_mixed<true><<<grid, CTA_THREADS, smem, s>>>(a);
+  else k_factor_solve_mixed<false><<<grid, CTA_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }

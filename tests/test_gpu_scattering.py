@@ -18,8 +18,10 @@ SciPy's (AMOS) Bessel functions.
 * sigma_min (k_verify_fp64) and the eigenvector certificate (k_certify) at those
   poles (to rounding) and off them (sigma_min as the upper bound inverse iteration
   reaches in its 30 steps), against the oracle.
-* The precision forms and the tensor-core residual are refused with EINVAL;
-  PREC_AUTO runs FP64.
+* The precision forms (FP32 LU on the FMA pipes or with tensor-core trailing
+  updates, FP64 residuals from the FP64 matrix) on a circle and an ellipse, and on
+  all 100 disks. PREC_AUTO runs the FP32 LU with FP64 refinement; the tensor-core
+  residual call is refused.
 """
 import json
 import os
@@ -119,7 +121,7 @@ def test_all_disks_n256_against_oracle_and_hankel_zeros(pm, scattering):
     assert _match_lam(res["lam"], lam_o) <= LAM_TOL
     zeros = [z for m, z in hankel_zeros_in(W.omega) for _ in range(2 if m else 1)]
     assert _match_lam(res["lam"], np.array(zeros)) <= LAM_TOL
-    assert res["stats"]["unverified"] == 0 and res["stats"]["tuned_fp64"] == 1
+    assert res["stats"]["unverified"] == 0 and res["stats"]["tuned_mixed"] == 1  # AUTO: FP32 LU + refinement
     # eigenvectors: unit, ||T(lambda) v|| at rounding level
     for i, lam in enumerate(res["lam"]):
         v = res["vecs"][:, i]
@@ -159,14 +161,60 @@ def test_verify_and_certify(pm):
     P.close()
 
 
-def test_precision_forms_refused(pm):
+FORMS = ["fp32ir", "tf32x3", "bf16x3"]
+
+
+def _form(pm, form):
+    return {"fp32ir": pm.PREC_FP32_IR, "tf32x3": pm.PREC_TF32X3_IR, "bf16x3": pm.PREC_BF16X3_IR}[form]
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("curve", ["circle", "ellipse"])
+def test_precision_form_moments(pm, form, curve):
+    """The precision forms on a boundary-integral problem: the factor group forms T(z_j) in FP64 (a
+    circulant one from its first column), the FP32 LU works on its rounding, and the refinement
+    residuals multiply the FP64 matrix. Refined solutions: |dX| <= 1e-9 |X| per node."""
+    n = 96 if curve == "circle" else 80
+    prob = _problem(w.circle_curve(n) if curve == "circle" else w.ellipse_curve(n, 1.4, 0.7))
+    V = w.probe_block(np.random.default_rng(21), n, 6)
+    regs = DISKS[:3] if curve == "circle" else [w.Region(1.2 - 0.9j, 0.3, 32), w.Region(2.6 - 2.1j, 0.25, 32)]
+    P = pm.Problem(prob.n, prob.terms)
+    C0, C1, _, _ = P.moments(regs, V, opt=pm.options(precision=_form(pm, form)))
+    for g, reg in enumerate(regs):
+        m = o.moments(prob, reg.c, reg.r, reg.N, V)
+        z, wts = o.nodes_weights(reg.c, reg.r, reg.N)
+        X = o.solve_nodes(prob, z, V)
+        scale = sum(abs(wts[j]) * np.linalg.norm(X[j]) for j in range(reg.N))
+        b0, b1, _ = _moment_bound(prob, reg, V)
+        assert np.linalg.norm(C0[g] - m.C0) <= b0 + 1e-9 * scale, g
+        assert np.linalg.norm(C1[g] - m.C1) <= b1 + 1e-9 * scale * (abs(reg.c) + reg.r), g
+    P.close()
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_precision_form_all_disks_n256(pm, scattering, form):
+    """All 100 disks of the n = 256 workload in each precision form: every decision and the eigenvalue
+    set equal the stored oracle run's."""
+    W = scattering
+    with open(os.path.join(GOLDEN, "scattering_disk_n256_oracle.json")) as fh:
+        run = json.load(fh)["runs"][repr(1e-6)]
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    res = P.solve(W.regions, W.V, want_vecs=False, opt=pm.options(precision=_form(pm, form)))
+    top = {rec[0]: rec for rec in run["records"] if rec[4] == 0}
+    for g in range(len(W.regions)):
+        assert bool(res["status"][g] & pm.RS_CANDIDATE) == top[g][6], g
+    lam_o = np.array([complex(a, b) for (a, b, _, _) in run["lam"]])
+    assert _match_lam(res["lam"], lam_o) <= LAM_TOL
+    assert res["stats"]["unverified"] == 0
+    P.close()
+
+
+def test_tensor_core_residual_refused(pm):
+    """pmcim_residual multiplies coefficient digits on the tensor cores: a boundary-integral term has
+    none, so the call is refused."""
     prob = _problem(w.circle_curve(32))
     V = w.probe_block(np.random.default_rng(6), 32, 4)
     P = pm.Problem(prob.n, prob.terms)
-    for prec in (pm.PREC_FP32_IR, pm.PREC_TF32X3_IR, pm.PREC_BF16X3_IR):
-        with pytest.raises(pm.PmcimError) as e:
-            P.solve(DISKS[:1], V, opt=pm.options(precision=prec))
-        assert e.value.code == EINVAL
     with pytest.raises(pm.PmcimError) as e:
         P.residual(np.array([1.0 - 1.0j]), V, np.zeros((1, 32, 4), np.complex128))
     assert e.value.code == EINVAL
@@ -183,3 +231,49 @@ def test_bad_curves_refused(pm):
     with pytest.raises(pm.PmcimError) as e:
         pm.Problem(16, two.terms)
     assert e.value.code == EINVAL
+
+
+def test_batch_mixes_coefficient_and_boundary_problems(pm):
+    """One batched launch with a quadratic problem and two boundary-integral problems (the kernel
+    instantiation with the term serves all of them): each problem's eigenvalues equal the oracle's."""
+    qd = w.quadratic_small(seed=11, n=40, l=6, N=32)
+    sc = w.scattering_disk(n=48, l=4)
+    el = _problem(w.ellipse_curve(48, 1.2, 0.9))
+    Vel = w.probe_block(np.random.default_rng(12), 48, 4)
+    batch = [(qd.problem, qd.regions[5:9], qd.V),
+             (sc.problem, [sc.regions[g] for g in (6, 35, 50)], sc.V),
+             (el, [g for i, g in enumerate(w.grid_regions(0.2, 3.2, -3.2, -0.2, 10, 10, 32)) if i in (6, 35)],
+              Vel)]  # disks holding two resonances each: the ellipse splits the circle's double poles
+    handles = [pm.Problem(p.n, p.terms) for (p, _, _) in batch]
+    res = pm.batch_solve(handles, [r for (_, r, _) in batch], [V for (_, _, V) in batch],
+                         opt=pm.options(precision=pm.PREC_AUTO))
+    st = res["stats"]
+    assert st["tuned_mixed"] >= 2  # the two boundary-integral problems
+    for q, (prob, regs, V) in enumerate(batch):
+        ref = o.pmcimb(prob, regs, V)
+        got = res["lam"][res["problem_of"] == q]
+        assert _match_lam(got, ref.lam) <= LAM_TOL, q
+    assert (res["problem_of"] == 1).sum() == 4 and (res["problem_of"] == 2).sum() == 4
+    for h in handles:
+        h.close()
+
+
+def test_two_pass_and_pmcima(pm):
+    """The two-pass schedule (indicator on 16 of the 64 nodes) returns the one-pass eigenvalues; pmCIMa
+    (tol_eps = 1e-6) returns the oracle's merged centres to rounding and each pole within tol_eps."""
+    W = w.scattering_disk(n=48, l=4)
+    regs = [W.regions[g] for g in (5, 6, 7, 35, 36, 50)]
+    P = pm.Problem(W.problem.n, W.problem.terms)
+    one = P.solve(regs, W.V)
+    two = P.solve(regs, W.V, opt=pm.options(indicator_N=16))
+    assert _match_lam(two["lam"], one["lam"]) <= LAM_TOL
+    assert two["stats"]["solves"] < one["stats"]["solves"]
+    regs16 = [w.Region(g.c, g.r, 16) for g in regs]
+    res = P.pmcima(regs16, W.V, tol_eps=1e-6)
+    ref = o.pmcima(W.problem, regs16, W.V, tol_eps=1e-6)
+    assert len(res["lam"]) == len(ref.lam) == 2
+    assert np.max(np.abs(res["lam"] - ref.lam)) <= 1e-12
+    zeros = np.array([z for _, z in hankel_zeros_in(W.omega)])
+    for lam in res["lam"]:
+        assert np.min(np.abs(zeros - lam)) <= 1e-6
+    P.close()

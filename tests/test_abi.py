@@ -67,3 +67,29 @@ def test_debug_wait_limits_reject_negative(lib):
         pmcim.debug_wait_limits(-1, 0)
     assert e.value.code == -1   # PMCIM_EINVAL
     pmcim.debug_wait_limits(0, 0)
+
+
+def test_term_kinds_match_header():
+    """The scalar-function kinds, the boundary-integral term's included, agree between the header, the
+    binding, the input generators and the oracle."""
+    src = open(os.path.join(ROOT, "include", "pmcim.h")).read()
+    kinds = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define PMCIM_F_(\w+)\s+(\d+)", src)}
+    assert kinds == {"MONOMIAL": 0, "EXP_NEG": 1, "HELMHOLTZ_DLP": 2}
+    from paper_2312_13117_gb300 import pmcim
+    import oracle
+    import workloads
+    assert (pmcim.F_MONOMIAL, pmcim.F_EXP_NEG, pmcim.F_HELMHOLTZ_DLP) == (0, 1, 2)
+    assert (workloads.MONOMIAL, workloads.EXP_NEG, workloads.HELMHOLTZ_DLP) == (0, 1, 2)
+    assert (oracle.MONOMIAL, oracle.EXP_NEG, oracle.HELMHOLTZ_DLP) == (0, 1, 2)
+
+
+def test_no_cpu_fallback_for_boundary_terms_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import workloads as w
+    from paper_2312_13117_gb300 import pmcim
+    W = w.scattering_disk(n=16, l=2)
+    with pytest.raises(pmcim.PmcimError) as e:
+        pmcim.Problem(W.problem.n, W.problem.terms)
+    assert e.value.code == -3  # PMCIM_ECUDA

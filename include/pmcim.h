@@ -104,7 +104,9 @@ typedef struct {
 #define PMCIM_PREC_AUTO 2      /* per problem, whichever of the forms solves
                                   nodes fastest on this device, measured on first
                                   use for each (n bucket, l, dense-term count) and
-                                  kept for the process; all meet the same accuracy */
+                                  kept for the process; all meet the same accuracy.
+                                  A problem with a boundary-integral term takes
+                                  PMCIM_PREC_FP32_IR without being timed */
 #define PMCIM_PREC_TF32X3_IR 3 /* FP32 LU whose trailing updates are complex
                                   products on the tensor cores, each FP32 operand
                                   split into two TF32 parts (3 products per real

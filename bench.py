@@ -578,6 +578,56 @@ def run_paper_quadratic(args, world, rank, local):
     return 0
 
 
+def library_lu_leg(W, disk, device="cuda", reps=2):
+    """External comparison, not part of the product path: the node solves of one disk,
+    T(z_j) X_j = V for its N nodes, through PyTorch's batched LU (torch.linalg.lu_factor and
+    lu_solve: cuSOLVER/cuBLAS getrf and getrs on a GPU) in complex128, and in complex64
+    (FP32 LU, no refinement: not FP64 accurate, for context). T(z_j) is assembled with torch
+    tensor operations before the timed region; the timed region is the factorisation and the
+    solve of the whole batch, `reps` times after one untimed run, with CUDA events."""
+    import torch
+    out = {"disk": disk, "note": "torch.linalg.lu_factor + lu_solve on the batch of the disk's N nodes"}
+    try:
+        reg = W.regions[disk]
+        N, n = reg.N, W.problem.n
+        th = 2.0 * np.pi * np.arange(N) / N
+        z = torch.tensor(reg.c + reg.r * np.exp(1j * th), dtype=torch.complex128, device=device)
+        T = torch.zeros((N, n, n), dtype=torch.complex128, device=device)
+        eye = torch.eye(n, dtype=torch.complex128, device=device)
+        for (A, kind, deg, tau) in W.problem.terms:
+            f = z ** deg if kind == 0 else torch.exp(-tau * z)
+            M = eye * complex(A) if np.isscalar(A) else torch.from_numpy(np.ascontiguousarray(A)).to(device)
+            T += f[:, None, None] * M[None]
+        V = torch.from_numpy(np.ascontiguousarray(W.V)).to(device)
+        for name, dt in (("complex128", torch.complex128), ("complex64", torch.complex64)):
+            Tb, Vb = T.to(dt), V.to(dt).expand(N, -1, -1)
+
+            def run():
+                LU, piv = torch.linalg.lu_factor(Tb)
+                return torch.linalg.lu_solve(LU, piv, Vb)
+            X = run()
+            if device == "cuda":
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    X = run()
+                e1.record()
+                e1.synchronize()
+                sec = e0.elapsed_time(e1) / 1e3 / reps
+            else:
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    X = run()
+                sec = (time.perf_counter() - t0) / reps
+            res = torch.linalg.matrix_norm(T @ X.to(torch.complex128) - V) / torch.linalg.matrix_norm(V)
+            out[name] = {"seconds_per_batch": sec, "solves_per_s": N / sec,
+                         "max_rel_residual": float(res.max())}
+    except Exception as e:  # a comparison only: report, never fail the benchmark line
+        out["error"] = "%s: %s" % (type(e).__name__, e)
+    return out
+
+
 def _hankel_zeros(omega, mmax=12):
     """Zeros of H_m^(1) (0 <= m <= mmax) inside the rectangle: the exact scattering poles of the
     sound-soft unit disk (Sec. 4.2), by Newton's method on SciPy's Hankel functions."""
@@ -1167,6 +1217,7 @@ def main():
     scat = None
     if rank == 0 and not args.no_scattering:
         scat = scattering_leg(pmcim, stream, steps=2)
+    liblu = library_lu_leg(W, args.region_offset) if rank == 0 else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1189,7 +1240,7 @@ def main():
             "other_precision_form": other, "third_precision_form": third, "residual_on_fp64_pipe": fp64res,
             "speedup_tensor_core_residual": (runs["tf32x3_fp64res"][0] / runs["tf32x3"][0]
                                              if "tf32x3_fp64res" in runs else None),
-            "clocks": clk, "scattering_poles": scat,
+            "clocks": clk, "scattering_poles": scat, "library_lu_comparison": liblu,
         }
         for key in ("tensor", "ir_sweeps_per_node", "ir_fallbacks", "tc_timeouts", "certified", "unverified"):
             if key in head:

@@ -93,3 +93,24 @@ def test_no_cpu_fallback_for_boundary_terms_without_gpu():
     with pytest.raises(pmcim.PmcimError) as e:
         pmcim.Problem(W.problem.n, W.problem.terms)
     assert e.value.code == -3  # PMCIM_ECUDA
+
+
+def test_header_compiles_as_c99_and_cxx(tmp_path):
+    """include/pmcim.h is a plain C header: it compiles with -std=c99 -pedantic and as C++."""
+    import shutil
+    import subprocess
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "pmcim.h"\\n'
+                   "int main(void) {\\n"
+                   "  pmcim_options o;\\n"
+                   "  pmcim_default_options(&o);\\n"
+                   "  pmcim_fterm f = {PMCIM_F_HELMHOLTZ_DLP, 0, 0.0, 0.5, 0.0};\\n"
+                   "  (void)f;\\n"
+                   "  return o.precision;\\n"
+                   "}\\n")
+    inc = "-I" + os.path.join(ROOT, "include")
+    for cc, flags in (("gcc", ["-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror"]),
+                      ("g++", ["-std=c++11", "-Wall", "-Werror", "-x", "c++"])):
+        if not shutil.which(cc):
+            pytest.skip(cc + " not found")
+        subprocess.run([cc, *flags, "-fsyntax-only", inc, str(src)], check=True)

@@ -100,14 +100,14 @@ def test_header_compiles_as_c99_and_cxx(tmp_path):
     import shutil
     import subprocess
     src = tmp_path / "use_header.c"
-    src.write_text('#include "pmcim.h"\\n'
-                   "int main(void) {\\n"
-                   "  pmcim_options o;\\n"
-                   "  pmcim_default_options(&o);\\n"
-                   "  pmcim_fterm f = {PMCIM_F_HELMHOLTZ_DLP, 0, 0.0, 0.5, 0.0};\\n"
-                   "  (void)f;\\n"
-                   "  return o.precision;\\n"
-                   "}\\n")
+    src.write_text('#include "pmcim.h"\n'
+                   "int main(void) {\n"
+                   "  pmcim_options o;\n"
+                   "  pmcim_default_options(&o);\n"
+                   "  pmcim_fterm f = {PMCIM_F_HELMHOLTZ_DLP, 0, 0.0, 0.5, 0.0};\n"
+                   "  (void)f;\n"
+                   "  return o.precision;\n"
+                   "}\n")
     inc = "-I" + os.path.join(ROOT, "include")
     for cc, flags in (("gcc", ["-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror"]),
                       ("g++", ["-std=c++11", "-Wall", "-Werror", "-x", "c++"])):

@@ -1,6 +1,6 @@
-// C ABI of libpmcim and the host-side driver of pmCIMb (Sec. 3.2).
+// C ABI of libpmcim and the host-side control of pmCIMb (Sec. 3.2).
 //
-// The driver turns lists of disks (of one or many problems) into levels of
+// The host side turns lists of disks (of one or many problems) into levels of
 // work: every node of every disk of a level is one linear system. A level is
 // captured as one CUDA graph: per HBM wave, the node kernels (one persistent
 // launch per arithmetic form, work handed out largest-first) and the segmented

@@ -154,3 +154,20 @@ def test_mutations_fail_a_pin(monkeypatch, mutation):
         monkeypatch.setattr(bie, "dlp_matrix", flipped)
         monkeypatch.setattr(o, "dlp_matrix", flipped)
     assert _mode_error(32, KAPPAS[:3], mmax=6) > 1e-6 or _weights_error((8, 16)) > 1e-6
+
+
+def test_scattering_two_pass_and_pmcima():
+    """The oracle's two-pass schedule (indicator on 16 of the 64 nodes) keeps the one-pass poles, and its
+    pmCIMa (Sec. 3.1) places each pole it finds within tol_eps of a zero of some H_m^(1)."""
+    W = w.scattering_disk(n=40, l=4)
+    zeros = [z for _, z in hankel_zeros_in(W.omega)]
+    disks = [g for g in W.regions if any(abs(complex(g.c) - z) < g.r for z in zeros)]
+    one = o.pmcimb(W.problem, disks, W.V, W.tol_ind, W.tol_svd, W.tol_verify)
+    two = o.pmcimb(W.problem, disks, W.V, W.tol_ind, W.tol_svd, W.tol_verify, indicator_N=16)
+    assert len(one.lam) == len(two.lam) == 12  # the 6 zeros (of H_2 .. H_5), each twice
+    assert np.max(np.abs(np.sort_complex(one.lam) - np.sort_complex(two.lam))) < 1e-12
+    regs16 = [w.Region(g.c, g.r, 16) for g in disks[:2]]
+    res = o.pmcima(W.problem, regs16, W.V, tol_eps=1e-6)
+    assert len(res.lam) >= 1
+    for lam in res.lam:
+        assert min(abs(lam - z) for z in zeros) <= 1e-6
